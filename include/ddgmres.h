@@ -1,0 +1,180 @@
+/*
+ * ddgmres.h -- C ABI of the data-driven GMRES library for 2D FDFD solves (sm_103a).
+ *
+ * The library solves A f = b, where A is the finite-difference frequency-domain
+ * operator of Maxwell's equations for the 2D TM polarisation (Ez), and can
+ * augment GMRES with a predicted subspace V (data-driven GMRES):
+ *   Eq. 1   [curl curl - omega^2 eps / c^2] E = -i omega mu0 J, discretised on a
+ *           periodic Yee grid with stretched-coordinate PML (Sec. II).
+ *   Eq. 2   GMRES: f_i = argmin over K_i(A, b) of ||A f - b||.
+ *   Eq. 3-4 data-driven GMRES: f_i = argmin over V + K_i(A~, b~),
+ *           A~ = P_perp(A V) A, b~ = P_perp(A V) b; update rule of the supplement
+ *           (Eqs. S1-S7: A V = C R, Arnoldi on A~, block least squares).
+ *
+ * Conventions shared by every call
+ *  - Complex vectors are interleaved (re, im) pairs: a complex128 vector of
+ *    length D is `double[2*D]`, a complex64 vector is `float[2*D]`.
+ *  - Grid vectors are row-major [ny][nx]: cell (i, j) at index j*nx + i.
+ *  - Pointer arguments are DEVICE pointers unless marked (host).  The caller
+ *    owns every buffer it passes; the library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are stream-ordered; calls that return ddg_info fill it on return
+ *    (they synchronise `stream`).
+ *  - Handles (ddg_context, ddg_op) belong to the device that was current when
+ *    they were created; use one ddg_context per host thread / stream.
+ *  - No C++ exception crosses this boundary.  On error the call returns a
+ *    status != DDG_OK and ddg_last_error() describes it.
+ */
+#ifndef DDGMRES_H
+#define DDGMRES_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DDG_OK = 0,
+    DDG_EINVAL = 1,      /* bad argument: sizes, tolerances, non-finite or non-positive eps */
+    DDG_ENOMEM = 2,      /* device allocation failed */
+    DDG_ECUDA = 3,       /* a CUDA runtime call failed (message in ddg_last_error) */
+    DDG_ENOCONV = 4,     /* iteration cap reached before the tolerance; x holds the best iterate */
+    DDG_EBREAKDOWN = 5,  /* reserved: unrecoverable Arnoldi breakdown */
+    DDG_ETIMEOUT = 6,    /* reserved: device watchdog expired */
+    DDG_ESINGULAR = 7    /* a small dense factorisation failed */
+} ddg_status;
+
+/* Precision of the Krylov loop. */
+typedef enum {
+    DDG_C128 = 0,        /* everything in complex128 / FP64 */
+    DDG_C64_REFINE = 1,  /* Arnoldi vectors and matvecs in complex64 (FP32 sums inside a
+                            block, FP64 across blocks); true residual r = b - A x, Givens
+                            rotations, Hessenberg least squares and the update of x in FP64.
+                            Every restart recomputes r in FP64 (iterative refinement). */
+    DDG_C64_ONLY = 2     /* reserved */
+} ddg_precision;
+
+/* Problem description (host struct).  Units: metres. */
+typedef struct {
+    int nx, ny;          /* cells along x (fastest index) and y */
+    double dx;           /* cell size h (square cells) */
+    double wavelength;   /* vacuum wavelength; k0 = 2 pi / wavelength */
+    int npml_x, npml_y;  /* PML thickness in cells (0 = none) on both ends of x / y */
+    double pml_order;    /* polynomial grading order m of the PML conductivity */
+    double pml_R;        /* target normal-incidence reflection R of the PML */
+} ddg_grid;
+
+/* Per-solve result (host struct). */
+typedef struct {
+    int iters;                       /* Arnoldi steps (matvecs in the Krylov loop) */
+    int cycles;                      /* restart cycles (each starts from an FP64 residual) */
+    int converged;                   /* 1 if true_rel_residual <= tol */
+    int fallback_used;               /* augmented solve ran as plain GMRES (V rejected) */
+    int breakdown;                   /* an Arnoldi step hit an invariant subspace */
+    double true_rel_residual;        /* ||b - A x|| / ||b||, FP64, recomputed at the end */
+    double first_step_rel_residual;  /* augmented: ||P_perp b|| / ||b|| = min over V (Eq. 6) */
+} ddg_info;
+
+typedef struct ddg_context ddg_context;   /* workspace + tuning, one per stream */
+typedef struct ddg_op ddg_op;             /* the operator A(eps, omega) of one problem */
+
+/* Status text; never NULL. */
+const char* ddg_status_str(ddg_status s);
+/* Last error message of the calling thread; never NULL. */
+const char* ddg_last_error(void);
+/* Library version as 10000*major + 100*minor + patch. */
+int ddg_version(void);
+
+/* Context: owns the device workspace (grown on demand, reused across calls). */
+ddg_status ddg_context_create(ddg_context** ctx);
+ddg_status ddg_context_destroy(ddg_context* ctx);
+/* Bytes of device workspace the context currently holds. */
+long long ddg_context_workspace_bytes(const ddg_context* ctx);
+/* Inner-cycle relative tolerance for DDG_C64_REFINE (a cycle ends once its
+   least-squares residual falls below eta times the cycle's starting residual).
+   Default 1e-5.  Must be in (0, 1). */
+ddg_status ddg_context_set_inner_tol(ddg_context* ctx, double eta);
+
+/*
+ * fdfd_operator -- set up A(eps, omega) of Eq. 1 (Sec. II) on the Yee grid:
+ *   (A x)_{i,j} = -[ (1/sxb_i)((x_{i+1,j}-x_{i,j})/sxf_i - (x_{i,j}-x_{i-1,j})/sxf_{i-1})
+ *                  + (1/syb_j)((x_{i,j+1}-x_{i,j})/syf_j - (x_{i,j}-x_{i,j-1})/syf_{j-1}) ]
+ *                - (k0 h)^2 eps_{i,j} x_{i,j},          indices periodic (mod nx, ny),
+ * i.e. Eq. 1 times h^2, with stretch s(p) = 1 - i smax (d(p)/L)^m at integer
+ * nodes (sxb) and half nodes p = i + 1/2 (sxf), d(p) the depth into the PML in
+ * cells, smax = -(m+1) ln(R) / (2 k0 h L).
+ *   g    (host)  grid description; nx, ny >= 3; 0 <= npml <= n/2; R in (0,1).
+ *   eps  device, ny*nx doubles, row-major; every value finite and > 0, else DDG_EINVAL.
+ *   A    (host)  receives the new handle; the operator keeps its own copy of eps.
+ * Synchronises `stream` (the eps check reads back one flag).
+ */
+ddg_status fdfd_operator(const ddg_grid* g, const double* eps, ddg_op** A, void* stream);
+ddg_status fdfd_operator_destroy(ddg_op* A);
+/* Number of unknowns D = nx*ny of the operator (0 for NULL). */
+long long fdfd_operator_size(const ddg_op* A);
+
+/* y = A x in complex128 (x, y: device, 2*D doubles, must not overlap). */
+ddg_status fdfd_apply(const ddg_op* A, const double* x, double* y, void* stream);
+/* y = A x in complex64 (coefficients rounded to FP32; x, y: 2*D floats). */
+ddg_status fdfd_apply_c64(const ddg_op* A, const float* x, float* y, void* stream);
+
+/*
+ * fdfd_source -- b = -i (k0 h) J (Eq. 1 right-hand side times h^2 up to the
+ * constant mu0 c): a line current on column i_src with Gaussian profile
+ * J_j = exp(-(j - j_c)^2 / (2 sigma^2)) along y, zero elsewhere.
+ *   b  device, 2*D doubles (written in full).  0 <= i_src < nx, sigma > 0.
+ */
+ddg_status fdfd_source(const ddg_op* A, int i_src, double sigma_cells, double j_c,
+                       double* b, void* stream);
+
+/*
+ * gmres_solve -- restarted GMRES(restart) for A x = b (Eq. 2), classical
+ * Gram-Schmidt with one reorthogonalisation (Eq. S2 applied twice), complex
+ * Givens least squares in FP64.  Stops when the FP64 true relative residual
+ * ||b - A x|| / ||b|| <= tol, or after maxit Arnoldi steps (DDG_ENOCONV).
+ *   b     device, 2*D doubles.
+ *   x     device, 2*D doubles: in = initial guess x0, out = solution.
+ *   tol   in (0, 1);  restart in [1, 1024];  maxit >= 1.
+ *   info  (host) may be NULL.
+ */
+ddg_status gmres_solve(ddg_context* ctx, const ddg_op* A, const double* b, double* x,
+                       double tol, int restart, int maxit, ddg_precision prec,
+                       ddg_info* info, void* stream);
+
+/*
+ * augmented_gmres_solve -- data-driven GMRES (Eqs. 3-4, supplement S1-S7):
+ * A V = C R by Cholesky QR applied twice (FP64), b~ = b - C C^H b, Arnoldi on
+ * A~ = (I - C C^H) A with B = C^H A Q kept, the block least-squares problem
+ * decoupled into y = argmin ||H y - ||b~|| e1|| and x_V = C^H b - B y, and
+ * f = V R^-1 x_V + Q y.  Restarts solve the residual equation with the same V.
+ *   U     device, D x k complex128, column-major (column n at U + 2*D*n), the
+ *         predicted vectors v_1..v_k; need not be orthonormal.
+ *   k     1 <= k <= 64.  If A U is numerically rank deficient the solve runs as
+ *         plain GMRES and info.fallback_used = 1 (status DDG_OK).
+ * Other arguments as gmres_solve.
+ */
+ddg_status augmented_gmres_solve(ddg_context* ctx, const ddg_op* A, const double* b,
+                                 const double* U, int k, double* x, double tol,
+                                 int restart, int maxit, ddg_precision prec,
+                                 ddg_info* info, void* stream);
+
+/*
+ * Batched forms: n independent solves (uneven grid sizes allowed) advanced
+ * together, every kernel launch covering all solves still running.
+ *   A, b, x, U  (host) arrays of n handles / device pointers.
+ *   info        (host) array of n results, may be NULL.
+ * Returns DDG_ENOCONV if any solve missed the tolerance.
+ */
+ddg_status gmres_solve_batched(ddg_context* ctx, int n, const ddg_op* const* A,
+                               const double* const* b, double* const* x, double tol,
+                               int restart, int maxit, ddg_precision prec,
+                               ddg_info* info, void* stream);
+ddg_status augmented_gmres_solve_batched(ddg_context* ctx, int n, const ddg_op* const* A,
+                                         const double* const* b, const double* const* U,
+                                         int k, double* const* x, double tol, int restart,
+                                         int maxit, ddg_precision prec, ddg_info* info,
+                                         void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDGMRES_H */

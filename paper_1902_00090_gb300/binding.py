@@ -1,0 +1,317 @@
+"""Thin ctypes binding of libddgmres.so (include/ddgmres.h): argument marshalling only.
+
+Every function keeps the name of the C entry point it calls.  Device memory
+comes from torch CUDA tensors (complex128 / complex64 are interleaved re/im,
+which is the library's layout); all arithmetic runs in the library's kernels.
+There is no CPU fallback: if the library is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import _build
+
+_LIB = None
+
+DDG_C128 = 0
+DDG_C64_REFINE = 1
+PRECISIONS = {"c128": DDG_C128, "c64": DDG_C64_REFINE, "c64_refine": DDG_C64_REFINE}
+
+STATUS = {0: "DDG_OK", 1: "DDG_EINVAL", 2: "DDG_ENOMEM", 3: "DDG_ECUDA", 4: "DDG_ENOCONV",
+          5: "DDG_EBREAKDOWN", 6: "DDG_ETIMEOUT", 7: "DDG_ESINGULAR"}
+
+
+class DdgError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class ddg_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("wavelength", C.c_double),
+                ("npml_x", C.c_int), ("npml_y", C.c_int), ("pml_order", C.c_double),
+                ("pml_R", C.c_double)]
+
+
+class ddg_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("cycles", C.c_int), ("converged", C.c_int),
+                ("fallback_used", C.c_int), ("breakdown", C.c_int),
+                ("true_rel_residual", C.c_double), ("first_step_rel_residual", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_vp = C.c_void_p
+_SIGS = {
+    "ddg_status_str": (C.c_char_p, [C.c_int]),
+    "ddg_last_error": (C.c_char_p, []),
+    "ddg_version": (C.c_int, []),
+    "ddg_context_create": (C.c_int, [C.POINTER(_vp)]),
+    "ddg_context_destroy": (C.c_int, [_vp]),
+    "ddg_context_workspace_bytes": (C.c_longlong, [_vp]),
+    "ddg_context_set_inner_tol": (C.c_int, [_vp, C.c_double]),
+    "fdfd_operator": (C.c_int, [C.POINTER(ddg_grid), _vp, C.POINTER(_vp), _vp]),
+    "fdfd_operator_destroy": (C.c_int, [_vp]),
+    "fdfd_operator_size": (C.c_longlong, [_vp]),
+    "fdfd_apply": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "fdfd_apply_c64": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "fdfd_source": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double, _vp, _vp]),
+    "gmres_solve": (C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int, C.c_int, C.c_int,
+                              C.POINTER(ddg_info), _vp]),
+    "augmented_gmres_solve": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, C.c_double, C.c_int,
+                                        C.c_int, C.c_int, C.POINTER(ddg_info), _vp]),
+    "gmres_solve_batched": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),
+                                      C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(ddg_info),
+                                      _vp]),
+    "augmented_gmres_solve_batched": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp),
+                                                C.POINTER(_vp), C.c_int, C.POINTER(_vp),
+                                                C.c_double, C.c_int, C.c_int, C.c_int,
+                                                C.POINTER(ddg_info), _vp]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads libddgmres.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is missing: run __graft_entry__.build() first")
+        lib = C.CDLL(_build.LIB)
+        for name, (res, args) in _SIGS.items():
+            if hasattr(lib, name):
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise DdgError(status, where, load().ddg_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("ddgmres needs a CUDA device; none is available")
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype, what, numel=None):
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{what}: need a contiguous CUDA tensor of {dtype}, got {t.dtype} "
+                         f"on {t.device} (contiguous={t.is_contiguous()})")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what}: expected {numel} elements, got {t.numel()}")
+    return _vp(t.data_ptr())
+
+
+class Context:
+    """ddg_context: device workspace and tuning for one stream."""
+
+    def __init__(self, inner_tol: float | None = None):
+        _torch()
+        h = _vp()
+        _check(load().ddg_context_create(C.byref(h)), "ddg_context_create")
+        self._h = h
+        if inner_tol is not None:
+            self.set_inner_tol(inner_tol)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_inner_tol(self, eta: float):
+        _check(load().ddg_context_set_inner_tol(self._h, float(eta)), "ddg_context_set_inner_tol")
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(load().ddg_context_workspace_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ddg_context_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ddg_context_create(inner_tol: float | None = None) -> Context:
+    return Context(inner_tol)
+
+
+class Operator:
+    """ddg_op: A(eps, omega) of one FDFD problem (keeps its own copy of eps)."""
+
+    def __init__(self, handle, nx, ny):
+        self._h, self.nx, self.ny = handle, nx, ny
+        self.D = nx * ny
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fdfd_operator_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_grid(grid) -> ddg_grid:
+    """ddg_grid from an inputs.Grid (or any object/dict with the same fields)."""
+    get = (lambda k: grid[k]) if isinstance(grid, dict) else (lambda k: getattr(grid, k))
+    def opt(k, d):
+        try:
+            return get(k)
+        except (KeyError, AttributeError):
+            return d
+    npml = opt("npml", 0)
+    return ddg_grid(int(get("nx")), int(get("ny")), float(get("dx")), float(get("wavelength")),
+                    int(opt("npml_x", npml)), int(opt("npml_y", npml)), float(opt("pml_order", 3.0)),
+                    float(opt("pml_R", 1e-8)))
+
+
+def fdfd_operator(grid, eps, stream=None) -> Operator:
+    """eps: CUDA float64 tensor (ny, nx)."""
+    torch = _torch()
+    g = make_grid(grid)
+    p = _dev_ptr(eps, torch.float64, "eps", g.nx * g.ny)
+    h = _vp()
+    _check(load().fdfd_operator(C.byref(g), p, C.byref(h), _stream(stream)), "fdfd_operator")
+    return Operator(h, g.nx, g.ny)
+
+
+def fdfd_apply(A: Operator, x, y=None, stream=None):
+    torch = _torch()
+    if y is None:
+        y = torch.empty_like(x)
+    _check(load().fdfd_apply(A.handle, _dev_ptr(x, torch.complex128, "x", A.D),
+                             _dev_ptr(y, torch.complex128, "y", A.D), _stream(stream)), "fdfd_apply")
+    return y
+
+
+def fdfd_apply_c64(A: Operator, x, y=None, stream=None):
+    torch = _torch()
+    if y is None:
+        y = torch.empty_like(x)
+    _check(load().fdfd_apply_c64(A.handle, _dev_ptr(x, torch.complex64, "x", A.D),
+                                 _dev_ptr(y, torch.complex64, "y", A.D), _stream(stream)),
+           "fdfd_apply_c64")
+    return y
+
+
+def fdfd_source(A: Operator, i_src: int, sigma_cells: float, j_c: float, b=None, stream=None):
+    torch = _torch()
+    if b is None:
+        b = torch.empty(A.D, dtype=torch.complex128, device="cuda")
+    _check(load().fdfd_source(A.handle, int(i_src), float(sigma_cells), float(j_c),
+                              _dev_ptr(b, torch.complex128, "b", A.D), _stream(stream)), "fdfd_source")
+    return b
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def gmres_solve(ctx: Context, A: Operator, b, x=None, tol=1e-6, restart=200, maxit=5000,
+                precision="c128", stream=None, check=False):
+    """Returns (x, info dict, status).  x (in/out) holds x0 on entry."""
+    torch = _torch()
+    if x is None:
+        x = torch.zeros_like(b)
+    info = ddg_info()
+    st = load().gmres_solve(ctx.handle, A.handle, _dev_ptr(b, torch.complex128, "b", A.D),
+                            _dev_ptr(x, torch.complex128, "x", A.D), float(tol), int(restart),
+                            int(maxit), _prec(precision), C.byref(info), _stream(stream))
+    if st not in (0, 4) or (check and st != 0):
+        _check(st, "gmres_solve")
+    return x, info.as_dict(), st
+
+
+def augmented_gmres_solve(ctx: Context, A: Operator, b, U, x=None, tol=1e-6, restart=200,
+                          maxit=5000, precision="c128", stream=None, check=False):
+    """U: CUDA complex128 tensor (k, D): row n is the predicted vector v_{n+1}
+    (the library's D x k column-major layout)."""
+    torch = _torch()
+    if x is None:
+        x = torch.zeros_like(b)
+    k = U.shape[0]
+    info = ddg_info()
+    st = load().augmented_gmres_solve(ctx.handle, A.handle, _dev_ptr(b, torch.complex128, "b", A.D),
+                                      _dev_ptr(U, torch.complex128, "U", k * A.D), int(k),
+                                      _dev_ptr(x, torch.complex128, "x", A.D), float(tol), int(restart),
+                                      int(maxit), _prec(precision), C.byref(info), _stream(stream))
+    if st not in (0, 4) or (check and st != 0):
+        _check(st, "augmented_gmres_solve")
+    return x, info.as_dict(), st
+
+
+def _ptr_array(ts, dtype, what, sizes):
+    arr = (_vp * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = _dev_ptr(t, dtype, f"{what}[{i}]", sizes[i]).value
+    return arr
+
+
+def gmres_solve_batched(ctx: Context, A, b, x=None, tol=1e-6, restart=200, maxit=5000,
+                        precision="c128", stream=None):
+    """A, b, x: lists (one entry per solve).  Returns (x list, info list, status)."""
+    torch = _torch()
+    n = len(A)
+    if x is None:
+        x = [torch.zeros_like(bb) for bb in b]
+    sizes = [a.D for a in A]
+    ha = (_vp * n)(*[a.handle.value for a in A])
+    infos = (ddg_info * n)()
+    st = load().gmres_solve_batched(ctx.handle, n, ha, _ptr_array(b, torch.complex128, "b", sizes),
+                                    _ptr_array(x, torch.complex128, "x", sizes), float(tol),
+                                    int(restart), int(maxit), _prec(precision), infos,
+                                    _stream(stream))
+    if st not in (0, 4):
+        _check(st, "gmres_solve_batched")
+    return x, [i.as_dict() for i in infos], st
+
+
+def augmented_gmres_solve_batched(ctx: Context, A, b, U, x=None, tol=1e-6, restart=200,
+                                  maxit=5000, precision="c128", stream=None):
+    """U: list of CUDA complex128 tensors (k, D), same k for every solve."""
+    torch = _torch()
+    n = len(A)
+    if x is None:
+        x = [torch.zeros_like(bb) for bb in b]
+    k = U[0].shape[0]
+    sizes = [a.D for a in A]
+    ha = (_vp * n)(*[a.handle.value for a in A])
+    infos = (ddg_info * n)()
+    st = load().augmented_gmres_solve_batched(
+        ctx.handle, n, ha, _ptr_array(b, torch.complex128, "b", sizes),
+        _ptr_array(U, torch.complex128, "U", [k * s for s in sizes]), int(k),
+        _ptr_array(x, torch.complex128, "x", sizes), float(tol), int(restart), int(maxit),
+        _prec(precision), infos, _stream(stream))
+    if st not in (0, 4):
+        _check(st, "augmented_gmres_solve_batched")
+    return x, [i.as_dict() for i in infos], st

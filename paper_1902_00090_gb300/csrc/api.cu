@@ -1,0 +1,109 @@
+// Status strings, per-thread error text and the solver context (workspace owner).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "engine.cuh"
+
+namespace ddg {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+ddg_status cuda_status(cudaError_t e, const char* what) {
+    set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return DDG_ENOMEM;
+    }
+    return DDG_ECUDA;
+}
+
+ddg_status Context::reserve(size_t bytes, cudaStream_t s) {
+    if (bytes <= ws_bytes) return DDG_OK;
+    if (ws) {
+        DDG_CHECK_CUDA(cudaStreamSynchronize(s));
+        cudaFree(ws);
+        ws = nullptr;
+        ws_bytes = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    cudaError_t e = cudaMalloc(&ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ws = nullptr;
+        set_error("workspace: cudaMalloc of %zu bytes failed", want);
+        return DDG_ENOMEM;
+    }
+    ws_bytes = want;
+    return DDG_OK;
+}
+
+}  // namespace ddg
+
+using namespace ddg;
+
+extern "C" const char* ddg_status_str(ddg_status s) {
+    switch (s) {
+        case DDG_OK: return "ok";
+        case DDG_EINVAL: return "invalid argument";
+        case DDG_ENOMEM: return "out of device memory";
+        case DDG_ECUDA: return "CUDA error";
+        case DDG_ENOCONV: return "not converged within the iteration cap";
+        case DDG_EBREAKDOWN: return "breakdown";
+        case DDG_ETIMEOUT: return "device watchdog expired";
+        case DDG_ESINGULAR: return "singular factorisation";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* ddg_last_error(void) { return g_err; }
+
+extern "C" int ddg_version(void) { return 100; }
+
+extern "C" ddg_status ddg_context_create(ddg_context** out) {
+    if (!out) { set_error("ddg_context_create: out is NULL"); return DDG_EINVAL; }
+    Context* c = new (std::nothrow) Context();
+    if (!c) return DDG_ENOMEM;
+    cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->sm_count <= 0) c->sm_count = 152;
+    cudaError_t e = cudaMallocHost(&c->host_counts, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[1], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_status(e, "ddg_context_create: cudaMallocHost");
+    }
+    *out = reinterpret_cast<ddg_context*>(c);
+    return DDG_OK;
+}
+
+extern "C" ddg_status ddg_context_destroy(ddg_context* ctx) {
+    if (!ctx) return DDG_OK;
+    Context* c = reinterpret_cast<Context*>(ctx);
+    cudaFree(c->ws);
+    cudaFreeHost(c->host_counts);
+    if (c->ev[0]) cudaEventDestroy(c->ev[0]);
+    if (c->ev[1]) cudaEventDestroy(c->ev[1]);
+    delete c;
+    return DDG_OK;
+}
+
+extern "C" long long ddg_context_workspace_bytes(const ddg_context* ctx) {
+    return ctx ? (long long)reinterpret_cast<const Context*>(ctx)->ws_bytes : 0;
+}
+
+extern "C" ddg_status ddg_context_set_inner_tol(ddg_context* ctx, double eta) {
+    if (!ctx || !(eta > 0.0 && eta < 1.0)) { set_error("inner tol must be in (0,1)"); return DDG_EINVAL; }
+    reinterpret_cast<Context*>(ctx)->inner_tol = eta;
+    return DDG_OK;
+}

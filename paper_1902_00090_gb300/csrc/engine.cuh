@@ -1,0 +1,82 @@
+// Internal types of the batched GMRES engine.
+#pragma once
+#include "common.cuh"
+
+namespace ddg {
+
+constexpr int kBlock = 256;          // threads per CTA of the streaming kernels
+constexpr int kWarps = kBlock / 32;
+constexpr int kMaxAug = 32;          // largest augmentation size k
+constexpr int kMaxRestart = 1024;
+
+// Solver context: device workspace (grow-only) and tuning.
+struct Context {
+    int device = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int* host_counts = nullptr;      // pinned, polled between launches
+    double inner_tol = 1e-5;         // DDG_C64_REFINE inner-cycle relative tolerance
+    int poll_every = 8;              // Arnoldi steps between host polls
+    int sm_count = 152;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    ddg_status reserve(size_t bytes, cudaStream_t s);
+};
+
+// Per-solve device pointers (read-only during a solve).
+struct SolvePtrs {
+    int nx, ny;
+    long long D;
+    double kh2;
+    const double* eps_d;
+    const void* eps_lo;        // float* or double* (precision of the Krylov loop)
+    const double2* coef_d;
+    const void* coef_lo;       // float2* or double2*
+    const double2* b;
+    double2* x;
+    double2* r;                // FP64 residual
+    void* M;                   // [C | Q] basis, T2, column-major, ld = D
+    const void* V;             // predicted vectors in T2 (D x N), column-major
+    const double2* U;          // caller's predicted vectors (FP64)
+    double2* W;                // FP64 scratch for A V during set-up (aliases M)
+    void* w[2];                // T2 Arnoldi vectors (double buffered)
+    double2* Rg;               // Givens-reduced Hessenberg, (m+1) x m, column-major
+    double2* B;                // C^H A Q, kMaxAug x m
+    double* cs;                // rotation cosines (m)
+    double2* sn;               // rotation sines (m)
+    double2* g;                // rotated right-hand side (m+1)
+    double2* hsum;             // Gram-Schmidt coefficients, sum of both passes (KP)
+    double2* hp;               // coefficients of the current pass (KP)
+    double2* part;             // per-CTA partial sums, nchunks x KP
+    double2* Rinv;             // R^-1 of A V = C R (N x N, column-major)
+    double2* Rtmp;             // first-pass triangular factor inverse (N x N)
+    double2* cr;               // C^H r at cycle start (N)
+    double2* coefy;            // [z = R^-1 x_V (N) | y (k)]
+    unsigned* ticket;
+    int chunk0, nchunks;
+};
+
+// Per-solve mutable state.
+struct SolveScal {
+    int N;            // augmentation size in use (0 = plain)
+    int active;       // solve still running
+    int in_cycle;     // Arnoldi loop of the current cycle still running
+    int pending;      // a cycle ran: back-substitute and update x
+    int k;            // Arnoldi steps in the current cycle
+    int iters, cycles, converged, breakdown, fallback;
+    double nb, rn, beta, target, hnorm, anorm, true_res, first_res;
+};
+
+struct BatchArgs {
+    SolvePtrs* P;
+    SolveScal* S;
+    const int* blk_solve;
+    int* counts;       // [0] solves inside an Arnoldi loop, [1] solves still active
+    int m;             // restart length
+    int KP;            // stride of coefficient vectors (>= Nmax + m + 2)
+    int nmax;          // leading dimension of B (= kMaxAug)
+    double tol;
+    double eta;        // inner relative tolerance (0 for complex128)
+    int maxit;
+};
+
+}  // namespace ddg

@@ -1,0 +1,951 @@
+// Batched restarted GMRES (Eq. 2) and data-driven GMRES (Eqs. 3-4, supplement
+// S1-S7) for FDFD operators.
+//
+// Execution model: n independent solves advance in lock step, one kernel launch
+// per phase covering every CTA of every solve still running; CTAs of finished
+// solves return at once.  Each solve is cut into chunks of kBlock*RPT rows (one
+// CTA per chunk).  Reductions are deterministic: every CTA writes its partial
+// sums, and the last CTA of a solve to finish (atomic ticket, no waiting) adds
+// them in chunk order and takes the solve's scalar decisions (Givens rotation,
+// convergence) in FP64.
+//
+// One Arnoldi step j (Eq. S2 with one reorthogonalisation, the augmentation
+// block C treated as leading columns of the basis, so that the C^H A q_j block
+// of Eq. S7 comes out of the same projections):
+//   k_step    q_j = w_{j-1} / h_{j,j-1} (stored), w = A q_j          (stencil)
+//   k_dots    h  = [C Q_j]^H w, and ||w||                             (pass 1)
+//   k_update  w -= [C Q_j] h
+//   k_dots    h' = [C Q_j]^H w                                        (pass 2)
+//   k_update  w -= [C Q_j] h', h_{j+1,j} = ||w||, Givens rotation, |g_{j+1}|
+// Cycle start: r = b - A x in FP64; (augmented) c_r = C^H r, r <- r - C c_r.
+// Cycle end: y from the rotated Hessenberg, x_V = c_r - B y, z = R^-1 x_V,
+// x += V z + Q y (FP64).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "engine.cuh"
+
+namespace ddg {
+
+// ---------------------------------------------------------------- helpers
+template <typename T> __device__ __forceinline__ c2_t<T> ld_as(const double2* p, long long i) {
+    return from_d2<c2_t<T>>(p[i]);
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* sm) {
+    v = warp_sum_d(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kWarps; ++w) t += sm[w];
+    return t;  // valid in thread 0
+}
+
+// Returns true in every thread of the CTA that is the last of `n` CTAs to
+// arrive on `ticket` (partials of all CTAs are then visible); resets the ticket.
+__device__ __forceinline__ bool arrive_last(unsigned* ticket, int n) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(ticket, 1u);
+        s_last = (t == (unsigned)(n - 1));
+        if (s_last) *ticket = 0u;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+// 5-point stencil of A at cell e; ld(idx) returns the input vector at idx.
+template <typename V, typename S, typename LD>
+__device__ __forceinline__ V stencil(long long e, int nx, int ny, const V* __restrict__ coef, S kh2eps,
+                                     const LD& ld) {
+    const int j = (int)(e / nx);
+    const int i = (int)(e - (long long)j * nx);
+    const V axp = coef[i], axm = coef[nx + i];
+    const V ayp = coef[2 * nx + j], aym = coef[2 * nx + ny + j];
+    const long long ip = (i == nx - 1) ? e - (nx - 1) : e + 1;
+    const long long im = (i == 0) ? e + (nx - 1) : e - 1;
+    const long long jp = (j == ny - 1) ? e - (long long)(ny - 1) * nx : e + nx;
+    const long long jm = (j == 0) ? e + (long long)(ny - 1) * nx : e - nx;
+    V d = cadd(cadd(axp, axm), cadd(ayp, aym));
+    d.x -= kh2eps;
+    V acc = cmul(d, ld(e));
+    cfms(acc, axp, ld(ip));
+    cfms(acc, axm, ld(im));
+    cfms(acc, ayp, ld(jp));
+    cfms(acc, aym, ld(jm));
+    return acc;
+}
+
+// Complex Givens rotation with real second entry b >= 0 (Golub & Van Loan 5.1.8):
+// [[c, s], [-conj(s), c]] [a; b] = [r; 0], c real.
+__device__ __forceinline__ void givens_d(double2 a, double b, double& c, double2& s, double2& r) {
+    double aa = hypot(a.x, a.y);
+    if (b == 0.0) {
+        c = 1.0; s = make_double2(0.0, 0.0); r = a;
+    } else if (aa == 0.0) {
+        c = 0.0; s = make_double2(1.0, 0.0); r = make_double2(b, 0.0);
+    } else {
+        double t = hypot(aa, b);
+        double2 ph = make_double2(a.x / aa, a.y / aa);
+        c = aa / t;
+        s = make_double2(ph.x * b / t, ph.y * b / t);
+        r = make_double2(ph.x * t, ph.y * t);
+    }
+}
+
+__device__ __forceinline__ void rotate(double c, double2 s, double2& u, double2& v) {
+    double2 nu = cadd(cscale(u, c), cmul(s, v));
+    double2 nv = csub(cscale(v, c), cmulc(s, u));
+    u = nu;
+    v = nv;
+}
+
+#define SOLVE_PROLOGUE()                                   \
+    const int s = a.blk_solve[blockIdx.x];                 \
+    SolveScal* S = a.S + s;                                \
+    const SolvePtrs& P = a.P[s];                           \
+    const int chunk = blockIdx.x - P.chunk0;               \
+    const long long row0 = (long long)chunk * (kBlock * RPT) + threadIdx.x;
+
+// ---------------------------------------------------------------- init
+__global__ void k_init(BatchArgs a, int n, int nreq) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    SolveScal* S = a.S + s;
+    S->N = nreq;
+    S->active = 1;
+    S->in_cycle = 0;
+    S->pending = 0;
+    S->k = 0;
+    S->iters = 0;
+    S->cycles = 0;
+    S->converged = 0;
+    S->breakdown = 0;
+    S->fallback = 0;
+    S->nb = -1.0;
+    S->rn = 0.0;
+    S->beta = 0.0;
+    S->target = 0.0;
+    S->hnorm = 1.0;
+    S->anorm = 0.0;
+    S->true_res = INFINITY;
+    S->first_res = NAN;
+    *a.P[s].ticket = 0u;
+}
+
+// ---------------------------------------------------------------- cycle start
+// r = b - A x (FP64); ||r||, ||b||; convergence / cap decisions.
+template <int RPT>
+__global__ void __launch_bounds__(kBlock) k_residual(BatchArgs a) {
+    SOLVE_PROLOGUE();
+    if (!S->active) return;
+    __shared__ double sm[kWarps];
+    const long long D = P.D;
+    const double2* __restrict__ x = P.x;
+    double accr = 0.0, accb = 0.0;
+    auto ld = [&](long long idx) { return x[idx]; };
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        long long e = row0 + (long long)q * kBlock;
+        if (e < D) {
+            double2 ax = stencil(e, P.nx, P.ny, P.coef_d, P.kh2 * P.eps_d[e], ld);
+            double2 bv = P.b[e];
+            double2 rv = csub(bv, ax);
+            P.r[e] = rv;
+            accr += cabs2(rv);
+            accb += cabs2(bv);
+        }
+    }
+    double tr = block_sum_d(accr, sm);
+    double tb = block_sum_d(accb, sm);
+    if (threadIdx.x == 0) P.part[chunk] = make_double2(tr, tb);
+    if (!arrive_last(P.ticket, P.nchunks)) return;
+    if (threadIdx.x != 0) return;
+    double rn2 = 0.0, nb2 = 0.0;
+    for (int c = 0; c < P.nchunks; ++c) {
+        double2 t = __ldcg(P.part + c);
+        rn2 += t.x;
+        nb2 += t.y;
+    }
+    if (S->nb < 0.0) S->nb = sqrt(nb2);
+    const double nb = S->nb, rn = sqrt(rn2);
+    S->rn = rn;
+    S->pending = 0;
+    S->k = 0;
+    S->in_cycle = 0;
+    if (nb == 0.0) {
+        S->true_res = 0.0;
+        S->converged = 1;
+        S->active = 0;
+        return;
+    }
+    S->true_res = rn / nb;
+    if (rn <= a.tol * nb) {
+        S->converged = 1;
+        S->active = 0;
+        return;
+    }
+    if (S->iters >= a.maxit || S->cycles >= a.maxit || !(rn == rn) || isinf(rn)) {
+        S->active = 0;
+        return;
+    }
+    atomicAdd(a.counts + 1, 1);
+    S->cycles += 1;
+    S->pending = 1;
+    if (S->N == 0) {
+        S->beta = rn;
+        S->hnorm = rn;
+        P.g[0] = make_double2(rn, 0.0);
+        S->target = fmax(a.tol * nb, a.eta * rn);
+        S->in_cycle = 1;
+        atomicAdd(a.counts, 1);
+    }
+    // augmented: k_dots (mode 2) and k_update (mode 2) finish the set-up
+}
+
+// ---------------------------------------------------------------- Arnoldi step: q_j, w = A q_j
+// Column j of Q is the previous (unnormalised) vector scaled by 1/h_{j,j-1}
+// (for j = 0: the cycle's start vector r scaled by 1/beta); w = A q_j uses the
+// same rounded values of q_j as the stored column.
+template <typename T, int RPT>
+__global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
+    using V = c2_t<T>;
+    SOLVE_PROLOGUE();
+    if (!S->in_cycle) return;
+    const long long D = P.D;
+    const int N = S->N;
+    const double inv = 1.0 / S->hnorm;
+    V* __restrict__ q = reinterpret_cast<V*>(P.M) + (long long)(N + j) * D;
+    V* __restrict__ w = reinterpret_cast<V*>(P.w[j & 1]);
+    const T* eps = reinterpret_cast<const T*>(P.eps_lo);
+    const V* coef = reinterpret_cast<const V*>(P.coef_lo);
+    const T kh2 = (T)P.kh2;
+    if (j == 0) {
+        const double2* __restrict__ src = P.r;
+        auto ld = [&](long long idx) { return from_d2<V>(cscale(src[idx], inv)); };
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) {
+            long long e = row0 + (long long)t * kBlock;
+            if (e < D) {
+                q[e] = ld(e);
+                w[e] = stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld);
+            }
+        }
+    } else {
+        const V* __restrict__ src = reinterpret_cast<const V*>(P.w[(j - 1) & 1]);
+        const T tinv = (T)inv;
+        auto ld = [&](long long idx) { return cscale(src[idx], tinv); };
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) {
+            long long e = row0 + (long long)t * kBlock;
+            if (e < D) {
+                q[e] = ld(e);
+                w[e] = stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- projections
+// out[k] = sum_e conj(M[k D + e]) v[e] for the columns k < K of one solve.
+//   mode 0: Arnoldi pass 1 (v = w, K = N + j + 1, also ||w||^2 -> anorm)
+//   mode 1: Arnoldi pass 2 (v = w, K = N + j + 1)
+//   mode 2: cycle start, c_r = C^H r (v = r in FP64, K = N)
+// TM: element type of M; TV: of v; TA: per-thread accumulator.
+template <typename TM, typename TV, typename TA, int RPT>
+__global__ void __launch_bounds__(kBlock) k_dots(BatchArgs a, int j, int mode) {
+    using VM = c2_t<TM>;
+    using VV = c2_t<TV>;
+    using VA = c2_t<TA>;
+    SOLVE_PROLOGUE();
+    const int N = S->N;
+    if (mode == 2) {
+        if (!S->pending || S->in_cycle || N == 0) return;
+    } else if (!S->in_cycle) {
+        return;
+    }
+    constexpr int TILE = 64;
+    __shared__ VA red[kWarps][TILE];
+    const long long D = P.D;
+    const int K = (mode == 2) ? N : N + j + 1;
+    const int Ktot = K + (mode == 0 ? 1 : 0);
+    const VV* __restrict__ v = (mode == 2) ? reinterpret_cast<const VV*>(P.r)
+                                           : reinterpret_cast<const VV*>(P.w[j & 1]);
+    const VM* __restrict__ M = reinterpret_cast<const VM*>(P.M);
+    VA vr[RPT];
+    bool ok[RPT];
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
+        long long e = row0 + (long long)t * kBlock;
+        ok[t] = e < D;
+        VV x = ok[t] ? v[e] : VV{0, 0};
+        vr[t] = mk((TA)x.x, (TA)x.y);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double2* part = P.part + (long long)chunk * a.KP;
+    for (int k0 = 0; k0 < Ktot; k0 += TILE) {
+        const int kt = min(TILE, Ktot - k0);
+        int kk = 0;
+        for (; kk + 4 <= kt && k0 + kk + 4 <= K; kk += 4) {
+            VA acc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = mk((TA)0, (TA)0);
+#pragma unroll
+            for (int t = 0; t < RPT; ++t) {
+                if (ok[t]) {
+                    long long e = row0 + (long long)t * kBlock;
+                    VM m4[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) m4[u] = M[(long long)(k0 + kk + u) * D + e];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) cfmac(acc[u], mk((TA)m4[u].x, (TA)m4[u].y), vr[t]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = warp_sum(acc[u]);
+            if (lane == 0) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) red[wid][kk + u] = acc[u];
+            }
+        }
+        for (; kk < kt; ++kk) {
+            const int k = k0 + kk;
+            VA acc = mk((TA)0, (TA)0);
+            if (k < K) {
+#pragma unroll
+                for (int t = 0; t < RPT; ++t)
+                    if (ok[t]) {
+                        VM mv = M[(long long)k * D + row0 + (long long)t * kBlock];
+                        cfmac(acc, mk((TA)mv.x, (TA)mv.y), vr[t]);
+                    }
+            } else {
+#pragma unroll
+                for (int t = 0; t < RPT; ++t) acc.x += vr[t].x * vr[t].x + vr[t].y * vr[t].y;
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) red[wid][kk] = acc;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < kt; t += kBlock) {
+            double2 sum = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) sum = cadd(sum, make_double2((double)red[w][t].x, (double)red[w][t].y));
+            part[k0 + t] = sum;
+        }
+        __syncthreads();
+    }
+    if (!arrive_last(P.ticket, P.nchunks)) return;
+    for (int k = threadIdx.x; k < Ktot; k += kBlock) {
+        double2 sum = make_double2(0.0, 0.0);
+        for (int c = 0; c < P.nchunks; ++c) sum = cadd(sum, __ldcg(P.part + (long long)c * a.KP + k));
+        if (k < K) {
+            P.hp[k] = sum;
+            if (mode == 0) P.hsum[k] = sum;
+            else if (mode == 1) P.hsum[k] = cadd(P.hsum[k], sum);
+            else P.cr[k] = sum;
+        } else {
+            S->anorm = sqrt(sum.x);
+        }
+    }
+}
+
+// v -= M[:, :K] hp.
+//   mode 0: Arnoldi pass 1 (v = w)
+//   mode 1: Arnoldi pass 2 (v = w), then ||w||, Hessenberg column, Givens, stop test
+//   mode 2: cycle start (v = r, K = N): r~ = r - C c_r, beta = ||r~||
+template <typename TM, typename TV, int RPT>
+__global__ void __launch_bounds__(kBlock) k_update(BatchArgs a, int j, int mode) {
+    using VM = c2_t<TM>;
+    using VV = c2_t<TV>;
+    SOLVE_PROLOGUE();
+    const int N = S->N;
+    if (mode == 2) {
+        if (!S->pending || S->in_cycle || N == 0) return;
+    } else if (!S->in_cycle) {
+        return;
+    }
+    __shared__ double sm[kWarps];
+    const long long D = P.D;
+    const int K = (mode == 2) ? N : N + j + 1;
+    VV* __restrict__ v = (mode == 2) ? reinterpret_cast<VV*>(P.r) : reinterpret_cast<VV*>(P.w[j & 1]);
+    const VM* __restrict__ M = reinterpret_cast<const VM*>(P.M);
+    const double2* __restrict__ hp = P.hp;
+    VV vr[RPT];
+    bool ok[RPT];
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
+        long long e = row0 + (long long)t * kBlock;
+        ok[t] = e < D;
+        vr[t] = ok[t] ? v[e] : VV{0, 0};
+    }
+    int k = 0;
+    for (; k + 4 <= K; k += 4) {
+        VV c4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            double2 h = hp[k + u];
+            c4[u] = mk((TV)h.x, (TV)h.y);
+        }
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) {
+            if (ok[t]) {
+                long long e = row0 + (long long)t * kBlock;
+                VM m4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) m4[u] = M[(long long)(k + u) * D + e];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) cfms(vr[t], mk((TV)m4[u].x, (TV)m4[u].y), c4[u]);
+            }
+        }
+    }
+    for (; k < K; ++k) {
+        double2 h = hp[k];
+        VV c = mk((TV)h.x, (TV)h.y);
+#pragma unroll
+        for (int t = 0; t < RPT; ++t)
+            if (ok[t]) {
+                VM mv = M[(long long)k * D + row0 + (long long)t * kBlock];
+                cfms(vr[t], mk((TV)mv.x, (TV)mv.y), c);
+            }
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < RPT; ++t)
+        if (ok[t]) {
+            v[row0 + (long long)t * kBlock] = vr[t];
+            acc += cabs2(vr[t]);
+        }
+    if (mode == 0) return;
+    double tot = block_sum_d(acc, sm);
+    if (threadIdx.x == 0) P.part[(long long)chunk * a.KP] = make_double2(tot, 0.0);
+    if (!arrive_last(P.ticket, P.nchunks)) return;
+    if (threadIdx.x != 0) return;
+    double n2 = 0.0;
+    for (int c = 0; c < P.nchunks; ++c) n2 += __ldcg(P.part + (long long)c * a.KP).x;
+    const double nrm = sqrt(n2);
+    if (mode == 2) {
+        // b~ = P_perp r: the Krylov loop starts from r~ / ||r~||
+        S->beta = nrm;
+        if (S->cycles == 1) S->first_res = nrm / S->nb;
+        S->k = 0;
+        if (nrm <= 1e-14 * S->rn) {
+            // r lies in span(A V): the V step alone solves the residual equation
+            S->breakdown = 1;
+            return;
+        }
+        S->hnorm = nrm;
+        P.g[0] = make_double2(nrm, 0.0);
+        S->target = fmax(a.tol * S->nb, a.eta * nrm);
+        S->in_cycle = 1;
+        atomicAdd(a.counts, 1);
+        return;
+    }
+    // mode 1: column j of H (rows 0..j from hsum[N..N+j], row j+1 = ||w||),
+    // column j of B = C^H A q_j (hsum[0..N)); Givens update of column j.
+    const int m = a.m, ldh = m + 1;
+    for (int n = 0; n < N; ++n) P.B[(long long)j * a.nmax + n] = P.hsum[n];
+    double2* col = P.Rg + (long long)j * ldh;
+    for (int i = 0; i <= j; ++i) col[i] = P.hsum[N + i];
+    for (int i = 0; i < j; ++i) rotate(P.cs[i], P.sn[i], col[i], col[i + 1]);
+    double c;
+    double2 sn, r;
+    givens_d(col[j], nrm, c, sn, r);
+    col[j] = r;
+    col[j + 1] = make_double2(0.0, 0.0);
+    P.cs[j] = c;
+    P.sn[j] = sn;
+    double2 gj = P.g[j];
+    P.g[j] = cscale(gj, c);
+    double2 gj1 = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));  // -conj(s) g_j
+    P.g[j + 1] = gj1;
+    const double est = hypot(gj1.x, gj1.y);
+    S->k = j + 1;
+    S->iters += 1;
+    S->hnorm = nrm;
+    bool brk = !(nrm > 1e-14 * S->anorm);
+    if (brk) S->breakdown = 1;
+    if (brk || est <= S->target || S->iters >= a.maxit || j + 1 >= m) {
+        S->in_cycle = 0;
+        atomicSub(a.counts, 1);
+    }
+}
+
+// ---------------------------------------------------------------- cycle end
+// One CTA per solve: y = R_H^-1 g (back substitution, FP64), x_V = c_r - B y,
+// z = R^-1 x_V; writes coefy = [z | y].
+__global__ void __launch_bounds__(128) k_backsub(BatchArgs a) {
+    const int s = blockIdx.x;
+    SolveScal* S = a.S + s;
+    if (!S->pending) return;
+    const SolvePtrs& P = a.P[s];
+    const int k = S->k, N = S->N, ldh = a.m + 1;
+    extern __shared__ double2 sh[];
+    double2* gg = sh;            // k
+    double2* y = sh + a.m;       // k
+    double2* xa = sh + 2 * a.m;  // N
+    for (int i = threadIdx.x; i < k; i += blockDim.x) gg[i] = P.g[i];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int i = k - 1; i >= 0; --i) {
+            const double2* col = P.Rg + (long long)i * ldh;
+            double2 yi = cdiv(gg[i], col[i]);
+            for (int l = lane; l < i; l += 32) gg[l] = csub(gg[l], cmul(col[l], yi));
+            if (lane == 0) y[i] = yi;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        double2 t = P.cr[n];
+        for (int i = 0; i < k; ++i) t = csub(t, cmul(P.B[(long long)i * a.nmax + n], y[i]));
+        xa[n] = t;
+    }
+    __syncthreads();
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int l = 0; l < N; ++l) t = cadd(t, cmul(P.Rinv[(long long)l * N + n], xa[l]));
+        P.coefy[n] = t;
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) P.coefy[N + i] = y[i];
+}
+
+// x += V z + Q y in FP64 (V, Q in the Krylov precision).
+template <typename T, int RPT>
+__global__ void __launch_bounds__(kBlock) k_update_x(BatchArgs a) {
+    using V = c2_t<T>;
+    SOLVE_PROLOGUE();
+    if (!S->pending) return;
+    const long long D = P.D;
+    const int N = S->N, k = S->k;
+    const V* __restrict__ Vv = reinterpret_cast<const V*>(P.V);
+    const V* __restrict__ Q = reinterpret_cast<const V*>(P.M) + (long long)N * D;
+    const double2* __restrict__ cy = P.coefy;
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
+        long long e = row0 + (long long)t * kBlock;
+        if (e >= D) continue;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int n = 0; n < N; ++n) cfma(acc, to_d2(Vv[(long long)n * D + e]), cy[n]);
+        for (int i = 0; i < k; ++i) cfma(acc, to_d2(Q[(long long)i * D + e]), cy[N + i]);
+        P.x[e] = cadd(P.x[e], acc);
+    }
+}
+
+// b = 0: the solution is x = 0 whatever x0 was.
+template <int RPT>
+__global__ void __launch_bounds__(kBlock) k_finalize(BatchArgs a) {
+    SOLVE_PROLOGUE();
+    if (S->nb != 0.0) return;
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
+        long long e = row0 + (long long)t * kBlock;
+        if (e < P.D) P.x[e] = make_double2(0.0, 0.0);
+    }
+}
+
+// ---------------------------------------------------------------- augmentation set-up
+// W = A U (FP64), column by column.
+template <int RPT>
+__global__ void __launch_bounds__(kBlock) k_aug_av(BatchArgs a) {
+    SOLVE_PROLOGUE();
+    const int N = S->N;
+    const long long D = P.D;
+    for (int n = 0; n < N; ++n) {
+        const double2* __restrict__ u = P.U + (long long)n * D;
+        auto ld = [&](long long idx) { return u[idx]; };
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) {
+            long long e = row0 + (long long)t * kBlock;
+            if (e < D) P.W[(long long)n * D + e] = stencil(e, P.nx, P.ny, P.coef_d, P.kh2 * P.eps_d[e], ld);
+        }
+    }
+}
+
+// Gram matrix G = W^H W (FP64) and, in the last CTA, its Cholesky factor
+// G = L L^H and the inverse of R_pass = L^H (upper triangular).
+// pass 0 writes R1^-1 to Rtmp; pass 1 writes R2^-1 to Rinv.
+// A non-positive or relatively tiny pivot marks the solve as rank deficient:
+// it then runs as plain GMRES (N = 0, fallback = 1).
+template <int RPT>
+__global__ void __launch_bounds__(kBlock) k_aug_gram(BatchArgs a, int pass) {
+    SOLVE_PROLOGUE();
+    const int N = S->N;
+    if (N == 0) return;
+    const long long D = P.D;
+    __shared__ double2 red[kWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double2* part = P.part + (long long)chunk * a.KP;
+    for (int p = 0; p < N; ++p)
+        for (int q = p; q < N; ++q) {
+            double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int t = 0; t < RPT; ++t) {
+                long long e = row0 + (long long)t * kBlock;
+                if (e < D) cfmac(acc, P.W[(long long)p * D + e], P.W[(long long)q * D + e]);
+            }
+            acc = warp_sum(acc);
+            __syncthreads();
+            if (lane == 0) red[wid] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double2 t = make_double2(0.0, 0.0);
+                for (int w = 0; w < kWarps; ++w) t = cadd(t, red[w]);
+                part[p * N + q] = t;
+            }
+        }
+    if (!arrive_last(P.ticket, P.nchunks)) return;
+    double2* G = P.hp;  // N x N, column-major, upper triangle used
+    for (int idx = threadIdx.x; idx < N * N; idx += kBlock) {
+        int p = idx / N, q = idx % N;
+        if (q < p) continue;
+        double2 sum = make_double2(0.0, 0.0);
+        for (int c = 0; c < P.nchunks; ++c) sum = cadd(sum, __ldcg(P.part + (long long)c * a.KP + idx));
+        G[q * N + p] = sum;  // G(p, q), p <= q
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    // Cholesky of the Hermitian G: G = R^H R with R upper triangular, in place
+    // in the upper triangle of G (column-major: R(p,q) at G[q*N + p]).
+    double dmax = 0.0;
+    for (int p = 0; p < N; ++p) dmax = fmax(dmax, G[p * N + p].x);
+    bool ok = dmax > 0.0;
+    for (int p = 0; p < N && ok; ++p) {
+        double d = G[p * N + p].x;
+        for (int l = 0; l < p; ++l) d -= cabs2(G[p * N + l]);
+        if (!(d > 1e-13 * dmax)) { ok = false; break; }
+        double rpp = sqrt(d);
+        G[p * N + p] = make_double2(rpp, 0.0);
+        for (int q = p + 1; q < N; ++q) {
+            double2 t = G[q * N + p];
+            for (int l = 0; l < p; ++l) t = csub(t, cmulc(G[p * N + l], G[q * N + l]));
+            G[q * N + p] = cscale(t, 1.0 / rpp);
+        }
+    }
+    if (!ok) {
+        S->N = 0;
+        S->fallback = 1;
+        return;
+    }
+    // inverse of the upper-triangular R (column-major), column by column
+    double2* Ri = pass == 0 ? P.Rtmp : P.Rinv;
+    for (int q = 0; q < N; ++q) {
+        for (int p = N - 1; p >= 0; --p) {
+            double2 t = make_double2(p == q ? 1.0 : 0.0, 0.0);
+            if (p > q) { Ri[q * N + p] = make_double2(0.0, 0.0); continue; }
+            for (int l = p + 1; l <= q; ++l) t = csub(t, cmul(G[l * N + p], Ri[q * N + l]));
+            Ri[q * N + p] = cdiv(t, G[p * N + p]);
+        }
+    }
+}
+
+// R^-1 of A V = C R with R = R2 R1: R^-1 = R1^-1 R2^-1 (one thread per solve).
+__global__ void k_aug_rinv(BatchArgs a, int n) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int N = a.S[s].N;
+    const SolvePtrs& P = a.P[s];
+    double2* G = P.hp;
+    for (int q = 0; q < N; ++q)
+        for (int p = 0; p < N; ++p) {
+            double2 t = make_double2(0.0, 0.0);
+            for (int l = 0; l < N; ++l) t = cadd(t, cmul(P.Rtmp[l * N + p], P.Rinv[q * N + l]));
+            G[q * N + p] = t;
+        }
+    for (int idx = 0; idx < N * N; ++idx) P.Rinv[idx] = G[idx];
+}
+
+// W <- W R_pass^-1 row by row (in place, columns from the last down).
+template <int RPT>
+__global__ void __launch_bounds__(kBlock) k_aug_tri(BatchArgs a, int pass) {
+    SOLVE_PROLOGUE();
+    const int N = S->N;
+    if (N == 0) return;
+    const long long D = P.D;
+    const double2* Ri = pass == 0 ? P.Rtmp : P.Rinv;
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
+        long long e = row0 + (long long)t * kBlock;
+        if (e >= D) continue;
+        for (int q = N - 1; q >= 0; --q) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int p = 0; p <= q; ++p) cfma(acc, P.W[(long long)p * D + e], Ri[q * N + p]);
+            P.W[(long long)q * D + e] = acc;
+        }
+    }
+}
+
+// C (Krylov precision) and V (Krylov precision) from W and U.
+template <typename T, int RPT>
+__global__ void __launch_bounds__(kBlock) k_aug_store(BatchArgs a) {
+    using V = c2_t<T>;
+    SOLVE_PROLOGUE();
+    const int N = S->N;
+    const long long D = P.D;
+    V* C = reinterpret_cast<V*>(P.M);
+    V* Vl = const_cast<V*>(reinterpret_cast<const V*>(P.V));
+    for (int n = 0; n < N; ++n)
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) {
+            long long e = row0 + (long long)t * kBlock;
+            if (e >= D) continue;
+            C[(long long)n * D + e] = from_d2<V>(P.W[(long long)n * D + e]);
+            Vl[(long long)n * D + e] = from_d2<V>(P.U[(long long)n * D + e]);
+        }
+}
+
+
+// ---------------------------------------------------------------- host driver
+static size_t align_up(size_t v, size_t al = 256) { return (v + al - 1) / al * al; }
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <typename X> X* take(size_t count) {
+        off = align_up(off);
+        X* p = base ? reinterpret_cast<X*>(base + off) : nullptr;
+        off += count * sizeof(X);
+        return p;
+    }
+};
+
+template <typename T, int RPT>
+static ddg_status run_batch_t(Context* ctx, int n, const ddg_op* const* A, const double* const* b,
+                              double* const* x, const double* const* U, int Nreq, double tol, int m,
+                              int maxit, double eta, ddg_info* info, cudaStream_t st) {
+    using V = c2_t<T>;
+    const long long RPB = (long long)kBlock * RPT;
+    int KP = std::max(kMaxAug + m + 2, Nreq * Nreq);
+    KP = (KP + 1) & ~1;
+    std::vector<SolvePtrs> hp(n);
+    long long total_ctas = 0;
+    for (int s = 0; s < n; ++s) {
+        hp[s].nchunks = (int)((A[s]->D + RPB - 1) / RPB);
+        hp[s].chunk0 = (int)total_ctas;
+        total_ctas += hp[s].nchunks;
+    }
+    // Two passes over the same layout: size it, then carve the workspace.
+    auto layout = [&](char* base) -> size_t {
+        Carver c{base};
+        for (int s = 0; s < n; ++s) {
+            const ddg_op* op = A[s];
+            const long long D = op->D;
+            SolvePtrs& P = hp[s];
+            size_t mbytes = sizeof(V) * (size_t)D * (size_t)(Nreq + m + 1);
+            size_t woff = 0;
+            if (Nreq > 0 && sizeof(T) == 4) {
+                woff = align_up(sizeof(V) * (size_t)D * Nreq);
+                mbytes = std::max(mbytes, woff + sizeof(double2) * (size_t)D * Nreq);
+            }
+            char* M = c.take<char>(mbytes);
+            P.M = M;
+            P.W = (Nreq > 0) ? reinterpret_cast<double2*>(M ? M + woff : nullptr) : nullptr;
+            P.w[0] = c.take<V>(D);
+            P.w[1] = c.take<V>(D);
+            P.r = c.take<double2>(D);
+            if (Nreq > 0 && sizeof(T) == 4) P.V = c.take<V>((size_t)D * Nreq);
+            else P.V = (Nreq > 0) ? (const void*)U[s] : nullptr;
+            P.Rg = c.take<double2>((size_t)(m + 1) * m);
+            P.B = c.take<double2>((size_t)kMaxAug * m);
+            P.cs = c.take<double>(m);
+            P.sn = c.take<double2>(m);
+            P.g = c.take<double2>(m + 1);
+            P.hsum = c.take<double2>(KP);
+            P.hp = c.take<double2>(KP);
+            P.part = c.take<double2>((size_t)P.nchunks * KP);
+            P.Rinv = c.take<double2>(std::max(1, Nreq * Nreq));
+            P.Rtmp = c.take<double2>(std::max(1, Nreq * Nreq));
+            P.cr = c.take<double2>(std::max(1, Nreq));
+            P.coefy = c.take<double2>(Nreq + m);
+            P.ticket = c.take<unsigned>(1);
+            P.nx = op->nx;
+            P.ny = op->ny;
+            P.D = D;
+            P.kh2 = op->kh * op->kh;
+            P.eps_d = op->eps_d;
+            P.coef_d = op->coef_d;
+            P.eps_lo = sizeof(T) == 4 ? (const void*)op->eps_f : (const void*)op->eps_d;
+            P.coef_lo = sizeof(T) == 4 ? (const void*)op->coef_f : (const void*)op->coef_d;
+            P.b = reinterpret_cast<const double2*>(b[s]);
+            P.x = reinterpret_cast<double2*>(x[s]);
+            P.U = (Nreq > 0) ? reinterpret_cast<const double2*>(U[s]) : nullptr;
+        }
+        return c.off + 4096;
+    };
+    size_t small_off = layout(nullptr);
+    Carver tail{nullptr, small_off};
+    tail.take<SolvePtrs>(n);
+    tail.take<SolveScal>(n);
+    tail.take<int>(total_ctas);
+    tail.take<int>(4);
+    DDG_TRY(ctx->reserve(tail.off + 4096, st));
+    char* base = reinterpret_cast<char*>(ctx->ws);
+    layout(base);
+    Carver t2{base, small_off};
+    BatchArgs args;
+    args.P = t2.take<SolvePtrs>(n);
+    args.S = t2.take<SolveScal>(n);
+    int* d_blk = t2.take<int>(total_ctas);
+    args.blk_solve = d_blk;
+    args.counts = t2.take<int>(4);
+    args.m = m;
+    args.KP = KP;
+    args.nmax = kMaxAug;
+    args.tol = tol;
+    args.eta = eta;
+    args.maxit = maxit;
+    std::vector<int> hblk(total_ctas);
+    for (int s = 0; s < n; ++s)
+        for (int c = 0; c < hp[s].nchunks; ++c) hblk[hp[s].chunk0 + c] = s;
+    DDG_CHECK_CUDA(cudaMemcpyAsync(args.P, hp.data(), sizeof(SolvePtrs) * n, cudaMemcpyHostToDevice, st));
+    DDG_CHECK_CUDA(cudaMemcpyAsync(d_blk, hblk.data(), sizeof(int) * total_ctas, cudaMemcpyHostToDevice, st));
+
+    const unsigned G = (unsigned)total_ctas;
+    k_init<<<(n + 127) / 128, 128, 0, st>>>(args, n, Nreq);
+    DDG_CHECK_LAUNCH("k_init");
+    if (Nreq > 0) {
+        k_aug_av<RPT><<<G, kBlock, 0, st>>>(args);
+        for (int pass = 0; pass < 2; ++pass) {
+            k_aug_gram<RPT><<<G, kBlock, 0, st>>>(args, pass);
+            k_aug_tri<RPT><<<G, kBlock, 0, st>>>(args, pass);
+        }
+        k_aug_rinv<<<(n + 63) / 64, 64, 0, st>>>(args, n);
+        if (sizeof(T) == 4) k_aug_store<T, RPT><<<G, kBlock, 0, st>>>(args);
+        DDG_CHECK_LAUNCH("augmentation set-up");
+    }
+    int* hc = ctx->host_counts;
+    const size_t bs_smem = sizeof(double2) * (2 * (size_t)m + kMaxAug);
+    for (long long cycle = 0; cycle <= (long long)maxit + 1; ++cycle) {
+        DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 4 * sizeof(int), st));
+        k_residual<RPT><<<G, kBlock, 0, st>>>(args);
+        if (Nreq > 0) {
+            k_dots<T, double, double, RPT><<<G, kBlock, 0, st>>>(args, 0, 2);
+            k_update<T, double, RPT><<<G, kBlock, 0, st>>>(args, 0, 2);
+        }
+        DDG_CHECK_LAUNCH("cycle start");
+        DDG_CHECK_CUDA(cudaMemcpyAsync(hc, args.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (hc[1] == 0) break;
+        if (hc[0] > 0) {
+            int polled = 0;
+            for (int j = 0; j < m; ++j) {
+                k_step<T, RPT><<<G, kBlock, 0, st>>>(args, j);
+                k_dots<T, T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 0);
+                k_update<T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 0);
+                k_dots<T, T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 1);
+                k_update<T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 1);
+                DDG_CHECK_LAUNCH("arnoldi step");
+                if ((j + 1) % ctx->poll_every == 0 && j + 1 < m) {
+                    const int slot = polled & 1;
+                    DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 2 + slot, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
+                    DDG_CHECK_CUDA(cudaEventRecord(ctx->ev[slot], st));
+                    if (polled > 0) {
+                        DDG_CHECK_CUDA(cudaEventSynchronize(ctx->ev[slot ^ 1]));
+                        if (hc[2 + (slot ^ 1)] == 0) break;
+                    }
+                    ++polled;
+                }
+            }
+        }
+        k_backsub<<<n, 128, bs_smem, st>>>(args);
+        k_update_x<T, RPT><<<G, kBlock, 0, st>>>(args);
+        DDG_CHECK_LAUNCH("cycle end");
+    }
+    k_finalize<RPT><<<G, kBlock, 0, st>>>(args);
+    DDG_CHECK_LAUNCH("k_finalize");
+    std::vector<SolveScal> hs(n);
+    DDG_CHECK_CUDA(cudaMemcpyAsync(hs.data(), args.S, sizeof(SolveScal) * n, cudaMemcpyDeviceToHost, st));
+    DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int s = 0; s < n; ++s) {
+        all = all && hs[s].converged;
+        if (info) {
+            info[s].iters = hs[s].iters;
+            info[s].cycles = hs[s].cycles;
+            info[s].converged = hs[s].converged;
+            info[s].fallback_used = hs[s].fallback;
+            info[s].breakdown = hs[s].breakdown;
+            info[s].true_rel_residual = hs[s].true_res;
+            info[s].first_step_rel_residual = hs[s].first_res;
+        }
+    }
+    return all ? DDG_OK : DDG_ENOCONV;
+}
+
+template <typename T>
+static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const double* const* b,
+                            double* const* x, const double* const* U, int Nreq, double tol, int m, int maxit,
+                            double eta, ddg_info* info, cudaStream_t st) {
+    long long c4 = 0, c2 = 0;
+    for (int s = 0; s < n; ++s) {
+        c4 += (A[s]->D + 4 * kBlock - 1) / (4 * kBlock);
+        c2 += (A[s]->D + 2 * kBlock - 1) / (2 * kBlock);
+    }
+    const long long want = 8LL * ctx->sm_count;
+    if (c4 >= want) return run_batch_t<T, 4>(ctx, n, A, b, x, U, Nreq, tol, m, maxit, eta, info, st);
+    if (c2 >= want) return run_batch_t<T, 2>(ctx, n, A, b, x, U, Nreq, tol, m, maxit, eta, info, st);
+    return run_batch_t<T, 1>(ctx, n, A, b, x, U, Nreq, tol, m, maxit, eta, info, st);
+}
+
+static ddg_status solve_entry(ddg_context* cptr, int n, const ddg_op* const* A, const double* const* b,
+                              const double* const* U, int k, double* const* x, double tol, int restart,
+                              int maxit, ddg_precision prec, ddg_info* info, void* stream, const char* who) {
+    if (!cptr) { set_error("%s: context is NULL", who); return DDG_EINVAL; }
+    if (n < 1 || !A || !b || !x) { set_error("%s: n=%d or NULL array", who, n); return DDG_EINVAL; }
+    if (!(tol > 0.0 && tol < 1.0)) { set_error("%s: tol=%g outside (0,1)", who, tol); return DDG_EINVAL; }
+    if (restart < 1 || restart > kMaxRestart) { set_error("%s: restart=%d outside [1,%d]", who, restart, kMaxRestart); return DDG_EINVAL; }
+    if (maxit < 1) { set_error("%s: maxit=%d < 1", who, maxit); return DDG_EINVAL; }
+    if (prec != DDG_C128 && prec != DDG_C64_REFINE) { set_error("%s: unsupported precision %d", who, (int)prec); return DDG_EINVAL; }
+    if (U && (k < 1 || k > kMaxAug)) { set_error("%s: k=%d outside [1,%d]", who, k, kMaxAug); return DDG_EINVAL; }
+    for (int s = 0; s < n; ++s) {
+        if (!A[s] || !b[s] || !x[s]) { set_error("%s: NULL operator/b/x at %d", who, s); return DDG_EINVAL; }
+        if (U && !U[s]) { set_error("%s: NULL U at %d", who, s); return DDG_EINVAL; }
+        if (A[s]->D > (1LL << 31) / 2) { set_error("%s: grid too large", who); return DDG_EINVAL; }
+    }
+    Context* ctx = reinterpret_cast<Context*>(cptr);
+    cudaStream_t st = as_stream(stream);
+    const int Nreq = U ? k : 0;
+    if (prec == DDG_C128)
+        return run_batch<double>(ctx, n, A, b, x, U, Nreq, tol, restart, maxit, 0.0, info, st);
+    return run_batch<float>(ctx, n, A, b, x, U, Nreq, tol, restart, maxit, ctx->inner_tol, info, st);
+}
+
+}  // namespace ddg
+
+using namespace ddg;
+
+extern "C" ddg_status gmres_solve(ddg_context* ctx, const ddg_op* A, const double* b, double* x, double tol,
+                                  int restart, int maxit, ddg_precision prec, ddg_info* info, void* stream) {
+    return solve_entry(ctx, 1, &A, &b, nullptr, 0, &x, tol, restart, maxit, prec, info, stream, "gmres_solve");
+}
+
+extern "C" ddg_status augmented_gmres_solve(ddg_context* ctx, const ddg_op* A, const double* b, const double* U,
+                                            int k, double* x, double tol, int restart, int maxit,
+                                            ddg_precision prec, ddg_info* info, void* stream) {
+    if (!U) { set_error("augmented_gmres_solve: U is NULL"); return DDG_EINVAL; }
+    return solve_entry(ctx, 1, &A, &b, &U, k, &x, tol, restart, maxit, prec, info, stream,
+                       "augmented_gmres_solve");
+}
+
+extern "C" ddg_status gmres_solve_batched(ddg_context* ctx, int n, const ddg_op* const* A, const double* const* b,
+                                          double* const* x, double tol, int restart, int maxit,
+                                          ddg_precision prec, ddg_info* info, void* stream) {
+    return solve_entry(ctx, n, A, b, nullptr, 0, x, tol, restart, maxit, prec, info, stream,
+                       "gmres_solve_batched");
+}
+
+extern "C" ddg_status augmented_gmres_solve_batched(ddg_context* ctx, int n, const ddg_op* const* A,
+                                                    const double* const* b, const double* const* U, int k,
+                                                    double* const* x, double tol, int restart, int maxit,
+                                                    ddg_precision prec, ddg_info* info, void* stream) {
+    if (!U) { set_error("augmented_gmres_solve_batched: U is NULL"); return DDG_EINVAL; }
+    return solve_entry(ctx, n, A, b, U, k, x, tol, restart, maxit, prec, info, stream,
+                       "augmented_gmres_solve_batched");
+}

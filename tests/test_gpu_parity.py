@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Bars: operator and source element by element (FP64 round-off, FP32 round-off
+for the complex64 stencil); solves by the true relative residual recomputed
+with the oracle's sparse operator (<= tol) and the relative L2 distance to the
+oracle's direct solution (<= 1e-5 at tol = 1e-6, i.e. forward-error factor 10).
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import fdfd, gmres, losses
+from paper_1902_00090_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1902_00090_gb300 as ddg  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return ddg.Context()
+
+
+def dev(a, dtype=torch.complex128):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+GRIDS = [
+    inputs.Grid(nx=37, ny=29, npml=5, i_src=9, sigma_src=3.0),      # ragged: not a multiple of any tile
+    inputs.Grid(nx=128, ny=128),
+    inputs.Grid(nx=192, ny=64, npml=10, i_src=20),
+    inputs.Grid(nx=3, ny=5, npml=1, i_src=1, sigma_src=1.0, slab_cells=1),   # smallest allowed
+]
+
+
+def problem(g, seed=0):
+    rng = np.random.default_rng(seed)
+    eps = inputs.background_eps(g) + 3.0 * rng.random((g.ny, g.nx))
+    return eps
+
+
+@pytest.mark.parametrize("g", GRIDS, ids=lambda g: f"{g.nx}x{g.ny}")
+def test_operator_matches_oracle(g):
+    eps = problem(g)
+    A = fdfd.operator_for(g, eps)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x = inputs.random_complex(g.D, seed=1)
+    y = host(ddg.fdfd_apply(op, dev(x)))
+    yo = A @ x
+    assert np.max(np.abs(y - yo)) <= 1e-13 * np.max(np.abs(yo))
+    y32 = host(ddg.fdfd_apply_c64(op, dev(x, torch.complex64)))
+    assert rel(y32, yo) <= 2e-6
+
+
+@pytest.mark.parametrize("g", GRIDS[:3], ids=lambda g: f"{g.nx}x{g.ny}")
+def test_source_matches_oracle(g):
+    eps = problem(g)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    b = host(ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src))
+    bo = fdfd.source_for(g)
+    assert np.max(np.abs(b - bo)) <= 1e-15 * np.max(np.abs(bo))
+
+
+def test_operator_rejects_bad_eps():
+    g = inputs.Grid(nx=16, ny=16, npml=3, i_src=4)
+    for bad in (-1.0, 0.0, float("nan"), float("inf")):
+        eps = inputs.background_eps(g)
+        eps[3, 5] = bad
+        with pytest.raises(ddg.DdgError) as e:
+            ddg.fdfd_operator(g, dev(eps, torch.float64))
+        assert e.value.status == 1
+
+
+def small(n=16, npml=3, seed=0):
+    g = inputs.Grid(nx=n, ny=n, npml=npml, i_src=n // 4, sigma_src=n / 8, slab_cells=max(2, n // 16))
+    rng = np.random.default_rng(seed)
+    eps = inputs.background_eps(g) + 0.5 * rng.random((g.ny, g.nx))
+    return g, eps, fdfd.operator_for(g, eps), fdfd.source_for(g)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_dense_direct_16x16(ctx, prec):
+    g, eps, A, b = small(16)
+    x_ref = np.linalg.solve(A.toarray(), b)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    tol = 1e-12 if prec == "c128" else 1e-10
+    x, info, st = ddg.gmres_solve(ctx, op, dev(b), tol=tol, restart=60, maxit=3000, precision=prec)
+    assert st == 0 and info["converged"]
+    assert rel(host(x), x_ref) <= (1e-10 if prec == "c128" else 1e-8)
+    assert np.linalg.norm(b - A @ host(x)) / np.linalg.norm(b) <= tol
+
+
+def test_plain_iterations_match_oracle_c128(ctx):
+    # Same algorithm in the same precision: equal Krylov step counts (up to a
+    # step at a tolerance crossing) and the same solution.
+    g, eps, A, b = small(32, npml=6, seed=1)
+    xo, io = gmres.plain_gmres(A, b, tol=1e-9, restart=25, maxit=3000)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x, info, st = ddg.gmres_solve(ctx, op, dev(b), tol=1e-9, restart=25, maxit=3000)
+    assert st == 0
+    assert abs(info["iters"] - io.iters) <= 1
+    assert info["cycles"] == io.cycles
+    assert rel(host(x), xo) <= 1e-6
+
+
+@pytest.fixture(scope="module")
+def config1():
+    g = inputs.grid_128()
+    eps = inputs.bernoulli_eps(g, 0)
+    A = fdfd.operator_for(g, eps)
+    b = fdfd.source_for(g)
+    xd = spla.spsolve(A.tocsc(), b)
+    return g, eps, A, b, xd
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_config1_plain_full_size(ctx, config1, prec):
+    g, eps, A, b, xd = config1
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    bd = ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src)
+    x, info, st = ddg.gmres_solve(ctx, op, bd, tol=1e-6, restart=200, maxit=5000, precision=prec)
+    assert st == 0 and info["converged"]
+    xh = host(x)
+    true_res = np.linalg.norm(b - A @ xh) / np.linalg.norm(b)
+    assert true_res <= 1e-6
+    assert abs(true_res - info["true_rel_residual"]) <= 1e-9
+    assert rel(xh, xd) <= 1e-5
+    # oracle GMRES(200) needs 1534 Krylov steps on this problem
+    assert 1300 <= info["iters"] <= 2200
+
+
+def rand_V(D, N, seed):
+    return inputs.random_complex(D, seed, shape=(N, D))
+
+
+def test_augmented_matches_oracle_c128(ctx):
+    g, eps, A, b = small(24, npml=4, seed=9)
+    V = rand_V(g.D, 4, 9)
+    xo, io = gmres.augmented_gmres(A, b, V.T, tol=1e-9, restart=30)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x, info, st = ddg.augmented_gmres_solve(ctx, op, dev(b), dev(V), tol=1e-9, restart=30)
+    assert st == 0 and info["converged"] and not info["fallback_used"]
+    assert abs(info["iters"] - io.iters) <= 1
+    assert rel(host(x), xo) <= 1e-6
+    lres = losses.residual_loss(A, V.T, b)
+    assert abs(info["first_step_rel_residual"] - np.sqrt(lres)) <= 1e-10
+    assert abs(info["first_step_rel_residual"] - io.first_step_rel_residual) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_augmented_solution_in_V_needs_no_krylov_step(ctx, prec):
+    g, eps, A, b = small(24, npml=4, seed=6)
+    xd = spla.spsolve(A.tocsc(), b)
+    V = np.stack([inputs.random_complex(g.D, 1), xd, inputs.random_complex(g.D, 2)])
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x, info, st = ddg.augmented_gmres_solve(ctx, op, dev(b), dev(V), tol=1e-6, restart=30,
+                                            precision=prec)
+    assert st == 0 and info["converged"]
+    if prec == "c128":
+        assert info["first_step_rel_residual"] <= 1e-12
+        assert info["iters"] == 0
+    else:
+        assert info["first_step_rel_residual"] <= 1e-6
+    assert rel(host(x), xd) <= 1e-6
+
+
+def test_rank_deficient_V_falls_back_to_plain(ctx):
+    g, eps, A, b = small(24, npml=4, seed=3)
+    v = inputs.random_complex(g.D, 5)
+    V = np.stack([v, 2.0 * v, inputs.random_complex(g.D, 6)])   # duplicate direction
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x, info, st = ddg.augmented_gmres_solve(ctx, op, dev(b), dev(V), tol=1e-8, restart=30)
+    assert st == 0 and info["converged"] and info["fallback_used"] == 1
+    assert np.linalg.norm(b - A @ host(x)) / np.linalg.norm(b) <= 1e-8
+
+
+def test_zero_rhs_gives_zero_solution(ctx):
+    g, eps, A, b = small(16)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x0 = dev(inputs.random_complex(g.D, 3))
+    x, info, st = ddg.gmres_solve(ctx, op, dev(np.zeros(g.D, complex)), x=x0, tol=1e-6)
+    assert st == 0 and info["converged"] and info["iters"] == 0
+    assert np.all(host(x) == 0)
+
+
+def test_iteration_cap_reports_no_convergence(ctx):
+    g, eps, A, b = small(32, npml=6)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x, info, st = ddg.gmres_solve(ctx, op, dev(b), tol=1e-12, restart=10, maxit=37)
+    assert st == 4 and not info["converged"]
+    assert info["iters"] == 37
+    res = np.linalg.norm(b - A @ host(x)) / np.linalg.norm(b)
+    assert abs(res - info["true_rel_residual"]) <= 1e-9 and res < 1.0
+
+
+def test_initial_guess_is_used(ctx):
+    g, eps, A, b = small(16)
+    xd = np.linalg.solve(A.toarray(), b)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x, info, st = ddg.gmres_solve(ctx, op, dev(b), x=dev(xd), tol=1e-8)
+    assert st == 0 and info["iters"] == 0
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_batched_uneven_sizes_match_single_solves(ctx, prec):
+    specs = [(16, 3, 0), (37, 5, 1), (64, 8, 2), (24, 4, 3), (16, 3, 4)]
+    ops, bs, As, bos = [], [], [], []
+    for n, L, seed in specs:
+        g = inputs.Grid(nx=n, ny=n + 3, npml=L, i_src=2 * L, sigma_src=n / 8, slab_cells=2)
+        rng = np.random.default_rng(seed)
+        eps = inputs.background_eps(g) + rng.random((g.ny, g.nx))
+        ops.append(ddg.fdfd_operator(g, dev(eps, torch.float64)))
+        As.append(fdfd.operator_for(g, eps))
+        bo = fdfd.source_for(g)
+        bos.append(bo)
+        bs.append(dev(bo))
+    xs, infos, st = ddg.gmres_solve_batched(ctx, ops, bs, tol=1e-8, restart=40, precision=prec)
+    assert st == 0
+    for i in range(len(specs)):
+        x1, info1, _ = ddg.gmres_solve(ctx, ops[i], bs[i], tol=1e-8, restart=40, precision=prec)
+        assert infos[i]["iters"] == info1["iters"]
+        assert np.array_equal(host(xs[i]), host(x1))           # same kernels, same order: bitwise
+        xh = host(xs[i])
+        assert np.linalg.norm(bos[i] - As[i] @ xh) / np.linalg.norm(bos[i]) <= 1e-8
+
+
+def test_batched_augmented_uneven(ctx):
+    specs = [(24, 4, 0), (33, 5, 1), (40, 5, 2)]
+    ops, bs, Us, As, bos = [], [], [], [], []
+    for n, L, seed in specs:
+        g = inputs.Grid(nx=n, ny=n, npml=L, i_src=2 * L, sigma_src=n / 8, slab_cells=2)
+        rng = np.random.default_rng(seed)
+        eps = inputs.background_eps(g) + rng.random((g.ny, g.nx))
+        ops.append(ddg.fdfd_operator(g, dev(eps, torch.float64)))
+        A = fdfd.operator_for(g, eps)
+        As.append(A)
+        bo = fdfd.source_for(g)
+        bos.append(bo)
+        bs.append(dev(bo))
+        # a useful subspace: the solution of a perturbed problem plus noise
+        A2 = fdfd.operator_for(g, eps * 1.01)
+        Us.append(dev(np.stack([spla.spsolve(A2.tocsc(), bo), inputs.random_complex(g.D, seed)])))
+    for prec in ("c128", "c64"):
+        xs, infos, st = ddg.augmented_gmres_solve_batched(ctx, ops, bs, Us, tol=1e-7, restart=30,
+                                                          precision=prec)
+        assert st == 0
+        for i in range(len(specs)):
+            xh = host(xs[i])
+            assert np.linalg.norm(bos[i] - As[i] @ xh) / np.linalg.norm(bos[i]) <= 1e-7
+            assert infos[i]["first_step_rel_residual"] < 0.5
