@@ -84,11 +84,33 @@ const char* ddg_last_error(void);
 /* Library version as 10000*major + 100*minor + patch. */
 int ddg_version(void);
 
+/* Kernel classes of the solver, for ddg_context_profile_read. */
+typedef enum {
+    DDG_K_STEP = 0,       /* q_j = w / h, w = A q_j (stencil) */
+    DDG_K_DOTS = 1,       /* Gram-Schmidt projections [C Q]^H w */
+    DDG_K_UPDATE = 2,     /* Gram-Schmidt updates w -= [C Q] h (+ norm, Givens) */
+    DDG_K_RESIDUAL = 3,   /* cycle start: r = b - A x (FP64), augmented projection */
+    DDG_K_CYCLE_END = 4,  /* back substitution and x += V z + Q y */
+    DDG_K_SETUP = 5,      /* augmentation set-up (A V, Cholesky QR twice), PCA fit */
+    DDG_K_NCLASSES = 6
+} ddg_kernel_class;
+
 /* Context: owns the device workspace (grown on demand, reused across calls). */
 ddg_status ddg_context_create(ddg_context** ctx);
 ddg_status ddg_context_destroy(ddg_context* ctx);
 /* Bytes of device workspace the context currently holds. */
 long long ddg_context_workspace_bytes(const ddg_context* ctx);
+/* Kernels launched through this context since it was created. */
+long long ddg_context_launches(const ddg_context* ctx);
+/* Profiling: with enable != 0 every later launch is bracketed by CUDA events on
+   its stream and each kernel adds its algorithmic bytes (the bytes the method
+   must move: every vector element read or written once) to a device counter.
+   Enabling (or disabling) clears the accumulators. */
+ddg_status ddg_context_profile_enable(ddg_context* ctx, int enable);
+/* Accumulated device time (ms), algorithmic bytes and launch count of one
+   ddg_kernel_class since profiling was enabled.  Synchronises the device. */
+ddg_status ddg_context_profile_read(ddg_context* ctx, int cls, double* ms, double* bytes,
+                                    long long* launches);
 /* Inner-cycle relative tolerance for DDG_C64_REFINE (a cycle ends once its
    least-squares residual falls below eta times the cycle's starting residual).
    Default 1e-5.  Must be in (0, 1). */
@@ -173,6 +195,24 @@ ddg_status augmented_gmres_solve_batched(ddg_context* ctx, int n, const ddg_op* 
                                          int k, double* const* x, double tol, int restart,
                                          int maxit, ddg_precision prec, ddg_info* info,
                                          void* stream);
+
+/*
+ * pca_fit -- principal components of training fields (Sec. III, "Principal
+ * component analysis": an incomplete SVD of the matrix whose columns are the
+ * training fields; uncentred, no normalisation).  U receives the k leading left
+ * singular vectors of F, computed by the method of snapshots in FP64: G = F^H F,
+ * its top-k eigenpairs by block subspace iteration (k + 16 vectors) with
+ * Rayleigh-Ritz, u_c = F w_c / sigma_c.  Singular vectors are defined up to a
+ * unit phase (and a rotation inside repeated singular values).
+ *   F      device, D x M complex128, column-major (field m at F + 2*D*m).
+ *   U      device, D x k complex128, column-major, written in full.
+ *   sigma  (host) k doubles (sigma_1 >= ... >= sigma_k), may be NULL.
+ *   1 <= k <= min(32, M), M <= D, M <= 8192.  Uses the context's workspace
+ *   (about (slices + 1) * M^2 * 16 bytes, slices <= 64); synchronises `stream`
+ *   when sigma is requested.
+ */
+ddg_status pca_fit(ddg_context* ctx, const double* F, long long D, int M, int k, double* U,
+                   double* sigma, void* stream);
 
 #ifdef __cplusplus
 }

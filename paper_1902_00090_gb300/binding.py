@@ -19,6 +19,8 @@ DDG_C128 = 0
 DDG_C64_REFINE = 1
 PRECISIONS = {"c128": DDG_C128, "c64": DDG_C64_REFINE, "c64_refine": DDG_C64_REFINE}
 
+KERNEL_CLASSES = ("step", "dots", "update", "residual", "cycle_end", "setup")
+
 STATUS = {0: "DDG_OK", 1: "DDG_EINVAL", 2: "DDG_ENOMEM", 3: "DDG_ECUDA", 4: "DDG_ENOCONV",
           5: "DDG_EBREAKDOWN", 6: "DDG_ETIMEOUT", 7: "DDG_ESINGULAR"}
 
@@ -53,6 +55,10 @@ _SIGS = {
     "ddg_context_destroy": (C.c_int, [_vp]),
     "ddg_context_workspace_bytes": (C.c_longlong, [_vp]),
     "ddg_context_set_inner_tol": (C.c_int, [_vp, C.c_double]),
+    "ddg_context_launches": (C.c_longlong, [_vp]),
+    "ddg_context_profile_enable": (C.c_int, [_vp, C.c_int]),
+    "ddg_context_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_longlong)]),
     "fdfd_operator": (C.c_int, [C.POINTER(ddg_grid), _vp, C.POINTER(_vp), _vp]),
     "fdfd_operator_destroy": (C.c_int, [_vp]),
     "fdfd_operator_size": (C.c_longlong, [_vp]),
@@ -66,6 +72,7 @@ _SIGS = {
     "gmres_solve_batched": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),
                                       C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(ddg_info),
                                       _vp]),
+    "pca_fit": (C.c_int, [_vp, _vp, C.c_longlong, C.c_int, C.c_int, _vp, C.POINTER(C.c_double), _vp]),
     "augmented_gmres_solve_batched": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp),
                                                 C.POINTER(_vp), C.c_int, C.POINTER(_vp),
                                                 C.c_double, C.c_int, C.c_int, C.c_int,
@@ -141,6 +148,24 @@ class Context:
     @property
     def workspace_bytes(self) -> int:
         return int(load().ddg_context_workspace_bytes(self._h))
+
+    @property
+    def launches(self) -> int:
+        """Kernels launched through this context (ddg_context_launches)."""
+        return int(load().ddg_context_launches(self._h))
+
+    def profile_enable(self, on: bool = True):
+        _check(load().ddg_context_profile_enable(self._h, int(bool(on))), "ddg_context_profile_enable")
+
+    def profile_read(self):
+        """{class name: (ms, algorithmic bytes, launches)} since profiling was enabled."""
+        out = {}
+        for cls, name in enumerate(KERNEL_CLASSES):
+            ms, by, n = C.c_double(), C.c_double(), C.c_longlong()
+            _check(load().ddg_context_profile_read(self._h, cls, C.byref(ms), C.byref(by), C.byref(n)),
+                   "ddg_context_profile_read")
+            out[name] = (ms.value, by.value, n.value)
+        return out
 
     def close(self):
         if getattr(self, "_h", None):
@@ -315,3 +340,16 @@ def augmented_gmres_solve_batched(ctx: Context, A, b, U, x=None, tol=1e-6, resta
     if st not in (0, 4):
         _check(st, "augmented_gmres_solve_batched")
     return x, [i.as_dict() for i in infos], st
+
+
+def pca_fit(ctx: Context, F, k: int, U=None, stream=None):
+    """F: CUDA complex128 tensor (M, D) -- row m is training field f_m (the library's
+    D x M column-major layout).  Returns (U as a (k, D) tensor, sigma list)."""
+    torch = _torch()
+    M, D = F.shape
+    if U is None:
+        U = torch.empty((k, D), dtype=torch.complex128, device=F.device)
+    sig = (C.c_double * k)()
+    _check(load().pca_fit(ctx.handle, _dev_ptr(F, torch.complex128, "F", M * D), int(D), int(M), int(k),
+                          _dev_ptr(U, torch.complex128, "U", k * D), sig, _stream(stream)), "pca_fit")
+    return U, list(sig)

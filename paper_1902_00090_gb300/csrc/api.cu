@@ -47,6 +47,31 @@ ddg_status Context::reserve(size_t bytes, cudaStream_t s) {
     return DDG_OK;
 }
 
+cudaEvent_t Context::get_event() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void Context::resolve() {
+    for (auto& p : pending) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms[p.cls] += t;
+        else cudaGetLastError();
+        pool.push_back(p.a);
+        pool.push_back(p.b);
+    }
+    pending.clear();
+}
+
 }  // namespace ddg
 
 using namespace ddg;
@@ -79,6 +104,8 @@ extern "C" ddg_status ddg_context_create(ddg_context** out) {
     cudaError_t e = cudaMallocHost(&c->host_counts, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[1], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_bytes, DDG_K_NCLASSES * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->d_bytes, 0, DDG_K_NCLASSES * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         delete c;
         return cuda_status(e, "ddg_context_create: cudaMallocHost");
@@ -94,6 +121,9 @@ extern "C" ddg_status ddg_context_destroy(ddg_context* ctx) {
     cudaFreeHost(c->host_counts);
     if (c->ev[0]) cudaEventDestroy(c->ev[0]);
     if (c->ev[1]) cudaEventDestroy(c->ev[1]);
+    cudaFree(c->d_bytes);
+    c->resolve();
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     delete c;
     return DDG_OK;
 }
@@ -105,5 +135,37 @@ extern "C" long long ddg_context_workspace_bytes(const ddg_context* ctx) {
 extern "C" ddg_status ddg_context_set_inner_tol(ddg_context* ctx, double eta) {
     if (!ctx || !(eta > 0.0 && eta < 1.0)) { set_error("inner tol must be in (0,1)"); return DDG_EINVAL; }
     reinterpret_cast<Context*>(ctx)->inner_tol = eta;
+    return DDG_OK;
+}
+
+extern "C" long long ddg_context_launches(const ddg_context* ctx) {
+    return ctx ? reinterpret_cast<const Context*>(ctx)->launches : 0;
+}
+
+extern "C" ddg_status ddg_context_profile_enable(ddg_context* ctx, int enable) {
+    if (!ctx) { set_error("ddg_context_profile_enable: NULL context"); return DDG_EINVAL; }
+    Context* c = reinterpret_cast<Context*>(ctx);
+    DDG_CHECK_CUDA(cudaDeviceSynchronize());
+    c->resolve();
+    for (int i = 0; i < DDG_K_NCLASSES; ++i) {
+        c->ms[i] = 0.0;
+        c->nlaunch[i] = 0;
+    }
+    DDG_CHECK_CUDA(cudaMemset(c->d_bytes, 0, DDG_K_NCLASSES * sizeof(unsigned long long)));
+    c->prof = enable != 0;
+    return DDG_OK;
+}
+
+extern "C" ddg_status ddg_context_profile_read(ddg_context* ctx, int cls, double* ms, double* bytes,
+                                               long long* launches) {
+    if (!ctx || cls < 0 || cls >= DDG_K_NCLASSES) { set_error("ddg_context_profile_read: bad argument"); return DDG_EINVAL; }
+    Context* c = reinterpret_cast<Context*>(ctx);
+    DDG_CHECK_CUDA(cudaDeviceSynchronize());
+    c->resolve();
+    unsigned long long hb[DDG_K_NCLASSES];
+    DDG_CHECK_CUDA(cudaMemcpy(hb, c->d_bytes, sizeof(hb), cudaMemcpyDeviceToHost));
+    if (ms) *ms = c->ms[cls];
+    if (bytes) *bytes = (double)hb[cls];
+    if (launches) *launches = c->nlaunch[cls];
     return DDG_OK;
 }

@@ -1,5 +1,7 @@
 // Internal types of the batched GMRES engine.
 #pragma once
+#include <vector>
+
 #include "common.cuh"
 
 namespace ddg {
@@ -19,7 +21,40 @@ struct Context {
     int poll_every = 8;              // Arnoldi steps between host polls
     int sm_count = 152;
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    // launch accounting and profiling
+    long long launches = 0;
+    bool prof = false;
+    unsigned long long* d_bytes = nullptr;   // device, DDG_K_NCLASSES counters
+    double ms[DDG_K_NCLASSES] = {};
+    long long nlaunch[DDG_K_NCLASSES] = {};
+    struct Pending { int cls; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
     ddg_status reserve(size_t bytes, cudaStream_t s);
+    cudaEvent_t get_event();
+    // Brackets one kernel launch: counts it and, when profiling, records events.
+    template <typename F> ddg_status launch(int cls, cudaStream_t s, F&& fn) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (prof) {
+            a = get_event();
+            if (a) cudaEventRecord(a, s);
+        }
+        fn();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_status(e, "kernel launch");
+        ++launches;
+        ++nlaunch[cls];
+        if (prof && a) {
+            b = get_event();
+            if (b) {
+                cudaEventRecord(b, s);
+                pending.push_back({cls, a, b});
+            }
+        }
+        return DDG_OK;
+    }
+    // Adds the elapsed times of recorded launches (call after a stream sync).
+    void resolve();
 };
 
 // Per-solve device pointers (read-only during a solve).
@@ -67,6 +102,7 @@ struct SolveScal {
 };
 
 struct BatchArgs {
+    unsigned long long* bytes;   // per-class algorithmic byte counters, or null
     SolvePtrs* P;
     SolveScal* S;
     const int* blk_solve;
@@ -78,5 +114,10 @@ struct BatchArgs {
     double eta;        // inner relative tolerance (0 for complex128)
     int maxit;
 };
+
+// Adds `v` to the class counter once per CTA (thread 0), when profiling.
+__device__ __forceinline__ void count_bytes(const BatchArgs& a, int cls, double v) {
+    if (a.bytes && threadIdx.x == 0) atomicAdd(a.bytes + cls, (unsigned long long)v);
+}
 
 }  // namespace ddg

@@ -112,7 +112,8 @@ __device__ __forceinline__ void rotate(double c, double2 s, double2& u, double2&
     SolveScal* S = a.S + s;                                \
     const SolvePtrs& P = a.P[s];                           \
     const int chunk = blockIdx.x - P.chunk0;               \
-    const long long row0 = (long long)chunk * (kBlock * RPT) + threadIdx.x;
+    const long long row0 = (long long)chunk * (kBlock * RPT) + threadIdx.x;                  \
+    const double rows = (double)min((long long)(kBlock * RPT), P.D - (long long)chunk * (kBlock * RPT));
 
 // ---------------------------------------------------------------- init
 __global__ void k_init(BatchArgs a, int n, int nreq) {
@@ -146,6 +147,7 @@ template <int RPT>
 __global__ void __launch_bounds__(kBlock) k_residual(BatchArgs a) {
     SOLVE_PROLOGUE();
     if (!S->active) return;
+    count_bytes(a, DDG_K_RESIDUAL, rows * (16.0 + 16.0 + 8.0 + 16.0));
     __shared__ double sm[kWarps];
     const long long D = P.D;
     const double2* __restrict__ x = P.x;
@@ -219,6 +221,7 @@ __global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
     using V = c2_t<T>;
     SOLVE_PROLOGUE();
     if (!S->in_cycle) return;
+    count_bytes(a, DDG_K_STEP, rows * ((j == 0 ? 16.0 : (double)sizeof(V)) + sizeof(T) + 2.0 * sizeof(V)));
     const long long D = P.D;
     const int N = S->N;
     const double inv = 1.0 / S->hnorm;
@@ -276,6 +279,7 @@ __global__ void __launch_bounds__(kBlock) k_dots(BatchArgs a, int j, int mode) {
     const long long D = P.D;
     const int K = (mode == 2) ? N : N + j + 1;
     const int Ktot = K + (mode == 0 ? 1 : 0);
+    count_bytes(a, mode == 2 ? DDG_K_RESIDUAL : DDG_K_DOTS, rows * ((double)K * sizeof(VM) + sizeof(VV)));
     const VV* __restrict__ v = (mode == 2) ? reinterpret_cast<const VV*>(P.r)
                                            : reinterpret_cast<const VV*>(P.w[j & 1]);
     const VM* __restrict__ M = reinterpret_cast<const VM*>(P.M);
@@ -374,6 +378,7 @@ __global__ void __launch_bounds__(kBlock) k_update(BatchArgs a, int j, int mode)
     __shared__ double sm[kWarps];
     const long long D = P.D;
     const int K = (mode == 2) ? N : N + j + 1;
+    count_bytes(a, mode == 2 ? DDG_K_RESIDUAL : DDG_K_UPDATE, rows * ((double)K * sizeof(VM) + 2.0 * sizeof(VV)));
     VV* __restrict__ v = (mode == 2) ? reinterpret_cast<VV*>(P.r) : reinterpret_cast<VV*>(P.w[j & 1]);
     const VM* __restrict__ M = reinterpret_cast<const VM*>(P.M);
     const double2* __restrict__ hp = P.hp;
@@ -525,6 +530,7 @@ __global__ void __launch_bounds__(kBlock) k_update_x(BatchArgs a) {
     if (!S->pending) return;
     const long long D = P.D;
     const int N = S->N, k = S->k;
+    count_bytes(a, DDG_K_CYCLE_END, rows * ((double)(N + k) * sizeof(V) + 32.0));
     const V* __restrict__ Vv = reinterpret_cast<const V*>(P.V);
     const V* __restrict__ Q = reinterpret_cast<const V*>(P.M) + (long long)N * D;
     const double2* __restrict__ cy = P.coefy;
@@ -795,6 +801,7 @@ static ddg_status run_batch_t(Context* ctx, int n, const ddg_op* const* A, const
     int* d_blk = t2.take<int>(total_ctas);
     args.blk_solve = d_blk;
     args.counts = t2.take<int>(4);
+    args.bytes = ctx->prof ? ctx->d_bytes : nullptr;
     args.m = m;
     args.KP = KP;
     args.nmax = kMaxAug;
@@ -808,40 +815,37 @@ static ddg_status run_batch_t(Context* ctx, int n, const ddg_op* const* A, const
     DDG_CHECK_CUDA(cudaMemcpyAsync(d_blk, hblk.data(), sizeof(int) * total_ctas, cudaMemcpyHostToDevice, st));
 
     const unsigned G = (unsigned)total_ctas;
-    k_init<<<(n + 127) / 128, 128, 0, st>>>(args, n, Nreq);
-    DDG_CHECK_LAUNCH("k_init");
+    DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_init<<<(n + 127) / 128, 128, 0, st>>>(args, n, Nreq); }));
     if (Nreq > 0) {
-        k_aug_av<RPT><<<G, kBlock, 0, st>>>(args);
+        DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_av<RPT><<<G, kBlock, 0, st>>>(args); }));
         for (int pass = 0; pass < 2; ++pass) {
-            k_aug_gram<RPT><<<G, kBlock, 0, st>>>(args, pass);
-            k_aug_tri<RPT><<<G, kBlock, 0, st>>>(args, pass);
+            DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_gram<RPT><<<G, kBlock, 0, st>>>(args, pass); }));
+            DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_tri<RPT><<<G, kBlock, 0, st>>>(args, pass); }));
         }
-        k_aug_rinv<<<(n + 63) / 64, 64, 0, st>>>(args, n);
-        if (sizeof(T) == 4) k_aug_store<T, RPT><<<G, kBlock, 0, st>>>(args);
-        DDG_CHECK_LAUNCH("augmentation set-up");
+        DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_rinv<<<(n + 63) / 64, 64, 0, st>>>(args, n); }));
+        if (sizeof(T) == 4)
+            DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_store<T, RPT><<<G, kBlock, 0, st>>>(args); }));
     }
     int* hc = ctx->host_counts;
     const size_t bs_smem = sizeof(double2) * (2 * (size_t)m + kMaxAug);
     for (long long cycle = 0; cycle <= (long long)maxit + 1; ++cycle) {
         DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 4 * sizeof(int), st));
-        k_residual<RPT><<<G, kBlock, 0, st>>>(args);
+        DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_residual<RPT><<<G, kBlock, 0, st>>>(args); }));
         if (Nreq > 0) {
-            k_dots<T, double, double, RPT><<<G, kBlock, 0, st>>>(args, 0, 2);
-            k_update<T, double, RPT><<<G, kBlock, 0, st>>>(args, 0, 2);
+            DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_dots<T, double, double, RPT><<<G, kBlock, 0, st>>>(args, 0, 2); }));
+            DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_update<T, double, RPT><<<G, kBlock, 0, st>>>(args, 0, 2); }));
         }
-        DDG_CHECK_LAUNCH("cycle start");
         DDG_CHECK_CUDA(cudaMemcpyAsync(hc, args.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DDG_CHECK_CUDA(cudaStreamSynchronize(st));
         if (hc[1] == 0) break;
         if (hc[0] > 0) {
             int polled = 0;
             for (int j = 0; j < m; ++j) {
-                k_step<T, RPT><<<G, kBlock, 0, st>>>(args, j);
-                k_dots<T, T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 0);
-                k_update<T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 0);
-                k_dots<T, T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 1);
-                k_update<T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 1);
-                DDG_CHECK_LAUNCH("arnoldi step");
+                DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_step<T, RPT><<<G, kBlock, 0, st>>>(args, j); }));
+                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots<T, T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 0); }));
+                DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update<T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 0); }));
+                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots<T, T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 1); }));
+                DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update<T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 1); }));
                 if ((j + 1) % ctx->poll_every == 0 && j + 1 < m) {
                     const int slot = polled & 1;
                     DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 2 + slot, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -854,15 +858,14 @@ static ddg_status run_batch_t(Context* ctx, int n, const ddg_op* const* A, const
                 }
             }
         }
-        k_backsub<<<n, 128, bs_smem, st>>>(args);
-        k_update_x<T, RPT><<<G, kBlock, 0, st>>>(args);
-        DDG_CHECK_LAUNCH("cycle end");
+        DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_backsub<<<n, 128, bs_smem, st>>>(args); }));
+        DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_update_x<T, RPT><<<G, kBlock, 0, st>>>(args); }));
     }
-    k_finalize<RPT><<<G, kBlock, 0, st>>>(args);
-    DDG_CHECK_LAUNCH("k_finalize");
+    DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_finalize<RPT><<<G, kBlock, 0, st>>>(args); }));
     std::vector<SolveScal> hs(n);
     DDG_CHECK_CUDA(cudaMemcpyAsync(hs.data(), args.S, sizeof(SolveScal) * n, cudaMemcpyDeviceToHost, st));
     DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+    ctx->resolve();
     bool all = true;
     for (int s = 0; s < n; ++s) {
         all = all && hs[s].converged;

@@ -261,3 +261,36 @@ def test_batched_augmented_uneven(ctx):
             xh = host(xs[i])
             assert np.linalg.norm(bos[i] - As[i] @ xh) / np.linalg.norm(bos[i]) <= 1e-7
             assert infos[i]["first_step_rel_residual"] < 0.5
+
+
+def test_pca_fit_matches_oracle_svd(ctx):
+    from oracle import pca
+    rng = np.random.default_rng(0)
+    D, M, k = 3000, 90, 12
+    F = (rng.standard_normal((D, M)) + 1j * rng.standard_normal((D, M))) * (0.8 ** np.arange(M))
+    Uo, so = pca.pca_basis(F, k)
+    U, sig = ddg.pca_fit(ctx, dev(F.T), k)
+    Ug = host(U).T
+    assert np.allclose(sig, so[:k], rtol=1e-10)
+    assert np.linalg.norm(Ug.conj().T @ Ug - np.eye(k)) <= 1e-10
+    assert np.linalg.norm(Ug @ Ug.conj().T - Uo @ Uo.conj().T, 2) <= 1e-8
+    assert abs(pca.captured_energy(Ug, F) - pca.captured_energy(Uo, F)) <= 1e-10
+
+
+def test_pca_fit_on_solved_training_fields(ctx):
+    # fields solved by the library itself (the config-2 training flow, small)
+    from oracle import pca
+    g = inputs.grid_for(64, 64, i_src=20)
+    eps_set = inputs.trajectory_set(g, 2, 4, steps=12)
+    ops = [ddg.fdfd_operator(g, dev(e, torch.float64)) for e in eps_set]
+    bs = [ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src) for op in ops]
+    xs, infos, st = ddg.gmres_solve_batched(ctx, ops, bs, tol=1e-10, restart=100, maxit=20000)
+    assert st == 0
+    F = torch.stack(xs)
+    U, sig = ddg.pca_fit(ctx, F, 8)
+    Uo, so = pca.pca_basis(host(F).T, 8)
+    gap_ok = so[7] > 1.05 * so[8]
+    assert np.allclose(sig, so[:8], rtol=1e-8)
+    if gap_ok:
+        Ug = host(U).T
+        assert np.linalg.norm(Ug @ Ug.conj().T - Uo @ Uo.conj().T, 2) <= 1e-6
