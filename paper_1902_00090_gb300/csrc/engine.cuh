@@ -11,6 +11,23 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kMaxAug = 32;          // largest augmentation size k
 constexpr int kMaxRestart = 1024;
 
+// 16-byte packs: every thread of a streaming kernel owns one pack (VEC complex
+// numbers) of each work column; a CTA covers kBlock * VEC consecutive rows.
+template <typename T> struct PackOf;
+template <> struct PackOf<float> { using type = float4; static constexpr int VEC = 2; };
+template <> struct PackOf<double> { using type = double2; static constexpr int VEC = 1; };
+template <typename T> using pack_t = typename PackOf<T>::type;
+template <typename T> __host__ __device__ constexpr int vec_of() { return PackOf<T>::VEC; }
+template <typename T> __host__ __device__ constexpr long long chunk_rows() { return (long long)kBlock * PackOf<T>::VEC; }
+
+__device__ __forceinline__ void unpack(const float4& p, float2 (&v)[2]) {
+    v[0] = make_float2(p.x, p.y);
+    v[1] = make_float2(p.z, p.w);
+}
+__device__ __forceinline__ void unpack(const double2& p, double2 (&v)[1]) { v[0] = p; }
+__device__ __forceinline__ float4 mkpack(const float2 (&v)[2]) { return make_float4(v[0].x, v[0].y, v[1].x, v[1].y); }
+__device__ __forceinline__ double2 mkpack(const double2 (&v)[1]) { return v[0]; }
+
 // Solver context: device workspace (grow-only) and tuning.
 struct Context {
     int device = 0;
@@ -61,6 +78,7 @@ struct Context {
 struct SolvePtrs {
     int nx, ny;
     long long D;
+    long long ld;              // leading dimension of every D-long work column (D rounded up to a chunk)
     double kh2;
     const double* eps_d;
     const void* eps_lo;        // float* or double* (precision of the Krylov loop)
@@ -68,11 +86,11 @@ struct SolvePtrs {
     const void* coef_lo;       // float2* or double2*
     const double2* b;
     double2* x;
-    double2* r;                // FP64 residual
-    void* M;                   // [C | Q] basis, T2, column-major, ld = D
-    const void* V;             // predicted vectors in T2 (D x N), column-major
-    const double2* U;          // caller's predicted vectors (FP64)
-    double2* W;                // FP64 scratch for A V during set-up (aliases M)
+    double2* r;                // FP64 residual (ld, zero past D)
+    void* M;                   // [C | Q] basis, T2, column-major, leading dimension ld
+    void* V;                   // predicted vectors in T2 (ld x N), column-major
+    const double2* U;          // caller's predicted vectors (FP64, D x N)
+    double2* W;                // FP64 scratch for A V during set-up (ld x N, aliases M)
     void* w[2];                // T2 Arnoldi vectors (double buffered)
     double2* Rg;               // Givens-reduced Hessenberg, (m+1) x m, column-major
     double2* B;                // C^H A Q, kMaxAug x m

@@ -3,20 +3,22 @@
 //
 // Execution model: n independent solves advance in lock step, one kernel launch
 // per phase covering every CTA of every solve still running; CTAs of finished
-// solves return at once.  Each solve is cut into chunks of kBlock*RPT rows (one
-// CTA per chunk).  Reductions are deterministic: every CTA writes its partial
-// sums, and the last CTA of a solve to finish (atomic ticket, no waiting) adds
-// them in chunk order and takes the solve's scalar decisions (Givens rotation,
-// convergence) in FP64.
+// solves return at once.  Each solve is cut into chunks of kBlock * VEC rows
+// (one CTA per chunk, one 16-byte pack of VEC complex numbers per thread); all
+// work columns use the padded leading dimension ld (a whole number of chunks,
+// zero past D), so the streaming loops carry no bounds checks.  Reductions are
+// deterministic: every CTA writes its partial sums, and the last CTA of a solve
+// to finish (atomic ticket, no waiting) adds them in chunk order and takes the
+// solve's scalar decisions (Givens rotation, convergence) in FP64.
 //
 // One Arnoldi step j (Eq. S2 with one reorthogonalisation, the augmentation
 // block C treated as leading columns of the basis, so that the C^H A q_j block
 // of Eq. S7 comes out of the same projections):
-//   k_step    q_j = w_{j-1} / h_{j,j-1} (stored), w = A q_j          (stencil)
-//   k_dots    h  = [C Q_j]^H w, and ||w||                             (pass 1)
-//   k_update  w -= [C Q_j] h
-//   k_dots    h' = [C Q_j]^H w                                        (pass 2)
-//   k_update  w -= [C Q_j] h', h_{j+1,j} = ||w||, Givens rotation, |g_{j+1}|
+//   k_step      q_j = w_{j-1} / h_{j,j-1} (stored), w = A q_j        (stencil)
+//   k_dots_w    h  = [C Q_j]^H w, and ||w||                           (pass 1)
+//   k_update_w  w -= [C Q_j] h
+//   k_dots_w    h' = [C Q_j]^H w                                      (pass 2)
+//   k_update_w  w -= [C Q_j] h', h_{j+1,j} = ||w||, Givens rotation, |g_{j+1}|
 // Cycle start: r = b - A x in FP64; (augmented) c_r = C^H r, r <- r - C c_r.
 // Cycle end: y from the rotated Hessenberg, x_V = c_r - B y, z = R^-1 x_V,
 // x += V z + Q y (FP64).
@@ -29,10 +31,6 @@
 namespace ddg {
 
 // ---------------------------------------------------------------- helpers
-template <typename T> __device__ __forceinline__ c2_t<T> ld_as(const double2* p, long long i) {
-    return from_d2<c2_t<T>>(p[i]);
-}
-
 __device__ __forceinline__ double block_sum_d(double v, double* sm) {
     v = warp_sum_d(v);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -107,13 +105,40 @@ __device__ __forceinline__ void rotate(double c, double2 s, double2& u, double2&
     v = nv;
 }
 
-#define SOLVE_PROLOGUE()                                   \
-    const int s = a.blk_solve[blockIdx.x];                 \
-    SolveScal* S = a.S + s;                                \
-    const SolvePtrs& P = a.P[s];                           \
-    const int chunk = blockIdx.x - P.chunk0;               \
-    const long long row0 = (long long)chunk * (kBlock * RPT) + threadIdx.x;                  \
-    const double rows = (double)min((long long)(kBlock * RPT), P.D - (long long)chunk * (kBlock * RPT));
+template <typename T> __device__ __forceinline__ pack_t<T> zero_pack();
+template <> __device__ __forceinline__ float4 zero_pack<float>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ double2 zero_pack<double>() { return make_double2(0.0, 0.0); }
+
+// Sum of 8 complex values over the 32 lanes of a warp with 9 exchanges
+// (butterfly: each level halves the values a lane holds).  On return lane L
+// holds the total of value ((L>>4)&1)*4 + ((L>>3)&1)*2 + ((L>>2)&1).
+template <typename V> __device__ __forceinline__ V reduce8(const V (&x)[8], int lane) {
+    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+    V y4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        V keep = b16 ? x[i + 4] : x[i];
+        V send = b16 ? x[i] : x[i + 4];
+        y4[i] = cadd(keep, shfl_xor(send, 16));
+    }
+    V y2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        V keep = b8 ? y4[i + 2] : y4[i];
+        V send = b8 ? y4[i] : y4[i + 2];
+        y2[i] = cadd(keep, shfl_xor(send, 8));
+    }
+    V y1 = cadd(b4 ? y2[1] : y2[0], shfl_xor(b4 ? y2[0] : y2[1], 4));
+    y1 = cadd(y1, shfl_xor(y1, 2));
+    y1 = cadd(y1, shfl_xor(y1, 1));
+    return y1;
+}
+
+#define SOLVE_PROLOGUE()                                  \
+    const int s = a.blk_solve[blockIdx.x];                \
+    SolveScal* S = a.S + s;                               \
+    const SolvePtrs& P = a.P[s];                          \
+    const int chunk = blockIdx.x - P.chunk0;
 
 // ---------------------------------------------------------------- init
 __global__ void k_init(BatchArgs a, int n, int nreq) {
@@ -142,37 +167,40 @@ __global__ void k_init(BatchArgs a, int n, int nreq) {
 }
 
 // ---------------------------------------------------------------- cycle start
-// r = b - A x (FP64); ||r||, ||b||; convergence / cap decisions.
-template <int RPT>
+// r = b - A x (FP64, zero past D); ||r||, ||b||; convergence / cap decisions.
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_residual(BatchArgs a) {
+    constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     if (!S->active) return;
-    count_bytes(a, DDG_K_RESIDUAL, rows * (16.0 + 16.0 + 8.0 + 16.0));
-    __shared__ double sm[kWarps];
     const long long D = P.D;
+    const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
+    count_bytes(a, DDG_K_RESIDUAL, (double)min((long long)chunk_rows<T>(), D - (long long)chunk * chunk_rows<T>()) * 56.0);
+    __shared__ double sm[kWarps];
     const double2* __restrict__ x = P.x;
     double accr = 0.0, accb = 0.0;
     auto ld = [&](long long idx) { return x[idx]; };
 #pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-        long long e = row0 + (long long)q * kBlock;
+    for (int q = 0; q < VEC; ++q) {
+        const long long e = e0 + q;
+        double2 rv = make_double2(0.0, 0.0);
         if (e < D) {
             double2 ax = stencil(e, P.nx, P.ny, P.coef_d, P.kh2 * P.eps_d[e], ld);
             double2 bv = P.b[e];
-            double2 rv = csub(bv, ax);
-            P.r[e] = rv;
+            rv = csub(bv, ax);
             accr += cabs2(rv);
             accb += cabs2(bv);
         }
+        P.r[e] = rv;
     }
     double tr = block_sum_d(accr, sm);
     double tb = block_sum_d(accb, sm);
-    if (threadIdx.x == 0) P.part[chunk] = make_double2(tr, tb);
+    if (threadIdx.x == 0) P.part[(long long)chunk * a.KP] = make_double2(tr, tb);
     if (!arrive_last(P.ticket, P.nchunks)) return;
     if (threadIdx.x != 0) return;
     double rn2 = 0.0, nb2 = 0.0;
     for (int c = 0; c < P.nchunks; ++c) {
-        double2 t = __ldcg(P.part + c);
+        double2 t = __ldcg(P.part + (long long)c * a.KP);
         rn2 += t.x;
         nb2 += t.y;
     }
@@ -209,225 +237,69 @@ __global__ void __launch_bounds__(kBlock) k_residual(BatchArgs a) {
         S->in_cycle = 1;
         atomicAdd(a.counts, 1);
     }
-    // augmented: k_dots (mode 2) and k_update (mode 2) finish the set-up
+    // augmented solves: k_dots_r and k_update_r finish the cycle start
 }
 
-// ---------------------------------------------------------------- Arnoldi step: q_j, w = A q_j
-// Column j of Q is the previous (unnormalised) vector scaled by 1/h_{j,j-1}
-// (for j = 0: the cycle's start vector r scaled by 1/beta); w = A q_j uses the
-// same rounded values of q_j as the stored column.
-template <typename T, int RPT>
-__global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
+// c_r = C^H r (FP64 r, C in the Krylov precision), one warp reduction per column.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_dots_r(BatchArgs a) {
     using V = c2_t<T>;
-    SOLVE_PROLOGUE();
-    if (!S->in_cycle) return;
-    count_bytes(a, DDG_K_STEP, rows * ((j == 0 ? 16.0 : (double)sizeof(V)) + sizeof(T) + 2.0 * sizeof(V)));
-    const long long D = P.D;
-    const int N = S->N;
-    const double inv = 1.0 / S->hnorm;
-    V* __restrict__ q = reinterpret_cast<V*>(P.M) + (long long)(N + j) * D;
-    V* __restrict__ w = reinterpret_cast<V*>(P.w[j & 1]);
-    const T* eps = reinterpret_cast<const T*>(P.eps_lo);
-    const V* coef = reinterpret_cast<const V*>(P.coef_lo);
-    const T kh2 = (T)P.kh2;
-    if (j == 0) {
-        const double2* __restrict__ src = P.r;
-        auto ld = [&](long long idx) { return from_d2<V>(cscale(src[idx], inv)); };
-#pragma unroll
-        for (int t = 0; t < RPT; ++t) {
-            long long e = row0 + (long long)t * kBlock;
-            if (e < D) {
-                q[e] = ld(e);
-                w[e] = stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld);
-            }
-        }
-    } else {
-        const V* __restrict__ src = reinterpret_cast<const V*>(P.w[(j - 1) & 1]);
-        const T tinv = (T)inv;
-        auto ld = [&](long long idx) { return cscale(src[idx], tinv); };
-#pragma unroll
-        for (int t = 0; t < RPT; ++t) {
-            long long e = row0 + (long long)t * kBlock;
-            if (e < D) {
-                q[e] = ld(e);
-                w[e] = stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld);
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------- projections
-// out[k] = sum_e conj(M[k D + e]) v[e] for the columns k < K of one solve.
-//   mode 0: Arnoldi pass 1 (v = w, K = N + j + 1, also ||w||^2 -> anorm)
-//   mode 1: Arnoldi pass 2 (v = w, K = N + j + 1)
-//   mode 2: cycle start, c_r = C^H r (v = r in FP64, K = N)
-// TM: element type of M; TV: of v; TA: per-thread accumulator.
-template <typename TM, typename TV, typename TA, int RPT>
-__global__ void __launch_bounds__(kBlock) k_dots(BatchArgs a, int j, int mode) {
-    using VM = c2_t<TM>;
-    using VV = c2_t<TV>;
-    using VA = c2_t<TA>;
+    constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     const int N = S->N;
-    if (mode == 2) {
-        if (!S->pending || S->in_cycle || N == 0) return;
-    } else if (!S->in_cycle) {
-        return;
-    }
-    constexpr int TILE = 64;
-    __shared__ VA red[kWarps][TILE];
-    const long long D = P.D;
-    const int K = (mode == 2) ? N : N + j + 1;
-    const int Ktot = K + (mode == 0 ? 1 : 0);
-    count_bytes(a, mode == 2 ? DDG_K_RESIDUAL : DDG_K_DOTS, rows * ((double)K * sizeof(VM) + sizeof(VV)));
-    const VV* __restrict__ v = (mode == 2) ? reinterpret_cast<const VV*>(P.r)
-                                           : reinterpret_cast<const VV*>(P.w[j & 1]);
-    const VM* __restrict__ M = reinterpret_cast<const VM*>(P.M);
-    VA vr[RPT];
-    bool ok[RPT];
+    if (!S->pending || S->in_cycle || N == 0) return;
+    const long long ld = P.ld;
+    const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
+    count_bytes(a, DDG_K_RESIDUAL, (double)chunk_rows<T>() * ((double)N * sizeof(V) + 16.0));
+    const V* __restrict__ C = reinterpret_cast<const V*>(P.M);
+    double2 rv[VEC];
 #pragma unroll
-    for (int t = 0; t < RPT; ++t) {
-        long long e = row0 + (long long)t * kBlock;
-        ok[t] = e < D;
-        VV x = ok[t] ? v[e] : VV{0, 0};
-        vr[t] = mk((TA)x.x, (TA)x.y);
-    }
+    for (int q = 0; q < VEC; ++q) rv[q] = P.r[e0 + q];
+    __shared__ double2 red[kWarps][kMaxAug];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int n = 0; n < N; ++n) {
+        double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) cfmac(acc, to_d2(C[(long long)n * ld + e0 + q]), rv[q]);
+        acc = warp_sum(acc);
+        if (lane == 0) red[wid][n] = acc;
+    }
+    __syncthreads();
     double2* part = P.part + (long long)chunk * a.KP;
-    for (int k0 = 0; k0 < Ktot; k0 += TILE) {
-        const int kt = min(TILE, Ktot - k0);
-        int kk = 0;
-        for (; kk + 4 <= kt && k0 + kk + 4 <= K; kk += 4) {
-            VA acc[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u] = mk((TA)0, (TA)0);
-#pragma unroll
-            for (int t = 0; t < RPT; ++t) {
-                if (ok[t]) {
-                    long long e = row0 + (long long)t * kBlock;
-                    VM m4[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) m4[u] = M[(long long)(k0 + kk + u) * D + e];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) cfmac(acc[u], mk((TA)m4[u].x, (TA)m4[u].y), vr[t]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u] = warp_sum(acc[u]);
-            if (lane == 0) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) red[wid][kk + u] = acc[u];
-            }
-        }
-        for (; kk < kt; ++kk) {
-            const int k = k0 + kk;
-            VA acc = mk((TA)0, (TA)0);
-            if (k < K) {
-#pragma unroll
-                for (int t = 0; t < RPT; ++t)
-                    if (ok[t]) {
-                        VM mv = M[(long long)k * D + row0 + (long long)t * kBlock];
-                        cfmac(acc, mk((TA)mv.x, (TA)mv.y), vr[t]);
-                    }
-            } else {
-#pragma unroll
-                for (int t = 0; t < RPT; ++t) acc.x += vr[t].x * vr[t].x + vr[t].y * vr[t].y;
-            }
-            acc = warp_sum(acc);
-            if (lane == 0) red[wid][kk] = acc;
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < kt; t += kBlock) {
-            double2 sum = make_double2(0.0, 0.0);
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) sum = cadd(sum, make_double2((double)red[w][t].x, (double)red[w][t].y));
-            part[k0 + t] = sum;
-        }
-        __syncthreads();
+    for (int n = threadIdx.x; n < N; n += kBlock) {
+        double2 sum = make_double2(0.0, 0.0);
+        for (int w = 0; w < kWarps; ++w) sum = cadd(sum, red[w][n]);
+        part[n] = sum;
     }
     if (!arrive_last(P.ticket, P.nchunks)) return;
-    for (int k = threadIdx.x; k < Ktot; k += kBlock) {
+    for (int n = threadIdx.x; n < N; n += kBlock) {
         double2 sum = make_double2(0.0, 0.0);
-        for (int c = 0; c < P.nchunks; ++c) sum = cadd(sum, __ldcg(P.part + (long long)c * a.KP + k));
-        if (k < K) {
-            P.hp[k] = sum;
-            if (mode == 0) P.hsum[k] = sum;
-            else if (mode == 1) P.hsum[k] = cadd(P.hsum[k], sum);
-            else P.cr[k] = sum;
-        } else {
-            S->anorm = sqrt(sum.x);
-        }
+        for (int c = 0; c < P.nchunks; ++c) sum = cadd(sum, __ldcg(P.part + (long long)c * a.KP + n));
+        P.cr[n] = sum;
     }
 }
 
-// v -= M[:, :K] hp.
-//   mode 0: Arnoldi pass 1 (v = w)
-//   mode 1: Arnoldi pass 2 (v = w), then ||w||, Hessenberg column, Givens, stop test
-//   mode 2: cycle start (v = r, K = N): r~ = r - C c_r, beta = ||r~||
-template <typename TM, typename TV, int RPT>
-__global__ void __launch_bounds__(kBlock) k_update(BatchArgs a, int j, int mode) {
-    using VM = c2_t<TM>;
-    using VV = c2_t<TV>;
+// r~ = r - C c_r (FP64), beta = ||r~||: start of the Krylov loop on A~ = P_perp A.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_update_r(BatchArgs a) {
+    using V = c2_t<T>;
+    constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     const int N = S->N;
-    if (mode == 2) {
-        if (!S->pending || S->in_cycle || N == 0) return;
-    } else if (!S->in_cycle) {
-        return;
-    }
+    if (!S->pending || S->in_cycle || N == 0) return;
+    const long long ld = P.ld;
+    const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
+    count_bytes(a, DDG_K_RESIDUAL, (double)chunk_rows<T>() * ((double)N * sizeof(V) + 32.0));
+    const V* __restrict__ C = reinterpret_cast<const V*>(P.M);
     __shared__ double sm[kWarps];
-    const long long D = P.D;
-    const int K = (mode == 2) ? N : N + j + 1;
-    count_bytes(a, mode == 2 ? DDG_K_RESIDUAL : DDG_K_UPDATE, rows * ((double)K * sizeof(VM) + 2.0 * sizeof(VV)));
-    VV* __restrict__ v = (mode == 2) ? reinterpret_cast<VV*>(P.r) : reinterpret_cast<VV*>(P.w[j & 1]);
-    const VM* __restrict__ M = reinterpret_cast<const VM*>(P.M);
-    const double2* __restrict__ hp = P.hp;
-    VV vr[RPT];
-    bool ok[RPT];
-#pragma unroll
-    for (int t = 0; t < RPT; ++t) {
-        long long e = row0 + (long long)t * kBlock;
-        ok[t] = e < D;
-        vr[t] = ok[t] ? v[e] : VV{0, 0};
-    }
-    int k = 0;
-    for (; k + 4 <= K; k += 4) {
-        VV c4[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            double2 h = hp[k + u];
-            c4[u] = mk((TV)h.x, (TV)h.y);
-        }
-#pragma unroll
-        for (int t = 0; t < RPT; ++t) {
-            if (ok[t]) {
-                long long e = row0 + (long long)t * kBlock;
-                VM m4[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) m4[u] = M[(long long)(k + u) * D + e];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) cfms(vr[t], mk((TV)m4[u].x, (TV)m4[u].y), c4[u]);
-            }
-        }
-    }
-    for (; k < K; ++k) {
-        double2 h = hp[k];
-        VV c = mk((TV)h.x, (TV)h.y);
-#pragma unroll
-        for (int t = 0; t < RPT; ++t)
-            if (ok[t]) {
-                VM mv = M[(long long)k * D + row0 + (long long)t * kBlock];
-                cfms(vr[t], mk((TV)mv.x, (TV)mv.y), c);
-            }
-    }
     double acc = 0.0;
 #pragma unroll
-    for (int t = 0; t < RPT; ++t)
-        if (ok[t]) {
-            v[row0 + (long long)t * kBlock] = vr[t];
-            acc += cabs2(vr[t]);
-        }
-    if (mode == 0) return;
+    for (int q = 0; q < VEC; ++q) {
+        double2 v = P.r[e0 + q];
+        for (int n = 0; n < N; ++n) cfms(v, to_d2(C[(long long)n * ld + e0 + q]), P.cr[n]);
+        P.r[e0 + q] = v;
+        acc += cabs2(v);
+    }
     double tot = block_sum_d(acc, sm);
     if (threadIdx.x == 0) P.part[(long long)chunk * a.KP] = make_double2(tot, 0.0);
     if (!arrive_last(P.ticket, P.nchunks)) return;
@@ -435,25 +307,218 @@ __global__ void __launch_bounds__(kBlock) k_update(BatchArgs a, int j, int mode)
     double n2 = 0.0;
     for (int c = 0; c < P.nchunks; ++c) n2 += __ldcg(P.part + (long long)c * a.KP).x;
     const double nrm = sqrt(n2);
-    if (mode == 2) {
-        // b~ = P_perp r: the Krylov loop starts from r~ / ||r~||
-        S->beta = nrm;
-        if (S->cycles == 1) S->first_res = nrm / S->nb;
-        S->k = 0;
-        if (nrm <= 1e-14 * S->rn) {
-            // r lies in span(A V): the V step alone solves the residual equation
-            S->breakdown = 1;
-            return;
-        }
-        S->hnorm = nrm;
-        P.g[0] = make_double2(nrm, 0.0);
-        S->target = fmax(a.tol * S->nb, a.eta * nrm);
-        S->in_cycle = 1;
-        atomicAdd(a.counts, 1);
+    S->beta = nrm;
+    if (S->cycles == 1) S->first_res = nrm / S->nb;
+    S->k = 0;
+    if (nrm <= 1e-14 * S->rn) {
+        // r lies in span(A V): the V step alone solves the residual equation
+        S->breakdown = 1;
         return;
     }
-    // mode 1: column j of H (rows 0..j from hsum[N..N+j], row j+1 = ||w||),
-    // column j of B = C^H A q_j (hsum[0..N)); Givens update of column j.
+    S->hnorm = nrm;
+    P.g[0] = make_double2(nrm, 0.0);
+    S->target = fmax(a.tol * S->nb, a.eta * nrm);
+    S->in_cycle = 1;
+    atomicAdd(a.counts, 1);
+}
+
+// ---------------------------------------------------------------- Arnoldi step: q_j, w = A q_j
+// Column j of Q is the previous (unnormalised) vector scaled by 1/h_{j,j-1}
+// (for j = 0: the cycle's start vector r scaled by 1/beta); w = A q_j uses the
+// same rounded values of q_j as the stored column.  Rows past D are zero.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
+    using V = c2_t<T>;
+    using PK = pack_t<T>;
+    constexpr int VEC = vec_of<T>();
+    SOLVE_PROLOGUE();
+    if (!S->in_cycle) return;
+    const long long D = P.D, ld = P.ld;
+    const int N = S->N;
+    count_bytes(a, DDG_K_STEP, (double)chunk_rows<T>() * ((j == 0 ? 16.0 : (double)sizeof(V)) + sizeof(T) + 2.0 * sizeof(V)));
+    const double inv = 1.0 / S->hnorm;
+    const long long p0 = (long long)chunk * kBlock + threadIdx.x;
+    const long long e0 = p0 * VEC;
+    PK* __restrict__ q = reinterpret_cast<PK*>(reinterpret_cast<V*>(P.M) + (long long)(N + j) * ld);
+    PK* __restrict__ w = reinterpret_cast<PK*>(P.w[j & 1]);
+    const T* eps = reinterpret_cast<const T*>(P.eps_lo);
+    const V* coef = reinterpret_cast<const V*>(P.coef_lo);
+    const T kh2 = (T)P.kh2;
+    V qv[VEC], wv[VEC];
+    if (j == 0) {
+        const double2* __restrict__ src = P.r;
+        auto ld_ = [&](long long idx) { return from_d2<V>(cscale(src[idx], inv)); };
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) {
+            const long long e = e0 + i;
+            if (e < D) {
+                qv[i] = ld_(e);
+                wv[i] = stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld_);
+            } else {
+                qv[i] = mk((T)0, (T)0);
+                wv[i] = mk((T)0, (T)0);
+            }
+        }
+    } else {
+        const V* __restrict__ src = reinterpret_cast<const V*>(P.w[(j - 1) & 1]);
+        const T tinv = (T)inv;
+        auto ld_ = [&](long long idx) { return cscale(src[idx], tinv); };
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) {
+            const long long e = e0 + i;
+            if (e < D) {
+                qv[i] = ld_(e);
+                wv[i] = stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld_);
+            } else {
+                qv[i] = mk((T)0, (T)0);
+                wv[i] = mk((T)0, (T)0);
+            }
+        }
+    }
+    q[p0] = mkpack(qv);
+    w[p0] = mkpack(wv);
+}
+
+// ---------------------------------------------------------------- Gram-Schmidt projections
+// h[k] = sum_e conj(M[k ld + e]) w[e] for the columns k < K = N + j + 1 of one
+// solve (mode 0: pass 1, also ||w||^2 -> anorm; mode 1: pass 2).  Columns are
+// read in batches of 8 (8 independent 16-byte loads per thread in flight).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_dots_w(BatchArgs a, int j, int mode) {
+    using V = c2_t<T>;
+    using PK = pack_t<T>;
+    constexpr int VEC = vec_of<T>();
+    SOLVE_PROLOGUE();
+    if (!S->in_cycle) return;
+    const int N = S->N;
+    const int K = N + j + 1;
+    count_bytes(a, DDG_K_DOTS, (double)chunk_rows<T>() * ((double)K + 1.0) * sizeof(V));
+    const long long ldp = P.ld / VEC;
+    const long long p0 = (long long)chunk * kBlock + threadIdx.x;
+    const PK* __restrict__ Mp = reinterpret_cast<const PK*>(P.M);
+    V v[VEC];
+    unpack(reinterpret_cast<const PK*>(P.w[j & 1])[p0], v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int vidx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    __shared__ V red[kWarps][64];
+    __shared__ double sm[kWarps];
+    double2* part = P.part + (long long)chunk * a.KP;
+    for (int k0 = 0; k0 < K; k0 += 64) {
+        const int kt = min(64, K - k0);
+        for (int kk = 0; kk < kt; kk += 8) {
+            const int nv = min(8, kt - kk);
+            const PK* col = Mp + (long long)(k0 + kk) * ldp + p0;
+            PK m[8];
+            if (nv == 8) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) m[u] = col[(long long)u * ldp];
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) m[u] = (u < nv) ? col[(long long)u * ldp] : zero_pack<T>();
+            }
+            V acc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                V mv[VEC];
+                unpack(m[u], mv);
+                acc[u] = mk((T)0, (T)0);
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) cfmac(acc[u], mv[i], v[i]);
+            }
+            V r = reduce8(acc, lane);
+            if ((lane & 3) == 0 && vidx < nv) red[wid][kk + vidx] = r;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < kt; t += kBlock) {
+            double2 sum = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) sum = cadd(sum, to_d2(red[w][t]));
+            part[k0 + t] = sum;
+        }
+        __syncthreads();
+    }
+    if (mode == 0) {
+        double nn = 0.0;
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) nn += cabs2(v[i]);
+        nn = block_sum_d(nn, sm);
+        if (threadIdx.x == 0) part[K] = make_double2(nn, 0.0);
+    }
+    if (!arrive_last(P.ticket, P.nchunks)) return;
+    const int Ktot = K + (mode == 0 ? 1 : 0);
+    for (int k = threadIdx.x; k < Ktot; k += kBlock) {
+        double2 sum = make_double2(0.0, 0.0);
+        for (int c = 0; c < P.nchunks; ++c) sum = cadd(sum, __ldcg(P.part + (long long)c * a.KP + k));
+        if (k < K) {
+            P.hp[k] = sum;
+            if (mode == 0) P.hsum[k] = sum;
+            else P.hsum[k] = cadd(P.hsum[k], sum);
+        } else {
+            S->anorm = sqrt(sum.x);
+        }
+    }
+}
+
+// w -= [C Q_j] h (coefficients staged in shared memory).
+//   mode 0: Arnoldi pass 1
+//   mode 1: Arnoldi pass 2, then ||w||, Hessenberg column, Givens, stop test
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_update_w(BatchArgs a, int j, int mode) {
+    using V = c2_t<T>;
+    using PK = pack_t<T>;
+    constexpr int VEC = vec_of<T>();
+    SOLVE_PROLOGUE();
+    if (!S->in_cycle) return;
+    const int N = S->N;
+    const int K = N + j + 1;
+    count_bytes(a, DDG_K_UPDATE, (double)chunk_rows<T>() * ((double)K + 2.0) * sizeof(V));
+    extern __shared__ unsigned char smraw[];
+    V* hs = reinterpret_cast<V*>(smraw);
+    __shared__ double sm[kWarps];
+    for (int t = threadIdx.x; t < K; t += kBlock) hs[t] = from_d2<V>(P.hp[t]);
+    __syncthreads();
+    const long long ldp = P.ld / VEC;
+    const long long p0 = (long long)chunk * kBlock + threadIdx.x;
+    const PK* __restrict__ Mp = reinterpret_cast<const PK*>(P.M);
+    PK* __restrict__ wp = reinterpret_cast<PK*>(P.w[j & 1]);
+    V v[VEC];
+    unpack(wp[p0], v);
+    int k = 0;
+    for (; k + 8 <= K; k += 8) {
+        const PK* col = Mp + (long long)k * ldp + p0;
+        PK m[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) m[u] = col[(long long)u * ldp];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            V mv[VEC];
+            unpack(m[u], mv);
+            const V c = hs[k + u];
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) cfms(v[i], mv[i], c);
+        }
+    }
+    for (; k < K; ++k) {
+        V mv[VEC];
+        unpack(Mp[(long long)k * ldp + p0], mv);
+        const V c = hs[k];
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) cfms(v[i], mv[i], c);
+    }
+    wp[p0] = mkpack(v);
+    if (mode == 0) return;
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) acc += cabs2(v[i]);
+    double tot = block_sum_d(acc, sm);
+    if (threadIdx.x == 0) P.part[(long long)chunk * a.KP] = make_double2(tot, 0.0);
+    if (!arrive_last(P.ticket, P.nchunks)) return;
+    if (threadIdx.x != 0) return;
+    double n2 = 0.0;
+    for (int c = 0; c < P.nchunks; ++c) n2 += __ldcg(P.part + (long long)c * a.KP).x;
+    const double nrm = sqrt(n2);
+    // column j of H (rows 0..j from hsum[N..N+j], row j+1 = ||w||), column j of
+    // B = C^H A q_j (hsum[0..N)); Givens update of column j.
     const int m = a.m, ldh = m + 1;
     for (int n = 0; n < N; ++n) P.B[(long long)j * a.nmax + n] = P.hsum[n];
     double2* col = P.Rg + (long long)j * ldh;
@@ -523,69 +588,75 @@ __global__ void __launch_bounds__(128) k_backsub(BatchArgs a) {
 }
 
 // x += V z + Q y in FP64 (V, Q in the Krylov precision).
-template <typename T, int RPT>
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_update_x(BatchArgs a) {
     using V = c2_t<T>;
+    constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     if (!S->pending) return;
-    const long long D = P.D;
+    const long long D = P.D, ld = P.ld;
     const int N = S->N, k = S->k;
-    count_bytes(a, DDG_K_CYCLE_END, rows * ((double)(N + k) * sizeof(V) + 32.0));
+    count_bytes(a, DDG_K_CYCLE_END, (double)chunk_rows<T>() * ((double)(N + k) * sizeof(V) + 32.0));
     const V* __restrict__ Vv = reinterpret_cast<const V*>(P.V);
-    const V* __restrict__ Q = reinterpret_cast<const V*>(P.M) + (long long)N * D;
+    const V* __restrict__ Q = reinterpret_cast<const V*>(P.M) + (long long)N * ld;
     const double2* __restrict__ cy = P.coefy;
+    const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
 #pragma unroll
-    for (int t = 0; t < RPT; ++t) {
-        long long e = row0 + (long long)t * kBlock;
+    for (int q = 0; q < VEC; ++q) {
+        const long long e = e0 + q;
         if (e >= D) continue;
         double2 acc = make_double2(0.0, 0.0);
-        for (int n = 0; n < N; ++n) cfma(acc, to_d2(Vv[(long long)n * D + e]), cy[n]);
-        for (int i = 0; i < k; ++i) cfma(acc, to_d2(Q[(long long)i * D + e]), cy[N + i]);
+        for (int n = 0; n < N; ++n) cfma(acc, to_d2(Vv[(long long)n * ld + e]), cy[n]);
+        for (int i = 0; i < k; ++i) cfma(acc, to_d2(Q[(long long)i * ld + e]), cy[N + i]);
         P.x[e] = cadd(P.x[e], acc);
     }
 }
 
 // b = 0: the solution is x = 0 whatever x0 was.
-template <int RPT>
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_finalize(BatchArgs a) {
+    constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     if (S->nb != 0.0) return;
+    const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
 #pragma unroll
-    for (int t = 0; t < RPT; ++t) {
-        long long e = row0 + (long long)t * kBlock;
-        if (e < P.D) P.x[e] = make_double2(0.0, 0.0);
-    }
+    for (int q = 0; q < VEC; ++q)
+        if (e0 + q < P.D) P.x[e0 + q] = make_double2(0.0, 0.0);
 }
 
 // ---------------------------------------------------------------- augmentation set-up
-// W = A U (FP64), column by column.
-template <int RPT>
+// W = A U (FP64, zero past D), column by column.
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_aug_av(BatchArgs a) {
+    constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     const int N = S->N;
-    const long long D = P.D;
+    const long long D = P.D, ld = P.ld;
+    const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
     for (int n = 0; n < N; ++n) {
         const double2* __restrict__ u = P.U + (long long)n * D;
-        auto ld = [&](long long idx) { return u[idx]; };
+        auto ldu = [&](long long idx) { return u[idx]; };
 #pragma unroll
-        for (int t = 0; t < RPT; ++t) {
-            long long e = row0 + (long long)t * kBlock;
-            if (e < D) P.W[(long long)n * D + e] = stencil(e, P.nx, P.ny, P.coef_d, P.kh2 * P.eps_d[e], ld);
+        for (int q = 0; q < VEC; ++q) {
+            const long long e = e0 + q;
+            P.W[(long long)n * ld + e] =
+                e < D ? stencil(e, P.nx, P.ny, P.coef_d, P.kh2 * P.eps_d[e], ldu) : make_double2(0.0, 0.0);
         }
     }
 }
 
 // Gram matrix G = W^H W (FP64) and, in the last CTA, its Cholesky factor
-// G = L L^H and the inverse of R_pass = L^H (upper triangular).
-// pass 0 writes R1^-1 to Rtmp; pass 1 writes R2^-1 to Rinv.
-// A non-positive or relatively tiny pivot marks the solve as rank deficient:
-// it then runs as plain GMRES (N = 0, fallback = 1).
-template <int RPT>
+// G = R^H R and R^-1 (upper triangular).  pass 0 writes R1^-1 to Rtmp; pass 1
+// writes R2^-1 to Rinv.  A non-positive or relatively tiny pivot marks the
+// solve as rank deficient: it then runs as plain GMRES (N = 0, fallback = 1).
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_aug_gram(BatchArgs a, int pass) {
+    constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     const int N = S->N;
     if (N == 0) return;
-    const long long D = P.D;
+    const long long ld = P.ld;
+    const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
     __shared__ double2 red[kWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double2* part = P.part + (long long)chunk * a.KP;
@@ -593,10 +664,7 @@ __global__ void __launch_bounds__(kBlock) k_aug_gram(BatchArgs a, int pass) {
         for (int q = p; q < N; ++q) {
             double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
-            for (int t = 0; t < RPT; ++t) {
-                long long e = row0 + (long long)t * kBlock;
-                if (e < D) cfmac(acc, P.W[(long long)p * D + e], P.W[(long long)q * D + e]);
-            }
+            for (int t = 0; t < VEC; ++t) cfmac(acc, P.W[(long long)p * ld + e0 + t], P.W[(long long)q * ld + e0 + t]);
             acc = warp_sum(acc);
             __syncthreads();
             if (lane == 0) red[wid] = acc;
@@ -644,8 +712,8 @@ __global__ void __launch_bounds__(kBlock) k_aug_gram(BatchArgs a, int pass) {
     double2* Ri = pass == 0 ? P.Rtmp : P.Rinv;
     for (int q = 0; q < N; ++q) {
         for (int p = N - 1; p >= 0; --p) {
-            double2 t = make_double2(p == q ? 1.0 : 0.0, 0.0);
             if (p > q) { Ri[q * N + p] = make_double2(0.0, 0.0); continue; }
+            double2 t = make_double2(p == q ? 1.0 : 0.0, 0.0);
             for (int l = p + 1; l <= q; ++l) t = csub(t, cmul(G[l * N + p], Ri[q * N + l]));
             Ri[q * N + p] = cdiv(t, G[p * N + p]);
         }
@@ -669,44 +737,45 @@ __global__ void k_aug_rinv(BatchArgs a, int n) {
 }
 
 // W <- W R_pass^-1 row by row (in place, columns from the last down).
-template <int RPT>
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_aug_tri(BatchArgs a, int pass) {
+    constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     const int N = S->N;
     if (N == 0) return;
-    const long long D = P.D;
+    const long long ld = P.ld;
     const double2* Ri = pass == 0 ? P.Rtmp : P.Rinv;
+    const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
 #pragma unroll
-    for (int t = 0; t < RPT; ++t) {
-        long long e = row0 + (long long)t * kBlock;
-        if (e >= D) continue;
+    for (int t = 0; t < VEC; ++t) {
+        const long long e = e0 + t;
         for (int q = N - 1; q >= 0; --q) {
             double2 acc = make_double2(0.0, 0.0);
-            for (int p = 0; p <= q; ++p) cfma(acc, P.W[(long long)p * D + e], Ri[q * N + p]);
-            P.W[(long long)q * D + e] = acc;
+            for (int p = 0; p <= q; ++p) cfma(acc, P.W[(long long)p * ld + e], Ri[q * N + p]);
+            P.W[(long long)q * ld + e] = acc;
         }
     }
 }
 
-// C (Krylov precision) and V (Krylov precision) from W and U.
-template <typename T, int RPT>
+// C and V in the Krylov precision (leading dimension ld, zero past D).
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_aug_store(BatchArgs a) {
     using V = c2_t<T>;
+    constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     const int N = S->N;
-    const long long D = P.D;
+    const long long D = P.D, ld = P.ld;
     V* C = reinterpret_cast<V*>(P.M);
-    V* Vl = const_cast<V*>(reinterpret_cast<const V*>(P.V));
+    V* Vl = reinterpret_cast<V*>(P.V);
+    const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
     for (int n = 0; n < N; ++n)
 #pragma unroll
-        for (int t = 0; t < RPT; ++t) {
-            long long e = row0 + (long long)t * kBlock;
-            if (e >= D) continue;
-            C[(long long)n * D + e] = from_d2<V>(P.W[(long long)n * D + e]);
-            Vl[(long long)n * D + e] = from_d2<V>(P.U[(long long)n * D + e]);
+        for (int t = 0; t < VEC; ++t) {
+            const long long e = e0 + t;
+            C[(long long)n * ld + e] = from_d2<V>(P.W[(long long)n * ld + e]);
+            Vl[(long long)n * ld + e] = e < D ? from_d2<V>(P.U[(long long)n * D + e]) : mk((T)0, (T)0);
         }
 }
-
 
 // ---------------------------------------------------------------- host driver
 static size_t align_up(size_t v, size_t al = 256) { return (v + al - 1) / al * al; }
@@ -722,19 +791,20 @@ struct Carver {
     }
 };
 
-template <typename T, int RPT>
-static ddg_status run_batch_t(Context* ctx, int n, const ddg_op* const* A, const double* const* b,
-                              double* const* x, const double* const* U, int Nreq, double tol, int m,
-                              int maxit, double eta, ddg_info* info, cudaStream_t st) {
+template <typename T>
+static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const double* const* b, double* const* x,
+                            const double* const* U, int Nreq, double tol, int m, int maxit, double eta,
+                            ddg_info* info, cudaStream_t st) {
     using V = c2_t<T>;
-    const long long RPB = (long long)kBlock * RPT;
+    const long long CH = chunk_rows<T>();
     int KP = std::max(kMaxAug + m + 2, Nreq * Nreq);
     KP = (KP + 1) & ~1;
     std::vector<SolvePtrs> hp(n);
     long long total_ctas = 0;
     for (int s = 0; s < n; ++s) {
-        hp[s].nchunks = (int)((A[s]->D + RPB - 1) / RPB);
+        hp[s].nchunks = (int)((A[s]->D + CH - 1) / CH);
         hp[s].chunk0 = (int)total_ctas;
+        hp[s].ld = (long long)hp[s].nchunks * CH;
         total_ctas += hp[s].nchunks;
     }
     // Two passes over the same layout: size it, then carve the workspace.
@@ -742,22 +812,21 @@ static ddg_status run_batch_t(Context* ctx, int n, const ddg_op* const* A, const
         Carver c{base};
         for (int s = 0; s < n; ++s) {
             const ddg_op* op = A[s];
-            const long long D = op->D;
             SolvePtrs& P = hp[s];
-            size_t mbytes = sizeof(V) * (size_t)D * (size_t)(Nreq + m + 1);
+            const long long ld = P.ld;
+            size_t mbytes = sizeof(V) * (size_t)ld * (size_t)(Nreq + m + 1);
             size_t woff = 0;
             if (Nreq > 0 && sizeof(T) == 4) {
-                woff = align_up(sizeof(V) * (size_t)D * Nreq);
-                mbytes = std::max(mbytes, woff + sizeof(double2) * (size_t)D * Nreq);
+                woff = align_up(sizeof(V) * (size_t)ld * Nreq);
+                mbytes = std::max(mbytes, woff + sizeof(double2) * (size_t)ld * Nreq);
             }
             char* M = c.take<char>(mbytes);
             P.M = M;
             P.W = (Nreq > 0) ? reinterpret_cast<double2*>(M ? M + woff : nullptr) : nullptr;
-            P.w[0] = c.take<V>(D);
-            P.w[1] = c.take<V>(D);
-            P.r = c.take<double2>(D);
-            if (Nreq > 0 && sizeof(T) == 4) P.V = c.take<V>((size_t)D * Nreq);
-            else P.V = (Nreq > 0) ? (const void*)U[s] : nullptr;
+            P.w[0] = c.take<V>(ld);
+            P.w[1] = c.take<V>(ld);
+            P.r = c.take<double2>(ld);
+            P.V = (Nreq > 0) ? (void*)c.take<V>((size_t)ld * Nreq) : nullptr;
             P.Rg = c.take<double2>((size_t)(m + 1) * m);
             P.B = c.take<double2>((size_t)kMaxAug * m);
             P.cs = c.take<double>(m);
@@ -773,7 +842,7 @@ static ddg_status run_batch_t(Context* ctx, int n, const ddg_op* const* A, const
             P.ticket = c.take<unsigned>(1);
             P.nx = op->nx;
             P.ny = op->ny;
-            P.D = D;
+            P.D = op->D;
             P.kh2 = op->kh * op->kh;
             P.eps_d = op->eps_d;
             P.coef_d = op->coef_d;
@@ -815,25 +884,25 @@ static ddg_status run_batch_t(Context* ctx, int n, const ddg_op* const* A, const
     DDG_CHECK_CUDA(cudaMemcpyAsync(d_blk, hblk.data(), sizeof(int) * total_ctas, cudaMemcpyHostToDevice, st));
 
     const unsigned G = (unsigned)total_ctas;
+    const size_t upd_smem = sizeof(V) * (size_t)(Nreq + m + 1);
     DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_init<<<(n + 127) / 128, 128, 0, st>>>(args, n, Nreq); }));
     if (Nreq > 0) {
-        DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_av<RPT><<<G, kBlock, 0, st>>>(args); }));
+        DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_av<T><<<G, kBlock, 0, st>>>(args); }));
         for (int pass = 0; pass < 2; ++pass) {
-            DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_gram<RPT><<<G, kBlock, 0, st>>>(args, pass); }));
-            DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_tri<RPT><<<G, kBlock, 0, st>>>(args, pass); }));
+            DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_gram<T><<<G, kBlock, 0, st>>>(args, pass); }));
+            DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_tri<T><<<G, kBlock, 0, st>>>(args, pass); }));
         }
         DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_rinv<<<(n + 63) / 64, 64, 0, st>>>(args, n); }));
-        if (sizeof(T) == 4)
-            DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_store<T, RPT><<<G, kBlock, 0, st>>>(args); }));
+        DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_store<T><<<G, kBlock, 0, st>>>(args); }));
     }
     int* hc = ctx->host_counts;
     const size_t bs_smem = sizeof(double2) * (2 * (size_t)m + kMaxAug);
     for (long long cycle = 0; cycle <= (long long)maxit + 1; ++cycle) {
         DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 4 * sizeof(int), st));
-        DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_residual<RPT><<<G, kBlock, 0, st>>>(args); }));
+        DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_residual<T><<<G, kBlock, 0, st>>>(args); }));
         if (Nreq > 0) {
-            DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_dots<T, double, double, RPT><<<G, kBlock, 0, st>>>(args, 0, 2); }));
-            DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_update<T, double, RPT><<<G, kBlock, 0, st>>>(args, 0, 2); }));
+            DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_dots_r<T><<<G, kBlock, 0, st>>>(args); }));
+            DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_update_r<T><<<G, kBlock, 0, st>>>(args); }));
         }
         DDG_CHECK_CUDA(cudaMemcpyAsync(hc, args.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DDG_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -841,11 +910,11 @@ static ddg_status run_batch_t(Context* ctx, int n, const ddg_op* const* A, const
         if (hc[0] > 0) {
             int polled = 0;
             for (int j = 0; j < m; ++j) {
-                DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_step<T, RPT><<<G, kBlock, 0, st>>>(args, j); }));
-                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots<T, T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 0); }));
-                DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update<T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 0); }));
-                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots<T, T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 1); }));
-                DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update<T, T, RPT><<<G, kBlock, 0, st>>>(args, j, 1); }));
+                DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_step<T><<<G, kBlock, 0, st>>>(args, j); }));
+                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots_w<T><<<G, kBlock, 0, st>>>(args, j, 0); }));
+                DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T><<<G, kBlock, upd_smem, st>>>(args, j, 0); }));
+                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots_w<T><<<G, kBlock, 0, st>>>(args, j, 1); }));
+                DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T><<<G, kBlock, upd_smem, st>>>(args, j, 1); }));
                 if ((j + 1) % ctx->poll_every == 0 && j + 1 < m) {
                     const int slot = polled & 1;
                     DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 2 + slot, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -859,9 +928,9 @@ static ddg_status run_batch_t(Context* ctx, int n, const ddg_op* const* A, const
             }
         }
         DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_backsub<<<n, 128, bs_smem, st>>>(args); }));
-        DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_update_x<T, RPT><<<G, kBlock, 0, st>>>(args); }));
+        DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_update_x<T><<<G, kBlock, 0, st>>>(args); }));
     }
-    DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_finalize<RPT><<<G, kBlock, 0, st>>>(args); }));
+    DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_finalize<T><<<G, kBlock, 0, st>>>(args); }));
     std::vector<SolveScal> hs(n);
     DDG_CHECK_CUDA(cudaMemcpyAsync(hs.data(), args.S, sizeof(SolveScal) * n, cudaMemcpyDeviceToHost, st));
     DDG_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -880,21 +949,6 @@ static ddg_status run_batch_t(Context* ctx, int n, const ddg_op* const* A, const
         }
     }
     return all ? DDG_OK : DDG_ENOCONV;
-}
-
-template <typename T>
-static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const double* const* b,
-                            double* const* x, const double* const* U, int Nreq, double tol, int m, int maxit,
-                            double eta, ddg_info* info, cudaStream_t st) {
-    long long c4 = 0, c2 = 0;
-    for (int s = 0; s < n; ++s) {
-        c4 += (A[s]->D + 4 * kBlock - 1) / (4 * kBlock);
-        c2 += (A[s]->D + 2 * kBlock - 1) / (2 * kBlock);
-    }
-    const long long want = 8LL * ctx->sm_count;
-    if (c4 >= want) return run_batch_t<T, 4>(ctx, n, A, b, x, U, Nreq, tol, m, maxit, eta, info, st);
-    if (c2 >= want) return run_batch_t<T, 2>(ctx, n, A, b, x, U, Nreq, tol, m, maxit, eta, info, st);
-    return run_batch_t<T, 1>(ctx, n, A, b, x, U, Nreq, tol, m, maxit, eta, info, st);
 }
 
 static ddg_status solve_entry(ddg_context* cptr, int n, const ddg_op* const* A, const double* const* b,

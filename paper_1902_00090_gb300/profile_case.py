@@ -1,0 +1,58 @@
+"""Fixed-size solver run for kernel profiling (ncu) and quick timing.
+
+Solves `--solves` held-out 128x128 problems of the synthetic trajectory set
+(seeded), batched, with an iteration cap so that the run is short and every
+launch sees the same Krylov-basis sizes from run to run.  Augmentation uses
+`--k` random vectors (the kernels' work does not depend on their quality).
+
+    python -m paper_1902_00090_gb300.profile_case --solves 64 --maxit 120 --k 20
+"""
+from __future__ import annotations
+
+import argparse
+import time
+
+import numpy as np
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--solves", type=int, default=64)
+    p.add_argument("--n", type=int, default=128)
+    p.add_argument("--maxit", type=int, default=120)
+    p.add_argument("--restart", type=int, default=200)
+    p.add_argument("--k", type=int, default=20)
+    p.add_argument("--precision", default="c64")
+    p.add_argument("--repeat", type=int, default=1)
+    a = p.parse_args()
+
+    import torch
+    import paper_1902_00090_gb300 as ddg
+    from paper_1902_00090_gb300 import inputs
+
+    g = inputs.grid_for(a.n, a.n)
+    eps = inputs.trajectory_set(g, 2, (a.solves + 15) // 16)[: a.solves]
+    ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device="cuda")) for e in eps]
+    bs = [ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src) for op in ops]
+    ctx = ddg.Context()
+    U = None
+    if a.k > 0:
+        U = torch.as_tensor(inputs.random_complex(g.D, 7, shape=(a.k, g.D)), device="cuda")
+    for r in range(a.repeat):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        if U is None:
+            xs, infos, st = ddg.gmres_solve_batched(ctx, ops, bs, tol=1e-6, restart=a.restart, maxit=a.maxit,
+                                                    precision=a.precision)
+        else:
+            xs, infos, st = ddg.augmented_gmres_solve_batched(ctx, ops, bs, [U] * len(ops), tol=1e-6,
+                                                              restart=a.restart, maxit=a.maxit,
+                                                              precision=a.precision)
+        torch.cuda.synchronize()
+        dt = time.time() - t0
+        print(f"run {r}: {len(ops)} solves, {dt * 1e3:.1f} ms, iters mean "
+              f"{np.mean([i['iters'] for i in infos]):.1f}, status {st}, launches {ctx.launches}")
+
+
+if __name__ == "__main__":
+    main()
