@@ -111,6 +111,16 @@ ddg_status ddg_context_profile_enable(ddg_context* ctx, int enable);
    ddg_kernel_class since profiling was enabled.  Synchronises the device. */
 ddg_status ddg_context_profile_read(ddg_context* ctx, int cls, double* ms, double* bytes,
                                     long long* launches);
+/* Gram-Schmidt scheme of the Arnoldi step (Eq. S2 and its reorthogonalisation). */
+typedef enum {
+    DDG_ORTH_CGS2 = 0,   /* classical Gram-Schmidt applied twice per step: 4 passes over the
+                            basis, 2 reductions per step */
+    DDG_ORTH_DCGS2 = 1   /* default: the second pass of step i-1 is merged into the single
+                            reduction of step i and the Hessenberg column corrected
+                            algebraically (delayed reorthogonalisation, Bielich et al.,
+                            Parallel Computing 112, 2022): 2 passes over the basis per step */
+} ddg_orthogonalization;
+ddg_status ddg_context_set_orthogonalization(ddg_context* ctx, int scheme);
 /* Inner-cycle relative tolerance for DDG_C64_REFINE (a cycle ends once its
    least-squares residual falls below eta times the cycle's starting residual).
    Default 1e-5.  Must be in (0, 1). */

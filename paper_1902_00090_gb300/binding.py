@@ -56,6 +56,7 @@ _SIGS = {
     "ddg_context_workspace_bytes": (C.c_longlong, [_vp]),
     "ddg_context_set_inner_tol": (C.c_int, [_vp, C.c_double]),
     "ddg_context_launches": (C.c_longlong, [_vp]),
+    "ddg_context_set_orthogonalization": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_enable": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_longlong)]),
@@ -130,13 +131,15 @@ def _dev_ptr(t, dtype, what, numel=None):
 class Context:
     """ddg_context: device workspace and tuning for one stream."""
 
-    def __init__(self, inner_tol: float | None = None):
+    def __init__(self, inner_tol: float | None = None, orthogonalization: str | None = None):
         _torch()
         h = _vp()
         _check(load().ddg_context_create(C.byref(h)), "ddg_context_create")
         self._h = h
         if inner_tol is not None:
             self.set_inner_tol(inner_tol)
+        if orthogonalization is not None:
+            self.set_orthogonalization(orthogonalization)
 
     @property
     def handle(self):
@@ -144,6 +147,11 @@ class Context:
 
     def set_inner_tol(self, eta: float):
         _check(load().ddg_context_set_inner_tol(self._h, float(eta)), "ddg_context_set_inner_tol")
+
+    def set_orthogonalization(self, scheme: str):
+        """'cgs2' (classical Gram-Schmidt twice) or 'dcgs2' (delayed reorthogonalisation)."""
+        code = {"cgs2": 0, "dcgs2": 1}[scheme]
+        _check(load().ddg_context_set_orthogonalization(self._h, code), "ddg_context_set_orthogonalization")
 
     @property
     def workspace_bytes(self) -> int:

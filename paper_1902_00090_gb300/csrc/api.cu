@@ -169,3 +169,12 @@ extern "C" ddg_status ddg_context_profile_read(ddg_context* ctx, int cls, double
     if (launches) *launches = c->nlaunch[cls];
     return DDG_OK;
 }
+
+extern "C" ddg_status ddg_context_set_orthogonalization(ddg_context* ctx, int scheme) {
+    if (!ctx || (scheme != DDG_ORTH_CGS2 && scheme != DDG_ORTH_DCGS2)) {
+        set_error("ddg_context_set_orthogonalization: bad context or scheme %d", scheme);
+        return DDG_EINVAL;
+    }
+    reinterpret_cast<Context*>(ctx)->orth = scheme;
+    return DDG_OK;
+}

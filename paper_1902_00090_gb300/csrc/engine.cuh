@@ -35,6 +35,7 @@ struct Context {
     size_t ws_bytes = 0;
     int* host_counts = nullptr;      // pinned, polled between launches
     double inner_tol = 1e-5;         // DDG_C64_REFINE inner-cycle relative tolerance
+    int orth = 1;                    // 0: CGS2 (two passes per step), 1: delayed CGS2 (one reduction)
     int poll_every = 8;              // Arnoldi steps between host polls
     int sm_count = 152;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -93,6 +94,8 @@ struct SolvePtrs {
     double2* W;                // FP64 scratch for A V during set-up (ld x N, aliases M)
     void* w[2];                // T2 Arnoldi vectors (double buffered)
     double2* Rg;               // Givens-reduced Hessenberg, (m+1) x m, column-major
+    double2* Hh;               // Hessenberg matrix before rotation, (m+1) x m (delayed scheme)
+    double2* tv;               // delayed scheme: [t = [C Q]^H z | s = Q^H u | alpha | gamma] (KP)
     double2* B;                // C^H A Q, kMaxAug x m
     double* cs;                // rotation cosines (m)
     double2* sn;               // rotation sines (m)

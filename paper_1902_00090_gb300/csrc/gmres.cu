@@ -379,6 +379,34 @@ __global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
     w[p0] = mkpack(wv);
 }
 
+// Delayed scheme: z = A u for the not yet reorthogonalised, unnormalised u
+// (in w[0]); z goes to w[1].  Rows past D are zero.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_stencil_u(BatchArgs a) {
+    using V = c2_t<T>;
+    using PK = pack_t<T>;
+    constexpr int VEC = vec_of<T>();
+    SOLVE_PROLOGUE();
+    if (!S->in_cycle) return;
+    const long long D = P.D;
+    count_bytes(a, DDG_K_STEP, (double)chunk_rows<T>() * ((double)sizeof(T) + 2.0 * sizeof(V)));
+    const long long p0 = (long long)chunk * kBlock + threadIdx.x;
+    const long long e0 = p0 * VEC;
+    const V* __restrict__ u = reinterpret_cast<const V*>(P.w[0]);
+    PK* __restrict__ z = reinterpret_cast<PK*>(P.w[1]);
+    const T* eps = reinterpret_cast<const T*>(P.eps_lo);
+    const V* coef = reinterpret_cast<const V*>(P.coef_lo);
+    const T kh2 = (T)P.kh2;
+    auto ld_ = [&](long long idx) { return u[idx]; };
+    V zv[VEC];
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) {
+        const long long e = e0 + i;
+        zv[i] = e < D ? stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld_) : mk((T)0, (T)0);
+    }
+    z[p0] = mkpack(zv);
+}
+
 // ---------------------------------------------------------------- Gram-Schmidt projections
 // h[k] = sum_e conj(M[k ld + e]) w[e] for the columns k < K = N + j + 1 of one
 // solve (mode 0: pass 1, also ||w||^2 -> anorm; mode 1: pass 2).  Columns are
@@ -545,6 +573,272 @@ __global__ void __launch_bounds__(kBlock) k_update_w(BatchArgs a, int j, int mod
         S->in_cycle = 0;
         atomicSub(a.counts, 1);
     }
+}
+
+// ---------------------------------------------------------------- delayed reorthogonalisation (DCGS2)
+// Iteration i >= 1 holds u = u_i (one Gram-Schmidt pass applied, not yet
+// normalised) and z = A u.  One reduction gives
+//   t = [C Q_i]^H z,  s = Q_i^H u,  alpha = u^H u,  gamma = u^H z
+// (at i = m only s and alpha).  The last CTA then
+//   * finalises column i-1: H[0:i, i-1] = h1 + s, beta = sqrt(alpha - |s|^2)
+//     (Pythagoras: q_i = (u - Q_i s) / beta), B[:, i-1] = h1_C, Givens, stop test;
+//   * forms the first-pass coefficients of column i without touching w_i = A q_i:
+//     with A Q_i s = [C Q_{i+1}] Hs, Hs = [B; H][:, 0:i] s,
+//       h1_C = (t_C - Hs_C)/beta,  h1_Q = (t_Q - Hs_Q)/beta,
+//       h1_i = (gamma - s^H t_Q)/beta^2 - Hs_i/beta,
+//     and c = Hs/beta + h1 for the update u_{i+1} = z/beta - [C Q_{i+1}] c.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_dots2(BatchArgs a, int i) {
+    using V = c2_t<T>;
+    using PK = pack_t<T>;
+    constexpr int VEC = vec_of<T>();
+    SOLVE_PROLOGUE();
+    if (!S->in_cycle) return;
+    const int N = S->N;
+    const bool hz = i < a.m;           // z exists (no matvec at the last column)
+    const int K = N + i;               // columns [C, q_0 .. q_{i-1}]
+    const int Ktot = N + 2 * i + 2;    // [t | s | alpha | gamma]
+    count_bytes(a, DDG_K_DOTS, (double)chunk_rows<T>() * ((double)(hz ? K : i) + 2.0) * sizeof(V));
+    const long long ldp = P.ld / VEC;
+    const long long p0 = (long long)chunk * kBlock + threadIdx.x;
+    const PK* __restrict__ Mp = reinterpret_cast<const PK*>(P.M);
+    V u[VEC], z[VEC];
+    unpack(reinterpret_cast<const PK*>(P.w[0])[p0], u);
+    if (hz) unpack(reinterpret_cast<const PK*>(P.w[1])[p0], z);
+    else {
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) z[q] = mk((T)0, (T)0);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int vidx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    __shared__ V red_t[kWarps][64];
+    __shared__ V red_s[kWarps][64];
+    __shared__ double sm[kWarps];
+    double2* part = P.part + (long long)chunk * a.KP;
+    const int kstart = hz ? 0 : N;     // at i = m the C columns are not needed
+    for (int k0 = kstart; k0 < K; k0 += 64) {
+        const int kt = min(64, K - k0);
+        for (int kk = 0; kk < kt; kk += 8) {
+            const int nv = min(8, kt - kk);
+            const PK* col = Mp + (long long)(k0 + kk) * ldp + p0;
+            PK m[8];
+            if (nv == 8) {
+#pragma unroll
+                for (int w = 0; w < 8; ++w) m[w] = col[(long long)w * ldp];
+            } else {
+#pragma unroll
+                for (int w = 0; w < 8; ++w) m[w] = (w < nv) ? col[(long long)w * ldp] : zero_pack<T>();
+            }
+            V at[8], as[8];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                V mv[VEC];
+                unpack(m[w], mv);
+                at[w] = mk((T)0, (T)0);
+                as[w] = mk((T)0, (T)0);
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    cfmac(at[w], mv[q], z[q]);
+                    cfmac(as[w], mv[q], u[q]);
+                }
+            }
+            V rt = reduce8(at, lane);
+            V rs = reduce8(as, lane);
+            if ((lane & 3) == 0 && vidx < nv) {
+                red_t[wid][kk + vidx] = rt;
+                red_s[wid][kk + vidx] = rs;
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < kt; t += kBlock) {
+            double2 st = make_double2(0.0, 0.0), ss = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                st = cadd(st, to_d2(red_t[w][t]));
+                ss = cadd(ss, to_d2(red_s[w][t]));
+            }
+            const int k = k0 + t;
+            part[k] = st;                              // t_k
+            if (k >= N) part[N + i + (k - N)] = ss;    // s_l, l = k - N
+        }
+        __syncthreads();
+    }
+    {
+        double al = 0.0, gr = 0.0, gi = 0.0;
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            al += cabs2(u[q]);
+            V g = cmulc(u[q], z[q]);
+            gr += (double)g.x;
+            gi += (double)g.y;
+        }
+        al = block_sum_d(al, sm);
+        gr = block_sum_d(gr, sm);
+        gi = block_sum_d(gi, sm);
+        if (threadIdx.x == 0) {
+            part[N + 2 * i] = make_double2(al, 0.0);
+            part[N + 2 * i + 1] = make_double2(gr, gi);
+        }
+    }
+    if (!arrive_last(P.ticket, P.nchunks)) return;
+    double2* tv = P.tv;
+    for (int k = threadIdx.x; k < Ktot; k += kBlock) {
+        if (!hz && k < N) { tv[k] = make_double2(0.0, 0.0); continue; }
+        double2 sum = make_double2(0.0, 0.0);
+        for (int c = 0; c < P.nchunks; ++c) sum = cadd(sum, __ldcg(P.part + (long long)c * a.KP + k));
+        tv[k] = sum;
+    }
+    __syncthreads();
+    __shared__ double s_beta;
+    __shared__ int s_go;
+    const double2* sv = tv + N + i;
+    const int m = a.m, ldh = m + 1;
+    if (threadIdx.x == 0) {
+        // finalise column i-1
+        const int j = i - 1;
+        const double alpha = tv[N + 2 * i].x;
+        double s2 = 0.0, h2 = 0.0;
+        for (int l = 0; l < i; ++l) s2 += cabs2(sv[l]);
+        for (int k = 0; k < N + i; ++k) h2 += cabs2(P.hsum[k]);
+        const double beta = sqrt(fmax(alpha - s2, 0.0));
+        const double anorm = sqrt(h2 + alpha);   // ||A q_{i-1}||
+        for (int n = 0; n < N; ++n) P.B[(long long)j * a.nmax + n] = P.hsum[n];
+        double2* hh = P.Hh + (long long)j * ldh;
+        double2* col = P.Rg + (long long)j * ldh;
+        for (int l = 0; l < i; ++l) {
+            hh[l] = cadd(P.hsum[N + l], sv[l]);
+            col[l] = hh[l];
+        }
+        hh[i] = make_double2(beta, 0.0);
+        for (int l = 0; l < j; ++l) rotate(P.cs[l], P.sn[l], col[l], col[l + 1]);
+        double c;
+        double2 sn, r;
+        givens_d(col[j], beta, c, sn, r);
+        col[j] = r;
+        col[j + 1] = make_double2(0.0, 0.0);
+        P.cs[j] = c;
+        P.sn[j] = sn;
+        double2 gj = P.g[j];
+        P.g[j] = cscale(gj, c);
+        double2 gj1 = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));  // -conj(s) g_j
+        P.g[j + 1] = gj1;
+        const double est = hypot(gj1.x, gj1.y);
+        S->k = i;
+        S->iters += 1;
+        S->hnorm = beta;
+        S->anorm = anorm;
+        bool brk = !(beta > 1e-14 * anorm);
+        if (brk) S->breakdown = 1;
+        int go = 1;
+        if (brk || est <= S->target || S->iters >= a.maxit || i >= m) {
+            S->in_cycle = 0;
+            atomicSub(a.counts, 1);
+            go = 0;
+        }
+        s_beta = beta;
+        s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    // Hs = [B; H][:, 0:i] s and the coefficients of the next step (every thread one row)
+    const double beta = s_beta;
+    const double2* tq = tv + N;
+    for (int row = threadIdx.x; row < N + i + 1; row += kBlock) {
+        double2 hs = make_double2(0.0, 0.0);
+        if (row < N) {
+            for (int l = 0; l < i; ++l) cfma(hs, P.B[(long long)l * a.nmax + row], sv[l]);
+        } else {
+            const int qr = row - N;  // row of H
+            for (int l = max(0, qr - 1); l < i; ++l) cfma(hs, P.Hh[(long long)l * ldh + qr], sv[l]);
+        }
+        double2 h1;
+        if (row < N + i) {
+            h1 = cscale(csub(tv[row], hs), 1.0 / beta);
+        } else {
+            double2 st = make_double2(0.0, 0.0);
+            for (int l = 0; l < i; ++l) cfmac(st, sv[l], tq[l]);
+            double2 gm = csub(tv[N + 2 * i + 1], st);
+            h1 = csub(cscale(gm, 1.0 / (beta * beta)), cscale(hs, 1.0 / beta));
+        }
+        P.hsum[row] = h1;
+        P.hp[row] = cadd(cscale(hs, 1.0 / beta), h1);
+    }
+}
+
+// One sweep over [C, Q_i]:  q_i = (u - Q_i s) / beta  (stored as column N+i)
+// and u <- z / beta - [C, Q_i] c[0:N+i] - q_i c[N+i]  (in place).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_update2(BatchArgs a, int i) {
+    using V = c2_t<T>;
+    using PK = pack_t<T>;
+    constexpr int VEC = vec_of<T>();
+    SOLVE_PROLOGUE();
+    if (!S->in_cycle) return;
+    const int N = S->N;
+    const int K = N + i;
+    count_bytes(a, DDG_K_UPDATE, (double)chunk_rows<T>() * ((double)K + 4.0) * sizeof(V));
+    extern __shared__ unsigned char smraw[];
+    V* cs = reinterpret_cast<V*>(smraw);      // c, N + i + 1
+    V* ss = cs + (N + a.m + 1);               // s, i
+    for (int t = threadIdx.x; t < K + 1; t += kBlock) cs[t] = from_d2<V>(P.hp[t]);
+    for (int t = threadIdx.x; t < i; t += kBlock) ss[t] = from_d2<V>(P.tv[N + i + t]);
+    __syncthreads();
+    const T ib = (T)(1.0 / S->hnorm);
+    const long long ldp = P.ld / VEC;
+    const long long p0 = (long long)chunk * kBlock + threadIdx.x;
+    const PK* __restrict__ Mp = reinterpret_cast<const PK*>(P.M);
+    PK* __restrict__ up = reinterpret_cast<PK*>(P.w[0]);
+    V u[VEC], nu[VEC];
+    unpack(up[p0], u);
+    unpack(reinterpret_cast<const PK*>(P.w[1])[p0], nu);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) nu[q] = cscale(nu[q], ib);
+    int k = 0;
+    // C columns: only the new vector
+    for (; k < N; ++k) {
+        V mv[VEC];
+        unpack(Mp[(long long)k * ldp + p0], mv);
+        const V c = cs[k];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) cfms(nu[q], mv[q], c);
+    }
+    // Q columns, 8 at a time: both vectors
+    for (; k + 8 <= K; k += 8) {
+        const PK* col = Mp + (long long)k * ldp + p0;
+        PK m[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) m[w] = col[(long long)w * ldp];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            V mv[VEC];
+            unpack(m[w], mv);
+            const V c = cs[k + w], sl = ss[k + w - N];
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                cfms(nu[q], mv[q], c);
+                cfms(u[q], mv[q], sl);
+            }
+        }
+    }
+    for (; k < K; ++k) {
+        V mv[VEC];
+        unpack(Mp[(long long)k * ldp + p0], mv);
+        const V c = cs[k], sl = ss[k - N];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            cfms(nu[q], mv[q], c);
+            cfms(u[q], mv[q], sl);
+        }
+    }
+    V qi[VEC];
+    const V cl = cs[K];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+        qi[q] = cscale(u[q], ib);
+        cfms(nu[q], qi[q], cl);
+    }
+    reinterpret_cast<PK*>(reinterpret_cast<V*>(P.M) + (long long)K * P.ld)[p0] = mkpack(qi);
+    up[p0] = mkpack(nu);
 }
 
 // ---------------------------------------------------------------- cycle end
@@ -797,7 +1091,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
                             ddg_info* info, cudaStream_t st) {
     using V = c2_t<T>;
     const long long CH = chunk_rows<T>();
-    int KP = std::max(kMaxAug + m + 2, Nreq * Nreq);
+    int KP = std::max(kMaxAug + 2 * m + 4, Nreq * Nreq);
     KP = (KP + 1) & ~1;
     std::vector<SolvePtrs> hp(n);
     long long total_ctas = 0;
@@ -828,6 +1122,8 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             P.r = c.take<double2>(ld);
             P.V = (Nreq > 0) ? (void*)c.take<V>((size_t)ld * Nreq) : nullptr;
             P.Rg = c.take<double2>((size_t)(m + 1) * m);
+            P.Hh = c.take<double2>((size_t)(m + 1) * m);
+            P.tv = c.take<double2>(KP);
             P.B = c.take<double2>((size_t)kMaxAug * m);
             P.cs = c.take<double>(m);
             P.sn = c.take<double2>(m);
@@ -884,7 +1180,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     DDG_CHECK_CUDA(cudaMemcpyAsync(d_blk, hblk.data(), sizeof(int) * total_ctas, cudaMemcpyHostToDevice, st));
 
     const unsigned G = (unsigned)total_ctas;
-    const size_t upd_smem = sizeof(V) * (size_t)(Nreq + m + 1);
+    const size_t upd_smem = sizeof(V) * (size_t)(Nreq + 2 * m + 2);
     DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_init<<<(n + 127) / 128, 128, 0, st>>>(args, n, Nreq); }));
     if (Nreq > 0) {
         DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_av<T><<<G, kBlock, 0, st>>>(args); }));
@@ -907,7 +1203,31 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
         DDG_CHECK_CUDA(cudaMemcpyAsync(hc, args.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DDG_CHECK_CUDA(cudaStreamSynchronize(st));
         if (hc[1] == 0) break;
-        if (hc[0] > 0) {
+        if (hc[0] > 0 && ctx->orth == 1) {
+            // delayed reorthogonalisation: first pass of step 0, then one
+            // reduction and one sweep per step
+            DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_step<T><<<G, kBlock, 0, st>>>(args, 0); }));
+            DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots_w<T><<<G, kBlock, 0, st>>>(args, 0, 0); }));
+            DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T><<<G, kBlock, upd_smem, st>>>(args, 0, 0); }));
+            int polled = 0;
+            for (int i = 1; i <= m; ++i) {
+                if (i < m)
+                    DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_stencil_u<T><<<G, kBlock, 0, st>>>(args); }));
+                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots2<T><<<G, kBlock, 0, st>>>(args, i); }));
+                if (i < m)
+                    DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update2<T><<<G, kBlock, upd_smem, st>>>(args, i); }));
+                if (i % ctx->poll_every == 0 && i < m) {
+                    const int slot = polled & 1;
+                    DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 2 + slot, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
+                    DDG_CHECK_CUDA(cudaEventRecord(ctx->ev[slot], st));
+                    if (polled > 0) {
+                        DDG_CHECK_CUDA(cudaEventSynchronize(ctx->ev[slot ^ 1]));
+                        if (hc[2 + (slot ^ 1)] == 0) break;
+                    }
+                    ++polled;
+                }
+            }
+        } else if (hc[0] > 0) {
             int polled = 0;
             for (int j = 0; j < m; ++j) {
                 DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_step<T><<<G, kBlock, 0, st>>>(args, j); }));

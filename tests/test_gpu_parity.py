@@ -294,3 +294,37 @@ def test_pca_fit_on_solved_training_fields(ctx):
     if gap_ok:
         Ug = host(U).T
         assert np.linalg.norm(Ug @ Ug.conj().T - Uo @ Uo.conj().T, 2) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_delayed_reorthogonalisation_matches_cgs2(prec):
+    # Same Krylov space and Hessenberg matrix in exact arithmetic: equal step
+    # counts up to a step at a tolerance crossing, both at the tolerance.
+    g, eps, A, b = small(48, npml=6, seed=11)
+    rng = np.random.default_rng(11)
+    V = rand_V(g.D, 3, 11)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    res = {}
+    for scheme in ("cgs2", "dcgs2"):
+        c = ddg.Context(orthogonalization=scheme)
+        x, info, st = ddg.gmres_solve(c, op, dev(b), tol=1e-8, restart=40, maxit=4000, precision=prec)
+        xa, ia, sa = ddg.augmented_gmres_solve(c, op, dev(b), dev(V), tol=1e-8, restart=40, maxit=4000,
+                                               precision=prec)
+        assert st == 0 and sa == 0
+        for xx in (x, xa):
+            assert np.linalg.norm(b - A @ host(xx)) / np.linalg.norm(b) <= 1e-8
+        res[scheme] = (info["iters"], ia["iters"])
+    for k in range(2):
+        a_, b_ = res["cgs2"][k], res["dcgs2"][k]
+        assert abs(a_ - b_) <= max(2, 0.03 * a_), res
+
+
+def test_dcgs2_is_default_and_matches_oracle_steps(ctx):
+    g, eps, A, b = small(32, npml=6, seed=1)
+    xo, io = gmres.plain_gmres(A, b, tol=1e-9, restart=25, maxit=3000)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    c = ddg.Context(orthogonalization="cgs2")
+    x1, i1, _ = ddg.gmres_solve(c, op, dev(b), tol=1e-9, restart=25, maxit=3000)
+    x2, i2, _ = ddg.gmres_solve(ctx, op, dev(b), tol=1e-9, restart=25, maxit=3000)
+    assert abs(i1["iters"] - io.iters) <= 1 and abs(i2["iters"] - io.iters) <= 1
+    assert rel(host(x2), xo) <= 1e-6
