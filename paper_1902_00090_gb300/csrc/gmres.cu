@@ -105,6 +105,78 @@ __device__ __forceinline__ void rotate(double c, double2 s, double2& u, double2&
     v = nv;
 }
 
+__device__ __forceinline__ double2 shfl_up_d2(double2 v, int d) {
+    return make_double2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ double2 shfl_idx_d2(double2 v, int src) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// Applies the j stored rotations to column j of the Hessenberg matrix, forms
+// rotation j and updates g (one warp; col, cs, sn, out in shared memory).
+// Applying rotations l = 0..j-1 in turn is the linear recurrence
+//   carry_0 = col_0,  out_l = c_l carry_l + s_l col_{l+1},
+//   carry_{l+1} = -conj(s_l) carry_l + c_l col_{l+1},
+// evaluated as a warp prefix scan of the affine maps carry -> a carry + b:
+// every lane composes the maps of its segment, the lanes scan the composites
+// (5 shuffle levels) and replay their segment from its starting carry.  The
+// dependent chain is O(j/32 + 5) instead of O(j): FP64 latency on this part is
+// long.  Returns |g_{j+1}| (valid in every lane); out[0..j] is the rotated column.
+__device__ __noinline__ double givens_column_warp(const double2* col, const double* cs, const double2* sn, int j,
+                                                  double sub, double2* out, double2* g, double* cs_out,
+                                                  double2* sn_out) {
+    const int lane = threadIdx.x & 31;
+    const int L = (j + 31) / 32;
+    const int l0 = min(j, lane * L), l1 = min(j, l0 + L);
+    double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
+    for (int l = l0; l < l1; ++l) {
+        const double2 a = make_double2(-sn[l].x, sn[l].y);  // -conj(s_l)
+        const double2 b = cscale(col[l + 1], cs[l]);
+        A = cmul(a, A);
+        B = cadd(cmul(a, B), b);
+    }
+    // inclusive scan: (A, B) <- (A, B) o (A_prev, B_prev)
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const double2 Ap = shfl_up_d2(A, d), Bp = shfl_up_d2(B, d);
+        if (lane >= d) {
+            B = cadd(cmul(A, Bp), B);
+            A = cmul(A, Ap);
+        }
+    }
+    double2 Ae = shfl_up_d2(A, 1), Be = shfl_up_d2(B, 1);
+    if (lane == 0) {
+        Ae = make_double2(1.0, 0.0);
+        Be = make_double2(0.0, 0.0);
+    }
+    const double2 c0 = col[0];
+    double2 carry = cadd(cmul(Ae, c0), Be);
+    for (int l = l0; l < l1; ++l) {
+        const double2 nx = col[l + 1];
+        out[l] = cadd(cscale(carry, cs[l]), cmul(sn[l], nx));
+        carry = cadd(cmul(make_double2(-sn[l].x, sn[l].y), carry), cscale(nx, cs[l]));
+    }
+    const double2 Af = shfl_idx_d2(A, 31), Bf = shfl_idx_d2(B, 31);
+    const double2 cj = cadd(cmul(Af, c0), Bf);   // column entry j after all rotations
+    double est = 0.0;
+    if (lane == 0) {
+        double c;
+        double2 snj, r;
+        givens_d(cj, sub, c, snj, r);
+        out[j] = r;
+        out[j + 1] = make_double2(0.0, 0.0);
+        *cs_out = c;
+        *sn_out = snj;
+        const double2 gj = g[j];
+        g[j] = cscale(gj, c);
+        const double2 gj1 = make_double2(-(snj.x * gj.x + snj.y * gj.y), -(snj.x * gj.y - snj.y * gj.x));
+        g[j + 1] = gj1;
+        est = hypot(gj1.x, gj1.y);
+    }
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, est, 0);
+}
+
 template <typename T> __device__ __forceinline__ pack_t<T> zero_pack();
 template <> __device__ __forceinline__ float4 zero_pack<float>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 template <> __device__ __forceinline__ double2 zero_pack<double>() { return make_double2(0.0, 0.0); }
@@ -500,7 +572,7 @@ __global__ void __launch_bounds__(kBlock) k_update_w(BatchArgs a, int j, int mod
     const int N = S->N;
     const int K = N + j + 1;
     count_bytes(a, DDG_K_UPDATE, (double)chunk_rows<T>() * ((double)K + 2.0) * sizeof(V));
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     V* hs = reinterpret_cast<V*>(smraw);
     __shared__ double sm[kWarps];
     for (int t = threadIdx.x; t < K; t += kBlock) hs[t] = from_d2<V>(P.hp[t]);
@@ -541,38 +613,44 @@ __global__ void __launch_bounds__(kBlock) k_update_w(BatchArgs a, int j, int mod
     double tot = block_sum_d(acc, sm);
     if (threadIdx.x == 0) P.part[(long long)chunk * a.KP] = make_double2(tot, 0.0);
     if (!arrive_last(P.ticket, P.nchunks)) return;
-    if (threadIdx.x != 0) return;
-    double n2 = 0.0;
-    for (int c = 0; c < P.nchunks; ++c) n2 += __ldcg(P.part + (long long)c * a.KP).x;
-    const double nrm = sqrt(n2);
     // column j of H (rows 0..j from hsum[N..N+j], row j+1 = ||w||), column j of
-    // B = C^H A q_j (hsum[0..N)); Givens update of column j.
+    // B = C^H A q_j (hsum[0..N)); Givens update of column j in shared memory.
     const int m = a.m, ldh = m + 1;
-    for (int n = 0; n < N; ++n) P.B[(long long)j * a.nmax + n] = P.hsum[n];
-    double2* col = P.Rg + (long long)j * ldh;
-    for (int i = 0; i <= j; ++i) col[i] = P.hsum[N + i];
-    for (int i = 0; i < j; ++i) rotate(P.cs[i], P.sn[i], col[i], col[i + 1]);
-    double c;
-    double2 sn, r;
-    givens_d(col[j], nrm, c, sn, r);
-    col[j] = r;
-    col[j + 1] = make_double2(0.0, 0.0);
-    P.cs[j] = c;
-    P.sn[j] = sn;
-    double2 gj = P.g[j];
-    P.g[j] = cscale(gj, c);
-    double2 gj1 = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));  // -conj(s) g_j
-    P.g[j + 1] = gj1;
-    const double est = hypot(gj1.x, gj1.y);
-    S->k = j + 1;
-    S->iters += 1;
-    S->hnorm = nrm;
-    bool brk = !(nrm > 1e-14 * S->anorm);
-    if (brk) S->breakdown = 1;
-    if (brk || est <= S->target || S->iters >= a.maxit || j + 1 >= m) {
-        S->in_cycle = 0;
-        atomicSub(a.counts, 1);
+    // 16-byte arrays first, the m doubles last (keeps every double2 aligned for any m)
+    double2* gcol = reinterpret_cast<double2*>(smraw);      // m + 2 entries
+    double2* gsn = gcol + (m + 2);                          // m entries
+    double2* gout = gsn + m;                                // m + 2 entries
+    double* gcs = reinterpret_cast<double*>(gout + (m + 2)); // m entries
+    for (int t = threadIdx.x; t <= j; t += kBlock) gcol[t] = P.hsum[N + t];
+    for (int t = threadIdx.x; t < j; t += kBlock) {
+        gcs[t] = P.cs[t];
+        gsn[t] = P.sn[t];
     }
+    for (int n = threadIdx.x; n < N; n += kBlock) P.B[(long long)j * a.nmax + n] = P.hsum[n];
+    __shared__ double s_nrm;
+    if (threadIdx.x == 0) {
+        double n2 = 0.0;
+        for (int c = 0; c < P.nchunks; ++c) n2 += __ldcg(P.part + (long long)c * a.KP).x;
+        s_nrm = sqrt(n2);
+    }
+    __syncthreads();
+    const double nrm = s_nrm;
+    if (threadIdx.x < 32) {
+        const double est = givens_column_warp(gcol, gcs, gsn, j, nrm, gout, P.g, P.cs + j, P.sn + j);
+        if (threadIdx.x != 0) goto cgs2_done;
+        S->k = j + 1;
+        S->iters += 1;
+        S->hnorm = nrm;
+        bool brk = !(nrm > 1e-14 * S->anorm);
+        if (brk) S->breakdown = 1;
+        if (brk || est <= S->target || S->iters >= a.maxit || j + 1 >= m) {
+            S->in_cycle = 0;
+            atomicSub(a.counts, 1);
+        }
+    }
+cgs2_done:
+    __syncthreads();
+    for (int t = threadIdx.x; t <= j + 1; t += kBlock) P.Rg[(long long)j * ldh + t] = gout[t];
 }
 
 // ---------------------------------------------------------------- delayed reorthogonalisation (DCGS2)
@@ -588,7 +666,7 @@ __global__ void __launch_bounds__(kBlock) k_update_w(BatchArgs a, int j, int mod
 //       h1_i = (gamma - s^H t_Q)/beta^2 - Hs_i/beta,
 //     and c = Hs/beta + h1 for the update u_{i+1} = z/beta - [C Q_{i+1}] c.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_dots2(BatchArgs a, int i) {
+__global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
     using V = c2_t<T>;
     using PK = pack_t<T>;
     constexpr int VEC = vec_of<T>();
@@ -616,37 +694,37 @@ __global__ void __launch_bounds__(kBlock) k_dots2(BatchArgs a, int i) {
     __shared__ double sm[kWarps];
     double2* part = P.part + (long long)chunk * a.KP;
     const int kstart = hz ? 0 : N;     // at i = m the C columns are not needed
+    // 4 columns per batch; their t- and s-partials share one 8-value butterfly
     for (int k0 = kstart; k0 < K; k0 += 64) {
         const int kt = min(64, K - k0);
-        for (int kk = 0; kk < kt; kk += 8) {
-            const int nv = min(8, kt - kk);
+        for (int kk = 0; kk < kt; kk += 4) {
+            const int nv = min(4, kt - kk);
             const PK* col = Mp + (long long)(k0 + kk) * ldp + p0;
-            PK m[8];
-            if (nv == 8) {
+            PK m[4];
+            if (nv == 4) {
 #pragma unroll
-                for (int w = 0; w < 8; ++w) m[w] = col[(long long)w * ldp];
+                for (int w = 0; w < 4; ++w) m[w] = col[(long long)w * ldp];
             } else {
 #pragma unroll
-                for (int w = 0; w < 8; ++w) m[w] = (w < nv) ? col[(long long)w * ldp] : zero_pack<T>();
+                for (int w = 0; w < 4; ++w) m[w] = (w < nv) ? col[(long long)w * ldp] : zero_pack<T>();
             }
-            V at[8], as[8];
+            V acc[8];
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
+            for (int w = 0; w < 4; ++w) {
                 V mv[VEC];
                 unpack(m[w], mv);
-                at[w] = mk((T)0, (T)0);
-                as[w] = mk((T)0, (T)0);
+                acc[w] = mk((T)0, (T)0);
+                acc[w + 4] = mk((T)0, (T)0);
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
-                    cfmac(at[w], mv[q], z[q]);
-                    cfmac(as[w], mv[q], u[q]);
+                    cfmac(acc[w], mv[q], z[q]);
+                    cfmac(acc[w + 4], mv[q], u[q]);
                 }
             }
-            V rt = reduce8(at, lane);
-            V rs = reduce8(as, lane);
-            if ((lane & 3) == 0 && vidx < nv) {
-                red_t[wid][kk + vidx] = rt;
-                red_s[wid][kk + vidx] = rs;
+            const V r = reduce8(acc, lane);
+            if ((lane & 3) == 0 && (vidx & 3) < nv) {
+                if (vidx < 4) red_t[wid][kk + vidx] = r;
+                else red_s[wid][kk + vidx - 4] = r;
             }
         }
         __syncthreads();
@@ -693,36 +771,50 @@ __global__ void __launch_bounds__(kBlock) k_dots2(BatchArgs a, int i) {
     __shared__ int s_go;
     const double2* sv = tv + N + i;
     const int m = a.m, ldh = m + 1;
-    if (threadIdx.x == 0) {
-        // finalise column i-1
-        const int j = i - 1;
-        const double alpha = tv[N + 2 * i].x;
-        double s2 = 0.0, h2 = 0.0;
-        for (int l = 0; l < i; ++l) s2 += cabs2(sv[l]);
-        for (int k = 0; k < N + i; ++k) h2 += cabs2(P.hsum[k]);
-        const double beta = sqrt(fmax(alpha - s2, 0.0));
-        const double anorm = sqrt(h2 + alpha);   // ||A q_{i-1}||
-        for (int n = 0; n < N; ++n) P.B[(long long)j * a.nmax + n] = P.hsum[n];
-        double2* hh = P.Hh + (long long)j * ldh;
-        double2* col = P.Rg + (long long)j * ldh;
-        for (int l = 0; l < i; ++l) {
-            hh[l] = cadd(P.hsum[N + l], sv[l]);
-            col[l] = hh[l];
+    const int j = i - 1;
+    // stage column j (= h1_Q + s), the rotations and ||h1||^2 in shared memory
+    extern __shared__ __align__(16) unsigned char smraw2[];
+    // 16-byte arrays first, the m doubles last (keeps every double2 aligned for any m)
+    double2* gcol = reinterpret_cast<double2*>(smraw2);    // m + 2 entries
+    double2* gsn = gcol + (m + 2);                         // m entries
+    double2* gout = gsn + m;                               // m + 2 entries
+    double* gcs = reinterpret_cast<double*>(gout + (m + 2)); // m entries
+    for (int t = threadIdx.x; t < i; t += kBlock) {
+        const double2 h = cadd(P.hsum[N + t], sv[t]);
+        gcol[t] = h;
+        P.Hh[(long long)j * ldh + t] = h;
+    }
+    for (int t = threadIdx.x; t < j; t += kBlock) {
+        gcs[t] = P.cs[t];
+        gsn[t] = P.sn[t];
+    }
+    for (int n = threadIdx.x; n < N; n += kBlock) P.B[(long long)j * a.nmax + n] = P.hsum[n];
+    double s2p = 0.0, h2p = 0.0;
+    for (int t = threadIdx.x; t < i; t += kBlock) s2p += cabs2(sv[t]);
+    for (int t = threadIdx.x; t < N + i; t += kBlock) h2p += cabs2(P.hsum[t]);
+    // s^H t_Q for the new column's first-pass coefficient (block reduction)
+    double str = 0.0, sti = 0.0;
+    if (hz)
+        for (int t = threadIdx.x; t < i; t += kBlock) {
+            const double2 pr = cmulc(sv[t], tv[N + t]);
+            str += pr.x;
+            sti += pr.y;
         }
-        hh[i] = make_double2(beta, 0.0);
-        for (int l = 0; l < j; ++l) rotate(P.cs[l], P.sn[l], col[l], col[l + 1]);
-        double c;
-        double2 sn, r;
-        givens_d(col[j], beta, c, sn, r);
-        col[j] = r;
-        col[j + 1] = make_double2(0.0, 0.0);
-        P.cs[j] = c;
-        P.sn[j] = sn;
-        double2 gj = P.g[j];
-        P.g[j] = cscale(gj, c);
-        double2 gj1 = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));  // -conj(s) g_j
-        P.g[j + 1] = gj1;
-        const double est = hypot(gj1.x, gj1.y);
+    __shared__ double2 s_st;
+    const double s2 = block_sum_d(s2p, sm);
+    const double h2 = block_sum_d(h2p, sm);
+    const double st_r = block_sum_d(str, sm);
+    const double st_i = block_sum_d(sti, sm);
+    if (threadIdx.x == 0) s_st = make_double2(st_r, st_i);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // finalise column j = i-1
+        const double alpha = tv[N + 2 * i].x;
+        const double beta = sqrt(fmax(alpha - s2, 0.0));
+        const double est = givens_column_warp(gcol, gcs, gsn, j, beta, gout, P.g, P.cs + j, P.sn + j);
+        if (threadIdx.x != 0) goto dcgs2_done;
+        const double anorm = sqrt(h2 + alpha);   // ||A q_{i-1}||
+        P.Hh[(long long)j * ldh + i] = make_double2(beta, 0.0);
         S->k = i;
         S->iters += 1;
         S->hnorm = beta;
@@ -738,26 +830,31 @@ __global__ void __launch_bounds__(kBlock) k_dots2(BatchArgs a, int i) {
         s_beta = beta;
         s_go = go;
     }
+dcgs2_done:
+    __syncthreads();
+    for (int t = threadIdx.x; t <= j + 1; t += kBlock) P.Rg[(long long)j * ldh + t] = gout[t];
     __syncthreads();
     if (!s_go) return;
     // Hs = [B; H][:, 0:i] s and the coefficients of the next step (every thread one row)
+    // Hs multiplies the reorthogonalisation coefficients s (of the order of the
+    // working precision times ||u||), so it is formed in the Krylov precision T.
     const double beta = s_beta;
-    const double2* tq = tv + N;
     for (int row = threadIdx.x; row < N + i + 1; row += kBlock) {
-        double2 hs = make_double2(0.0, 0.0);
+        // row-wise sum over columns l: loads of one column are contiguous over rows
+        V hst = mk((T)0, (T)0);
         if (row < N) {
-            for (int l = 0; l < i; ++l) cfma(hs, P.B[(long long)l * a.nmax + row], sv[l]);
+            for (int l = 0; l < i; ++l) cfma(hst, from_d2<V>(P.B[(long long)l * a.nmax + row]), from_d2<V>(sv[l]));
         } else {
-            const int qr = row - N;  // row of H
-            for (int l = max(0, qr - 1); l < i; ++l) cfma(hs, P.Hh[(long long)l * ldh + qr], sv[l]);
+            const int qr = row - N;  // row of H; column l holds rows 0..l+1
+            for (int l = max(0, qr - 1); l < i; ++l)
+                cfma(hst, from_d2<V>(P.Hh[(long long)l * ldh + qr]), from_d2<V>(sv[l]));
         }
+        const double2 hs = to_d2(hst);
         double2 h1;
         if (row < N + i) {
             h1 = cscale(csub(tv[row], hs), 1.0 / beta);
         } else {
-            double2 st = make_double2(0.0, 0.0);
-            for (int l = 0; l < i; ++l) cfmac(st, sv[l], tq[l]);
-            double2 gm = csub(tv[N + 2 * i + 1], st);
+            const double2 gm = csub(tv[N + 2 * i + 1], s_st);
             h1 = csub(cscale(gm, 1.0 / (beta * beta)), cscale(hs, 1.0 / beta));
         }
         P.hsum[row] = h1;
@@ -777,7 +874,7 @@ __global__ void __launch_bounds__(kBlock) k_update2(BatchArgs a, int i) {
     const int N = S->N;
     const int K = N + i;
     count_bytes(a, DDG_K_UPDATE, (double)chunk_rows<T>() * ((double)K + 4.0) * sizeof(V));
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     V* cs = reinterpret_cast<V*>(smraw);      // c, N + i + 1
     V* ss = cs + (N + a.m + 1);               // s, i
     for (int t = threadIdx.x; t < K + 1; t += kBlock) cs[t] = from_d2<V>(P.hp[t]);
@@ -850,7 +947,7 @@ __global__ void __launch_bounds__(128) k_backsub(BatchArgs a) {
     if (!S->pending) return;
     const SolvePtrs& P = a.P[s];
     const int k = S->k, N = S->N, ldh = a.m + 1;
-    extern __shared__ double2 sh[];
+    extern __shared__ __align__(16) double2 sh[];
     double2* gg = sh;            // k
     double2* y = sh + a.m;       // k
     double2* xa = sh + 2 * a.m;  // N
@@ -1180,7 +1277,8 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     DDG_CHECK_CUDA(cudaMemcpyAsync(d_blk, hblk.data(), sizeof(int) * total_ctas, cudaMemcpyHostToDevice, st));
 
     const unsigned G = (unsigned)total_ctas;
-    const size_t upd_smem = sizeof(V) * (size_t)(Nreq + 2 * m + 2);
+    const size_t giv_smem = 56 * (size_t)m + 128;  // Givens staging: column, sines, cosines, result
+    const size_t upd_smem = std::max(sizeof(V) * (size_t)(Nreq + 2 * m + 2), giv_smem);
     DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_init<<<(n + 127) / 128, 128, 0, st>>>(args, n, Nreq); }));
     if (Nreq > 0) {
         DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_av<T><<<G, kBlock, 0, st>>>(args); }));
@@ -1213,7 +1311,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             for (int i = 1; i <= m; ++i) {
                 if (i < m)
                     DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_stencil_u<T><<<G, kBlock, 0, st>>>(args); }));
-                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots2<T><<<G, kBlock, 0, st>>>(args, i); }));
+                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots2<T><<<G, kBlock, giv_smem, st>>>(args, i); }));
                 if (i < m)
                     DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update2<T><<<G, kBlock, upd_smem, st>>>(args, i); }));
                 if (i % ctx->poll_every == 0 && i < m) {

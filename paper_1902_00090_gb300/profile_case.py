@@ -24,6 +24,8 @@ def main():
     p.add_argument("--k", type=int, default=20)
     p.add_argument("--precision", default="c64")
     p.add_argument("--repeat", type=int, default=1)
+    p.add_argument("--orth", default=None, choices=[None, "cgs2", "dcgs2"])
+    p.add_argument("--profile", action="store_true", help="print per-kernel-class time and GB/s")
     a = p.parse_args()
 
     import torch
@@ -34,11 +36,13 @@ def main():
     eps = inputs.trajectory_set(g, 2, (a.solves + 15) // 16)[: a.solves]
     ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device="cuda")) for e in eps]
     bs = [ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src) for op in ops]
-    ctx = ddg.Context()
+    ctx = ddg.Context(orthogonalization=a.orth)
     U = None
     if a.k > 0:
         U = torch.as_tensor(inputs.random_complex(g.D, 7, shape=(a.k, g.D)), device="cuda")
     for r in range(a.repeat):
+        if a.profile and r == a.repeat - 1:
+            ctx.profile_enable(True)
         torch.cuda.synchronize()
         t0 = time.time()
         if U is None:
@@ -52,6 +56,11 @@ def main():
         dt = time.time() - t0
         print(f"run {r}: {len(ops)} solves, {dt * 1e3:.1f} ms, iters mean "
               f"{np.mean([i['iters'] for i in infos]):.1f}, status {st}, launches {ctx.launches}")
+    if a.profile:
+        for name, (ms, by, n) in ctx.profile_read().items():
+            if n:
+                print(f"  {name:10s} {n:6d} launches {ms:9.2f} ms  {by / max(ms, 1e-9) / 1e6:8.1f} GB/s "
+                      f" {ms * 1e3 / n:8.1f} us/launch")
 
 
 if __name__ == "__main__":
