@@ -94,7 +94,7 @@ struct SolvePtrs {
     double2* W;                // FP64 scratch for A V during set-up (ld x N, aliases M)
     void* w[2];                // T2 Arnoldi vectors (double buffered)
     double2* Rg;               // Givens-reduced Hessenberg, (m+1) x m, column-major
-    double2* Hh;               // Hessenberg matrix before rotation, (m+1) x m (delayed scheme)
+    double2* Hh;               // delayed scheme: H and B before rotation, in T2 (ld m+1 and kMaxAug)
     double2* tv;               // delayed scheme: [t = [C Q]^H z | s = Q^H u | alpha | gamma] (KP)
     double2* B;                // C^H A Q, kMaxAug x m
     double* cs;                // rotation cosines (m)

@@ -43,6 +43,21 @@ __device__ __forceinline__ double block_sum_d(double v, double* sm) {
     return t;  // valid in thread 0
 }
 
+// Sum over the CTA in precision T (every thread gets the total).
+template <typename T> __device__ __forceinline__ T block_sum_all(T v, T* sm) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[wid] = v;
+    __syncthreads();
+    T t = (T)0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t += sm[w];
+    __syncthreads();
+    return t;
+}
+
 // Returns true in every thread of the CTA that is the last of `n` CTAs to
 // arrive on `ticket` (partials of all CTAs are then visible); resets the ticket.
 __device__ __forceinline__ bool arrive_last(unsigned* ticket, int n) {
@@ -501,8 +516,9 @@ __global__ void __launch_bounds__(kBlock) k_dots_w(BatchArgs a, int j, int mode)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int vidx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     __shared__ V red[kWarps][64];
-    __shared__ double sm[kWarps];
-    double2* part = P.part + (long long)chunk * a.KP;
+    __shared__ T smt[kWarps];
+    // partial sums stay in the Krylov precision (one conversion per coefficient at the end)
+    V* part = reinterpret_cast<V*>(P.part) + (long long)chunk * a.KP;
     for (int k0 = 0; k0 < K; k0 += 64) {
         const int kt = min(64, K - k0);
         for (int kk = 0; kk < kt; kk += 8) {
@@ -530,25 +546,27 @@ __global__ void __launch_bounds__(kBlock) k_dots_w(BatchArgs a, int j, int mode)
         }
         __syncthreads();
         for (int t = threadIdx.x; t < kt; t += kBlock) {
-            double2 sum = make_double2(0.0, 0.0);
+            V sum = mk((T)0, (T)0);
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) sum = cadd(sum, to_d2(red[w][t]));
+            for (int w = 0; w < kWarps; ++w) sum = cadd(sum, red[w][t]);
             part[k0 + t] = sum;
         }
         __syncthreads();
     }
     if (mode == 0) {
-        double nn = 0.0;
+        T nn = (T)0;
 #pragma unroll
-        for (int i = 0; i < VEC; ++i) nn += cabs2(v[i]);
-        nn = block_sum_d(nn, sm);
-        if (threadIdx.x == 0) part[K] = make_double2(nn, 0.0);
+        for (int i = 0; i < VEC; ++i) nn += v[i].x * v[i].x + v[i].y * v[i].y;
+        nn = block_sum_all(nn, smt);
+        if (threadIdx.x == 0) part[K] = mk(nn, (T)0);
     }
     if (!arrive_last(P.ticket, P.nchunks)) return;
     const int Ktot = K + (mode == 0 ? 1 : 0);
+    const V* pall = reinterpret_cast<const V*>(P.part);
     for (int k = threadIdx.x; k < Ktot; k += kBlock) {
-        double2 sum = make_double2(0.0, 0.0);
-        for (int c = 0; c < P.nchunks; ++c) sum = cadd(sum, __ldcg(P.part + (long long)c * a.KP + k));
+        V sv_ = mk((T)0, (T)0);
+        for (int c = 0; c < P.nchunks; ++c) sv_ = cadd(sv_, __ldcg(pall + (long long)c * a.KP + k));
+        const double2 sum = to_d2(sv_);
         if (k < K) {
             P.hp[k] = sum;
             if (mode == 0) P.hsum[k] = sum;
@@ -607,11 +625,13 @@ __global__ void __launch_bounds__(kBlock) k_update_w(BatchArgs a, int j, int mod
     }
     wp[p0] = mkpack(v);
     if (mode == 0) return;
-    double acc = 0.0;
+    __shared__ T smt[kWarps];
+    T acc = (T)0;
 #pragma unroll
-    for (int i = 0; i < VEC; ++i) acc += cabs2(v[i]);
-    double tot = block_sum_d(acc, sm);
-    if (threadIdx.x == 0) P.part[(long long)chunk * a.KP] = make_double2(tot, 0.0);
+    for (int i = 0; i < VEC; ++i) acc += v[i].x * v[i].x + v[i].y * v[i].y;
+    const T tot = block_sum_all(acc, smt);
+    V* partv = reinterpret_cast<V*>(P.part);
+    if (threadIdx.x == 0) partv[(long long)chunk * a.KP] = mk(tot, (T)0);
     if (!arrive_last(P.ticket, P.nchunks)) return;
     // column j of H (rows 0..j from hsum[N..N+j], row j+1 = ||w||), column j of
     // B = C^H A q_j (hsum[0..N)); Givens update of column j in shared memory.
@@ -629,9 +649,9 @@ __global__ void __launch_bounds__(kBlock) k_update_w(BatchArgs a, int j, int mod
     for (int n = threadIdx.x; n < N; n += kBlock) P.B[(long long)j * a.nmax + n] = P.hsum[n];
     __shared__ double s_nrm;
     if (threadIdx.x == 0) {
-        double n2 = 0.0;
-        for (int c = 0; c < P.nchunks; ++c) n2 += __ldcg(P.part + (long long)c * a.KP).x;
-        s_nrm = sqrt(n2);
+        T n2 = (T)0;
+        for (int c = 0; c < P.nchunks; ++c) n2 += __ldcg(reinterpret_cast<const V*>(P.part) + (long long)c * a.KP).x;
+        s_nrm = sqrt((double)n2);
     }
     __syncthreads();
     const double nrm = s_nrm;
@@ -692,7 +712,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
     __shared__ V red_t[kWarps][64];
     __shared__ V red_s[kWarps][64];
     __shared__ double sm[kWarps];
-    double2* part = P.part + (long long)chunk * a.KP;
+    __shared__ T smt[kWarps];
+    // partial sums stay in the Krylov precision until the last CTA
+    V* part = reinterpret_cast<V*>(P.part) + (long long)chunk * a.KP;
     const int kstart = hz ? 0 : N;     // at i = m the C columns are not needed
     // 4 columns per batch; their t- and s-partials share one 8-value butterfly
     for (int k0 = kstart; k0 < K; k0 += 64) {
@@ -729,11 +751,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
         }
         __syncthreads();
         for (int t = threadIdx.x; t < kt; t += kBlock) {
-            double2 st = make_double2(0.0, 0.0), ss = make_double2(0.0, 0.0);
+            V st = mk((T)0, (T)0), ss = mk((T)0, (T)0);
 #pragma unroll
             for (int w = 0; w < kWarps; ++w) {
-                st = cadd(st, to_d2(red_t[w][t]));
-                ss = cadd(ss, to_d2(red_s[w][t]));
+                st = cadd(st, red_t[w][t]);
+                ss = cadd(ss, red_s[w][t]);
             }
             const int k = k0 + t;
             part[k] = st;                              // t_k
@@ -742,29 +764,29 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
         __syncthreads();
     }
     {
-        double al = 0.0, gr = 0.0, gi = 0.0;
+        T al = (T)0;
+        V gg = mk((T)0, (T)0);
 #pragma unroll
         for (int q = 0; q < VEC; ++q) {
-            al += cabs2(u[q]);
-            V g = cmulc(u[q], z[q]);
-            gr += (double)g.x;
-            gi += (double)g.y;
+            al += u[q].x * u[q].x + u[q].y * u[q].y;
+            cfmac(gg, u[q], z[q]);
         }
-        al = block_sum_d(al, sm);
-        gr = block_sum_d(gr, sm);
-        gi = block_sum_d(gi, sm);
+        al = block_sum_all(al, smt);
+        const T gr = block_sum_all(gg.x, smt);
+        const T gi = block_sum_all(gg.y, smt);
         if (threadIdx.x == 0) {
-            part[N + 2 * i] = make_double2(al, 0.0);
-            part[N + 2 * i + 1] = make_double2(gr, gi);
+            part[N + 2 * i] = mk(al, (T)0);
+            part[N + 2 * i + 1] = mk(gr, gi);
         }
     }
     if (!arrive_last(P.ticket, P.nchunks)) return;
     double2* tv = P.tv;
+    const V* pall = reinterpret_cast<const V*>(P.part);
     for (int k = threadIdx.x; k < Ktot; k += kBlock) {
         if (!hz && k < N) { tv[k] = make_double2(0.0, 0.0); continue; }
-        double2 sum = make_double2(0.0, 0.0);
-        for (int c = 0; c < P.nchunks; ++c) sum = cadd(sum, __ldcg(P.part + (long long)c * a.KP + k));
-        tv[k] = sum;
+        V sum = mk((T)0, (T)0);
+        for (int c = 0; c < P.nchunks; ++c) sum = cadd(sum, __ldcg(pall + (long long)c * a.KP + k));
+        tv[k] = to_d2(sum);
     }
     __syncthreads();
     __shared__ double s_beta;
@@ -778,12 +800,17 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
     double2* gcol = reinterpret_cast<double2*>(smraw2);    // m + 2 entries
     double2* gsn = gcol + (m + 2);                         // m entries
     double2* gout = gsn + m;                               // m + 2 entries
-    double* gcs = reinterpret_cast<double*>(gout + (m + 2)); // m entries
+    V* svl = reinterpret_cast<V*>(gout + (m + 2));         // s in the Krylov precision, m entries
+    double* gcs = reinterpret_cast<double*>(svl + m);      // m entries (last: 8-byte items)
+    V* Hl = reinterpret_cast<V*>(P.Hh);                       // Krylov-precision copy of H
+    V* Bl = reinterpret_cast<V*>(P.Hh + (size_t)(m + 1) * m);  // and of B
     for (int t = threadIdx.x; t < i; t += kBlock) {
         const double2 h = cadd(P.hsum[N + t], sv[t]);
         gcol[t] = h;
-        P.Hh[(long long)j * ldh + t] = h;
+        Hl[(long long)j * ldh + t] = from_d2<V>(h);
+        svl[t] = from_d2<V>(sv[t]);
     }
+    for (int n = threadIdx.x; n < N; n += kBlock) Bl[(long long)j * a.nmax + n] = from_d2<V>(P.hsum[n]);
     for (int t = threadIdx.x; t < j; t += kBlock) {
         gcs[t] = P.cs[t];
         gsn[t] = P.sn[t];
@@ -814,7 +841,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
         const double est = givens_column_warp(gcol, gcs, gsn, j, beta, gout, P.g, P.cs + j, P.sn + j);
         if (threadIdx.x != 0) goto dcgs2_done;
         const double anorm = sqrt(h2 + alpha);   // ||A q_{i-1}||
-        P.Hh[(long long)j * ldh + i] = make_double2(beta, 0.0);
+        Hl[(long long)j * ldh + i] = mk((T)beta, (T)0);
         S->k = i;
         S->iters += 1;
         S->hnorm = beta;
@@ -843,11 +870,10 @@ dcgs2_done:
         // row-wise sum over columns l: loads of one column are contiguous over rows
         V hst = mk((T)0, (T)0);
         if (row < N) {
-            for (int l = 0; l < i; ++l) cfma(hst, from_d2<V>(P.B[(long long)l * a.nmax + row]), from_d2<V>(sv[l]));
+            for (int l = 0; l < i; ++l) cfma(hst, Bl[(long long)l * a.nmax + row], svl[l]);
         } else {
             const int qr = row - N;  // row of H; column l holds rows 0..l+1
-            for (int l = max(0, qr - 1); l < i; ++l)
-                cfma(hst, from_d2<V>(P.Hh[(long long)l * ldh + qr]), from_d2<V>(sv[l]));
+            for (int l = max(0, qr - 1); l < i; ++l) cfma(hst, Hl[(long long)l * ldh + qr], svl[l]);
         }
         const double2 hs = to_d2(hst);
         double2 h1;
@@ -1219,7 +1245,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             P.r = c.take<double2>(ld);
             P.V = (Nreq > 0) ? (void*)c.take<V>((size_t)ld * Nreq) : nullptr;
             P.Rg = c.take<double2>((size_t)(m + 1) * m);
-            P.Hh = c.take<double2>((size_t)(m + 1) * m);
+            P.Hh = c.take<double2>((size_t)(m + 1) * m + (size_t)kMaxAug * m);   // H and B in T2
             P.tv = c.take<double2>(KP);
             P.B = c.take<double2>((size_t)kMaxAug * m);
             P.cs = c.take<double>(m);
@@ -1277,7 +1303,8 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     DDG_CHECK_CUDA(cudaMemcpyAsync(d_blk, hblk.data(), sizeof(int) * total_ctas, cudaMemcpyHostToDevice, st));
 
     const unsigned G = (unsigned)total_ctas;
-    const size_t giv_smem = 56 * (size_t)m + 128;  // Givens staging: column, sines, cosines, result
+    // Givens staging (column, sines, result, cosines) and s in the Krylov precision
+    const size_t giv_smem = 56 * (size_t)m + 128 + sizeof(V) * (size_t)m;
     const size_t upd_smem = std::max(sizeof(V) * (size_t)(Nreq + 2 * m + 2), giv_smem);
     DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_init<<<(n + 127) / 128, 128, 0, st>>>(args, n, Nreq); }));
     if (Nreq > 0) {
