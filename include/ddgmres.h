@@ -224,6 +224,33 @@ ddg_status augmented_gmres_solve_batched(ddg_context* ctx, int n, const ddg_op* 
 ddg_status pca_fit(ddg_context* ctx, const double* F, long long D, int M, int k, double* U,
                    double* sigma, void* stream);
 
+/*
+ * gmres_solve_noalloc -- gmres_solve without any device allocation.  (The paper
+ * has no counterpart: this is a library convenience.)
+ *
+ * Some callers cannot let a library call cudaMalloc: their device memory is
+ * owned in full by another allocator (a framework's caching allocator or a
+ * fixed budget that a stray cudaMalloc would break), or they cannot afford the
+ * device-wide synchronisation that cudaMalloc and cudaFree may cause.  This
+ * entry point needs no ddg_context: its whole workspace lives in one static
+ * device array of DDG_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads
+ * the library holds until the process exits.  It runs one plain restarted
+ * GMRES solve with the same kernels as gmres_solve (delayed
+ * reorthogonalisation; for DDG_C64_REFINE the inner tolerance is fixed at 1e-5).
+ *   - Sizes whose workspace exceeds the array are rejected with DDG_EINVAL
+ *     (about (restart + 4) * D * 8 bytes for DDG_C64_REFINE, twice that for
+ *     DDG_C128, plus O(restart^2) bytes: D = 128 x 128 fits restart = 200).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the array and it keeps the last call's contents (the
+ *     call initialises what must start at zero).  Calls that overlap on the GPU
+ *     (other streams, other host threads) race on it and must be serialised.
+ * Arguments and results as gmres_solve; the caller still owns b, x and A.
+ */
+#define DDG_NOALLOC_SCRATCH_BYTES (32LL << 20)
+ddg_status gmres_solve_noalloc(const ddg_op* A, const double* b, double* x, double tol, int restart,
+                               int maxit, ddg_precision prec, ddg_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

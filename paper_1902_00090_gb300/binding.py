@@ -73,6 +73,8 @@ _SIGS = {
     "gmres_solve_batched": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),
                                       C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(ddg_info),
                                       _vp]),
+    "gmres_solve_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, C.c_int,
+                                      C.POINTER(ddg_info), _vp]),
     "pca_fit": (C.c_int, [_vp, _vp, C.c_longlong, C.c_int, C.c_int, _vp, C.POINTER(C.c_double), _vp]),
     "augmented_gmres_solve_batched": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp),
                                                 C.POINTER(_vp), C.c_int, C.POINTER(_vp),
@@ -361,3 +363,19 @@ def pca_fit(ctx: Context, F, k: int, U=None, stream=None):
     _check(load().pca_fit(ctx.handle, _dev_ptr(F, torch.complex128, "F", M * D), int(D), int(M), int(k),
                           _dev_ptr(U, torch.complex128, "U", k * D), sig, _stream(stream)), "pca_fit")
     return U, list(sig)
+
+
+def gmres_solve_noalloc(A: Operator, b, x=None, tol=1e-6, restart=200, maxit=5000, precision="c128",
+                        stream=None):
+    """gmres_solve without device allocation (library-owned static scratch).
+    Returns (x, info dict, status); raises on errors other than DDG_ENOCONV."""
+    torch = _torch()
+    if x is None:
+        x = torch.zeros_like(b)
+    info = ddg_info()
+    st = load().gmres_solve_noalloc(A.handle, _dev_ptr(b, torch.complex128, "b", A.D),
+                                    _dev_ptr(x, torch.complex128, "x", A.D), float(tol), int(restart),
+                                    int(maxit), _prec(precision), C.byref(info), _stream(stream))
+    if st not in (0, 4):
+        _check(st, "gmres_solve_noalloc")
+    return x, info.as_dict(), st

@@ -24,6 +24,7 @@
 // x += V z + Q y (FP64).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "engine.cuh"
@@ -1450,4 +1451,189 @@ extern "C" ddg_status augmented_gmres_solve_batched(ddg_context* ctx, int n, con
     if (!U) { set_error("augmented_gmres_solve_batched: U is NULL"); return DDG_EINVAL; }
     return solve_entry(ctx, n, A, b, U, k, x, tol, restart, maxit, prec, info, stream,
                        "augmented_gmres_solve_batched");
+}
+
+// ---------------------------------------------------------------- solve without device allocation
+// gmres_solve_noalloc: one plain GMRES solve whose whole workspace lives in a
+// file-scope device array, for callers that must not allocate device memory.
+namespace ddg {
+
+constexpr size_t kNoAllocBytes = (size_t)DDG_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static void* g_noalloc_base[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name only stands in for it, so the address is looked up once per
+// device (with that device current) and kept.
+static ddg_status noalloc_base(char** out) {
+    int dev = 0;
+    DDG_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("gmres_solve_noalloc: device %d beyond the %d supported", dev, kNoAllocMaxDevices);
+        return DDG_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(e, "gmres_solve_noalloc: cudaGetSymbolAddress");
+        g_noalloc_base[dev] = p;
+    }
+    *out = reinterpret_cast<char*>(g_noalloc_base[dev]);
+    return DDG_OK;
+}
+
+// Same kernels and order as run_batch for one solve without augmentation and
+// the delayed reorthogonalisation; the workspace is carved from the static
+// array; polls by synchronising the stream (no pinned buffer, no events).
+template <typename T>
+static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x, double tol, int m, int maxit,
+                                     double eta, ddg_info* info, cudaStream_t st) {
+    using V = c2_t<T>;
+    const long long CH = chunk_rows<T>();
+    int KP = kMaxAug + 2 * m + 4;
+    KP = (KP + 1) & ~1;
+    SolvePtrs hp{};
+    hp.nchunks = (int)((A->D + CH - 1) / CH);
+    hp.chunk0 = 0;
+    hp.ld = (long long)hp.nchunks * CH;
+    const long long ld = hp.ld;
+    auto layout = [&](char* base) -> size_t {
+        Carver c{base};
+        hp.M = c.take<char>(sizeof(V) * (size_t)ld * (size_t)(m + 1));
+        hp.W = nullptr;
+        hp.w[0] = c.take<V>(ld);
+        hp.w[1] = c.take<V>(ld);
+        hp.r = c.take<double2>(ld);
+        hp.V = nullptr;
+        hp.Rg = c.take<double2>((size_t)(m + 1) * m);
+        hp.Hh = c.take<double2>((size_t)(m + 1) * m + (size_t)kMaxAug * m);
+        hp.tv = c.take<double2>(KP);
+        hp.B = c.take<double2>((size_t)kMaxAug * m);
+        hp.cs = c.take<double>(m);
+        hp.sn = c.take<double2>(m);
+        hp.g = c.take<double2>(m + 1);
+        hp.hsum = c.take<double2>(KP);
+        hp.hp = c.take<double2>(KP);
+        hp.part = c.take<double2>((size_t)hp.nchunks * KP);
+        hp.Rinv = c.take<double2>(1);
+        hp.Rtmp = c.take<double2>(1);
+        hp.cr = c.take<double2>(1);
+        hp.coefy = c.take<double2>(m);
+        hp.ticket = c.take<unsigned>(1);
+        return c.off;
+    };
+    size_t small_off = align_up(layout(nullptr));
+    Carver tail{nullptr, small_off};
+    tail.take<SolvePtrs>(1);
+    tail.take<SolveScal>(1);
+    tail.take<int>(hp.nchunks);
+    tail.take<int>(4);
+    const size_t need = tail.off;
+    if (need > kNoAllocBytes) {
+        set_error("gmres_solve_noalloc: this solve needs %zu bytes of scratch, more than the %zu-byte static "
+                  "buffer (use a smaller restart or grid, or gmres_solve)", need, kNoAllocBytes);
+        return DDG_EINVAL;
+    }
+    char* base = nullptr;
+    DDG_TRY(noalloc_base(&base));
+    layout(base);
+    hp.nx = A->nx;
+    hp.ny = A->ny;
+    hp.D = A->D;
+    hp.kh2 = A->kh * A->kh;
+    hp.eps_d = A->eps_d;
+    hp.coef_d = A->coef_d;
+    hp.eps_lo = sizeof(T) == 4 ? (const void*)A->eps_f : (const void*)A->eps_d;
+    hp.coef_lo = sizeof(T) == 4 ? (const void*)A->coef_f : (const void*)A->coef_d;
+    hp.b = reinterpret_cast<const double2*>(b);
+    hp.x = reinterpret_cast<double2*>(x);
+    hp.U = nullptr;
+    Carver t2{base, small_off};
+    BatchArgs args;
+    args.P = t2.take<SolvePtrs>(1);
+    args.S = t2.take<SolveScal>(1);
+    int* d_blk = t2.take<int>(hp.nchunks);
+    args.blk_solve = d_blk;
+    args.counts = t2.take<int>(4);
+    args.bytes = nullptr;
+    args.m = m;
+    args.KP = KP;
+    args.nmax = kMaxAug;
+    args.tol = tol;
+    args.eta = eta;
+    args.maxit = maxit;
+    // every launch reads these: the array keeps the previous call's contents
+    std::vector<int> hblk(hp.nchunks, 0);
+    DDG_CHECK_CUDA(cudaMemcpyAsync(args.P, &hp, sizeof(SolvePtrs), cudaMemcpyHostToDevice, st));
+    DDG_CHECK_CUDA(cudaMemcpyAsync(d_blk, hblk.data(), sizeof(int) * hp.nchunks, cudaMemcpyHostToDevice, st));
+    const unsigned G = (unsigned)hp.nchunks;
+    const size_t giv_smem = 56 * (size_t)m + 128 + sizeof(V) * (size_t)m;
+    const size_t upd_smem = std::max(sizeof(V) * (size_t)(2 * m + 2), giv_smem);
+    k_init<<<1, 128, 0, st>>>(args, 1, 0);   // also zeroes the reduction ticket
+    DDG_CHECK_LAUNCH("k_init");
+    int hc[2] = {0, 0};
+    for (long long cycle = 0; cycle <= (long long)maxit + 1; ++cycle) {
+        DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 4 * sizeof(int), st));
+        k_residual<T><<<G, kBlock, 0, st>>>(args);
+        DDG_CHECK_LAUNCH("k_residual");
+        DDG_CHECK_CUDA(cudaMemcpyAsync(hc, args.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (hc[1] == 0) break;
+        if (hc[0] > 0) {
+            k_step<T><<<G, kBlock, 0, st>>>(args, 0);
+            k_dots_w<T><<<G, kBlock, 0, st>>>(args, 0, 0);
+            k_update_w<T><<<G, kBlock, upd_smem, st>>>(args, 0, 0);
+            DDG_CHECK_LAUNCH("first Arnoldi step");
+            for (int i = 1; i <= m; ++i) {
+                if (i < m) k_stencil_u<T><<<G, kBlock, 0, st>>>(args);
+                k_dots2<T><<<G, kBlock, giv_smem, st>>>(args, i);
+                if (i < m) k_update2<T><<<G, kBlock, upd_smem, st>>>(args, i);
+                DDG_CHECK_LAUNCH("Arnoldi step");
+                if (i % 16 == 0 && i < m) {
+                    int in_cycle = 0;
+                    DDG_CHECK_CUDA(cudaMemcpyAsync(&in_cycle, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
+                    DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+                    if (in_cycle == 0) break;
+                }
+            }
+        }
+        k_backsub<<<1, 128, sizeof(double2) * (2 * (size_t)m + kMaxAug), st>>>(args);
+        k_update_x<T><<<G, kBlock, 0, st>>>(args);
+        DDG_CHECK_LAUNCH("cycle end");
+    }
+    k_finalize<T><<<G, kBlock, 0, st>>>(args);
+    DDG_CHECK_LAUNCH("k_finalize");
+    SolveScal hs;
+    DDG_CHECK_CUDA(cudaMemcpyAsync(&hs, args.S, sizeof(SolveScal), cudaMemcpyDeviceToHost, st));
+    DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (info) {
+        info->iters = hs.iters;
+        info->cycles = hs.cycles;
+        info->converged = hs.converged;
+        info->fallback_used = 0;
+        info->breakdown = hs.breakdown;
+        info->true_rel_residual = hs.true_res;
+        info->first_step_rel_residual = hs.first_res;
+    }
+    return hs.converged ? DDG_OK : DDG_ENOCONV;
+}
+
+}  // namespace ddg
+
+extern "C" ddg_status gmres_solve_noalloc(const ddg_op* A, const double* b, double* x, double tol, int restart,
+                                          int maxit, ddg_precision prec, ddg_info* info, void* stream) {
+    using namespace ddg;
+    if (!A || !b || !x) { set_error("gmres_solve_noalloc: NULL operator, b or x"); return DDG_EINVAL; }
+    if (!(tol > 0.0 && tol < 1.0)) { set_error("gmres_solve_noalloc: tol=%g outside (0,1)", tol); return DDG_EINVAL; }
+    if (restart < 1 || restart > kMaxRestart) { set_error("gmres_solve_noalloc: restart=%d outside [1,%d]", restart, kMaxRestart); return DDG_EINVAL; }
+    if (maxit < 1) { set_error("gmres_solve_noalloc: maxit=%d < 1", maxit); return DDG_EINVAL; }
+    cudaStream_t st = as_stream(stream);
+    if (prec == DDG_C128) return run_single_noalloc<double>(A, b, x, tol, restart, maxit, 0.0, info, st);
+    if (prec == DDG_C64_REFINE) return run_single_noalloc<float>(A, b, x, tol, restart, maxit, 1e-5, info, st);
+    set_error("gmres_solve_noalloc: unsupported precision %d", (int)prec);
+    return DDG_EINVAL;
 }
