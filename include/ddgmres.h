@@ -225,6 +225,52 @@ ddg_status pca_fit(ddg_context* ctx, const double* F, long long D, int M, int k,
                    double* sigma, void* stream);
 
 /*
+ * Subspace predictor (Sec. III, "Convolutional neural network", Fig. 3a): a CNN
+ * mapping the permittivity to k complex vectors v_1..v_k that span the
+ * predicted subspace, trained with the projection loss (Eq. 5) and Adam
+ * (Methods).  Architecture: `levels` resolutions with channels[l] channels, two
+ * 3x3 convolutions + ReLU per level, 2x2 average pooling between encoder levels,
+ * nearest 2x upsampling concatenated with the encoder output of the same level
+ * in the decoder, a 1x1 head to 2k channels (pair (2c, 2c+1) = (Re, Im) of v_c).
+ * Inputs per cell: (eps - 2.1)/10.15, (wavelength - 1.3 um)/0.25 um, PML mask,
+ * source profile exp(-(j - j_c)^2 / (2 sigma^2)) on column i_src.
+ * Parameters: a flat FP32 vector, per layer the weights [Cout][Cin][kh][kw]
+ * then the biases, layers in the order enc0a, enc0b, ..., enc{L-1}b,
+ * dec{L-2}a, dec{L-2}b, ..., dec0b, head.  The forward pass uses BF16 weights
+ * and activations with FP32 accumulation; gradients and Adam are FP32.
+ * A batch must share one grid size, with nx and ny divisible by 2^(levels-1).
+ */
+typedef struct ddg_predictor ddg_predictor;
+/* k complex outputs (1..16); channels: `levels` (1..8) host ints.  Weights start at 0. */
+ddg_status predictor_create(int k, int levels, const int* channels, ddg_predictor** P);
+ddg_status predictor_destroy(ddg_predictor* P);
+long long predictor_num_params(const ddg_predictor* P);
+/* theta: host, n = predictor_num_params floats.  Setting resets the Adam state. */
+ddg_status predictor_set_params(ddg_predictor* P, const float* theta, long long n);
+ddg_status predictor_get_params(const ddg_predictor* P, float* theta, long long n);
+/* Raw network output for n problems: y device FP32 [n][ny][nx][2k]. */
+ddg_status predictor_forward(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
+                             double j_c, float* y, void* stream);
+/* subspace_predict -- the predicted vectors of each problem: U[s] device, D x k
+   complex128 column-major (ready for augmented_gmres_solve).  Synchronises. */
+ddg_status subspace_predict(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
+                            double j_c, double* const* U, void* stream);
+/* Mean projection loss (Eq. 5) over the batch against the solved fields f[s]
+   (device, D complex128 each) and its gradient (kept inside the predictor; also
+   copied to `grad`, device FP32 [nparams], when not NULL).  Synchronises. */
+ddg_status predictor_loss_grad(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
+                               double j_c, const double* const* f, double* loss, float* grad, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradient. */
+ddg_status predictor_adam_step(ddg_predictor* P, float lr, void* stream);
+/* predictor_loss_grad followed by predictor_adam_step. */
+ddg_status predictor_train_step(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
+                                double j_c, const double* const* f, float lr, double* loss, void* stream);
+/* Checkpoint of the weights, Adam moments and step, with a checksum; load checks
+   the architecture and the checksum (DDG_EINVAL on mismatch). */
+ddg_status predictor_save(const ddg_predictor* P, const char* path);
+ddg_status predictor_load(ddg_predictor* P, const char* path);
+
+/*
  * gmres_solve_noalloc -- gmres_solve without any device allocation.  (The paper
  * has no counterpart: this is a library convenience.)
  *

@@ -89,6 +89,27 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
+def bf16_round(x):
+    """Round to the nearest bfloat16 (the upper 16 bits of an IEEE binary32,
+    round to nearest, ties to even); returns float64.  Used to emulate a
+    network that stores weights and activations in bfloat16."""
+    a = np.ascontiguousarray(x, dtype=np.float32).copy()
+    u = a.view(np.uint32)
+    r = ((u + np.uint32(0x7FFF) + ((u >> np.uint32(16)) & np.uint32(1))) & np.uint32(0xFFFF0000)).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def round_weights(cfg, theta, rnd):
+    """theta with every weight (not the biases) passed through rnd."""
+    out = np.array(theta, dtype=np.float64)
+    off = 0
+    for _, co, ci, kk in layer_shapes(cfg):
+        nw = co * ci * kk * kk
+        out[off:off + nw] = rnd(out[off:off + nw])
+        off += nw + co
+    return out
+
+
 # ---------------------------------------------------------------- network
 @dataclass
 class CNNConfig:
@@ -140,8 +161,10 @@ def unpack_params(cfg: CNNConfig, theta: np.ndarray):
     return out
 
 
-def forward(cfg: CNNConfig, theta, x, keep=False):
-    """x (B, H, W, cin) -> output (B, H, W, 2k); with keep, also the cache."""
+def forward(cfg: CNNConfig, theta, x, keep=False, store=None):
+    """x (B, H, W, cin) -> output (B, H, W, 2k); with keep, also the cache.
+    store (optional) is applied to every stored activation (e.g. bf16_round)."""
+    st = store if store is not None else (lambda z: z)
     P = unpack_params(cfg, theta)
     L = cfg.levels
     cache = {"x": x}
@@ -149,20 +172,20 @@ def forward(cfg: CNNConfig, theta, x, keep=False):
     skips = []
     for l in range(L):
         if l > 0:
-            h = avgpool2(h)
+            h = st(avgpool2(h))
         cache[f"in_enc{l}a"] = h
-        h = relu(conv3x3(h, *P[f"enc{l}a"]))
+        h = st(relu(conv3x3(h, *P[f"enc{l}a"])))
         cache[f"out_enc{l}a"] = h
-        h = relu(conv3x3(h, *P[f"enc{l}b"]))
+        h = st(relu(conv3x3(h, *P[f"enc{l}b"])))
         cache[f"out_enc{l}b"] = h
         skips.append(h)
     for l in range(L - 2, -1, -1):
         u = upsample2(h)
         cat = np.concatenate([u, skips[l]], axis=-1)
         cache[f"in_dec{l}a"] = cat
-        h = relu(conv3x3(cat, *P[f"dec{l}a"]))
+        h = st(relu(conv3x3(cat, *P[f"dec{l}a"])))
         cache[f"out_dec{l}a"] = h
-        h = relu(conv3x3(h, *P[f"dec{l}b"]))
+        h = st(relu(conv3x3(h, *P[f"dec{l}b"])))
         cache[f"out_dec{l}b"] = h
     cache["in_head"] = h
     y = conv1x1(h, *P["head"])
@@ -229,9 +252,9 @@ def projection_loss_and_grad(V: np.ndarray, f: np.ndarray):
     return loss, 2.0 * wb.real, 2.0 * wb.imag
 
 
-def batch_loss_and_grad(cfg: CNNConfig, theta, x, fields):
+def batch_loss_and_grad(cfg: CNNConfig, theta, x, fields, store=None):
     """Mean projection loss over the batch and its gradient w.r.t. theta."""
-    y, cache = forward(cfg, theta, x, keep=True)
+    y, cache = forward(cfg, theta, x, keep=True, store=store)
     V = to_complex_fields(y)
     B = x.shape[0]
     gy = np.zeros_like(y)

@@ -73,6 +73,21 @@ _SIGS = {
     "gmres_solve_batched": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),
                                       C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(ddg_info),
                                       _vp]),
+    "predictor_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp)]),
+    "predictor_destroy": (C.c_int, [_vp]),
+    "predictor_num_params": (C.c_longlong, [_vp]),
+    "predictor_set_params": (C.c_int, [_vp, _vp, C.c_longlong]),
+    "predictor_get_params": (C.c_int, [_vp, _vp, C.c_longlong]),
+    "predictor_forward": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_double, C.c_double, _vp, _vp]),
+    "subspace_predict": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_double, C.c_double,
+                                   C.POINTER(_vp), _vp]),
+    "predictor_loss_grad": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_double, C.c_double,
+                                      C.POINTER(_vp), C.POINTER(C.c_double), _vp, _vp]),
+    "predictor_adam_step": (C.c_int, [_vp, C.c_float, _vp]),
+    "predictor_train_step": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_double, C.c_double,
+                                       C.POINTER(_vp), C.c_float, C.POINTER(C.c_double), _vp]),
+    "predictor_save": (C.c_int, [_vp, C.c_char_p]),
+    "predictor_load": (C.c_int, [_vp, C.c_char_p]),
     "gmres_solve_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, C.c_int,
                                       C.POINTER(ddg_info), _vp]),
     "pca_fit": (C.c_int, [_vp, _vp, C.c_longlong, C.c_int, C.c_int, _vp, C.POINTER(C.c_double), _vp]),
@@ -379,3 +394,124 @@ def gmres_solve_noalloc(A: Operator, b, x=None, tol=1e-6, restart=200, maxit=500
     if st not in (0, 4):
         _check(st, "gmres_solve_noalloc")
     return x, info.as_dict(), st
+
+
+def predictor_layer_shapes(channels, k, cin=4):
+    """(name, Cout, Cin, kernel) per layer in the library's parameter order."""
+    L = len(channels)
+    out = []
+    for l in range(L):
+        out.append((f"enc{l}a", channels[l], cin if l == 0 else channels[l - 1], 3))
+        out.append((f"enc{l}b", channels[l], channels[l], 3))
+    for l in range(L - 2, -1, -1):
+        out.append((f"dec{l}a", channels[l], channels[l + 1] + channels[l], 3))
+        out.append((f"dec{l}b", channels[l], channels[l], 3))
+    out.append(("head", 2 * k, channels[0], 1))
+    return out
+
+
+class Predictor:
+    """ddg_predictor: the subspace-predicting CNN (weights on the device)."""
+
+    def __init__(self, k=8, channels=(32, 48, 64, 96, 128, 128)):
+        _torch()
+        self.k, self.channels = int(k), tuple(int(c) for c in channels)
+        arr = (C.c_int * len(self.channels))(*self.channels)
+        h = _vp()
+        _check(load().predictor_create(self.k, len(self.channels), arr, C.byref(h)), "predictor_create")
+        self._h = h
+        self.nparams = int(load().predictor_num_params(h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def layer_shapes(self):
+        return predictor_layer_shapes(self.channels, self.k)
+
+    def set_params(self, theta):
+        import numpy as np
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(load().predictor_set_params(self._h, _vp(a.ctypes.data), a.size), "predictor_set_params")
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.nparams, dtype=np.float32)
+        _check(load().predictor_get_params(self._h, _vp(a.ctypes.data), a.size), "predictor_get_params")
+        return a
+
+    def init_he(self, seed=0):
+        """He-normal weights (std sqrt(2 / fan_in)), zero biases, drawn from `seed`."""
+        import numpy as np
+        from . import inputs
+        parts = []
+        for i, (name, co, ci, kk) in enumerate(self.layer_shapes()):
+            w = inputs.standard_normal(co * ci * kk * kk, seed * 1000 + i) * np.sqrt(2.0 / (ci * kk * kk))
+            parts += [w, np.zeros(co)]
+        self.set_params(np.concatenate(parts))
+
+    def _ops(self, A):
+        return (_vp * len(A))(*[a.handle.value for a in A])
+
+    def forward(self, A, src, stream=None):
+        torch = _torch()
+        i_src, sigma, j_c = src
+        y = torch.empty((len(A), A[0].ny, A[0].nx, 2 * self.k), dtype=torch.float32, device="cuda")
+        _check(load().predictor_forward(self._h, len(A), self._ops(A), int(i_src), float(sigma), float(j_c),
+                                        _vp(y.data_ptr()), _stream(stream)), "predictor_forward")
+        return y
+
+    def predict(self, A, src, U=None, stream=None):
+        """subspace_predict: list of (k, D) complex128 tensors (D x k column-major)."""
+        torch = _torch()
+        i_src, sigma, j_c = src
+        if U is None:
+            U = [torch.empty((self.k, a.D), dtype=torch.complex128, device="cuda") for a in A]
+        arr = _ptr_array(U, torch.complex128, "U", [self.k * a.D for a in A])
+        _check(load().subspace_predict(self._h, len(A), self._ops(A), int(i_src), float(sigma), float(j_c),
+                                       arr, _stream(stream)), "subspace_predict")
+        return U
+
+    def loss_grad(self, A, src, fields, want_grad=True, stream=None):
+        torch = _torch()
+        i_src, sigma, j_c = src
+        loss = C.c_double()
+        g = torch.empty(self.nparams, dtype=torch.float32, device="cuda") if want_grad else None
+        arr = _ptr_array(fields, torch.complex128, "f", [a.D for a in A])
+        _check(load().predictor_loss_grad(self._h, len(A), self._ops(A), int(i_src), float(sigma), float(j_c),
+                                          arr, C.byref(loss), _vp(g.data_ptr()) if g is not None else None,
+                                          _stream(stream)), "predictor_loss_grad")
+        return loss.value, g
+
+    def adam_step(self, lr, stream=None):
+        _check(load().predictor_adam_step(self._h, float(lr), _stream(stream)), "predictor_adam_step")
+
+    def train_step(self, A, src, fields, lr, stream=None):
+        torch = _torch()
+        i_src, sigma, j_c = src
+        loss = C.c_double()
+        arr = _ptr_array(fields, torch.complex128, "f", [a.D for a in A])
+        _check(load().predictor_train_step(self._h, len(A), self._ops(A), int(i_src), float(sigma), float(j_c),
+                                           arr, float(lr), C.byref(loss), _stream(stream)), "predictor_train_step")
+        return loss.value
+
+    def save(self, path):
+        _check(load().predictor_save(self._h, str(path).encode()), "predictor_save")
+
+    def load_file(self, path):
+        _check(load().predictor_load(self._h, str(path).encode()), "predictor_load")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().predictor_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def predictor_create(k=8, channels=(32, 48, 64, 96, 128, 128)) -> Predictor:
+    return Predictor(k, channels)

@@ -1,0 +1,1021 @@
+// Subspace-predicting CNN (Sec. III, "Convolutional neural network", Fig. 3a):
+// permittivity and cheap input channels -> 2k real channels = k complex
+// vectors v_1..v_k spanning the predicted subspace; trained on solved fields
+// with the projection loss (Eq. 5) and Adam (Methods).
+//
+// Architecture (the paper gives none): `levels` resolutions, two 3x3
+// convolutions + ReLU per level, 2x2 average pooling between encoder levels,
+// nearest 2x upsampling concatenated with the encoder output of the same level
+// in the decoder, a 1x1 head to 2k channels.  NHWC tensors; weights
+// [Cout][Cin][3][3] then bias per layer, in the order enc0a, enc0b, ...,
+// enc{L-1}b, dec{L-2}a, dec{L-2}b, ..., dec0b, head.
+//
+// Precision: FP32 master weights and Adam moments; BF16 copies of the weights
+// and BF16 activations in the forward pass; FP32 accumulation; FP32 gradients.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "engine.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace ddg {
+namespace cnn {
+
+constexpr int kMaxLevels = 8;
+constexpr int TX = 32, TY = 16;   // output tile (pixels)
+constexpr int COB = 16;           // output channels per CTA
+constexpr int CIB = 8;            // input channels per shared-memory chunk
+
+struct Layer {
+    int co, ci, kk;
+    long long w_off, b_off;
+};
+
+// ---------------------------------------------------------------- input loaders
+// Forward / weight-gradient input: channels [0, c1) from x1 (half resolution
+// when up1: nearest upsampling), channels [c1, c1 + c2) from x2.
+struct LoadCat {
+    const bf16* x1;
+    int c1, up1, h1, w1;  // dimensions of x1's own grid
+    const bf16* x2;
+    int c2;
+    __device__ __forceinline__ float operator()(int b, int y, int x, int H, int W, int c) const {
+        if (c < c1) {
+            if (up1) return __bfloat162float(x1[(((long long)b * h1 + (y >> 1)) * w1 + (x >> 1)) * c1 + c]);
+            return __bfloat162float(x1[(((long long)b * H + y) * W + x) * c1 + c]);
+        }
+        return __bfloat162float(x2[(((long long)b * H + y) * W + x) * c2 + (c - c1)]);
+    }
+};
+
+// Gradient input of the backward-data convolution: g masked by ReLU'(out).
+struct LoadGrad {
+    const float* g;
+    const bf16* y;   // forward output after ReLU (mask = y > 0)
+    int C;
+    __device__ __forceinline__ float operator()(int b, int yy, int x, int H, int W, int c) const {
+        const long long i = (((long long)b * H + yy) * W + x) * C + c;
+        return __bfloat162float(y[i]) > 0.f ? g[i] : 0.f;
+    }
+};
+
+__device__ __forceinline__ void store_out(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void store_out(float* p, float v) { *p = v; }
+
+// ---------------------------------------------------------------- 3x3 convolution
+// out[b, y, x, co] = bias[co] + sum_{ci, dy, dx} in[b, y+dy-1, x+dx-1, ci] wk[ci][3 dy + dx][co]
+// (zero padding), optional ReLU.  One CTA: a 32x16 pixel tile, 16 output
+// channels; each thread two neighbouring pixels of one row.  wk is BF16
+// [Ci][9][Co].
+template <class LD, typename TOUT>
+__global__ void __launch_bounds__(256) k_conv3(LD ld, int B, int H, int W, int Ci, int Co,
+                                               const bf16* __restrict__ wk, const float* __restrict__ bias,
+                                               int relu, TOUT* __restrict__ out) {
+    __shared__ float s_in[CIB][TY + 2][TX + 2];
+    __shared__ __align__(16) float s_w[CIB][9][COB];
+    const int ncob = (Co + COB - 1) / COB;
+    const int b = blockIdx.z / ncob, cob = blockIdx.z % ncob;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int t = threadIdx.x, ty = t >> 4, tx2 = (t & 15) * 2;
+    float acc0[COB], acc1[COB];
+#pragma unroll
+    for (int c = 0; c < COB; ++c) acc0[c] = acc1[c] = 0.f;
+    for (int c0 = 0; c0 < Ci; c0 += CIB) {
+        __syncthreads();
+        for (int idx = t; idx < CIB * (TY + 2) * (TX + 2); idx += 256) {
+            const int c = idx / ((TY + 2) * (TX + 2));
+            const int r = (idx / (TX + 2)) % (TY + 2);
+            const int q = idx % (TX + 2);
+            const int yy = y0 + r - 1, xx = x0 + q - 1, ci = c0 + c;
+            float v = 0.f;
+            if (ci < Ci && yy >= 0 && yy < H && xx >= 0 && xx < W) v = ld(b, yy, xx, H, W, ci);
+            s_in[c][r][q] = v;
+        }
+        for (int idx = t; idx < CIB * 9 * COB; idx += 256) {
+            const int c = idx / (9 * COB), tap = (idx / COB) % 9, o = idx % COB;
+            const int ci = c0 + c, co = cob * COB + o;
+            s_w[c][tap][o] = (ci < Ci && co < Co) ? __bfloat162float(wk[((long long)ci * 9 + tap) * Co + co]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int c = 0; c < CIB; ++c) {
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy) {
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const float v0 = s_in[c][ty + dy][tx2 + dx];
+                    const float v1 = s_in[c][ty + dy][tx2 + 1 + dx];
+                    const float4* wp = reinterpret_cast<const float4*>(&s_w[c][dy * 3 + dx][0]);
+#pragma unroll
+                    for (int q = 0; q < COB / 4; ++q) {
+                        const float4 w4 = wp[q];
+                        acc0[4 * q + 0] = fmaf(v0, w4.x, acc0[4 * q + 0]);
+                        acc0[4 * q + 1] = fmaf(v0, w4.y, acc0[4 * q + 1]);
+                        acc0[4 * q + 2] = fmaf(v0, w4.z, acc0[4 * q + 2]);
+                        acc0[4 * q + 3] = fmaf(v0, w4.w, acc0[4 * q + 3]);
+                        acc1[4 * q + 0] = fmaf(v1, w4.x, acc1[4 * q + 0]);
+                        acc1[4 * q + 1] = fmaf(v1, w4.y, acc1[4 * q + 1]);
+                        acc1[4 * q + 2] = fmaf(v1, w4.z, acc1[4 * q + 2]);
+                        acc1[4 * q + 3] = fmaf(v1, w4.w, acc1[4 * q + 3]);
+                    }
+                }
+            }
+        }
+    }
+    const int y = y0 + ty;
+    if (y >= H) return;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int x = x0 + tx2 + p;
+        if (x >= W) continue;
+        TOUT* o = out + (((long long)b * H + y) * W + x) * Co;
+#pragma unroll
+        for (int c = 0; c < COB; ++c) {
+            const int co = cob * COB + c;
+            if (co >= Co) break;
+            float v = (p == 0 ? acc0[c] : acc1[c]) + (bias ? bias[co] : 0.f);
+            if (relu) v = fmaxf(v, 0.f);
+            store_out(o + co, v);
+        }
+    }
+}
+
+// Weight gradient of a 3x3 convolution: dW[co][ci][tap] += sum_p g[p, co] in[p + tap, ci],
+// db[co] += sum_p g[p, co], with g masked by ReLU'(out).  One CTA: 16 output x
+// 16 input channels (one (co, ci) pair per thread, 9 taps) over a slice of
+// 16x16 pixel tiles; partial sums added atomically.
+template <class LX>
+__global__ void __launch_bounds__(256) k_conv3_wgrad(LX lx, const float* __restrict__ g, const bf16* __restrict__ yout,
+                                                     int B, int H, int W, int Ci, int Co, int tiles_per_cta,
+                                                     float* __restrict__ dW, float* __restrict__ db) {
+    __shared__ float s_g[256][17];
+    __shared__ float s_x[16][18][19];
+    const int nci = (Ci + 15) / 16;
+    const int cob = blockIdx.y / nci, cib = blockIdx.y % nci;
+    const int t = threadIdx.x, o = t >> 4, i = t & 15;
+    const int co = cob * 16 + o, ci = cib * 16 + i;
+    const int tw = (W + 15) / 16, th = (H + 15) / 16;
+    const long long ntiles = (long long)B * tw * th;
+    float acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.f;
+    float accb = 0.f;
+    for (long long tile = (long long)blockIdx.x * tiles_per_cta;
+         tile < min(ntiles, (long long)(blockIdx.x + 1) * tiles_per_cta); ++tile) {
+        const int b = (int)(tile / (tw * th));
+        const int rem = (int)(tile % (tw * th));
+        const int y0 = (rem / tw) * 16, x0 = (rem % tw) * 16;
+        __syncthreads();
+        for (int idx = t; idx < 256 * 16; idx += 256) {
+            const int p = idx >> 4, c = idx & 15;
+            const int yy = y0 + (p >> 4), xx = x0 + (p & 15), cc = cob * 16 + c;
+            float v = 0.f;
+            if (yy < H && xx < W && cc < Co) {
+                const long long q = (((long long)b * H + yy) * W + xx) * Co + cc;
+                v = __bfloat162float(yout[q]) > 0.f ? g[q] : 0.f;
+            }
+            s_g[p][c] = v;
+        }
+        for (int idx = t; idx < 16 * 18 * 18; idx += 256) {
+            const int c = idx / (18 * 18), r = (idx / 18) % 18, q = idx % 18;
+            const int yy = y0 + r - 1, xx = x0 + q - 1, cc = cib * 16 + c;
+            float v = 0.f;
+            if (cc < Ci && yy >= 0 && yy < H && xx >= 0 && xx < W) v = lx(b, yy, xx, H, W, cc);
+            s_x[c][r][q] = v;
+        }
+        __syncthreads();
+        for (int p = 0; p < 256; ++p) {
+            const float gv = s_g[p][o];
+            const int py = p >> 4, px = p & 15;
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) acc[dy * 3 + dx] = fmaf(gv, s_x[i][py + dy][px + dx], acc[dy * 3 + dx]);
+            accb += gv;
+        }
+    }
+    if (co < Co && ci < Ci) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) atomicAdd(dW + ((long long)co * Ci + ci) * 9 + k, acc[k]);
+    }
+    if (i == 0 && cib == 0 && co < Co) atomicAdd(db + co, accb);
+}
+
+// ---------------------------------------------------------------- small kernels
+// forward weights BF16 [co][ci][9] -> [ci][9][co]
+__global__ void k_w_fwd(const bf16* __restrict__ w, int Co, int Ci, bf16* __restrict__ wk) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)Co * Ci * 9) return;
+    const int co = (int)(idx / (Ci * 9)), ci = (int)((idx / 9) % Ci), tap = (int)(idx % 9);
+    wk[((long long)ci * 9 + tap) * Co + co] = w[idx];
+}
+// backward-data weights: input channel = co, output channel = ci, taps flipped:
+// wb[co][tap'][ci] = w[co][ci][8 - tap']
+__global__ void k_w_bwd(const bf16* __restrict__ w, int Co, int Ci, bf16* __restrict__ wb) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)Co * Ci * 9) return;
+    const int co = (int)(idx / (Ci * 9)), ci = (int)((idx / 9) % Ci), tap = (int)(idx % 9);
+    wb[((long long)co * 9 + (8 - tap)) * Ci + ci] = w[idx];
+}
+
+__global__ void k_avgpool2(const bf16* __restrict__ x, int B, int H, int W, int C, bf16* __restrict__ y) {
+    const long long n = (long long)B * (H / 2) * (W / 2) * C;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int c = (int)(idx % C);
+    long long p = idx / C;
+    const int xo = (int)(p % (W / 2));
+    p /= (W / 2);
+    const int yo = (int)(p % (H / 2));
+    const int b = (int)(p / (H / 2));
+    auto at = [&](int yy, int xx) { return __bfloat162float(x[(((long long)b * H + yy) * W + xx) * C + c]); };
+    const float s = at(2 * yo, 2 * xo) + at(2 * yo, 2 * xo + 1) + at(2 * yo + 1, 2 * xo) + at(2 * yo + 1, 2 * xo + 1);
+    y[idx] = __float2bfloat16_rn(0.25f * s);
+}
+
+// g_in[b, y, x, c] (+)= g_out[b, y/2, x/2, c] / 4  (backward of the average pool)
+__global__ void k_avgpool2_bwd(const float* __restrict__ go, int B, int H, int W, int C, float* __restrict__ gi,
+                               int accumulate) {
+    const long long n = (long long)B * H * W * C;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int c = (int)(idx % C);
+    long long p = idx / C;
+    const int x = (int)(p % W);
+    p /= W;
+    const int y = (int)(p % H);
+    const int b = (int)(p / H);
+    const float v = 0.25f * go[(((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
+    gi[idx] = accumulate ? gi[idx] + v : v;
+}
+
+// Splits the gradient of a concatenated decoder input [up(h) | skip]:
+// g_h[b, y', x', c] = sum of the 2x2 block (c < cu); g_skip = remaining channels.
+__global__ void k_split_cat_bwd(const float* __restrict__ gx, int B, int H, int W, int cu, int cs,
+                                float* __restrict__ gh, float* __restrict__ gskip) {
+    const int C = cu + cs;
+    const long long nlow = (long long)B * (H / 2) * (W / 2) * cu;
+    const long long nsk = (long long)B * H * W * cs;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < nlow) {
+        const int c = (int)(idx % cu);
+        long long p = idx / cu;
+        const int xo = (int)(p % (W / 2));
+        p /= (W / 2);
+        const int yo = (int)(p % (H / 2));
+        const int b = (int)(p / (H / 2));
+        float s = 0.f;
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx)
+                s += gx[(((long long)b * H + 2 * yo + dy) * W + 2 * xo + dx) * C + c];
+        gh[idx] = s;
+    } else if (idx < nlow + nsk) {
+        const long long j = idx - nlow;
+        const int c = (int)(j % cs);
+        const long long p = j / cs;
+        gskip[j] = gx[p * C + cu + c];
+    }
+}
+
+__global__ void k_add(float* __restrict__ a, const float* __restrict__ b, long long n) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n) a[idx] += b[idx];
+}
+
+// 1x1 head: y[p, o] = b[o] + sum_c h[p, c] w[o][c]   (FP32 output)
+__global__ void k_head_fwd(const bf16* __restrict__ h, long long P, int C, int O, const bf16* __restrict__ w,
+                           const float* __restrict__ bias, float* __restrict__ y) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= P * O) return;
+    const long long p = idx / O;
+    const int o = (int)(idx % O);
+    float s = bias[o];
+    for (int c = 0; c < C; ++c) s = fmaf(__bfloat162float(h[p * C + c]), __bfloat162float(w[(long long)o * C + c]), s);
+    y[idx] = s;
+}
+
+// head backward: gh[p, c] = sum_o gy[p, o] w[o][c]; dW[o][c] += sum_p gy[p, o] h[p, c]; db[o] += sum_p gy
+__global__ void k_head_bwd_data(const float* __restrict__ gy, long long P, int C, int O, const bf16* __restrict__ w,
+                                float* __restrict__ gh) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= P * C) return;
+    const long long p = idx / C;
+    const int c = (int)(idx % C);
+    float s = 0.f;
+    for (int o = 0; o < O; ++o) s = fmaf(gy[p * O + o], __bfloat162float(w[(long long)o * C + c]), s);
+    gh[idx] = s;
+}
+__global__ void k_head_bwd_w(const float* __restrict__ gy, const bf16* __restrict__ h, long long P, int C, int O,
+                             float* __restrict__ dW, float* __restrict__ db) {
+    // one CTA per (o, c) pair (+ one row c == C for the bias); block reduction over pixels
+    const int o = blockIdx.x / (C + 1), c = blockIdx.x % (C + 1);
+    float s = 0.f;
+    for (long long p = threadIdx.x; p < P; p += blockDim.x)
+        s += gy[p * O + o] * (c < C ? __bfloat162float(h[p * C + c]) : 1.f);
+    for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    __shared__ float sm[32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float tot = 0.f;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot += sm[w2];
+        if (c < C) dW[(long long)o * C + c] += tot;
+        else db[o] += tot;
+    }
+}
+
+// network input: (eps - 2.1)/10.15, (lambda - 1.3um)/0.25um, PML mask, source profile
+struct InputDesc {
+    const double* eps;
+    int nx, ny, npml;
+    double wavelength;
+};
+__global__ void k_input(const InputDesc* __restrict__ desc, int B, int H, int W, int i_src, double sigma, double j_c,
+                        bf16* __restrict__ x) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)B * H * W) return;
+    const int b = (int)(idx / ((long long)H * W));
+    const int e = (int)(idx % ((long long)H * W));
+    const int j = e / W, i = e % W;
+    const InputDesc d = desc[b];
+    const int L = d.npml;
+    const bool inside = i >= L && i < W - L && j >= L && j < H - L;
+    const double t = (double)j - j_c;
+    bf16* o = x + idx * 4;
+    o[0] = __float2bfloat16_rn((float)((d.eps[e] - 2.1) / 10.15));
+    o[1] = __float2bfloat16_rn((float)((d.wavelength - 1.3e-6) / 0.25e-6));
+    o[2] = __float2bfloat16_rn(inside ? 0.f : 1.f);
+    o[3] = __float2bfloat16_rn(i == i_src ? (float)exp(-t * t / (2.0 * sigma * sigma)) : 0.f);
+}
+
+// Projection loss (Eq. 5) per sample and d loss / d y for the batch mean.
+// One CTA per sample: a = V^H f, G = V^H V (warp per entry, FP32 sums over
+// the pixels of a lane, FP64 across lanes), Cholesky solve G z = a (FP64,
+// tiny ridge), l = 1 - Re(a^H z)/|f|^2, gy = 2 (Re, Im) of -(f - V z) z^H /(|f|^2 B).
+__global__ void __launch_bounds__(256) k_proj_loss(const float* __restrict__ y, const double2* const* __restrict__ f,
+                                                   int D, int k, int B, double* __restrict__ loss,
+                                                   float* __restrict__ gy) {
+    extern __shared__ double2 sh[];   // a (k), G (k*k), z (k)
+    const int s = blockIdx.x;
+    const float* ys = y + (long long)s * D * 2 * k;
+    const double2* fs = f[s];
+    float* gs = gy + (long long)s * D * 2 * k;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double2* a = sh;
+    double2* G = sh + k;
+    double2* z = sh + k + k * k;
+    __shared__ double sF;
+    // entries: 0..k-1 -> a_c ; k.. -> G(c, d) for c <= d ; last -> |f|^2
+    const int nent = k + k * (k + 1) / 2 + 1;
+    for (int ent = wid; ent < nent; ent += nw) {
+        float sr = 0.f, si = 0.f;
+        if (ent < k) {
+            const int c = ent;
+            for (int e = lane; e < D; e += 32) {
+                const float vr = ys[(long long)e * 2 * k + 2 * c], vi = ys[(long long)e * 2 * k + 2 * c + 1];
+                const double2 fe = fs[e];
+                const float fr = (float)fe.x, fi = (float)fe.y;
+                sr += vr * fr + vi * fi;
+                si += vr * fi - vi * fr;
+            }
+        } else if (ent < nent - 1) {
+            int q = ent - k, c = 0;
+            while (q >= k - c) { q -= k - c; ++c; }
+            const int d = c + q;
+            for (int e = lane; e < D; e += 32) {
+                const float cr = ys[(long long)e * 2 * k + 2 * c], ci = ys[(long long)e * 2 * k + 2 * c + 1];
+                const float dr = ys[(long long)e * 2 * k + 2 * d], di = ys[(long long)e * 2 * k + 2 * d + 1];
+                sr += cr * dr + ci * di;
+                si += cr * di - ci * dr;
+            }
+        } else {
+            for (int e = lane; e < D; e += 32) {
+                const double2 fe = fs[e];
+                sr += (float)(fe.x * fe.x + fe.y * fe.y);
+            }
+        }
+        double dr = sr, di = si;
+        for (int m = 16; m > 0; m >>= 1) {
+            dr += __shfl_xor_sync(0xffffffffu, dr, m);
+            di += __shfl_xor_sync(0xffffffffu, di, m);
+        }
+        if (lane == 0) {
+            if (ent < k) a[ent] = make_double2(dr, di);
+            else if (ent < nent - 1) {
+                int q = ent - k, c = 0;
+                while (q >= k - c) { q -= k - c; ++c; }
+                const int d = c + q;
+                G[d * k + c] = make_double2(dr, di);       // G(c, d)
+                G[c * k + d] = make_double2(dr, -di);      // G(d, c)
+            } else sF = dr;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // Cholesky G = R^H R (upper R in place, column-major), ridge 1e-10 max diag
+        double dmax = 0.0;
+        for (int c = 0; c < k; ++c) dmax = fmax(dmax, G[c * k + c].x);
+        for (int c = 0; c < k; ++c) G[c * k + c].x += 1e-10 * dmax + 1e-300;
+        for (int p = 0; p < k; ++p) {
+            double dd = G[p * k + p].x;
+            for (int l = 0; l < p; ++l) dd -= cabs2(G[p * k + l]);
+            const double rpp = sqrt(fmax(dd, 1e-300));
+            G[p * k + p] = make_double2(rpp, 0.0);
+            for (int q = p + 1; q < k; ++q) {
+                double2 tq = G[q * k + p];
+                for (int l = 0; l < p; ++l) tq = csub(tq, cmulc(G[p * k + l], G[q * k + l]));
+                G[q * k + p] = cscale(tq, 1.0 / rpp);
+            }
+        }
+        // R^H w = a (forward), R z = w (backward)
+        for (int p = 0; p < k; ++p) {
+            double2 tq = a[p];
+            for (int l = 0; l < p; ++l) tq = csub(tq, cmulc(G[p * k + l], z[l]));
+            z[p] = cscale(tq, 1.0 / G[p * k + p].x);
+        }
+        for (int p = k - 1; p >= 0; --p) {
+            double2 tq = z[p];
+            for (int l = p + 1; l < k; ++l) tq = csub(tq, cmul(G[l * k + p], z[l]));
+            z[p] = cscale(tq, 1.0 / G[p * k + p].x);
+        }
+        double az = 0.0;
+        for (int c = 0; c < k; ++c) az += a[c].x * z[c].x + a[c].y * z[c].y;   // Re(a^H z)
+        loss[s] = 1.0 - az / sF;
+    }
+    __syncthreads();
+    const float scale = (float)(-2.0 / (sF * B));
+    for (int e = threadIdx.x; e < D; e += blockDim.x) {
+        const double2 fe = fs[e];
+        float rr = (float)fe.x, ri = (float)fe.y;
+        for (int c = 0; c < k; ++c) {
+            const float vr = ys[(long long)e * 2 * k + 2 * c], vi = ys[(long long)e * 2 * k + 2 * c + 1];
+            const float zr = (float)z[c].x, zi = (float)z[c].y;
+            rr -= vr * zr - vi * zi;
+            ri -= vr * zi + vi * zr;
+        }
+        for (int c = 0; c < k; ++c) {
+            const float zr = (float)z[c].x, zi = (float)z[c].y;
+            // r conj(z_c)
+            gs[(long long)e * 2 * k + 2 * c] = scale * (rr * zr + ri * zi);
+            gs[(long long)e * 2 * k + 2 * c + 1] = scale * (ri * zr - rr * zi);
+        }
+    }
+}
+
+// Adam (Kingma & Ba 2015, Algorithm 1) on the FP32 master weights; refreshes the BF16 copy.
+__global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       bf16* __restrict__ thb, long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float t = th[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    th[i] = t;
+    thb[i] = __float2bfloat16_rn(t);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, bf16* __restrict__ b, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+}
+
+// network output (B, D, 2k) FP32 -> U_b (D x k complex128, column-major)
+__global__ void k_to_complex(const float* __restrict__ y, int D, int k, double2* const* __restrict__ U, int B) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)B * D * k) return;
+    const int b = (int)(idx / ((long long)D * k));
+    const long long r = idx % ((long long)D * k);
+    const int c = (int)(r / D), e = (int)(r % D);
+    const float* ye = y + ((long long)b * D + e) * 2 * k;
+    U[b][(long long)c * D + e] = make_double2(ye[2 * c], ye[2 * c + 1]);
+}
+
+inline unsigned nblk(long long n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace cnn
+}  // namespace ddg
+
+// ---------------------------------------------------------------- predictor object
+struct ddg_predictor {
+    int cin = 4, levels = 0, k = 0;
+    int ch[ddg::cnn::kMaxLevels] = {};
+    int device = 0;
+    long long nparams = 0;
+    std::vector<ddg::cnn::Layer> layers;
+    float* theta = nullptr;       // FP32 master
+    bf16* theta_bf = nullptr;     // BF16 copy
+    float* grad = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    long long step = 0;
+    bf16* wk = nullptr;           // per-layer re-laid-out BF16 weights (forward / backward)
+    // activation workspace
+    void* act = nullptr;
+    size_t act_bytes = 0;
+    double* d_loss = nullptr;     // per-sample losses
+    void* d_desc = nullptr;       // InputDesc / pointer arrays (device)
+    size_t desc_bytes = 0;
+};
+
+namespace ddg {
+namespace cnn {
+
+static int layer_index(const ddg_predictor* P, bool dec, int level, int ab) {
+    // enc l: 2l + ab ; dec l (l = L-2 .. 0): 2L + 2 (L-2-l) + ab ; head: last
+    if (!dec) return 2 * level + ab;
+    return 2 * P->levels + 2 * (P->levels - 2 - level) + ab;
+}
+
+struct Acts {
+    // device pointers for one batch size / grid
+    bf16* x0;
+    bf16* ea[kMaxLevels];
+    bf16* eb[kMaxLevels];
+    bf16* pooled[kMaxLevels];
+    bf16* da[kMaxLevels];
+    bf16* db[kMaxLevels];
+    float* y;
+    float* gy;
+    float* g1;     // scratch gradients (largest tensor)
+    float* g2;
+    float* g3;
+    float* gskip[kMaxLevels];
+};
+
+static size_t plan_acts(const ddg_predictor* P, int B, int H, int W, char* base, Acts* A) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        off = (off + 255) / 256 * 256;
+        char* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    const int L = P->levels;
+    size_t maxg = 0;
+    A->x0 = (bf16*)take(sizeof(bf16) * (size_t)B * H * W * P->cin);
+    for (int l = 0; l < L; ++l) {
+        const size_t px = (size_t)B * (H >> l) * (W >> l);
+        if (l > 0) A->pooled[l] = (bf16*)take(sizeof(bf16) * px * P->ch[l - 1]);
+        A->ea[l] = (bf16*)take(sizeof(bf16) * px * P->ch[l]);
+        A->eb[l] = (bf16*)take(sizeof(bf16) * px * P->ch[l]);
+        if (l < L - 1) {
+            A->da[l] = (bf16*)take(sizeof(bf16) * px * P->ch[l]);
+            A->db[l] = (bf16*)take(sizeof(bf16) * px * P->ch[l]);
+            A->gskip[l] = (float*)take(sizeof(float) * px * P->ch[l]);
+            maxg = std::max(maxg, px * (size_t)(P->ch[l] + P->ch[l + 1]));
+        }
+        maxg = std::max(maxg, px * (size_t)std::max(P->ch[l], l > 0 ? P->ch[l - 1] : P->cin));
+    }
+    A->y = (float*)take(sizeof(float) * (size_t)B * H * W * 2 * P->k);
+    A->gy = (float*)take(sizeof(float) * (size_t)B * H * W * 2 * P->k);
+    A->g1 = (float*)take(sizeof(float) * maxg);
+    A->g2 = (float*)take(sizeof(float) * maxg);
+    A->g3 = (float*)take(sizeof(float) * maxg);
+    return off + 256;
+}
+
+static ddg_status ensure_acts(ddg_predictor* P, int B, int H, int W, Acts* A) {
+    const size_t need = plan_acts(P, B, H, W, nullptr, A);
+    if (need > P->act_bytes) {
+        cudaFree(P->act);
+        P->act = nullptr;
+        P->act_bytes = 0;
+        cudaError_t e = cudaMalloc(&P->act, need);
+        if (e != cudaSuccess) { cudaGetLastError(); set_error("predictor: cudaMalloc of %zu bytes failed", need); return DDG_ENOMEM; }
+        P->act_bytes = need;
+    }
+    plan_acts(P, B, H, W, reinterpret_cast<char*>(P->act), A);
+    return DDG_OK;
+}
+
+static const bf16* wbf(const ddg_predictor* P, int li) { return P->theta_bf + P->layers[li].w_off; }
+static const float* bias32(const ddg_predictor* P, int li) { return P->theta + P->layers[li].b_off; }
+
+template <class LD, typename TOUT>
+static ddg_status conv3(ddg_predictor* P, const LD& ld, int B, int H, int W, int Ci, int Co, const bf16* wk,
+                        const float* bias, int relu, TOUT* out, cudaStream_t st) {
+    dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, B * ((Co + COB - 1) / COB));
+    k_conv3<LD, TOUT><<<grid, 256, 0, st>>>(ld, B, H, W, Ci, Co, wk, bias, relu, out);
+    DDG_CHECK_LAUNCH("k_conv3");
+    return DDG_OK;
+}
+
+// forward pass for B samples of one grid size; result in A->y
+static ddg_status forward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaStream_t st) {
+    const int L = P->levels;
+    const bf16* h = A->x0;
+    int hc = P->cin;
+    for (int l = 0; l < L; ++l) {
+        const int Hl = H >> l, Wl = W >> l;
+        const bf16* in = h;
+        if (l > 0) {
+            k_avgpool2<<<nblk((long long)B * Hl * Wl * hc), 256, 0, st>>>(h, B, Hl * 2, Wl * 2, hc, A->pooled[l]);
+            in = A->pooled[l];
+        }
+        for (int ab = 0; ab < 2; ++ab) {
+            const int li = layer_index(P, false, l, ab);
+            const Layer& Ly = P->layers[li];
+            k_w_fwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
+            LoadCat ld{ab == 0 ? in : A->ea[l], Ly.ci, 0, Hl, Wl, nullptr, 0};
+            DDG_TRY(conv3(P, ld, B, Hl, Wl, Ly.ci, Ly.co, P->wk, bias32(P, li), 1, ab == 0 ? A->ea[l] : A->eb[l], st));
+        }
+        h = A->eb[l];
+        hc = P->ch[l];
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        const int Hl = H >> l, Wl = W >> l;
+        for (int ab = 0; ab < 2; ++ab) {
+            const int li = layer_index(P, true, l, ab);
+            const Layer& Ly = P->layers[li];
+            k_w_fwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
+            LoadCat ld = ab == 0 ? LoadCat{h, hc, 1, Hl / 2, Wl / 2, A->eb[l], P->ch[l]}
+                                 : LoadCat{A->da[l], Ly.ci, 0, Hl, Wl, nullptr, 0};
+            DDG_TRY(conv3(P, ld, B, Hl, Wl, Ly.ci, Ly.co, P->wk, bias32(P, li), 1, ab == 0 ? A->da[l] : A->db[l], st));
+        }
+        h = A->db[l];
+        hc = P->ch[l];
+    }
+    const int lh = (int)P->layers.size() - 1;
+    k_head_fwd<<<nblk((long long)B * H * W * 2 * P->k), 256, 0, st>>>(h, (long long)B * H * W, hc, 2 * P->k, wbf(P, lh),
+                                                                    bias32(P, lh), A->y);
+    DDG_CHECK_LAUNCH("forward");
+    return DDG_OK;
+}
+
+static unsigned wgrad_slices(long long ntiles, int blocks_yz) {
+    long long want = std::max(1LL, (long long)(4 * 152) / std::max(1, blocks_yz));
+    return (unsigned)std::min(ntiles, want);
+}
+
+template <class LX>
+static ddg_status wgrad(ddg_predictor* P, const LX& lx, const float* g, const bf16* yout, int B, int H, int W, int li,
+                        cudaStream_t st) {
+    const Layer& Ly = P->layers[li];
+    const long long ntiles = (long long)B * ((W + 15) / 16) * ((H + 15) / 16);
+    const int gy = ((Ly.co + 15) / 16) * ((Ly.ci + 15) / 16);
+    const unsigned sl = wgrad_slices(ntiles, gy);
+    const int per = (int)((ntiles + sl - 1) / sl);
+    dim3 grid(sl, gy);
+    k_conv3_wgrad<LX><<<grid, 256, 0, st>>>(lx, g, yout, B, H, W, Ly.ci, Ly.co, per, P->grad + Ly.w_off,
+                                            P->grad + Ly.b_off);
+    DDG_CHECK_LAUNCH("k_conv3_wgrad");
+    return DDG_OK;
+}
+
+// gradient w.r.t. the input of conv layer li given the gradient g of its output (masked by ReLU'(yout))
+static ddg_status bdata(ddg_predictor* P, const float* g, const bf16* yout, int B, int H, int W, int li, float* gx,
+                        cudaStream_t st) {
+    const Layer& Ly = P->layers[li];
+    k_w_bwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
+    LoadGrad ld{g, yout, Ly.co};
+    return conv3(P, ld, B, H, W, Ly.co, Ly.ci, P->wk, (const float*)nullptr, 0, gx, st);
+}
+
+// backward pass: A->gy holds d loss / d y; accumulates into P->grad
+static ddg_status backward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaStream_t st) {
+    const int L = P->levels;
+    const int lh = (int)P->layers.size() - 1;
+    const long long px0 = (long long)B * H * W;
+    const int O = 2 * P->k, C0 = P->ch[0];
+    const bf16* hin = L > 1 ? A->db[0] : A->eb[0];   // input of the 1x1 head
+    k_head_bwd_w<<<O * (C0 + 1), 256, 0, st>>>(A->gy, hin, px0, C0, O, P->grad + P->layers[lh].w_off,
+                                              P->grad + P->layers[lh].b_off);
+    k_head_bwd_data<<<nblk(px0 * C0), 256, 0, st>>>(A->gy, px0, C0, O, wbf(P, lh), A->g1);
+    DDG_CHECK_LAUNCH("head backward");
+    float* gh = A->g1;      // gradient w.r.t. the current level's output (post-ReLU)
+    float* ga = A->g2;
+    float* gx = A->g3;
+    for (int l = 0; l <= L - 2; ++l) {
+        const int Hl = H >> l, Wl = W >> l;
+        const int lb = layer_index(P, true, l, 1), la = layer_index(P, true, l, 0);
+        LoadCat xb{A->da[l], P->ch[l], 0, Hl, Wl, nullptr, 0};
+        DDG_TRY(wgrad(P, xb, gh, A->db[l], B, Hl, Wl, lb, st));
+        DDG_TRY(bdata(P, gh, A->db[l], B, Hl, Wl, lb, ga, st));
+        const bf16* below = (l + 1 == L - 1) ? A->eb[L - 1] : A->db[l + 1];
+        const int cu = P->ch[l + 1];
+        LoadCat xa{below, cu, 1, Hl / 2, Wl / 2, A->eb[l], P->ch[l]};
+        DDG_TRY(wgrad(P, xa, ga, A->da[l], B, Hl, Wl, la, st));
+        DDG_TRY(bdata(P, ga, A->da[l], B, Hl, Wl, la, gx, st));
+        const long long nlow = (long long)B * (Hl / 2) * (Wl / 2) * cu;
+        const long long nsk = (long long)B * Hl * Wl * P->ch[l];
+        k_split_cat_bwd<<<nblk(nlow + nsk), 256, 0, st>>>(gx, B, Hl, Wl, cu, P->ch[l], gh, A->gskip[l]);
+        DDG_CHECK_LAUNCH("k_split_cat_bwd");
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        const int Hl = H >> l, Wl = W >> l;
+        const long long n = (long long)B * Hl * Wl * P->ch[l];
+        if (l < L - 1) k_add<<<nblk(n), 256, 0, st>>>(gh, A->gskip[l], n);
+        const int lb = layer_index(P, false, l, 1), la = layer_index(P, false, l, 0);
+        LoadCat xb{A->ea[l], P->ch[l], 0, Hl, Wl, nullptr, 0};
+        DDG_TRY(wgrad(P, xb, gh, A->eb[l], B, Hl, Wl, lb, st));
+        DDG_TRY(bdata(P, gh, A->eb[l], B, Hl, Wl, lb, ga, st));
+        const bf16* in = l > 0 ? A->pooled[l] : A->x0;
+        const int cin = l > 0 ? P->ch[l - 1] : P->cin;
+        LoadCat xa{in, cin, 0, Hl, Wl, nullptr, 0};
+        DDG_TRY(wgrad(P, xa, ga, A->ea[l], B, Hl, Wl, la, st));
+        if (l > 0) {
+            DDG_TRY(bdata(P, ga, A->ea[l], B, Hl, Wl, la, gx, st));
+            const long long nin = (long long)B * (Hl * 2) * (Wl * 2) * cin;
+            k_avgpool2_bwd<<<nblk(nin), 256, 0, st>>>(gx, B, Hl * 2, Wl * 2, cin, gh, 0);
+            DDG_CHECK_LAUNCH("k_avgpool2_bwd");
+        }
+    }
+    return DDG_OK;
+}
+
+static ddg_status check_batch(const ddg_predictor* P, int n, const ddg_op* const* A, int* H, int* W) {
+    if (!P || n < 1 || !A) { set_error("predictor: bad arguments"); return DDG_EINVAL; }
+    for (int s = 0; s < n; ++s) {
+        if (!A[s]) { set_error("predictor: NULL operator %d", s); return DDG_EINVAL; }
+        if (A[s]->nx != A[0]->nx || A[s]->ny != A[0]->ny) { set_error("predictor: a batch needs one grid size"); return DDG_EINVAL; }
+    }
+    const int div = 1 << (P->levels - 1);
+    if (A[0]->nx % div || A[0]->ny % div) {
+        set_error("predictor: grid %dx%d not divisible by %d", A[0]->nx, A[0]->ny, div);
+        return DDG_EINVAL;
+    }
+    *H = A[0]->ny;
+    *W = A[0]->nx;
+    return DDG_OK;
+}
+
+static ddg_status build_input(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma, double j_c,
+                              Acts* acts, cudaStream_t st) {
+    std::vector<InputDesc> hd(n);
+    for (int s = 0; s < n; ++s) hd[s] = InputDesc{A[s]->eps_d, A[s]->nx, A[s]->ny, A[s]->npml_x, A[s]->wavelength};
+    const size_t need = sizeof(InputDesc) * n + sizeof(void*) * 2 * n + 256;
+    if (need > P->desc_bytes) {
+        cudaFree(P->d_desc);
+        P->d_desc = nullptr;
+        P->desc_bytes = 0;
+        DDG_CHECK_CUDA(cudaMalloc(&P->d_desc, need));
+        P->desc_bytes = need;
+    }
+    DDG_CHECK_CUDA(cudaMemcpyAsync(P->d_desc, hd.data(), sizeof(InputDesc) * n, cudaMemcpyHostToDevice, st));
+    const int H = A[0]->ny, W = A[0]->nx;
+    k_input<<<nblk((long long)n * H * W), 256, 0, st>>>(reinterpret_cast<InputDesc*>(P->d_desc), n, H, W, i_src,
+                                                       sigma, j_c, acts->x0);
+    DDG_CHECK_LAUNCH("k_input");
+    return DDG_OK;
+}
+
+static void** ptr_slots(ddg_predictor* P, int n) {
+    return reinterpret_cast<void**>(reinterpret_cast<char*>(P->d_desc) + ((sizeof(InputDesc) * n + 15) / 16) * 16);
+}
+
+static void free_predictor(ddg_predictor* P) {
+    if (!P) return;
+    cudaFree(P->theta);
+    cudaFree(P->theta_bf);
+    cudaFree(P->grad);
+    cudaFree(P->adam_m);
+    cudaFree(P->adam_v);
+    cudaFree(P->wk);
+    cudaFree(P->act);
+    cudaFree(P->d_loss);
+    cudaFree(P->d_desc);
+    delete P;
+}
+
+}  // namespace cnn
+}  // namespace ddg
+
+using namespace ddg;
+using namespace ddg::cnn;
+
+extern "C" ddg_status predictor_create(int k, int levels, const int* channels, ddg_predictor** out) {
+    if (!out) { set_error("predictor_create: out is NULL"); return DDG_EINVAL; }
+    *out = nullptr;
+    if (k < 1 || k > 16 || levels < 1 || levels > kMaxLevels || !channels) {
+        set_error("predictor_create: need 1 <= k <= 16, 1 <= levels <= %d, channels", kMaxLevels);
+        return DDG_EINVAL;
+    }
+    ddg_predictor* P = new (std::nothrow) ddg_predictor();
+    if (!P) return DDG_ENOMEM;
+    P->k = k;
+    P->levels = levels;
+    for (int l = 0; l < levels; ++l) {
+        if (channels[l] < 1 || channels[l] > 1024) { delete P; set_error("predictor_create: bad channel count"); return DDG_EINVAL; }
+        P->ch[l] = channels[l];
+    }
+    cudaGetDevice(&P->device);
+    long long off = 0;
+    size_t maxw = 0;
+    auto add = [&](int co, int ci, int kk) {
+        Layer Ly{co, ci, kk, off, off + (long long)co * ci * kk * kk};
+        off = Ly.b_off + co;
+        P->layers.push_back(Ly);
+        maxw = std::max(maxw, (size_t)co * ci * kk * kk);
+    };
+    for (int l = 0; l < levels; ++l) {
+        add(P->ch[l], l == 0 ? P->cin : P->ch[l - 1], 3);
+        add(P->ch[l], P->ch[l], 3);
+    }
+    for (int l = levels - 2; l >= 0; --l) {
+        add(P->ch[l], P->ch[l + 1] + P->ch[l], 3);
+        add(P->ch[l], P->ch[l], 3);
+    }
+    add(2 * k, P->ch[0], 1);
+    P->nparams = off;
+    const size_t n = (size_t)off;
+    cudaError_t e = cudaMalloc(&P->theta, 4 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&P->theta_bf, 2 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&P->grad, 4 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&P->adam_m, 4 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&P->adam_v, 4 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&P->wk, 2 * maxw);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_loss, sizeof(double) * 4096);
+    if (e == cudaSuccess) e = cudaMemset(P->theta, 0, 4 * n);
+    if (e == cudaSuccess) e = cudaMemset(P->theta_bf, 0, 2 * n);
+    if (e == cudaSuccess) e = cudaMemset(P->adam_m, 0, 4 * n);
+    if (e == cudaSuccess) e = cudaMemset(P->adam_v, 0, 4 * n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_predictor(P);
+        set_error("predictor_create: cudaMalloc failed");
+        return DDG_ENOMEM;
+    }
+    *out = P;
+    return DDG_OK;
+}
+
+extern "C" ddg_status predictor_destroy(ddg_predictor* P) {
+    free_predictor(P);
+    return DDG_OK;
+}
+
+extern "C" long long predictor_num_params(const ddg_predictor* P) { return P ? P->nparams : 0; }
+
+extern "C" ddg_status predictor_set_params(ddg_predictor* P, const float* theta, long long n) {
+    if (!P || !theta || n != P->nparams) { set_error("predictor_set_params: need %lld values", P ? P->nparams : 0LL); return DDG_EINVAL; }
+    DDG_CHECK_CUDA(cudaMemcpy(P->theta, theta, 4 * (size_t)n, cudaMemcpyHostToDevice));
+    k_to_bf16<<<nblk(n), 256>>>(P->theta, P->theta_bf, n);
+    DDG_CHECK_LAUNCH("k_to_bf16");
+    DDG_CHECK_CUDA(cudaMemset(P->adam_m, 0, 4 * (size_t)n));
+    DDG_CHECK_CUDA(cudaMemset(P->adam_v, 0, 4 * (size_t)n));
+    P->step = 0;
+    DDG_CHECK_CUDA(cudaDeviceSynchronize());
+    return DDG_OK;
+}
+
+extern "C" ddg_status predictor_get_params(const ddg_predictor* P, float* theta, long long n) {
+    if (!P || !theta || n != P->nparams) { set_error("predictor_get_params: need %lld values", P ? P->nparams : 0LL); return DDG_EINVAL; }
+    DDG_CHECK_CUDA(cudaDeviceSynchronize());
+    DDG_CHECK_CUDA(cudaMemcpy(theta, P->theta, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+    return DDG_OK;
+}
+
+extern "C" ddg_status predictor_forward(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
+                                        double j_c, float* y, void* stream) {
+    int H = 0, W = 0;
+    DDG_TRY(check_batch(P, n, A, &H, &W));
+    if (!y) { set_error("predictor_forward: y is NULL"); return DDG_EINVAL; }
+    cudaStream_t st = as_stream(stream);
+    Acts acts;
+    DDG_TRY(ensure_acts(P, n, H, W, &acts));
+    DDG_TRY(build_input(P, n, A, i_src, sigma, j_c, &acts, st));
+    DDG_TRY(forward(P, n, H, W, &acts, st));
+    DDG_CHECK_CUDA(cudaMemcpyAsync(y, acts.y, sizeof(float) * (size_t)n * H * W * 2 * P->k, cudaMemcpyDeviceToDevice, st));
+    return DDG_OK;
+}
+
+extern "C" ddg_status subspace_predict(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
+                                       double j_c, double* const* U, void* stream) {
+    int H = 0, W = 0;
+    DDG_TRY(check_batch(P, n, A, &H, &W));
+    if (!U) { set_error("subspace_predict: U is NULL"); return DDG_EINVAL; }
+    for (int s = 0; s < n; ++s)
+        if (!U[s]) { set_error("subspace_predict: U[%d] is NULL", s); return DDG_EINVAL; }
+    cudaStream_t st = as_stream(stream);
+    Acts acts;
+    DDG_TRY(ensure_acts(P, n, H, W, &acts));
+    DDG_TRY(build_input(P, n, A, i_src, sigma, j_c, &acts, st));
+    DDG_TRY(forward(P, n, H, W, &acts, st));
+    void** slots = ptr_slots(P, n);
+    DDG_CHECK_CUDA(cudaMemcpyAsync(slots, U, sizeof(void*) * n, cudaMemcpyHostToDevice, st));
+    k_to_complex<<<nblk((long long)n * H * W * P->k), 256, 0, st>>>(acts.y, H * W, P->k,
+                                                                    reinterpret_cast<double2* const*>(slots), n);
+    DDG_CHECK_LAUNCH("k_to_complex");
+    DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+    return DDG_OK;
+}
+
+extern "C" ddg_status predictor_loss_grad(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
+                                          double j_c, const double* const* f, double* loss, float* grad, void* stream) {
+    int H = 0, W = 0;
+    DDG_TRY(check_batch(P, n, A, &H, &W));
+    if (!f || n > 4096) { set_error("predictor_loss_grad: f is NULL or batch > 4096"); return DDG_EINVAL; }
+    cudaStream_t st = as_stream(stream);
+    Acts acts;
+    DDG_TRY(ensure_acts(P, n, H, W, &acts));
+    DDG_TRY(build_input(P, n, A, i_src, sigma, j_c, &acts, st));
+    DDG_TRY(forward(P, n, H, W, &acts, st));
+    void** slots = ptr_slots(P, n);
+    DDG_CHECK_CUDA(cudaMemcpyAsync(slots, f, sizeof(void*) * n, cudaMemcpyHostToDevice, st));
+    const int k = P->k;
+    const size_t smem = sizeof(double2) * (size_t)(2 * k + k * k);
+    k_proj_loss<<<n, 256, smem, st>>>(acts.y, reinterpret_cast<const double2* const*>(slots), H * W, k, n, P->d_loss,
+                                      acts.gy);
+    DDG_CHECK_LAUNCH("k_proj_loss");
+    DDG_CHECK_CUDA(cudaMemsetAsync(P->grad, 0, 4 * (size_t)P->nparams, st));
+    DDG_TRY(backward(P, n, H, W, &acts, st));
+    std::vector<double> hl(n);
+    DDG_CHECK_CUDA(cudaMemcpyAsync(hl.data(), P->d_loss, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    if (grad) DDG_CHECK_CUDA(cudaMemcpyAsync(grad, P->grad, 4 * (size_t)P->nparams, cudaMemcpyDeviceToDevice, st));
+    DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+    double tot = 0.0;
+    for (double v : hl) tot += v;
+    if (loss) *loss = tot / n;
+    return DDG_OK;
+}
+
+extern "C" ddg_status predictor_adam_step(ddg_predictor* P, float lr, void* stream) {
+    if (!P || !(lr > 0.f)) { set_error("predictor_adam_step: bad arguments"); return DDG_EINVAL; }
+    P->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)P->step), c2 = 1.f - powf(b2, (float)P->step);
+    k_adam<<<nblk(P->nparams), 256, 0, as_stream(stream)>>>(P->theta, P->grad, P->adam_m, P->adam_v, P->theta_bf,
+                                                            P->nparams, lr, b1, b2, 1e-8f, c1, c2);
+    DDG_CHECK_LAUNCH("k_adam");
+    return DDG_OK;
+}
+
+extern "C" ddg_status predictor_train_step(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
+                                           double j_c, const double* const* f, float lr, double* loss, void* stream) {
+    DDG_TRY(predictor_loss_grad(P, n, A, i_src, sigma, j_c, f, loss, nullptr, stream));
+    return predictor_adam_step(P, lr, stream);
+}
+
+// Checkpoint: header (magic, version, k, levels, channels, nparams, step),
+// FP32 weights, Adam m and v, then an FNV-1a checksum of everything before it.
+static unsigned long long fnv1a(const unsigned char* p, size_t n, unsigned long long h) {
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ULL;
+    }
+    return h;
+}
+
+extern "C" ddg_status predictor_save(const ddg_predictor* P, const char* path) {
+    if (!P || !path) { set_error("predictor_save: bad arguments"); return DDG_EINVAL; }
+    const size_t n = (size_t)P->nparams;
+    std::vector<float> buf(3 * n);
+    DDG_CHECK_CUDA(cudaDeviceSynchronize());
+    DDG_CHECK_CUDA(cudaMemcpy(buf.data(), P->theta, 4 * n, cudaMemcpyDeviceToHost));
+    DDG_CHECK_CUDA(cudaMemcpy(buf.data() + n, P->adam_m, 4 * n, cudaMemcpyDeviceToHost));
+    DDG_CHECK_CUDA(cudaMemcpy(buf.data() + 2 * n, P->adam_v, 4 * n, cudaMemcpyDeviceToHost));
+    long long hdr[4 + kMaxLevels] = {0x4444474d50524544LL, 1, P->k, P->levels};
+    for (int l = 0; l < kMaxLevels; ++l) hdr[4 + l] = l < P->levels ? P->ch[l] : 0;
+    long long tail[2] = {P->nparams, P->step};
+    FILE* fp = fopen(path, "wb");
+    if (!fp) { set_error("predictor_save: cannot open %s", path); return DDG_EINVAL; }
+    unsigned long long h = 1469598103934665603ULL;
+    h = fnv1a(reinterpret_cast<const unsigned char*>(hdr), sizeof(hdr), h);
+    h = fnv1a(reinterpret_cast<const unsigned char*>(tail), sizeof(tail), h);
+    h = fnv1a(reinterpret_cast<const unsigned char*>(buf.data()), 4 * buf.size(), h);
+    bool ok = fwrite(hdr, sizeof(hdr), 1, fp) == 1 && fwrite(tail, sizeof(tail), 1, fp) == 1 &&
+              fwrite(buf.data(), 4, buf.size(), fp) == buf.size() && fwrite(&h, sizeof(h), 1, fp) == 1;
+    ok = (fclose(fp) == 0) && ok;
+    if (!ok) { set_error("predictor_save: write to %s failed", path); return DDG_EINVAL; }
+    return DDG_OK;
+}
+
+extern "C" ddg_status predictor_load(ddg_predictor* P, const char* path) {
+    if (!P || !path) { set_error("predictor_load: bad arguments"); return DDG_EINVAL; }
+    FILE* fp = fopen(path, "rb");
+    if (!fp) { set_error("predictor_load: cannot open %s", path); return DDG_EINVAL; }
+    long long hdr[4 + kMaxLevels], tail[2];
+    const size_t n = (size_t)P->nparams;
+    std::vector<float> buf(3 * n);
+    unsigned long long hf = 0;
+    bool ok = fread(hdr, sizeof(hdr), 1, fp) == 1 && fread(tail, sizeof(tail), 1, fp) == 1;
+    ok = ok && hdr[0] == 0x4444474d50524544LL && hdr[1] == 1 && hdr[2] == P->k && hdr[3] == P->levels &&
+         tail[0] == P->nparams;
+    for (int l = 0; ok && l < P->levels; ++l) ok = hdr[4 + l] == P->ch[l];
+    ok = ok && fread(buf.data(), 4, buf.size(), fp) == buf.size() && fread(&hf, sizeof(hf), 1, fp) == 1;
+    fclose(fp);
+    if (!ok) { set_error("predictor_load: %s does not match this predictor", path); return DDG_EINVAL; }
+    unsigned long long h = 1469598103934665603ULL;
+    h = fnv1a(reinterpret_cast<const unsigned char*>(hdr), sizeof(hdr), h);
+    h = fnv1a(reinterpret_cast<const unsigned char*>(tail), sizeof(tail), h);
+    h = fnv1a(reinterpret_cast<const unsigned char*>(buf.data()), 4 * buf.size(), h);
+    if (h != hf) { set_error("predictor_load: checksum mismatch in %s", path); return DDG_EINVAL; }
+    DDG_CHECK_CUDA(cudaMemcpy(P->theta, buf.data(), 4 * n, cudaMemcpyHostToDevice));
+    DDG_CHECK_CUDA(cudaMemcpy(P->adam_m, buf.data() + n, 4 * n, cudaMemcpyHostToDevice));
+    DDG_CHECK_CUDA(cudaMemcpy(P->adam_v, buf.data() + 2 * n, 4 * n, cudaMemcpyHostToDevice));
+    k_to_bf16<<<nblk((long long)n), 256>>>(P->theta, P->theta_bf, (long long)n);
+    DDG_CHECK_LAUNCH("k_to_bf16");
+    P->step = tail[1];
+    DDG_CHECK_CUDA(cudaDeviceSynchronize());
+    return DDG_OK;
+}

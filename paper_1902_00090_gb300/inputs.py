@@ -165,3 +165,8 @@ def random_complex(n: int, seed: int, shape=None) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     shp = (n,) if shape is None else shape
     return (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)) / np.sqrt(2.0)
+
+
+def standard_normal(n: int, seed: int) -> np.ndarray:
+    """n independent N(0, 1) draws (float64)."""
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal(n)

@@ -1,0 +1,204 @@
+"""GPU parity of the subspace-predicting CNN against the oracle (oracle/cnn.py).
+
+The GPU network stores weights and activations in bfloat16 and accumulates in
+FP32.  Bars: (1) against the oracle with the same bfloat16 storage (weights
+and every stored activation rounded to nearest-even bfloat16): output within
+2e-3 relative L2, loss within 1e-4, gradient cosine >= 0.9999; (2) against the
+pure fp64 oracle on the same FP32 weights: output within 3e-2 relative L2,
+loss within 2 %, gradient cosine >= 0.98 (what bfloat16 storage itself gives);
+Adam by its formula applied to the GPU's own gradient (FP32 round-off).
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import cnn as ocnn
+from oracle import fdfd
+from paper_1902_00090_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1902_00090_gb300 as ddg  # noqa: E402
+
+SMALL = dict(k=2, channels=(8, 16, 16))
+
+
+def small_problems(n=2, N=32, seed=0):
+    g = inputs.Grid(nx=N, ny=N, npml=4, i_src=6, sigma_src=3.0, slab_cells=4)
+    eps = inputs.trajectory_set(g, 2, 1, steps=n) if seed == 0 else \
+        inputs.trajectory_set(g, 2, seed + 1, steps=n)[-n:]
+    ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device="cuda")) for e in eps]
+    return g, eps, ops
+
+
+def oracle_inputs(g, eps):
+    return np.stack([ocnn.input_channels(e, g.wavelength, g.npml, g.i_src, g.sigma_src, g.j_src) for e in eps])
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_layer_order_matches_oracle():
+    cfg = ocnn.CNNConfig(cin=4, channels=SMALL["channels"], k=SMALL["k"])
+    assert [s[1:] for s in ocnn.layer_shapes(cfg)] == \
+        [s[1:] for s in ddg.binding.predictor_layer_shapes(SMALL["channels"], SMALL["k"])]
+    P = ddg.Predictor(**SMALL)
+    assert P.nparams == ocnn.num_params(cfg)
+
+
+def test_forward_matches_oracle():
+    g, eps, ops = small_problems()
+    P = ddg.Predictor(**SMALL)
+    P.init_he(seed=3)
+    theta = P.get_params().astype(np.float64)
+    y = P.forward(ops, (g.i_src, g.sigma_src, g.j_src)).cpu().numpy()
+    cfg = ocnn.CNNConfig(cin=4, channels=SMALL["channels"], k=SMALL["k"])
+    x = oracle_inputs(g, eps)
+    yo = ocnn.forward(cfg, theta, x)
+    assert y.shape == yo.shape
+    assert rel(y, yo) <= 3e-2
+    # same storage precision as the GPU (bfloat16 weights and activations)
+    yb = ocnn.forward(cfg, ocnn.round_weights(cfg, theta, ocnn.bf16_round), ocnn.bf16_round(x),
+                      store=ocnn.bf16_round)
+    assert rel(y, yb) <= 2e-3
+
+
+def test_predict_layout():
+    g, eps, ops = small_problems()
+    P = ddg.Predictor(**SMALL)
+    P.init_he(seed=4)
+    src = (g.i_src, g.sigma_src, g.j_src)
+    y = P.forward(ops, src).cpu().numpy()
+    U = P.predict(ops, src)
+    for s in range(len(ops)):
+        Us = U[s].cpu().numpy()                       # (k, D): row c = v_c
+        V = ocnn.to_complex_fields(y[s:s + 1])[0]     # (D, k)
+        assert np.array_equal(Us.T, V.astype(np.complex128))
+
+
+def test_loss_and_gradient_match_oracle():
+    g, eps, ops = small_problems()
+    P = ddg.Predictor(**SMALL)
+    P.init_he(seed=5)
+    theta = P.get_params().astype(np.float64)
+    fields = [inputs.random_complex(g.D, 10 + s) for s in range(len(ops))]
+    src = (g.i_src, g.sigma_src, g.j_src)
+    loss, grad = P.loss_grad(ops, src, [torch.as_tensor(f, device="cuda") for f in fields])
+    cfg = ocnn.CNNConfig(cin=4, channels=SMALL["channels"], k=SMALL["k"])
+    x = oracle_inputs(g, eps)
+    gg = grad.cpu().numpy().astype(np.float64)
+    assert 0.0 <= loss <= 1.0
+    # (1) the oracle with bfloat16 storage, as the GPU network: tight
+    lb, gb = ocnn.batch_loss_and_grad(cfg, ocnn.round_weights(cfg, theta, ocnn.bf16_round), ocnn.bf16_round(x),
+                                      np.stack(fields), store=ocnn.bf16_round)
+    assert abs(loss - lb) <= 1e-4
+    assert gg @ gb / (np.linalg.norm(gg) * np.linalg.norm(gb)) >= 0.9999
+    assert rel(gg, gb) <= 1e-2
+    # (2) the fp64 oracle: bfloat16 storage (8 significant bits) perturbs a
+    # near-unit loss's small gradient by ~15 % here (the emulation above gives
+    # the same cosine, 0.988, to eight digits)
+    lo, go = ocnn.batch_loss_and_grad(cfg, theta, x, np.stack(fields))
+    assert abs(loss - lo) <= 2e-2 * max(lo, 1e-3)
+    assert gg @ go / (np.linalg.norm(gg) * np.linalg.norm(go)) >= 0.98
+
+
+def test_adam_step_matches_formula():
+    g, eps, ops = small_problems()
+    P = ddg.Predictor(**SMALL)
+    P.init_he(seed=6)
+    theta0 = P.get_params().astype(np.float64)
+    fields = [torch.as_tensor(inputs.random_complex(g.D, 20 + s), device="cuda") for s in range(len(ops))]
+    src = (g.i_src, g.sigma_src, g.j_src)
+    st = ocnn.AdamState(m=np.zeros_like(theta0), v=np.zeros_like(theta0))
+    th = theta0.copy()
+    for it in range(3):
+        _, grad = P.loss_grad(ops, src, fields)
+        P.adam_step(1e-3)
+        th = ocnn.adam_step(th, grad.cpu().numpy().astype(np.float64), st, lr=1e-3)
+        got = P.get_params().astype(np.float64)
+        assert np.max(np.abs(got - th)) <= 1e-6 + 1e-5 * np.max(np.abs(th))
+
+
+def test_checkpoint_round_trip_and_corruption():
+    P = ddg.Predictor(**SMALL)
+    P.init_he(seed=7)
+    g, eps, ops = small_problems()
+    fields = [torch.as_tensor(inputs.random_complex(g.D, 30 + s), device="cuda") for s in range(len(ops))]
+    P.train_step(ops, (g.i_src, g.sigma_src, g.j_src), fields, 1e-3)
+    theta = P.get_params()
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "p.bin")
+        P.save(path)
+        Q = ddg.Predictor(**SMALL)
+        Q.load_file(path)
+        assert np.array_equal(Q.get_params(), theta)
+        raw = bytearray(open(path, "rb").read())
+        raw[200] ^= 0xFF
+        open(path, "wb").write(bytes(raw))
+        with pytest.raises(ddg.DdgError):
+            Q.load_file(path)
+        R = ddg.Predictor(k=3, channels=SMALL["channels"])
+        P.save(path)
+        with pytest.raises(ddg.DdgError):
+            R.load_file(path)
+
+
+def test_training_reduces_loss_and_helps_the_solver():
+    # Solved training fields (the library's own solver), a few hundred Adam steps,
+    # then the trained predictor's subspace must capture much more of held-out
+    # solutions than the untrained one (Eq. 5 on held-out fields, and the
+    # V-only residual of Eq. 6 reported by the augmented solver).
+    N = 64
+    g = inputs.grid_for(N, N)
+    eps_tr = inputs.trajectory_set(g, 2, 6, steps=8)
+    eps_te = inputs.trajectory_eps(g, 2, 30, steps=4)
+    ctx = ddg.Context()
+    src = (g.i_src, g.sigma_src, g.j_src)
+
+    def solve(eps_set):
+        ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device="cuda")) for e in eps_set]
+        bs = [ddg.fdfd_source(op, *src) for op in ops]
+        xs, infos, st = ddg.gmres_solve_batched(ctx, ops, bs, tol=1e-6, restart=100, maxit=20000, precision="c64")
+        assert st == 0
+        return ops, bs, xs
+
+    ops_tr, _, f_tr = solve(eps_tr)
+    ops_te, bs_te, f_te = solve(eps_te)
+    P = ddg.Predictor(k=4, channels=(16, 32, 32, 48))
+    P.init_he(seed=1)
+    l_te0, _ = P.loss_grad(ops_te, src, f_te, want_grad=False)
+    U0 = P.predict(ops_te, src)
+    rng = np.random.default_rng(0)
+    losses = []
+    for it in range(300):
+        idx = rng.choice(len(ops_tr), 8, replace=False)
+        losses.append(P.train_step([ops_tr[i] for i in idx], src, [f_tr[i] for i in idx], 2e-3))
+    assert np.mean(losses[-20:]) < 0.5 * np.mean(losses[:5])
+    l_te1, _ = P.loss_grad(ops_te, src, f_te, want_grad=False)
+    assert l_te1 < 0.5 * l_te0, (l_te0, l_te1)
+    U1 = P.predict(ops_te, src)
+    r0 = [ddg.augmented_gmres_solve(ctx, op, b, U, tol=1e-6, restart=100, maxit=20000, precision="c64")[1]
+          for op, b, U in zip(ops_te, bs_te, U0)]
+    r1 = [ddg.augmented_gmres_solve(ctx, op, b, U, tol=1e-6, restart=100, maxit=20000, precision="c64")[1]
+          for op, b, U in zip(ops_te, bs_te, U1)]
+    assert all(i["converged"] for i in r0 + r1)
+    first0 = np.mean([i["first_step_rel_residual"] for i in r0])
+    first1 = np.mean([i["first_step_rel_residual"] for i in r1])
+    assert first1 < 0.7 * first0, (first0, first1)
+
+
+def test_full_size_network_runs_at_128():
+    g = inputs.grid_128()
+    eps = inputs.trajectory_set(g, 2, 1, steps=2)
+    ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device="cuda")) for e in eps]
+    P = ddg.Predictor(k=8)
+    P.init_he(seed=0)
+    y = P.forward(ops, (g.i_src, g.sigma_src, g.j_src))
+    assert y.shape == (2, 128, 128, 16) and torch.isfinite(y).all()

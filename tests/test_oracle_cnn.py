@@ -121,3 +121,14 @@ def test_layer_shapes_and_param_count():
     assert names[0] == "enc0a" and names[-1] == "head" and len(names) == 23
     d = dict((s[0], s[1:]) for s in cnn.layer_shapes(cfg))
     assert d["dec4a"] == (128, 256, 3) and d["dec0a"] == (32, 80, 3) and d["head"] == (16, 32, 1)
+
+
+def test_bf16_rounding_definition():
+    # bfloat16 keeps 8 significant bits; ties go to even
+    assert cnn.bf16_round(1.0) == 1.0
+    assert cnn.bf16_round(1.0 + 2.0 ** -8) == 1.0            # tie -> even (1.0)
+    assert cnn.bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6   # tie -> even mantissa
+    assert cnn.bf16_round(1.0 + 2.0 ** -7) == 1.0 + 2.0 ** -7
+    x = np.random.default_rng(0).standard_normal(1000)
+    r = cnn.bf16_round(x)
+    assert np.max(np.abs(r - x) / np.abs(x)) <= 2.0 ** -8
