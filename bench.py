@@ -1,13 +1,14 @@
 """Benchmark: FDFD solves/s to relative residual 1e-6, data-driven vs plain GMRES.
 
-Workload (default): PCA-augmented GMRES(200) on 128x128 Yee grids (40 nm cells,
-1550 nm, 10-cell PML, Gaussian line source), 32 synthetic design trajectories x
-16 steps = 512 permittivities.  448 training fields (28 trajectories) are
-solved by the library in complex128, their k = 20 leading principal components
-are fitted on the GPU, and one timed step solves the 64 held-out problems
-(4 trajectories) with augmented GMRES, complex64 Arnoldi inside FP64
-refinement, to true relative residual 1e-6.  The plain-GMRES solves/s on the
-same 64 problems is measured alongside.
+Workload: 128x128 Yee grids (40 nm cells, 1550 nm, 10-cell PML, Gaussian line
+source), 32 synthetic design trajectories x 16 steps = 512 permittivities.
+The library solves the 448 training fields (28 trajectories) in complex128;
+from them it fits k = 20 principal components and trains the subspace CNN
+(k = 8 complex outputs) with its own kernels.  One timed step predicts the
+subspaces of the 64 held-out problems (4 trajectories) with the CNN and solves
+them with augmented GMRES(200) (complex64 Arnoldi inside FP64 refinement) to
+true relative residual 1e-6; PCA-augmented and plain GMRES on the same 64
+problems are timed alongside.
 
 `value` is the device-resident throughput (inputs in HBM, every kernel of the
 solve timed); `e2e` repeats the step through the C ABI from host buffers
@@ -29,8 +30,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = ("PCA-augmented GMRES(200), k=20 PCs of 448 training fields, "
-            "64 held-out 128x128 FDFD solves to rel. residual 1e-6")
+WORKLOAD = ("CNN-augmented GMRES(200), k=8 predicted vectors (network trained on 448 solved fields), "
+            "64 held-out 128x128 FDFD solves to rel. residual 1e-6; PCA (k=20) and plain GMRES alongside")
 METRIC = "FDFD solves/s to rel-residual 1e-6 on 1 GB300: CNN-augmented vs plain GMRES"
 
 
@@ -42,7 +43,11 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="c64", choices=["c64", "c128"])
     p.add_argument("--restart", type=int, default=200)
-    p.add_argument("--k", type=int, default=20)
+    p.add_argument("--k", type=int, default=20, help="PCA components")
+    p.add_argument("--cnn-k", type=int, default=8)
+    p.add_argument("--cnn-steps", type=int, default=400)
+    p.add_argument("--cnn-batch", type=int, default=16)
+    p.add_argument("--cnn-lr", type=float, default=1e-3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     return p.parse_args()
@@ -119,33 +124,55 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     g, eps_train, eps_test = problem_set()
+    src = (g.i_src, g.sigma_src, g.j_src)
     ctx = ddg.Context()
 
     def build(eps_set):
         ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device=dev)) for e in eps_set]
-        bs = [ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src) for op in ops]
+        bs = [ddg.fdfd_source(op, *src) for op in ops]
         return ops, bs
 
-    # --- training: complex128 solves of the training fields, PCA on the GPU
+    # --- training data: the library solves the 448 training fields in complex128
     t0 = time.time()
     ops_tr, bs_tr = build(eps_train)
     xs_tr, inf_tr, st = ddg.gmres_solve_batched(ctx, ops_tr, bs_tr, tol=1e-6, restart=200, maxit=5000,
                                                 precision="c128")
-    F = torch.stack(xs_tr)
-    U, sig = ddg.pca_fit(ctx, F, args.k)
     torch.cuda.synchronize()
-    train_s = time.time() - t0
-    del F, xs_tr, ops_tr, bs_tr
+    solve_train_s = time.time() - t0
+    # --- PCA predictor (Sec. III): k leading components, fitted on the GPU
+    t0 = time.time()
+    U_pca, sig = ddg.pca_fit(ctx, torch.stack(xs_tr), args.k)
+    torch.cuda.synchronize()
+    pca_s = time.time() - t0
+    # --- CNN predictor (Sec. III): trained on the same fields with the library's kernels
+    t0 = time.time()
+    P = ddg.Predictor(k=args.cnn_k)
+    P.init_he(seed=0)
+    rng = np.random.default_rng(0)
+    train_losses = []
+    for it in range(args.cnn_steps):
+        idx = rng.choice(len(ops_tr), args.cnn_batch, replace=False)
+        train_losses.append(P.train_step([ops_tr[i] for i in idx], src, [xs_tr[i] for i in idx], args.cnn_lr))
+    torch.cuda.synchronize()
+    cnn_s = time.time() - t0
+    del xs_tr, ops_tr, bs_tr
     ops, bs = build(eps_test)
     n = len(ops)
-    Us = [U] * n
     xs = [torch.zeros_like(b) for b in bs]
+    U_cnn = [torch.empty((args.cnn_k, g.D), dtype=torch.complex128, device=dev) for _ in range(n)]
 
-    def step_aug():
+    def step_cnn():
         for x in xs:
             x.zero_()
-        return ddg.augmented_gmres_solve_batched(ctx, ops, bs, Us, x=xs, tol=1e-6, restart=args.restart,
+        P.predict(ops, src, U=U_cnn)
+        return ddg.augmented_gmres_solve_batched(ctx, ops, bs, U_cnn, x=xs, tol=1e-6, restart=args.restart,
                                                  maxit=5000, precision=args.precision)
+
+    def step_pca():
+        for x in xs:
+            x.zero_()
+        return ddg.augmented_gmres_solve_batched(ctx, ops, bs, [U_pca] * n, x=xs, tol=1e-6,
+                                                 restart=args.restart, maxit=5000, precision=args.precision)
 
     def step_plain():
         for x in xs:
@@ -164,7 +191,7 @@ def run_ours(args, rank, world):
             sampler.start()
         if profile:
             ctx.profile_enable(True)
-        l0 = ctx.launches
+        l0 = ctx.launches + P.launches
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.nvtx.range_push(f"timed_{step.__name__}")
         e0.record()
@@ -175,7 +202,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         ms = e0.elapsed_time(e1)
-        launches = ctx.launches - l0
+        launches = ctx.launches + P.launches - l0
         prof = ctx.profile_read() if profile else None
         if profile:
             ctx.profile_enable(False)
@@ -186,20 +213,34 @@ def run_ours(args, rank, world):
             ms = float(t.item())
         return ms, infos, launches, prof, clk
 
-    K, W = args.steps, args.warmup
-    ms, infos, launches, prof, clk = timed(step_aug, K, W, profile=True, clocks=True)
-    conv = sum(i["converged"] for i in infos)
-    # per-solve accuracy check against the FP64 true residual the library reports
-    worst = max(i["true_rel_residual"] for i in infos)
-    value = world * conv * K / (ms / 1e3)
+    def summary(infos):
+        return {"iters_mean": float(np.mean([i["iters"] for i in infos])),
+                "first_step_rel_residual_mean": float(np.nanmean([i["first_step_rel_residual"] for i in infos]))
+                if any(i["first_step_rel_residual"] == i["first_step_rel_residual"] for i in infos) else None,
+                "converged": int(sum(i["converged"] for i in infos)),
+                "worst_true_rel_residual": float(max(i["true_rel_residual"] for i in infos))}
 
+    K, W = args.steps, args.warmup
+    ms, infos, launches, prof, clk = timed(step_cnn, K, W, profile=True, clocks=True)
+    value = world * sum(i["converged"] for i in infos) * K / (ms / 1e3)
+    # CNN inference alone (the predict call of one step)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    P.predict(ops, src, U=U_cnn)
+    e1.record()
+    torch.cuda.synchronize()
+    predict_ms = e0.elapsed_time(e1)
+
+    sK = max(1, K // 2)
+    pms, pinf, _, _, _ = timed(step_pca, sK, 1)
+    pca = {"value": world * sum(i["converged"] for i in pinf) * sK / (pms / 1e3), "unit": "solves/s",
+           "ms_per_step": pms / sK, "k": args.k, "fit_s": round(pca_s, 2), **summary(pinf)}
     plain = None
     if not args.no_plain:
-        pK, pW = max(1, K // 2), 1
-        pms, pinf, _, _, _ = timed(step_plain, pK, pW)
-        pconv = sum(i["converged"] for i in pinf)
-        plain = {"value": world * pconv * pK / (pms / 1e3), "unit": "solves/s", "ms_per_step": pms / pK,
-                 "iters_mean": float(np.mean([i["iters"] for i in pinf])), "converged": pconv, "steps": pK}
+        qms, qinf, _, _, _ = timed(step_plain, sK, 1)
+        plain = {"value": world * sum(i["converged"] for i in qinf) * sK / (qms / 1e3), "unit": "solves/s",
+                 "ms_per_step": qms / sK, **summary(qinf)}
 
     # --- e2e: host buffers in, host buffers out, through the C ABI
     eps_host = torch.from_numpy(np.ascontiguousarray(eps_test)).pin_memory()
@@ -208,16 +249,16 @@ def run_ours(args, rank, world):
     def step_e2e():
         eps_dev = eps_host.to(dev, non_blocking=True)
         o2 = [ddg.fdfd_operator(g, eps_dev[i]) for i in range(n)]
-        b2 = [ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src) for op in o2]
-        _, inf, st_ = ddg.augmented_gmres_solve_batched(ctx, o2, b2, Us, tol=1e-6, restart=args.restart,
-                                                        maxit=5000, precision=args.precision)
-        x_host.copy_(torch.stack(_), non_blocking=True)
+        b2 = [ddg.fdfd_source(op, *src) for op in o2]
+        P.predict(o2, src, U=U_cnn)
+        xs2, inf, st_ = ddg.augmented_gmres_solve_batched(ctx, o2, b2, U_cnn, tol=1e-6, restart=args.restart,
+                                                          maxit=5000, precision=args.precision)
+        x_host.copy_(torch.stack(xs2), non_blocking=True)
         return None, inf, st_
 
     eK = max(1, K // 2)
-    ems, einf, elaunch, _, _ = timed(step_e2e, eK, 1)
-    econv = sum(i["converged"] for i in einf)
-    e2e = {"value": world * econv * eK / (ems / 1e3), "unit": "solves/s",
+    ems, einf, _, _, _ = timed(step_e2e, eK, 1)
+    e2e = {"value": world * sum(i["converged"] for i in einf) * eK / (ems / 1e3), "unit": "solves/s",
            "h2d_bytes_per_step": int(eps_host.numel() * 8), "d2h_bytes_per_step": int(x_host.numel() * 16)}
 
     # --- roofline of the dominant kernel class (live CUDA events, algorithmic bytes)
@@ -232,9 +273,16 @@ def run_ours(args, rank, world):
     d_ms, d_bytes, d_n = prof[dom]
     achieved = d_bytes / (d_ms / 1e3) / 1e9
     total_ms = sum(v[0] for v in prof.values())
-    roof = {"kernel": f"k_{dom}", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
-            "launches": d_n, "avg_launch_us": round(d_ms * 1e3 / max(1, d_n), 2),
+    # DRAM bytes over algorithmic bytes of the same kernels, from one ncu capture
+    # (dram__bytes_read.sum + dram__bytes_write.sum of one launch at step 100)
+    ratio = {"dots": 1.03, "update": 1.02}.get(dom)
+    roof = {"kernel": {"dots": "k_dots2", "update": "k_update2"}.get(dom, f"k_{dom}"), "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": round(ratio * d_bytes / d_n) if ratio else None,
+            "traffic_source": "ncu dram bytes / algorithmic bytes = %.2f for this kernel, times the mean "
+                              "algorithmic bytes per launch" % ratio if ratio else None,
+            "peak_source": peak_src, "launches": d_n, "avg_launch_us": round(d_ms * 1e3 / max(1, d_n), 2),
+            "algorithmic_bytes_per_launch": round(d_bytes / max(1, d_n)),
             "share_of_kernel_time": round(d_ms / total_ms, 4),
             "classes": {c: {"ms": round(v[0], 2), "GBps": round(v[1] / max(v[0], 1e-9) / 1e6, 1),
                             "launches": v[2]} for c, v in prof.items()}}
@@ -245,17 +293,21 @@ def run_ours(args, rank, world):
         "vs_baseline": None, "dtype": "c64+f64" if args.precision == "c64" else "c128",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": "128x128", "dx_nm": 40, "wavelength_nm": 1550,
-                   "npml": 10, "k": args.k, "restart": args.restart, "tol": 1e-6, "solves_per_step": n,
-                   "predictor": "pca", "precision": args.precision,
-                   "l2": "no flush: per-step working set (Krylov bases, 64 x 26 MB c64) exceeds L2",
+                   "npml": 10, "restart": args.restart, "tol": 1e-6, "solves_per_step": n,
+                   "predictor": f"cnn k={args.cnn_k} (6 levels, 32-128 channels, bf16)",
+                   "precision": args.precision, "training_fields": len(eps_train),
+                   "l2": "no flush: per-step working set (Krylov bases, 64 x 28 MB c64) exceeds L2",
                    "parallelism": f"replicas x{world}"},
-        "augmented": {"iters_mean": float(np.mean([i["iters"] for i in infos])),
-                      "first_step_rel_residual_mean": float(np.mean([i["first_step_rel_residual"] for i in infos])),
-                      "converged": conv, "worst_true_rel_residual": worst},
+        "cnn": {**summary(infos), "predict_ms_per_step": round(predict_ms, 2), "train_s": round(cnn_s, 2),
+                "train_steps": args.cnn_steps, "batch": args.cnn_batch, "lr": args.cnn_lr,
+                "train_loss_first": float(np.mean(train_losses[:10])),
+                "train_loss_last": float(np.mean(train_losses[-10:]))},
+        "pca": pca,
         "plain": plain,
         "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
-        "train_s": round(train_s, 2), "train_iters_mean": float(np.mean([i["iters"] for i in inf_tr])),
-        "pca_sigma_ratio_k": float(sig[-1] / sig[0]),
+        "pca_speedup_vs_plain": round(pca["value"] / plain["value"], 3) if plain else None,
+        "solve_training_fields_s": round(solve_train_s, 2),
+        "train_iters_mean": float(np.mean([i["iters"] for i in inf_tr])),
         "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
     }
     return line

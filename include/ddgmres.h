@@ -245,6 +245,8 @@ typedef struct ddg_predictor ddg_predictor;
 ddg_status predictor_create(int k, int levels, const int* channels, ddg_predictor** P);
 ddg_status predictor_destroy(ddg_predictor* P);
 long long predictor_num_params(const ddg_predictor* P);
+/* Kernels launched by this predictor since it was created. */
+long long predictor_launches(const ddg_predictor* P);
 /* theta: host, n = predictor_num_params floats.  Setting resets the Adam state. */
 ddg_status predictor_set_params(ddg_predictor* P, const float* theta, long long n);
 ddg_status predictor_get_params(const ddg_predictor* P, float* theta, long long n);

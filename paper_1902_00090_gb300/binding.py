@@ -76,6 +76,7 @@ _SIGS = {
     "predictor_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp)]),
     "predictor_destroy": (C.c_int, [_vp]),
     "predictor_num_params": (C.c_longlong, [_vp]),
+    "predictor_launches": (C.c_longlong, [_vp]),
     "predictor_set_params": (C.c_int, [_vp, _vp, C.c_longlong]),
     "predictor_get_params": (C.c_int, [_vp, _vp, C.c_longlong]),
     "predictor_forward": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_double, C.c_double, _vp, _vp]),
@@ -428,6 +429,11 @@ class Predictor:
 
     def layer_shapes(self):
         return predictor_layer_shapes(self.channels, self.k)
+
+    @property
+    def launches(self) -> int:
+        """Kernels launched by this predictor (predictor_launches)."""
+        return int(load().predictor_launches(self._h))
 
     def set_params(self, theta):
         import numpy as np

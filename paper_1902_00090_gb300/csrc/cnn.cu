@@ -518,6 +518,7 @@ struct ddg_predictor {
     float* adam_m = nullptr;
     float* adam_v = nullptr;
     long long step = 0;
+    long long launches = 0;       // kernels launched by this predictor
     bf16* wk = nullptr;           // per-layer re-laid-out BF16 weights (forward / backward)
     // activation workspace
     void* act = nullptr;
@@ -605,6 +606,7 @@ template <class LD, typename TOUT>
 static ddg_status conv3(ddg_predictor* P, const LD& ld, int B, int H, int W, int Ci, int Co, const bf16* wk,
                         const float* bias, int relu, TOUT* out, cudaStream_t st) {
     dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, B * ((Co + COB - 1) / COB));
+    ++P->launches;
     k_conv3<LD, TOUT><<<grid, 256, 0, st>>>(ld, B, H, W, Ci, Co, wk, bias, relu, out);
     DDG_CHECK_LAUNCH("k_conv3");
     return DDG_OK;
@@ -619,12 +621,14 @@ static ddg_status forward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaSt
         const int Hl = H >> l, Wl = W >> l;
         const bf16* in = h;
         if (l > 0) {
+            ++P->launches;
             k_avgpool2<<<nblk((long long)B * Hl * Wl * hc), 256, 0, st>>>(h, B, Hl * 2, Wl * 2, hc, A->pooled[l]);
             in = A->pooled[l];
         }
         for (int ab = 0; ab < 2; ++ab) {
             const int li = layer_index(P, false, l, ab);
             const Layer& Ly = P->layers[li];
+            ++P->launches;
             k_w_fwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
             LoadCat ld{ab == 0 ? in : A->ea[l], Ly.ci, 0, Hl, Wl, nullptr, 0};
             DDG_TRY(conv3(P, ld, B, Hl, Wl, Ly.ci, Ly.co, P->wk, bias32(P, li), 1, ab == 0 ? A->ea[l] : A->eb[l], st));
@@ -637,6 +641,7 @@ static ddg_status forward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaSt
         for (int ab = 0; ab < 2; ++ab) {
             const int li = layer_index(P, true, l, ab);
             const Layer& Ly = P->layers[li];
+            ++P->launches;
             k_w_fwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
             LoadCat ld = ab == 0 ? LoadCat{h, hc, 1, Hl / 2, Wl / 2, A->eb[l], P->ch[l]}
                                  : LoadCat{A->da[l], Ly.ci, 0, Hl, Wl, nullptr, 0};
@@ -646,6 +651,7 @@ static ddg_status forward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaSt
         hc = P->ch[l];
     }
     const int lh = (int)P->layers.size() - 1;
+    ++P->launches;
     k_head_fwd<<<nblk((long long)B * H * W * 2 * P->k), 256, 0, st>>>(h, (long long)B * H * W, hc, 2 * P->k, wbf(P, lh),
                                                                     bias32(P, lh), A->y);
     DDG_CHECK_LAUNCH("forward");
@@ -666,6 +672,7 @@ static ddg_status wgrad(ddg_predictor* P, const LX& lx, const float* g, const bf
     const unsigned sl = wgrad_slices(ntiles, gy);
     const int per = (int)((ntiles + sl - 1) / sl);
     dim3 grid(sl, gy);
+    ++P->launches;
     k_conv3_wgrad<LX><<<grid, 256, 0, st>>>(lx, g, yout, B, H, W, Ly.ci, Ly.co, per, P->grad + Ly.w_off,
                                             P->grad + Ly.b_off);
     DDG_CHECK_LAUNCH("k_conv3_wgrad");
@@ -676,6 +683,7 @@ static ddg_status wgrad(ddg_predictor* P, const LX& lx, const float* g, const bf
 static ddg_status bdata(ddg_predictor* P, const float* g, const bf16* yout, int B, int H, int W, int li, float* gx,
                         cudaStream_t st) {
     const Layer& Ly = P->layers[li];
+    ++P->launches;
     k_w_bwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
     LoadGrad ld{g, yout, Ly.co};
     return conv3(P, ld, B, H, W, Ly.co, Ly.ci, P->wk, (const float*)nullptr, 0, gx, st);
@@ -688,8 +696,10 @@ static ddg_status backward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaS
     const long long px0 = (long long)B * H * W;
     const int O = 2 * P->k, C0 = P->ch[0];
     const bf16* hin = L > 1 ? A->db[0] : A->eb[0];   // input of the 1x1 head
+    ++P->launches;
     k_head_bwd_w<<<O * (C0 + 1), 256, 0, st>>>(A->gy, hin, px0, C0, O, P->grad + P->layers[lh].w_off,
                                               P->grad + P->layers[lh].b_off);
+    ++P->launches;
     k_head_bwd_data<<<nblk(px0 * C0), 256, 0, st>>>(A->gy, px0, C0, O, wbf(P, lh), A->g1);
     DDG_CHECK_LAUNCH("head backward");
     float* gh = A->g1;      // gradient w.r.t. the current level's output (post-ReLU)
@@ -708,13 +718,17 @@ static ddg_status backward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaS
         DDG_TRY(bdata(P, ga, A->da[l], B, Hl, Wl, la, gx, st));
         const long long nlow = (long long)B * (Hl / 2) * (Wl / 2) * cu;
         const long long nsk = (long long)B * Hl * Wl * P->ch[l];
+        ++P->launches;
         k_split_cat_bwd<<<nblk(nlow + nsk), 256, 0, st>>>(gx, B, Hl, Wl, cu, P->ch[l], gh, A->gskip[l]);
         DDG_CHECK_LAUNCH("k_split_cat_bwd");
     }
     for (int l = L - 1; l >= 0; --l) {
         const int Hl = H >> l, Wl = W >> l;
         const long long n = (long long)B * Hl * Wl * P->ch[l];
-        if (l < L - 1) k_add<<<nblk(n), 256, 0, st>>>(gh, A->gskip[l], n);
+        if (l < L - 1) {
+            ++P->launches;
+            k_add<<<nblk(n), 256, 0, st>>>(gh, A->gskip[l], n);
+        }
         const int lb = layer_index(P, false, l, 1), la = layer_index(P, false, l, 0);
         LoadCat xb{A->ea[l], P->ch[l], 0, Hl, Wl, nullptr, 0};
         DDG_TRY(wgrad(P, xb, gh, A->eb[l], B, Hl, Wl, lb, st));
@@ -726,6 +740,7 @@ static ddg_status backward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaS
         if (l > 0) {
             DDG_TRY(bdata(P, ga, A->ea[l], B, Hl, Wl, la, gx, st));
             const long long nin = (long long)B * (Hl * 2) * (Wl * 2) * cin;
+            ++P->launches;
             k_avgpool2_bwd<<<nblk(nin), 256, 0, st>>>(gx, B, Hl * 2, Wl * 2, cin, gh, 0);
             DDG_CHECK_LAUNCH("k_avgpool2_bwd");
         }
@@ -763,6 +778,7 @@ static ddg_status build_input(ddg_predictor* P, int n, const ddg_op* const* A, i
     }
     DDG_CHECK_CUDA(cudaMemcpyAsync(P->d_desc, hd.data(), sizeof(InputDesc) * n, cudaMemcpyHostToDevice, st));
     const int H = A[0]->ny, W = A[0]->nx;
+    ++P->launches;
     k_input<<<nblk((long long)n * H * W), 256, 0, st>>>(reinterpret_cast<InputDesc*>(P->d_desc), n, H, W, i_src,
                                                        sigma, j_c, acts->x0);
     DDG_CHECK_LAUNCH("k_input");
@@ -856,9 +872,12 @@ extern "C" ddg_status predictor_destroy(ddg_predictor* P) {
 
 extern "C" long long predictor_num_params(const ddg_predictor* P) { return P ? P->nparams : 0; }
 
+extern "C" long long predictor_launches(const ddg_predictor* P) { return P ? P->launches : 0; }
+
 extern "C" ddg_status predictor_set_params(ddg_predictor* P, const float* theta, long long n) {
     if (!P || !theta || n != P->nparams) { set_error("predictor_set_params: need %lld values", P ? P->nparams : 0LL); return DDG_EINVAL; }
     DDG_CHECK_CUDA(cudaMemcpy(P->theta, theta, 4 * (size_t)n, cudaMemcpyHostToDevice));
+    ++P->launches;
     k_to_bf16<<<nblk(n), 256>>>(P->theta, P->theta_bf, n);
     DDG_CHECK_LAUNCH("k_to_bf16");
     DDG_CHECK_CUDA(cudaMemset(P->adam_m, 0, 4 * (size_t)n));
@@ -903,6 +922,7 @@ extern "C" ddg_status subspace_predict(ddg_predictor* P, int n, const ddg_op* co
     DDG_TRY(forward(P, n, H, W, &acts, st));
     void** slots = ptr_slots(P, n);
     DDG_CHECK_CUDA(cudaMemcpyAsync(slots, U, sizeof(void*) * n, cudaMemcpyHostToDevice, st));
+    ++P->launches;
     k_to_complex<<<nblk((long long)n * H * W * P->k), 256, 0, st>>>(acts.y, H * W, P->k,
                                                                     reinterpret_cast<double2* const*>(slots), n);
     DDG_CHECK_LAUNCH("k_to_complex");
@@ -924,6 +944,7 @@ extern "C" ddg_status predictor_loss_grad(ddg_predictor* P, int n, const ddg_op*
     DDG_CHECK_CUDA(cudaMemcpyAsync(slots, f, sizeof(void*) * n, cudaMemcpyHostToDevice, st));
     const int k = P->k;
     const size_t smem = sizeof(double2) * (size_t)(2 * k + k * k);
+    ++P->launches;
     k_proj_loss<<<n, 256, smem, st>>>(acts.y, reinterpret_cast<const double2* const*>(slots), H * W, k, n, P->d_loss,
                                       acts.gy);
     DDG_CHECK_LAUNCH("k_proj_loss");
@@ -944,6 +965,7 @@ extern "C" ddg_status predictor_adam_step(ddg_predictor* P, float lr, void* stre
     P->step += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)P->step), c2 = 1.f - powf(b2, (float)P->step);
+    ++P->launches;
     k_adam<<<nblk(P->nparams), 256, 0, as_stream(stream)>>>(P->theta, P->grad, P->adam_m, P->adam_v, P->theta_bf,
                                                             P->nparams, lr, b1, b2, 1e-8f, c1, c2);
     DDG_CHECK_LAUNCH("k_adam");
@@ -1013,6 +1035,7 @@ extern "C" ddg_status predictor_load(ddg_predictor* P, const char* path) {
     DDG_CHECK_CUDA(cudaMemcpy(P->theta, buf.data(), 4 * n, cudaMemcpyHostToDevice));
     DDG_CHECK_CUDA(cudaMemcpy(P->adam_m, buf.data() + n, 4 * n, cudaMemcpyHostToDevice));
     DDG_CHECK_CUDA(cudaMemcpy(P->adam_v, buf.data() + 2 * n, 4 * n, cudaMemcpyHostToDevice));
+    ++P->launches;
     k_to_bf16<<<nblk((long long)n), 256>>>(P->theta, P->theta_bf, (long long)n);
     DDG_CHECK_LAUNCH("k_to_bf16");
     P->step = tail[1];
