@@ -121,6 +121,12 @@ typedef enum {
                             Parallel Computing 112, 2022): 2 passes over the basis per step */
 } ddg_orthogonalization;
 ddg_status ddg_context_set_orthogonalization(ddg_context* ctx, int scheme);
+/* Augmented solves: when the V-only relative residual ||b~|| / ||b|| of the first
+   cycle (Eq. 6's minimum over V) exceeds `threshold`, the predicted subspace is
+   judged to have failed: its least-squares step is kept (x += V R^-1 C^H b) and
+   the solve continues as plain GMRES (info.fallback_used = 1).  Default 0.5;
+   a threshold >= 1 never falls back. */
+ddg_status ddg_context_set_fallback(ddg_context* ctx, double threshold);
 /* Inner-cycle relative tolerance for DDG_C64_REFINE (a cycle ends once its
    least-squares residual falls below eta times the cycle's starting residual).
    Default 1e-5.  Must be in (0, 1). */

@@ -57,6 +57,7 @@ _SIGS = {
     "ddg_context_set_inner_tol": (C.c_int, [_vp, C.c_double]),
     "ddg_context_launches": (C.c_longlong, [_vp]),
     "ddg_context_set_orthogonalization": (C.c_int, [_vp, C.c_int]),
+    "ddg_context_set_fallback": (C.c_int, [_vp, C.c_double]),
     "ddg_context_profile_enable": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_longlong)]),
@@ -170,6 +171,10 @@ class Context:
         """'cgs2' (classical Gram-Schmidt twice) or 'dcgs2' (delayed reorthogonalisation)."""
         code = {"cgs2": 0, "dcgs2": 1}[scheme]
         _check(load().ddg_context_set_orthogonalization(self._h, code), "ddg_context_set_orthogonalization")
+
+    def set_fallback(self, threshold: float):
+        """V-only relative residual above which an augmented solve continues as plain GMRES."""
+        _check(load().ddg_context_set_fallback(self._h, float(threshold)), "ddg_context_set_fallback")
 
     @property
     def workspace_bytes(self) -> int:

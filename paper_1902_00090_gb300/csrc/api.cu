@@ -178,3 +178,9 @@ extern "C" ddg_status ddg_context_set_orthogonalization(ddg_context* ctx, int sc
     reinterpret_cast<Context*>(ctx)->orth = scheme;
     return DDG_OK;
 }
+
+extern "C" ddg_status ddg_context_set_fallback(ddg_context* ctx, double threshold) {
+    if (!ctx || !(threshold > 0.0)) { set_error("ddg_context_set_fallback: threshold must be > 0"); return DDG_EINVAL; }
+    reinterpret_cast<Context*>(ctx)->fallback = threshold;
+    return DDG_OK;
+}

@@ -36,6 +36,7 @@ struct Context {
     int* host_counts = nullptr;      // pinned, polled between launches
     double inner_tol = 1e-5;         // DDG_C64_REFINE inner-cycle relative tolerance
     int orth = 1;                    // 0: CGS2 (two passes per step), 1: delayed CGS2 (one reduction)
+    double fallback = 0.5;           // augmented: V-only residual above this -> plain GMRES after the V step
     int poll_every = 8;              // Arnoldi steps between host polls
     int sm_count = 152;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -133,6 +134,7 @@ struct BatchArgs {
     int nmax;          // leading dimension of B (= kMaxAug)
     double tol;
     double eta;        // inner relative tolerance (0 for complex128)
+    double fallback;   // V-only relative residual above which an augmented solve continues as plain GMRES
     int maxit;
 };
 

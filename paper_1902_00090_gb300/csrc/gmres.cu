@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(BatchArgs a) {
         nb2 += t.y;
     }
     if (S->nb < 0.0) S->nb = sqrt(nb2);
+    if (S->fallback) S->N = 0;   // after a fallback (or a rank-deficient V) the solve is plain GMRES
     const double nb = S->nb, rn = sqrt(rn2);
     S->rn = rn;
     S->pending = 0;
@@ -398,6 +399,12 @@ __global__ void __launch_bounds__(kBlock) k_update_r(BatchArgs a) {
     S->beta = nrm;
     if (S->cycles == 1) S->first_res = nrm / S->nb;
     S->k = 0;
+    if (S->cycles == 1 && nrm > a.fallback * S->nb) {
+        // the predicted subspace fails to cut the residual: keep its least-squares
+        // step (x += V R^-1 C^H r at the cycle end) and continue as plain GMRES
+        S->fallback = 1;
+        return;
+    }
     if (nrm <= 1e-14 * S->rn) {
         // r lies in span(A V): the V step alone solves the residual equation
         S->breakdown = 1;
@@ -1297,6 +1304,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     args.tol = tol;
     args.eta = eta;
     args.maxit = maxit;
+    args.fallback = ctx->fallback;
     std::vector<int> hblk(total_ctas);
     for (int s = 0; s < n; ++s)
         for (int c = 0; c < hp[s].nchunks; ++c) hblk[hp[s].chunk0 + c] = s;
@@ -1566,6 +1574,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     args.tol = tol;
     args.eta = eta;
     args.maxit = maxit;
+    args.fallback = 1e300;
     // every launch reads these: the array keeps the previous call's contents
     std::vector<int> hblk(hp.nchunks, 0);
     DDG_CHECK_CUDA(cudaMemcpyAsync(args.P, &hp, sizeof(SolvePtrs), cudaMemcpyHostToDevice, st));

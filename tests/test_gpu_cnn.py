@@ -160,6 +160,7 @@ def test_training_reduces_loss_and_helps_the_solver():
     eps_tr = inputs.trajectory_set(g, 2, 6, steps=8)
     eps_te = inputs.trajectory_eps(g, 2, 30, steps=4)
     ctx = ddg.Context()
+    ctx.set_fallback(2.0)    # compare the two subspaces inside the augmented method
     src = (g.i_src, g.sigma_src, g.j_src)
 
     def solve(eps_set):

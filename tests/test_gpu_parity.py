@@ -23,7 +23,9 @@ import paper_1902_00090_gb300 as ddg  # noqa: E402
 
 @pytest.fixture(scope="module")
 def ctx():
-    return ddg.Context()
+    c = ddg.Context()
+    c.set_fallback(2.0)     # parity with the oracle's augmented method: never fall back
+    return c
 
 
 def dev(a, dtype=torch.complex128):
@@ -307,6 +309,7 @@ def test_delayed_reorthogonalisation_matches_cgs2(prec):
     res = {}
     for scheme in ("cgs2", "dcgs2"):
         c = ddg.Context(orthogonalization=scheme)
+        c.set_fallback(2.0)
         x, info, st = ddg.gmres_solve(c, op, dev(b), tol=1e-8, restart=40, maxit=4000, precision=prec)
         xa, ia, sa = ddg.augmented_gmres_solve(c, op, dev(b), dev(V), tol=1e-8, restart=40, maxit=4000,
                                                precision=prec)
@@ -328,3 +331,27 @@ def test_dcgs2_is_default_and_matches_oracle_steps(ctx):
     x2, i2, _ = ddg.gmres_solve(ctx, op, dev(b), tol=1e-9, restart=25, maxit=3000)
     assert abs(i1["iters"] - io.iters) <= 1 and abs(i2["iters"] - io.iters) <= 1
     assert rel(host(x2), xo) <= 1e-6
+
+
+def test_poor_subspace_falls_back_to_plain_after_its_step():
+    # V-only residual above the threshold: the solve keeps the least-squares
+    # step over V (Eq. 3 with K empty) and continues as plain GMRES (Eq. 2).
+    g, eps, A, b = small(32, npml=6, seed=12)
+    V = rand_V(g.D, 3, 12)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    c = ddg.Context()
+    c.set_fallback(0.5)
+    x, info, st = ddg.augmented_gmres_solve(c, op, dev(b), dev(V), tol=1e-9, restart=25, maxit=3000)
+    assert st == 0 and info["converged"] and info["fallback_used"] == 1
+    assert info["first_step_rel_residual"] > 0.5
+    # oracle: the same V step, then plain GMRES from it
+    AV = np.column_stack([A @ V[n] for n in range(V.shape[0])])
+    z, *_ = np.linalg.lstsq(AV, b, rcond=None)
+    x1 = V.T @ z
+    xo, io = gmres.plain_gmres(A, b, x0=x1, tol=1e-9, restart=25, maxit=3000)
+    assert abs(info["iters"] - io.iters) <= 1
+    assert rel(host(x), xo) <= 1e-6
+    # a threshold >= 1 keeps the augmented method
+    c.set_fallback(2.0)
+    x2, i2, s2 = ddg.augmented_gmres_solve(c, op, dev(b), dev(V), tol=1e-9, restart=25, maxit=3000)
+    assert s2 == 0 and i2["fallback_used"] == 0
