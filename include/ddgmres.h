@@ -127,6 +127,12 @@ ddg_status ddg_context_set_orthogonalization(ddg_context* ctx, int scheme);
    the solve continues as plain GMRES (info.fallback_used = 1).  Default 0.5;
    a threshold >= 1 never falls back. */
 ddg_status ddg_context_set_fallback(ddg_context* ctx, double threshold);
+/* Restarted augmented solves (the paper does not restart): the first `cycles`
+   restart cycles run data-driven GMRES with V (Eqs. 3-4, S1-S7); later cycles
+   continue as plain GMRES from the current iterate.  Default 1 (the paper's
+   method for the first cycle); 0 keeps only the least-squares step over V;
+   a value >= maxit keeps V in every cycle. */
+ddg_status ddg_context_set_augmented_cycles(ddg_context* ctx, int cycles);
 /* Inner-cycle relative tolerance for DDG_C64_REFINE (a cycle ends once its
    least-squares residual falls below eta times the cycle's starting residual).
    Default 1e-5.  Must be in (0, 1). */
@@ -263,12 +269,20 @@ ddg_status predictor_forward(ddg_predictor* P, int n, const ddg_op* const* A, in
    complex128 column-major (ready for augmented_gmres_solve).  Synchronises. */
 ddg_status subspace_predict(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
                             double j_c, double* const* U, void* stream);
-/* Mean projection loss (Eq. 5) over the batch against the solved fields f[s]
-   (device, D complex128 each) and its gradient (kept inside the predictor; also
-   copied to `grad`, device FP32 [nparams], when not NULL).  Synchronises. */
+/* Training loss: 0 = projection loss (Eq. 5), the default: f[s] are solved
+   fields; 1 = residual loss (Eq. 6), unsupervised: f[s] are the right-hand
+   sides b (l = min over z of ||A V z - b||^2 / ||b||^2 with the problem's own A;
+   its gradient is A^H applied to Eq. 5's gradient in W = A V, with
+   A^H x = conj(S_b A S_b^-1 conj(x)), S_b = diag(sxb_i syb_j)). */
+ddg_status predictor_set_loss(ddg_predictor* P, int kind);
+/* Mean training loss over the batch (f[s]: device, D complex128 each: the
+   solved fields, or the right-hand sides for the residual loss) and its
+   gradient (kept inside the predictor; also copied to `grad`, device FP32
+   [nparams], when not NULL).  Synchronises. */
 ddg_status predictor_loss_grad(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
                                double j_c, const double* const* f, double* loss, float* grad, void* stream);
-/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradient. */
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradient;
+   skipped (weights and moments unchanged) when the last loss was not finite. */
 ddg_status predictor_adam_step(ddg_predictor* P, float lr, void* stream);
 /* predictor_loss_grad followed by predictor_adam_step. */
 ddg_status predictor_train_step(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,

@@ -301,3 +301,35 @@ def input_channels(eps: np.ndarray, wavelength: float, npml: int, src_col: int, 
     x[..., 2] = np.where(inside, 0.0, 1.0)
     x[..., 3][:, src_col] = np.exp(-((np.arange(ny) - j_c) ** 2) / (2 * sigma * sigma))
     return x
+
+
+# ---------------------------------------------------------------- residual loss (Eq. 6)
+def residual_loss_and_grad(A, V: np.ndarray, b: np.ndarray):
+    """Eq. 6 for one sample: l = min over z of ||A V z - b||^2 / ||b||^2.
+    With W = A V it is Eq. 5's expression with (W, b) in place of (V, f), so
+    dl/d(conj V) = A^H dl/d(conj W).  Returns (loss, dl/dRe V, dl/dIm V)."""
+    W = np.column_stack([A @ V[:, c] for c in range(V.shape[1])])
+    loss, gr, gi = projection_loss_and_grad(W, b)
+    gw = 0.5 * (gr + 1j * gi)                       # dl / d conj(W)
+    AH = A.conj().T
+    gv = np.column_stack([AH @ gw[:, c] for c in range(V.shape[1])])
+    return loss, 2.0 * gv.real, 2.0 * gv.imag
+
+
+def batch_residual_loss_and_grad(cfg: CNNConfig, theta, x, ops, rhs, store=None):
+    """Mean Eq. 6 loss over the batch (ops: sparse A per sample, rhs: b per
+    sample) and its gradient w.r.t. theta."""
+    y, cache = forward(cfg, theta, x, keep=True, store=store)
+    V = to_complex_fields(y)
+    B = x.shape[0]
+    gy = np.zeros_like(y)
+    tot = 0.0
+    for s in range(B):
+        l, gr, gi = residual_loss_and_grad(ops[s], V[s], rhs[s])
+        tot += l
+        g = np.zeros((V.shape[1], 2 * cfg.k))
+        g[:, 0::2] = gr
+        g[:, 1::2] = gi
+        gy[s] = g.reshape(y.shape[1:]) / B
+    gtheta, _ = backward(cfg, theta, cache, gy)
+    return tot / B, gtheta

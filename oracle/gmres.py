@@ -197,8 +197,13 @@ def augmentation_setup(A, V: np.ndarray) -> Augmentation:
 
 def augmented_gmres(A, b: np.ndarray, V: np.ndarray, x0=None, tol: float = 1e-6,
                     restart: int = 200, maxit: int = 5000, reorth: bool = True,
-                    breakdown_tol: float = 1e-14, keep_basis: bool = False):
+                    breakdown_tol: float = 1e-14, keep_basis: bool = False,
+                    aug_cycles: int | None = None):
     """Data-driven GMRES (Eq. 3) with the update rule of the supplement.
+
+    aug_cycles (restart reading): None keeps V in every cycle; an integer c runs
+    the augmented method in the first max(c, 1) cycles and continues as plain
+    GMRES (Eq. 2) from the current iterate afterwards.
 
     Returns (f, info); with keep_basis also a dict holding C, Q, H, B of the last
     cycle for invariant checks (C^H Q = 0, Eq. S3).
@@ -225,6 +230,19 @@ def augmented_gmres(A, b: np.ndarray, V: np.ndarray, x0=None, tol: float = 1e-6,
             info.converged = True
             break
         if info.iters >= maxit or info.breakdown:
+            break
+        if aug_cycles is not None and info.cycles >= max(1, aug_cycles):
+            # the augmented cycles are done: plain GMRES from the current iterate
+            xp, ip = plain_gmres(A, b, x0=x, tol=tol, restart=restart, maxit=maxit - info.iters,
+                                 reorth=reorth, breakdown_tol=breakdown_tol)
+            x = xp
+            info.iters += ip.iters
+            info.cycles += ip.cycles
+            info.converged = ip.converged
+            info.true_rel_residual = ip.true_rel_residual
+            info.est_history += ip.est_history
+            info.true_history += ip.true_history[1:]
+            info.cycle_estimates += ip.cycle_estimates
             break
         info.cycles += 1
         # b~ = P_perp r (Eq. 4 applied to the residual equation)

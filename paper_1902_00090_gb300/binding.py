@@ -58,6 +58,7 @@ _SIGS = {
     "ddg_context_launches": (C.c_longlong, [_vp]),
     "ddg_context_set_orthogonalization": (C.c_int, [_vp, C.c_int]),
     "ddg_context_set_fallback": (C.c_int, [_vp, C.c_double]),
+    "ddg_context_set_augmented_cycles": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_enable": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_longlong)]),
@@ -86,6 +87,7 @@ _SIGS = {
     "predictor_loss_grad": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_double, C.c_double,
                                       C.POINTER(_vp), C.POINTER(C.c_double), _vp, _vp]),
     "predictor_adam_step": (C.c_int, [_vp, C.c_float, _vp]),
+    "predictor_set_loss": (C.c_int, [_vp, C.c_int]),
     "predictor_train_step": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_double, C.c_double,
                                        C.POINTER(_vp), C.c_float, C.POINTER(C.c_double), _vp]),
     "predictor_save": (C.c_int, [_vp, C.c_char_p]),
@@ -171,6 +173,10 @@ class Context:
         """'cgs2' (classical Gram-Schmidt twice) or 'dcgs2' (delayed reorthogonalisation)."""
         code = {"cgs2": 0, "dcgs2": 1}[scheme]
         _check(load().ddg_context_set_orthogonalization(self._h, code), "ddg_context_set_orthogonalization")
+
+    def set_augmented_cycles(self, cycles: int):
+        """Restart cycles of an augmented solve that keep V (later cycles: plain GMRES)."""
+        _check(load().ddg_context_set_augmented_cycles(self._h, int(cycles)), "ddg_context_set_augmented_cycles")
 
     def set_fallback(self, threshold: float):
         """V-only relative residual above which an augmented solve continues as plain GMRES."""
@@ -493,6 +499,10 @@ class Predictor:
                                           arr, C.byref(loss), _vp(g.data_ptr()) if g is not None else None,
                                           _stream(stream)), "predictor_loss_grad")
         return loss.value, g
+
+    def set_loss(self, kind: str):
+        """'projection' (Eq. 5; train with solved fields) or 'residual' (Eq. 6; train with b)."""
+        _check(load().predictor_set_loss(self._h, {"projection": 0, "residual": 1}[kind]), "predictor_set_loss")
 
     def adam_step(self, lr, stream=None):
         _check(load().predictor_adam_step(self._h, float(lr), _stream(stream)), "predictor_adam_step")

@@ -184,3 +184,9 @@ extern "C" ddg_status ddg_context_set_fallback(ddg_context* ctx, double threshol
     reinterpret_cast<Context*>(ctx)->fallback = threshold;
     return DDG_OK;
 }
+
+extern "C" ddg_status ddg_context_set_augmented_cycles(ddg_context* ctx, int cycles) {
+    if (!ctx || cycles < 0) { set_error("ddg_context_set_augmented_cycles: cycles must be >= 0"); return DDG_EINVAL; }
+    reinterpret_cast<Context*>(ctx)->aug_cycles = cycles;
+    return DDG_OK;
+}

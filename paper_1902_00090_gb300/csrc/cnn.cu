@@ -419,10 +419,11 @@ __global__ void __launch_bounds__(256) k_proj_loss(const float* __restrict__ y, 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        // Cholesky G = R^H R (upper R in place, column-major), ridge 1e-10 max diag
+        // Cholesky G = R^H R (upper R in place, column-major) with a ridge of 1e-6 max diag:
+        // keeps the loss finite when the predicted vectors become dependent
         double dmax = 0.0;
         for (int c = 0; c < k; ++c) dmax = fmax(dmax, G[c * k + c].x);
-        for (int c = 0; c < k; ++c) G[c * k + c].x += 1e-10 * dmax + 1e-300;
+        for (int c = 0; c < k; ++c) G[c * k + c].x += 1e-6 * dmax + 1e-300;
         for (int p = 0; p < k; ++p) {
             double dd = G[p * k + p].x;
             for (int l = 0; l < p; ++l) dd -= cabs2(G[p * k + l]);
@@ -500,6 +501,72 @@ __global__ void k_to_complex(const float* __restrict__ y, int D, int k, double2*
     U[b][(long long)c * D + e] = make_double2(ye[2 * c], ye[2 * c + 1]);
 }
 
+// Per-sample operator for the residual loss (FP32 coefficients).
+struct FieldOpDesc {
+    const float* eps;
+    const float2* coef;   // [axp(nx) | axm(nx) | ayp(ny) | aym(ny)]
+    const float2* sb;     // [sxb(nx) | syb(ny)]
+    int nx, ny;
+    float kh2;
+};
+
+// out[s][e][c] = (A f_c)[e] for the k complex columns of a [B][D][2k] tensor.
+__global__ void k_fields_apply(const FieldOpDesc* __restrict__ ops, const float* __restrict__ in, int B, int D, int k,
+                               float* __restrict__ out) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)B * D) return;
+    const int s = (int)(idx / D), e = (int)(idx % D);
+    const FieldOpDesc o = ops[s];
+    const int nx = o.nx, ny = o.ny;
+    const int j = e / nx, i = e % nx;
+    const float2 axp = o.coef[i], axm = o.coef[nx + i];
+    const float2 ayp = o.coef[2 * nx + j], aym = o.coef[2 * nx + ny + j];
+    const int ip = (i == nx - 1) ? e - (nx - 1) : e + 1;
+    const int im = (i == 0) ? e + (nx - 1) : e - 1;
+    const int jp = (j == ny - 1) ? e - (ny - 1) * nx : e + nx;
+    const int jm = (j == 0) ? e + (ny - 1) * nx : e - nx;
+    float2 d = cadd(cadd(axp, axm), cadd(ayp, aym));
+    d.x -= o.kh2 * o.eps[e];
+    const float2* f = reinterpret_cast<const float2*>(in) + (long long)s * D * k;
+    float2* y = reinterpret_cast<float2*>(out) + (long long)s * D * k;
+    for (int c = 0; c < k; ++c) {
+        float2 acc = cmul(d, f[(long long)e * k + c]);
+        cfms(acc, axp, f[(long long)ip * k + c]);
+        cfms(acc, axm, f[(long long)im * k + c]);
+        cfms(acc, ayp, f[(long long)jp * k + c]);
+        cfms(acc, aym, f[(long long)jm * k + c]);
+        y[(long long)e * k + c] = acc;
+    }
+}
+
+// A^H g = conj(S_b A S_b^-1 conj(g)) (A^T = S_b A S_b^-1 from the complex
+// symmetry of S_b A): the two diagonal steps around k_fields_apply.
+__global__ void k_adj_pre(const FieldOpDesc* __restrict__ ops, const float* __restrict__ g, int B, int D, int k,
+                          float* __restrict__ u) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)B * D * k) return;
+    const int s = (int)(idx / ((long long)D * k));
+    const int e = (int)((idx / k) % D);
+    const FieldOpDesc o = ops[s];
+    const float2 sb = cmul(o.sb[e % o.nx], o.sb[o.nx + e / o.nx]);
+    const float2 gv = reinterpret_cast<const float2*>(g)[idx];
+    const float2 cg = make_float2(gv.x, -gv.y);
+    // conj(g) / sb
+    const float den = sb.x * sb.x + sb.y * sb.y;
+    reinterpret_cast<float2*>(u)[idx] = make_float2((cg.x * sb.x + cg.y * sb.y) / den, (cg.y * sb.x - cg.x * sb.y) / den);
+}
+__global__ void k_adj_post(const FieldOpDesc* __restrict__ ops, float* __restrict__ v, int B, int D, int k) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)B * D * k) return;
+    const int s = (int)(idx / ((long long)D * k));
+    const int e = (int)((idx / k) % D);
+    const FieldOpDesc o = ops[s];
+    const float2 sb = cmul(o.sb[e % o.nx], o.sb[o.nx + e / o.nx]);
+    float2* vp = reinterpret_cast<float2*>(v) + idx;
+    const float2 w = cmul(sb, *vp);
+    *vp = make_float2(w.x, -w.y);
+}
+
 inline unsigned nblk(long long n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace cnn
@@ -519,6 +586,8 @@ struct ddg_predictor {
     float* adam_v = nullptr;
     long long step = 0;
     long long launches = 0;       // kernels launched by this predictor
+    int loss_kind = 0;            // 0: projection loss (Eq. 5), 1: residual loss (Eq. 6)
+    bool last_finite = true;      // the last loss was finite (else the next Adam step is skipped)
     bf16* wk = nullptr;           // per-layer re-laid-out BF16 weights (forward / backward)
     // activation workspace
     void* act = nullptr;
@@ -547,6 +616,8 @@ struct Acts {
     bf16* db[kMaxLevels];
     float* y;
     float* gy;
+    float* y2;     // residual loss: A V, then S_b^-1 conj(dl/dW)
+    float* gy2;    // residual loss: dl/dW
     float* g1;     // scratch gradients (largest tensor)
     float* g2;
     float* g3;
@@ -579,6 +650,8 @@ static size_t plan_acts(const ddg_predictor* P, int B, int H, int W, char* base,
     }
     A->y = (float*)take(sizeof(float) * (size_t)B * H * W * 2 * P->k);
     A->gy = (float*)take(sizeof(float) * (size_t)B * H * W * 2 * P->k);
+    A->y2 = (float*)take(sizeof(float) * (size_t)B * H * W * 2 * P->k);
+    A->gy2 = (float*)take(sizeof(float) * (size_t)B * H * W * 2 * P->k);
     A->g1 = (float*)take(sizeof(float) * maxg);
     A->g2 = (float*)take(sizeof(float) * maxg);
     A->g3 = (float*)take(sizeof(float) * maxg);
@@ -764,11 +837,18 @@ static ddg_status check_batch(const ddg_predictor* P, int n, const ddg_op* const
     return DDG_OK;
 }
 
+static FieldOpDesc* field_ops(ddg_predictor* P, int n);
+
 static ddg_status build_input(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma, double j_c,
                               Acts* acts, cudaStream_t st) {
     std::vector<InputDesc> hd(n);
-    for (int s = 0; s < n; ++s) hd[s] = InputDesc{A[s]->eps_d, A[s]->nx, A[s]->ny, A[s]->npml_x, A[s]->wavelength};
-    const size_t need = sizeof(InputDesc) * n + sizeof(void*) * 2 * n + 256;
+    std::vector<FieldOpDesc> hf(n);
+    for (int s = 0; s < n; ++s) {
+        hd[s] = InputDesc{A[s]->eps_d, A[s]->nx, A[s]->ny, A[s]->npml_x, A[s]->wavelength};
+        hf[s] = FieldOpDesc{A[s]->eps_f, A[s]->coef_f, A[s]->sb_f, A[s]->nx, A[s]->ny, (float)(A[s]->kh * A[s]->kh)};
+    }
+    const size_t need = ((sizeof(InputDesc) * n + 15) / 16) * 16 + ((sizeof(FieldOpDesc) * n + 15) / 16) * 16 +
+                        sizeof(void*) * 2 * n + 256;
     if (need > P->desc_bytes) {
         cudaFree(P->d_desc);
         P->d_desc = nullptr;
@@ -777,6 +857,7 @@ static ddg_status build_input(ddg_predictor* P, int n, const ddg_op* const* A, i
         P->desc_bytes = need;
     }
     DDG_CHECK_CUDA(cudaMemcpyAsync(P->d_desc, hd.data(), sizeof(InputDesc) * n, cudaMemcpyHostToDevice, st));
+    DDG_CHECK_CUDA(cudaMemcpyAsync(field_ops(P, n), hf.data(), sizeof(FieldOpDesc) * n, cudaMemcpyHostToDevice, st));
     const int H = A[0]->ny, W = A[0]->nx;
     ++P->launches;
     k_input<<<nblk((long long)n * H * W), 256, 0, st>>>(reinterpret_cast<InputDesc*>(P->d_desc), n, H, W, i_src,
@@ -785,8 +866,12 @@ static ddg_status build_input(ddg_predictor* P, int n, const ddg_op* const* A, i
     return DDG_OK;
 }
 
+static FieldOpDesc* field_ops(ddg_predictor* P, int n) {
+    return reinterpret_cast<FieldOpDesc*>(reinterpret_cast<char*>(P->d_desc) + ((sizeof(InputDesc) * n + 15) / 16) * 16);
+}
 static void** ptr_slots(ddg_predictor* P, int n) {
-    return reinterpret_cast<void**>(reinterpret_cast<char*>(P->d_desc) + ((sizeof(InputDesc) * n + 15) / 16) * 16);
+    return reinterpret_cast<void**>(reinterpret_cast<char*>(field_ops(P, n)) +
+                                    ((sizeof(FieldOpDesc) * n + 15) / 16) * 16);
 }
 
 static void free_predictor(ddg_predictor* P) {
@@ -943,11 +1028,31 @@ extern "C" ddg_status predictor_loss_grad(ddg_predictor* P, int n, const ddg_op*
     void** slots = ptr_slots(P, n);
     DDG_CHECK_CUDA(cudaMemcpyAsync(slots, f, sizeof(void*) * n, cudaMemcpyHostToDevice, st));
     const int k = P->k;
+    const int D = H * W;
     const size_t smem = sizeof(double2) * (size_t)(2 * k + k * k);
-    ++P->launches;
-    k_proj_loss<<<n, 256, smem, st>>>(acts.y, reinterpret_cast<const double2* const*>(slots), H * W, k, n, P->d_loss,
-                                      acts.gy);
-    DDG_CHECK_LAUNCH("k_proj_loss");
+    if (P->loss_kind == 0) {
+        // Eq. 5: V against the solved fields f
+        ++P->launches;
+        k_proj_loss<<<n, 256, smem, st>>>(acts.y, reinterpret_cast<const double2* const*>(slots), D, k, n,
+                                          P->d_loss, acts.gy);
+    } else {
+        // Eq. 6: W = A V against the right-hand sides b, then dl/dV = A^H dl/dW
+        FieldOpDesc* fo = field_ops(P, n);
+        const long long nk = (long long)n * D * k;
+        ++P->launches;
+        k_fields_apply<<<nblk((long long)n * D), 256, 0, st>>>(fo, acts.y, n, D, k, acts.y2);
+        ++P->launches;
+        k_proj_loss<<<n, 256, smem, st>>>(acts.y2, reinterpret_cast<const double2* const*>(slots), D, k, n,
+                                          P->d_loss, acts.gy2);
+        ++P->launches;
+        k_adj_pre<<<nblk(nk), 256, 0, st>>>(fo, acts.gy2, n, D, k, acts.y2);
+        ++P->launches;
+        k_fields_apply<<<nblk((long long)n * D), 256, 0, st>>>(fo, acts.y2, n, D, k, acts.gy);
+        ++P->launches;
+        k_adj_post<<<nblk(nk), 256, 0, st>>>(fo, acts.gy, n, D, k);
+    }
+    DDG_CHECK_LAUNCH("loss");
+
     DDG_CHECK_CUDA(cudaMemsetAsync(P->grad, 0, 4 * (size_t)P->nparams, st));
     DDG_TRY(backward(P, n, H, W, &acts, st));
     std::vector<double> hl(n);
@@ -957,11 +1062,13 @@ extern "C" ddg_status predictor_loss_grad(ddg_predictor* P, int n, const ddg_op*
     double tot = 0.0;
     for (double v : hl) tot += v;
     if (loss) *loss = tot / n;
+    P->last_finite = std::isfinite(tot);
     return DDG_OK;
 }
 
 extern "C" ddg_status predictor_adam_step(ddg_predictor* P, float lr, void* stream) {
     if (!P || !(lr > 0.f)) { set_error("predictor_adam_step: bad arguments"); return DDG_EINVAL; }
+    if (!P->last_finite) return DDG_OK;   // a non-finite loss: leave weights and moments unchanged
     P->step += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)P->step), c2 = 1.f - powf(b2, (float)P->step);
@@ -1040,5 +1147,11 @@ extern "C" ddg_status predictor_load(ddg_predictor* P, const char* path) {
     DDG_CHECK_LAUNCH("k_to_bf16");
     P->step = tail[1];
     DDG_CHECK_CUDA(cudaDeviceSynchronize());
+    return DDG_OK;
+}
+
+extern "C" ddg_status predictor_set_loss(ddg_predictor* P, int kind) {
+    if (!P || (kind != 0 && kind != 1)) { set_error("predictor_set_loss: kind must be 0 (Eq. 5) or 1 (Eq. 6)"); return DDG_EINVAL; }
+    P->loss_kind = kind;
     return DDG_OK;
 }

@@ -119,6 +119,10 @@ struct ddg_op {
     //   axp_i = 1/(sxb_i sxf_i), axm_i = 1/(sxb_i sxf_{i-1}), same along y
     double2* coef_d = nullptr;
     float2* coef_f = nullptr;
+    // stretch factors at integer nodes: [sxb(nx) | syb(ny)]; diag(sxb_i syb_j) A is
+    // complex symmetric, which gives A^T = S_b A S_b^-1
+    double2* sb_d = nullptr;
+    float2* sb_f = nullptr;
 };
 
 namespace ddg {

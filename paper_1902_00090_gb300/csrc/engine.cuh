@@ -37,6 +37,7 @@ struct Context {
     double inner_tol = 1e-5;         // DDG_C64_REFINE inner-cycle relative tolerance
     int orth = 1;                    // 0: CGS2 (two passes per step), 1: delayed CGS2 (one reduction)
     double fallback = 0.5;           // augmented: V-only residual above this -> plain GMRES after the V step
+    int aug_cycles = 1;              // augmented: restart cycles that keep V (later cycles run plain GMRES)
     int poll_every = 8;              // Arnoldi steps between host polls
     int sm_count = 152;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -135,6 +136,7 @@ struct BatchArgs {
     double tol;
     double eta;        // inner relative tolerance (0 for complex128)
     double fallback;   // V-only relative residual above which an augmented solve continues as plain GMRES
+    int aug_cycles;    // restart cycles of an augmented solve that keep V (0: its least-squares step only)
     int maxit;
 };
 

@@ -293,7 +293,9 @@ __global__ void __launch_bounds__(kBlock) k_residual(BatchArgs a) {
         nb2 += t.y;
     }
     if (S->nb < 0.0) S->nb = sqrt(nb2);
-    if (S->fallback) S->N = 0;   // after a fallback (or a rank-deficient V) the solve is plain GMRES
+    // after a fallback (or a rank-deficient V), or once the augmented cycles are
+    // done, the solve continues as plain GMRES
+    if (S->fallback || (S->N > 0 && S->cycles >= max(1, a.aug_cycles))) S->N = 0;
     const double nb = S->nb, rn = sqrt(rn2);
     S->rn = rn;
     S->pending = 0;
@@ -399,7 +401,7 @@ __global__ void __launch_bounds__(kBlock) k_update_r(BatchArgs a) {
     S->beta = nrm;
     if (S->cycles == 1) S->first_res = nrm / S->nb;
     S->k = 0;
-    if (S->cycles == 1 && nrm > a.fallback * S->nb) {
+    if (S->cycles == 1 && (nrm > a.fallback * S->nb || a.aug_cycles == 0)) {
         // the predicted subspace fails to cut the residual: keep its least-squares
         // step (x += V R^-1 C^H r at the cycle end) and continue as plain GMRES
         S->fallback = 1;
@@ -1305,6 +1307,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     args.eta = eta;
     args.maxit = maxit;
     args.fallback = ctx->fallback;
+    args.aug_cycles = ctx->aug_cycles;
     std::vector<int> hblk(total_ctas);
     for (int s = 0; s < n; ++s)
         for (int c = 0; c < hp[s].nchunks; ++c) hblk[hp[s].chunk0 + c] = s;
@@ -1575,6 +1578,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     args.eta = eta;
     args.maxit = maxit;
     args.fallback = 1e300;
+    args.aug_cycles = 1;
     // every launch reads these: the array keeps the previous call's contents
     std::vector<int> hblk(hp.nchunks, 0);
     DDG_CHECK_CUDA(cudaMemcpyAsync(args.P, &hp, sizeof(SolvePtrs), cudaMemcpyHostToDevice, st));

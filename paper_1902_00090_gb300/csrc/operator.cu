@@ -22,7 +22,7 @@ __device__ __forceinline__ double2 stretch_at(double p, int n, int L, double sma
 // One thread per index of x (t < nx) then y (t >= nx): coefficients
 // ap_t = 1/(sb_t sf_t), am_t = 1/(sb_t sf_{t-1}) in FP64 and FP32.
 __global__ void k_pml_coef(int nx, int ny, int Lx, int Ly, double smx, double smy, double m,
-                           double2* coef_d, float2* coef_f) {
+                           double2* coef_d, float2* coef_f, double2* sb_d, float2* sb_f) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nx + ny) return;
     const bool isx = t < nx;
@@ -43,6 +43,8 @@ __global__ void k_pml_coef(int nx, int ny, int Lx, int Ly, double smx, double sm
     cd[n + i] = am;
     cf[i] = make_float2((float)ap.x, (float)ap.y);
     cf[n + i] = make_float2((float)am.x, (float)am.y);
+    sb_d[t] = sb;
+    sb_f[t] = make_float2((float)sb.x, (float)sb.y);
 }
 
 // Copies eps to the operator (FP64 and FP32) and flags non-finite / non-positive values.
@@ -121,6 +123,8 @@ static void free_op(ddg_op* A) {
     cudaFree(A->eps_f);
     cudaFree(A->coef_d);
     cudaFree(A->coef_f);
+    cudaFree(A->sb_d);
+    cudaFree(A->sb_f);
     delete A;
 }
 
@@ -160,7 +164,9 @@ extern "C" ddg_status fdfd_operator(const ddg_grid* g, const double* eps, ddg_op
     cudaError_t e3 = cudaMalloc(&A->coef_d, ncoef * sizeof(double2));
     cudaError_t e4 = cudaMalloc(&A->coef_f, ncoef * sizeof(float2));
     cudaError_t e5 = cudaMalloc(&bad, sizeof(int));
-    if (e1 || e2 || e3 || e4 || e5) {
+    cudaError_t e6 = cudaMalloc(&A->sb_d, (g->nx + g->ny) * sizeof(double2));
+    cudaError_t e7 = cudaMalloc(&A->sb_f, (g->nx + g->ny) * sizeof(float2));
+    if (e1 || e2 || e3 || e4 || e5 || e6 || e7) {
         cudaGetLastError();
         cudaFree(bad);
         free_op(A);
@@ -173,7 +179,7 @@ extern "C" ddg_status fdfd_operator(const ddg_grid* g, const double* eps, ddg_op
     cudaError_t ce = cudaMemsetAsync(bad, 0, sizeof(int), s);
     if (ce == cudaSuccess) {
         k_pml_coef<<<(g->nx + g->ny + 127) / 128, 128, 0, s>>>(g->nx, g->ny, g->npml_x, g->npml_y, smx, smy,
-                                                             g->pml_order, A->coef_d, A->coef_f);
+                                                             g->pml_order, A->coef_d, A->coef_f, A->sb_d, A->sb_f);
         k_eps_copy<<<(unsigned)((A->D + 255) / 256), 256, 0, s>>>(eps, A->D, A->eps_d, A->eps_f, bad);
         ce = cudaGetLastError();
     }

@@ -203,3 +203,27 @@ def test_full_size_network_runs_at_128():
     P.init_he(seed=0)
     y = P.forward(ops, (g.i_src, g.sigma_src, g.j_src))
     assert y.shape == (2, 128, 128, 16) and torch.isfinite(y).all()
+
+
+def test_residual_loss_and_gradient_match_oracle():
+    g, eps, ops = small_problems()
+    P = ddg.Predictor(**SMALL)
+    P.init_he(seed=8)
+    P.set_loss("residual")
+    theta = P.get_params().astype(np.float64)
+    src = (g.i_src, g.sigma_src, g.j_src)
+    bs = [ddg.fdfd_source(op, *src) for op in ops]
+    loss, grad = P.loss_grad(ops, src, bs)
+    cfg = ocnn.CNNConfig(cin=4, channels=SMALL["channels"], k=SMALL["k"])
+    x = oracle_inputs(g, eps)
+    As = [fdfd.operator_for(g, e) for e in eps]
+    rhs = [b.cpu().numpy() for b in bs]
+    gg = grad.cpu().numpy().astype(np.float64)
+    assert 0.0 <= loss <= 1.0
+    lb, gb = ocnn.batch_residual_loss_and_grad(cfg, ocnn.round_weights(cfg, theta, ocnn.bf16_round),
+                                               ocnn.bf16_round(x), As, rhs, store=ocnn.bf16_round)
+    assert abs(loss - lb) <= 1e-3 * max(lb, 1e-2)
+    assert gg @ gb / (np.linalg.norm(gg) * np.linalg.norm(gb)) >= 0.999
+    lo, go = ocnn.batch_residual_loss_and_grad(cfg, theta, x, As, rhs)
+    assert abs(loss - lo) <= 2e-2 * max(lo, 1e-2)
+    assert gg @ go / (np.linalg.norm(gg) * np.linalg.norm(go)) >= 0.98

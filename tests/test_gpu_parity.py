@@ -24,7 +24,8 @@ import paper_1902_00090_gb300 as ddg  # noqa: E402
 @pytest.fixture(scope="module")
 def ctx():
     c = ddg.Context()
-    c.set_fallback(2.0)     # parity with the oracle's augmented method: never fall back
+    c.set_fallback(2.0)           # parity with the oracle's augmented method: never fall back,
+    c.set_augmented_cycles(10**6)  # and keep V in every restart cycle
     return c
 
 
@@ -355,3 +356,21 @@ def test_poor_subspace_falls_back_to_plain_after_its_step():
     c.set_fallback(2.0)
     x2, i2, s2 = ddg.augmented_gmres_solve(c, op, dev(b), dev(V), tol=1e-9, restart=25, maxit=3000)
     assert s2 == 0 and i2["fallback_used"] == 0
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_first_cycle_augmented_then_plain(prec):
+    # default restart reading: the paper's method in the first cycle, plain GMRES after
+    g, eps, A, b = small(32, npml=6, seed=14)
+    A2 = fdfd.operator_for(g, eps * 1.01)
+    V = np.stack([spla.spsolve(A2.tocsc(), b), inputs.random_complex(g.D, 14)])
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    c = ddg.Context()
+    x, info, st = ddg.augmented_gmres_solve(c, op, dev(b), dev(V), tol=1e-9, restart=25, maxit=3000,
+                                            precision=prec)
+    assert st == 0 and info["converged"] and not info["fallback_used"]
+    xo, io = gmres.augmented_gmres(A, b, V.T, tol=1e-9, restart=25, maxit=3000, aug_cycles=1)
+    assert np.linalg.norm(b - A @ host(x)) / np.linalg.norm(b) <= 1e-9
+    if prec == "c128":
+        assert abs(info["iters"] - io.iters) <= 1
+        assert rel(host(x), xo) <= 1e-6

@@ -132,3 +132,22 @@ def test_bf16_rounding_definition():
     x = np.random.default_rng(0).standard_normal(1000)
     r = cnn.bf16_round(x)
     assert np.max(np.abs(r - x) / np.abs(x)) <= 2.0 ** -8
+
+
+def test_residual_loss_value_and_gradient():
+    from oracle import fdfd
+    from paper_1902_00090_gb300 import inputs
+    g = inputs.Grid(nx=12, ny=10, npml=3, i_src=3, sigma_src=2.0, slab_cells=2)
+    rng = np.random.default_rng(6)
+    A = fdfd.operator_for(g, inputs.background_eps(g) + rng.random((g.ny, g.nx)))
+    b = fdfd.source_for(g)
+    V = rng.standard_normal((g.D, 3)) + 1j * rng.standard_normal((g.D, 3))
+    l, gr, gi = cnn.residual_loss_and_grad(A, V, b)
+    assert abs(l - losses.residual_loss(A, V, b)) <= 1e-12          # Eq. 6 by lstsq
+    for _ in range(12):
+        r, c = rng.integers(g.D), rng.integers(3)
+        for part, gg in ((1.0, gr), (1j, gi)):
+            dV = np.zeros_like(V)
+            dV[r, c] = 1e-7 * part
+            fd = (cnn.residual_loss_and_grad(A, V + dV, b)[0] - cnn.residual_loss_and_grad(A, V - dV, b)[0]) / 2e-7
+            assert abs(fd - gg[r, c]) <= 1e-6 * max(1.0, abs(fd))

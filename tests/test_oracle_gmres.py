@@ -172,3 +172,15 @@ def test_losses_range_and_extremes():
     assert abs(losses.projection_loss(V, f_perp) - 1.0) <= 1e-12
     f = rng.standard_normal(D) + 1j * rng.standard_normal(D)
     assert 0.0 <= losses.projection_loss(V, f) <= 1.0
+
+
+def test_augmented_first_cycle_then_plain_reading():
+    # aug_cycles = 1: the first cycle is the paper's method, the rest plain GMRES
+    g, A, b = small_problem(24, npml=4, seed=13)
+    rng = np.random.default_rng(13)
+    V = rng.standard_normal((b.size, 3)) + 1j * rng.standard_normal((b.size, 3))
+    x1, i1 = gmres.augmented_gmres(A, b, V, tol=1e-9, restart=20, maxit=20)
+    xp, ip = gmres.plain_gmres(A, b, x0=x1, tol=1e-9, restart=20, maxit=4000)
+    x, info = gmres.augmented_gmres(A, b, V, tol=1e-9, restart=20, maxit=4000, aug_cycles=1)
+    assert info.converged and info.iters == i1.iters + ip.iters
+    assert np.linalg.norm(x - xp) <= 1e-12 * np.linalg.norm(xp)
