@@ -118,6 +118,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ ranks
+def reduce_over_ranks(ms: float, solved: int, world: int, device=None):
+    """Max of the timed region over ranks and the total solves of all ranks
+    (torch.distributed; the identity on a single process)."""
+    if world <= 1:
+        return ms, solved
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    n = torch.tensor([solved], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(n.item()))
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args, rank, world):
     import torch
@@ -211,11 +226,9 @@ def run_ours(args, rank, world):
         if profile:
             ctx.profile_enable(False)
         clk = sampler.stop() if sampler else None
-        if world > 1:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, infos, launches, prof, clk
+        solved = K * int(sum(i["converged"] for i in infos))
+        ms, solved = reduce_over_ranks(ms, solved, world, dev)
+        return ms, infos, launches, prof, clk, solved
 
     def summary(infos):
         return {"iters_mean": float(np.mean([i["iters"] for i in infos])),
@@ -225,8 +238,8 @@ def run_ours(args, rank, world):
                 "worst_true_rel_residual": float(max(i["true_rel_residual"] for i in infos))}
 
     K, W = args.steps, args.warmup
-    ms, infos, launches, prof, clk = timed(step_cnn, K, W, profile=True, clocks=True)
-    value = world * sum(i["converged"] for i in infos) * K / (ms / 1e3)
+    ms, infos, launches, prof, clk, solved = timed(step_cnn, K, W, profile=True, clocks=True)
+    value = solved / (ms / 1e3)
     # CNN inference alone (the predict call of one step)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -237,13 +250,13 @@ def run_ours(args, rank, world):
     predict_ms = e0.elapsed_time(e1)
 
     sK = max(1, K // 2)
-    pms, pinf, _, _, _ = timed(step_pca, sK, 1)
-    pca = {"value": world * sum(i["converged"] for i in pinf) * sK / (pms / 1e3), "unit": "solves/s",
+    pms, pinf, _, _, _, psolved = timed(step_pca, sK, 1)
+    pca = {"value": psolved / (pms / 1e3), "unit": "solves/s",
            "ms_per_step": pms / sK, "k": args.k, "fit_s": round(pca_s, 2), **summary(pinf)}
     plain = None
     if not args.no_plain:
-        qms, qinf, _, _, _ = timed(step_plain, sK, 1)
-        plain = {"value": world * sum(i["converged"] for i in qinf) * sK / (qms / 1e3), "unit": "solves/s",
+        qms, qinf, _, _, _, qsolved = timed(step_plain, sK, 1)
+        plain = {"value": qsolved / (qms / 1e3), "unit": "solves/s",
                  "ms_per_step": qms / sK, **summary(qinf)}
 
     # --- e2e: host buffers in, host buffers out, through the C ABI
@@ -261,8 +274,8 @@ def run_ours(args, rank, world):
         return None, inf, st_
 
     eK = max(1, K // 2)
-    ems, einf, _, _, _ = timed(step_e2e, eK, 1)
-    e2e = {"value": world * sum(i["converged"] for i in einf) * eK / (ems / 1e3), "unit": "solves/s",
+    ems, einf, _, _, _, esolved = timed(step_e2e, eK, 1)
+    e2e = {"value": esolved / (ems / 1e3), "unit": "solves/s",
            "h2d_bytes_per_step": int(eps_host.numel() * 8), "d2h_bytes_per_step": int(x_host.numel() * 16)}
 
     # --- roofline of the dominant kernel class (live CUDA events, algorithmic bytes)

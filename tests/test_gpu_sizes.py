@@ -1,0 +1,81 @@
+"""Parity at the other workload sizes: 256x256 at two wavelengths, a batch of
+uneven grids (128^2, 192^2, 256^2, 384x256), and the 1024x1024 large grid
+(20 nm cells, 20-cell PML), checked against the oracle's operator."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import fdfd
+from paper_1902_00090_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1902_00090_gb300 as ddg  # noqa: E402
+
+
+def dev(a, dtype=torch.complex128):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def relres(A, x, b):
+    return np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("wl", [1300e-9, 1550e-9])
+def test_256_two_wavelengths(wl):
+    g = inputs.grid_for(256, 256, wavelength=wl)
+    eps = inputs.trajectory_eps(g, 3, 0, steps=2)[1]
+    A = fdfd.operator_for(g, eps)
+    b = fdfd.source_for(g)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    bd = ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src)
+    ctx = ddg.Context()
+    x, info, st = ddg.gmres_solve(ctx, op, bd, tol=1e-6, restart=200, maxit=20000, precision="c64")
+    assert st == 0 and info["converged"]
+    xh = x.cpu().numpy()
+    assert relres(A, xh, b) <= 1e-6
+    xd = spla.spsolve(A.tocsc(), b)
+    assert np.linalg.norm(xh - xd) / np.linalg.norm(xd) <= 1e-5
+
+
+def test_uneven_batch_of_workload_grids():
+    sizes = [(128, 128), (192, 192), (256, 256), (384, 256)]
+    ops, bs, As, bos = [], [], [], []
+    for t, (nx, ny) in enumerate(sizes):
+        g = inputs.grid_for(nx, ny)
+        eps = inputs.trajectory_eps(g, 4, t, steps=1)[0]
+        ops.append(ddg.fdfd_operator(g, dev(eps, torch.float64)))
+        bs.append(ddg.fdfd_source(ops[-1], g.i_src, g.sigma_src, g.j_src))
+        As.append(fdfd.operator_for(g, eps))
+        bos.append(fdfd.source_for(g))
+    ctx = ddg.Context()
+    xs, infos, st = ddg.gmres_solve_batched(ctx, ops, bs, tol=1e-6, restart=200, maxit=20000, precision="c64")
+    assert st == 0
+    for A, b, x, i in zip(As, bos, xs, infos):
+        assert i["converged"] and relres(A, x.cpu().numpy(), b) <= 1e-6
+
+
+def test_large_grid_1024_properties():
+    # 1M unknowns: operator element by element on a random vector, and a capped
+    # c64 solve whose FP64 true residual (reported by the library) equals the
+    # oracle's recomputation and decreases.
+    g = inputs.grid_1024()
+    eps = inputs.trajectory_eps(g, 5, 0, steps=1)[0]
+    A = fdfd.operator_for(g, eps)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    v = inputs.random_complex(g.D, 3)
+    y = ddg.fdfd_apply(op, dev(v)).cpu().numpy()
+    yo = A @ v
+    assert np.max(np.abs(y - yo)) <= 1e-13 * np.max(np.abs(yo))
+    b = fdfd.source_for(g)
+    bd = ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src)
+    ctx = ddg.Context()
+    x, info, st = ddg.gmres_solve(ctx, op, bd, tol=1e-6, restart=100, maxit=300, precision="c64")
+    assert st == 4 and info["iters"] == 300
+    r = relres(A, x.cpu().numpy(), b)
+    assert abs(r - info["true_rel_residual"]) <= 1e-10
+    assert r < 1.0
