@@ -102,7 +102,8 @@ struct SolvePtrs {
     double* cs;                // rotation cosines (m)
     double2* sn;               // rotation sines (m)
     double2* g;                // rotated right-hand side (m+1)
-    double2* hsum;             // Gram-Schmidt coefficients, sum of both passes (KP)
+    double2* hsum;             // Gram-Schmidt coefficients, sum of both passes (CGS2); DCGS2: first-pass
+                               // coefficients h1 of column j in buffer j & 1 (2 x KP)
     double2* hp;               // coefficients of the current pass (KP)
     double2* part;             // per-CTA partial sums, nchunks x KP
     double2* Rinv;             // R^-1 of A V = C R (N x N, column-major)
@@ -138,6 +139,7 @@ struct BatchArgs {
     double fallback;   // V-only relative residual above which an augmented solve continues as plain GMRES
     int aug_cycles;    // restart cycles of an augmented solve that keep V (0: its least-squares step only)
     int maxit;
+    int nsolves;       // solves in the batch (k_update2 puts one block per solve in front of its sweep)
 };
 
 // Adds `v` to the class counter once per CTA (thread 0), when profiling.

@@ -602,7 +602,6 @@ __global__ void __launch_bounds__(kBlock) k_update_w(BatchArgs a, int j, int mod
     count_bytes(a, DDG_K_UPDATE, (double)chunk_rows<T>() * ((double)K + 2.0) * sizeof(V));
     extern __shared__ __align__(16) unsigned char smraw[];
     V* hs = reinterpret_cast<V*>(smraw);
-    __shared__ double sm[kWarps];
     for (int t = threadIdx.x; t < K; t += kBlock) hs[t] = from_d2<V>(P.hp[t]);
     __syncthreads();
     const long long ldp = P.ld / VEC;
@@ -684,6 +683,107 @@ cgs2_done:
 }
 
 // ---------------------------------------------------------------- delayed reorthogonalisation (DCGS2)
+// Finishes Arnoldi column j = i-1 once k_dots2 has reduced s, alpha and beta
+// (tv[N+i ..), tv[N+2i], tv[N+2i+2]):
+//   H[0:i, j] = h1 + s,  H[i, j] = beta,  B[:, j] = h1_C   (h1: pass-1 coefficients of column j)
+// then its Givens rotation, the residual estimate |g_{j+1}| and the stop test.
+// With `next` (i < m; one CTA per solve launched in front of k_update2's sweep)
+// warps 1.. meanwhile form h1 of column i, with A Q_i s = [C Q_{i+1}] Hs,
+//   Hs = [B; H][:, 0:i] s,  h1 = (t - Hs) / beta  (rows < N+i),
+//   h1_i = (gamma - s^H t_Q) / beta^2 - Hs_i / beta,
+// into the other h1 buffer.  Nothing here feeds the sweep it runs beside.
+// The BatchArgs fields dcgs2_finish_column reads, passed by value (a reference
+// to the kernel parameter block would be copied to the stack).
+struct FinishArgs {
+    int m, KP, nmax, maxit;
+    int* counts;
+};
+__device__ __forceinline__ FinishArgs finish_args(const BatchArgs& a) {
+    return FinishArgs{a.m, a.KP, a.nmax, a.maxit, a.counts};
+}
+
+template <typename T>
+__device__ __noinline__ void dcgs2_finish_column(FinishArgs a, SolveScal* S, const SolvePtrs& P, int i, bool next,
+                                                 unsigned char* smraw) {
+    using V = c2_t<T>;
+    const int N = S->N;
+    const int m = a.m, ldh = m + 1;
+    const int j = i - 1;
+    const double2* tv = P.tv;
+    const double2* sv = tv + N + i;
+    const double2* h1p = P.hsum + (size_t)(j & 1) * a.KP;   // h1 of column j
+    double2* h1n = P.hsum + (size_t)(i & 1) * a.KP;         // h1 of column i
+    // 16-byte arrays first, the m doubles last (keeps every double2 aligned for any m)
+    double2* gcol = reinterpret_cast<double2*>(smraw);    // m + 2 entries
+    double2* gsn = gcol + (m + 2);                        // m entries
+    double2* gout = gsn + m;                              // m + 2 entries
+    V* svl = reinterpret_cast<V*>(gout + (m + 2));        // s in the Krylov precision, m entries
+    double* gcs = reinterpret_cast<double*>(svl + m);     // m entries (last: 8-byte items)
+    V* Hl = reinterpret_cast<V*>(P.Hh);                       // Krylov-precision copy of H
+    V* Bl = reinterpret_cast<V*>(P.Hh + (size_t)(m + 1) * m);  // and of B
+    __shared__ double smf[kWarps];
+    const double beta = tv[N + 2 * i + 2].x;
+    for (int t = threadIdx.x; t < i; t += kBlock) {
+        const double2 h = cadd(h1p[N + t], sv[t]);
+        gcol[t] = h;
+        Hl[(long long)j * ldh + t] = from_d2<V>(h);
+        svl[t] = from_d2<V>(sv[t]);
+    }
+    if (threadIdx.x == 0) Hl[(long long)j * ldh + i] = mk((T)beta, (T)0);
+    for (int n = threadIdx.x; n < N; n += kBlock) {
+        Bl[(long long)j * a.nmax + n] = from_d2<V>(h1p[n]);
+        P.B[(long long)j * a.nmax + n] = h1p[n];
+    }
+    for (int t = threadIdx.x; t < j; t += kBlock) {
+        gcs[t] = P.cs[t];
+        gsn[t] = P.sn[t];
+    }
+    double h2p = 0.0;
+    for (int t = threadIdx.x; t < N + i; t += kBlock) h2p += cabs2(h1p[t]);
+    const double h2 = block_sum_d(h2p, smf);   // synchronises the staging above
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const double est = givens_column_warp(gcol, gcs, gsn, j, beta, gout, P.g, P.cs + j, P.sn + j);
+        if (threadIdx.x == 0) {
+            const double alpha = tv[N + 2 * i].x;
+            const double anorm = sqrt(h2 + alpha);   // ||A q_{i-1}||
+            S->k = i;
+            S->iters += 1;
+            S->hnorm = beta;
+            S->anorm = anorm;
+            const bool brk = !(beta > 1e-14 * anorm);
+            if (brk) S->breakdown = 1;
+            if (brk || est <= S->target || S->iters >= a.maxit || i >= m) {
+                S->in_cycle = 0;
+                atomicSub(a.counts, 1);
+            }
+        }
+        __syncwarp();
+        for (int t = threadIdx.x; t <= j + 1; t += 32) P.Rg[(long long)j * ldh + t] = gout[t];
+        return;
+    }
+    if (!next) return;
+    // Hs multiplies the reorthogonalisation coefficients s (of the order of the
+    // working precision times ||u||), so it is formed in the Krylov precision T.
+    const double ib = 1.0 / beta;
+    const double2 gm = csub(tv[N + 2 * i + 1], tv[N + 2 * i + 3]);   // gamma - s^H t_Q
+    for (int row = threadIdx.x - 32; row < N + i + 1; row += kBlock - 32) {
+        // row-wise sum over columns l: loads of one column are contiguous over rows
+        V hst = mk((T)0, (T)0);
+        if (row < N) {
+#pragma unroll 4
+            for (int l = 0; l < i; ++l) cfma(hst, Bl[(long long)l * a.nmax + row], svl[l]);
+        } else {
+            const int qr = row - N;  // row of H; column l holds rows 0..l+1
+#pragma unroll 4
+            for (int l = max(0, qr - 1); l < i; ++l) cfma(hst, Hl[(long long)l * ldh + qr], svl[l]);
+        }
+        const double2 hs = to_d2(hst);
+        h1n[row] = (row < N + i) ? cscale(csub(tv[row], hs), ib) : csub(cscale(gm, ib * ib), cscale(hs, ib));
+    }
+}
+
+
 // Iteration i >= 1 holds u = u_i (one Gram-Schmidt pass applied, not yet
 // normalised) and z = A u.  One reduction gives
 //   t = [C Q_i]^H z,  s = Q_i^H u,  alpha = u^H u,  gamma = u^H z
@@ -790,133 +890,104 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
         }
     }
     if (!arrive_last(P.ticket, P.nchunks)) return;
+    // Last CTA of this solve: only what the next sweep needs stays here (the
+    // sums over the chunks, beta and the coefficients c); the rest of column
+    // i-1 (Givens rotation, stop test, Hs and h1 of column i) runs in
+    // dcgs2_finish_column, in front of k_update2's sweep.
     double2* tv = P.tv;
     const V* pall = reinterpret_cast<const V*>(P.part);
+    extern __shared__ __align__(16) unsigned char smraw2[];
+    double2* tvs = reinterpret_cast<double2*>(smraw2);   // Ktot entries
+    const int nch = P.nchunks;
     for (int k = threadIdx.x; k < Ktot; k += kBlock) {
-        if (!hz && k < N) { tv[k] = make_double2(0.0, 0.0); continue; }
+        // one coefficient per thread, chunks in order, 16 loads in flight
         V sum = mk((T)0, (T)0);
-        for (int c = 0; c < P.nchunks; ++c) sum = cadd(sum, __ldcg(pall + (long long)c * a.KP + k));
-        tv[k] = to_d2(sum);
+        if (hz || k >= N) {
+            const V* pk = pall + k;
+            int c = 0;
+            for (; c + 16 <= nch; c += 16) {
+                V v[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] = __ldcg(pk + (long long)(c + q) * a.KP);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) sum = cadd(sum, v[q]);
+            }
+            for (; c < nch; ++c) sum = cadd(sum, __ldcg(pk + (long long)c * a.KP));
+        }
+        const double2 d = to_d2(sum);
+        tvs[k] = d;
+        tv[k] = d;
     }
     __syncthreads();
-    __shared__ double s_beta;
-    __shared__ int s_go;
-    const double2* sv = tv + N + i;
-    const int m = a.m, ldh = m + 1;
-    const int j = i - 1;
-    // stage column j (= h1_Q + s), the rotations and ||h1||^2 in shared memory
-    extern __shared__ __align__(16) unsigned char smraw2[];
-    // 16-byte arrays first, the m doubles last (keeps every double2 aligned for any m)
-    double2* gcol = reinterpret_cast<double2*>(smraw2);    // m + 2 entries
-    double2* gsn = gcol + (m + 2);                         // m entries
-    double2* gout = gsn + m;                               // m + 2 entries
-    V* svl = reinterpret_cast<V*>(gout + (m + 2));         // s in the Krylov precision, m entries
-    double* gcs = reinterpret_cast<double*>(svl + m);      // m entries (last: 8-byte items)
-    V* Hl = reinterpret_cast<V*>(P.Hh);                       // Krylov-precision copy of H
-    V* Bl = reinterpret_cast<V*>(P.Hh + (size_t)(m + 1) * m);  // and of B
+    // |s|^2 and s^H t_Q (block reductions)
+    double s2p = 0.0, str = 0.0, sti = 0.0;
     for (int t = threadIdx.x; t < i; t += kBlock) {
-        const double2 h = cadd(P.hsum[N + t], sv[t]);
-        gcol[t] = h;
-        Hl[(long long)j * ldh + t] = from_d2<V>(h);
-        svl[t] = from_d2<V>(sv[t]);
-    }
-    for (int n = threadIdx.x; n < N; n += kBlock) Bl[(long long)j * a.nmax + n] = from_d2<V>(P.hsum[n]);
-    for (int t = threadIdx.x; t < j; t += kBlock) {
-        gcs[t] = P.cs[t];
-        gsn[t] = P.sn[t];
-    }
-    for (int n = threadIdx.x; n < N; n += kBlock) P.B[(long long)j * a.nmax + n] = P.hsum[n];
-    double s2p = 0.0, h2p = 0.0;
-    for (int t = threadIdx.x; t < i; t += kBlock) s2p += cabs2(sv[t]);
-    for (int t = threadIdx.x; t < N + i; t += kBlock) h2p += cabs2(P.hsum[t]);
-    // s^H t_Q for the new column's first-pass coefficient (block reduction)
-    double str = 0.0, sti = 0.0;
-    if (hz)
-        for (int t = threadIdx.x; t < i; t += kBlock) {
-            const double2 pr = cmulc(sv[t], tv[N + t]);
+        const double2 st_ = tvs[N + i + t];
+        s2p += cabs2(st_);
+        if (hz) {
+            const double2 pr = cmulc(st_, tvs[N + t]);
             str += pr.x;
             sti += pr.y;
         }
+    }
+    __shared__ double s_beta;
     __shared__ double2 s_st;
     const double s2 = block_sum_d(s2p, sm);
-    const double h2 = block_sum_d(h2p, sm);
     const double st_r = block_sum_d(str, sm);
     const double st_i = block_sum_d(sti, sm);
-    if (threadIdx.x == 0) s_st = make_double2(st_r, st_i);
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        // finalise column j = i-1
-        const double alpha = tv[N + 2 * i].x;
-        const double beta = sqrt(fmax(alpha - s2, 0.0));
-        const double est = givens_column_warp(gcol, gcs, gsn, j, beta, gout, P.g, P.cs + j, P.sn + j);
-        if (threadIdx.x != 0) goto dcgs2_done;
-        const double anorm = sqrt(h2 + alpha);   // ||A q_{i-1}||
-        Hl[(long long)j * ldh + i] = mk((T)beta, (T)0);
-        S->k = i;
-        S->iters += 1;
-        S->hnorm = beta;
-        S->anorm = anorm;
-        bool brk = !(beta > 1e-14 * anorm);
-        if (brk) S->breakdown = 1;
-        int go = 1;
-        if (brk || est <= S->target || S->iters >= a.maxit || i >= m) {
-            S->in_cycle = 0;
-            atomicSub(a.counts, 1);
-            go = 0;
-        }
+    if (threadIdx.x == 0) {
+        const double alpha = tvs[N + 2 * i].x;
+        const double beta = sqrt(fmax(alpha - s2, 0.0));   // Pythagoras: ||u - Q_i s||
         s_beta = beta;
-        s_go = go;
+        s_st = make_double2(st_r, st_i);
+        tv[N + 2 * i + 2] = make_double2(beta, s2);
+        tv[N + 2 * i + 3] = s_st;
     }
-dcgs2_done:
     __syncthreads();
-    for (int t = threadIdx.x; t <= j + 1; t += kBlock) P.Rg[(long long)j * ldh + t] = gout[t];
-    __syncthreads();
-    if (!s_go) return;
-    // Hs = [B; H][:, 0:i] s and the coefficients of the next step (every thread one row)
-    // Hs multiplies the reorthogonalisation coefficients s (of the order of the
-    // working precision times ||u||), so it is formed in the Krylov precision T.
-    const double beta = s_beta;
-    for (int row = threadIdx.x; row < N + i + 1; row += kBlock) {
-        // row-wise sum over columns l: loads of one column are contiguous over rows
-        V hst = mk((T)0, (T)0);
-        if (row < N) {
-            for (int l = 0; l < i; ++l) cfma(hst, Bl[(long long)l * a.nmax + row], svl[l]);
-        } else {
-            const int qr = row - N;  // row of H; column l holds rows 0..l+1
-            for (int l = max(0, qr - 1); l < i; ++l) cfma(hst, Hl[(long long)l * ldh + qr], svl[l]);
-        }
-        const double2 hs = to_d2(hst);
-        double2 h1;
-        if (row < N + i) {
-            h1 = cscale(csub(tv[row], hs), 1.0 / beta);
-        } else {
-            const double2 gm = csub(tv[N + 2 * i + 1], s_st);
-            h1 = csub(cscale(gm, 1.0 / (beta * beta)), cscale(hs, 1.0 / beta));
-        }
-        P.hsum[row] = h1;
-        P.hp[row] = cadd(cscale(hs, 1.0 / beta), h1);
+    if (!hz) {
+        // i = m: no next step, column m-1 is finished here
+        dcgs2_finish_column<T>(finish_args(a), S, P, i, false, smraw2);
+        return;
     }
+    // coefficients of u_{i+1} = z / beta - [C Q_{i+1}] c:
+    //   c = t / beta (rows < N+i),  c_i = (gamma - s^H t_Q) / beta^2
+    const double ib = 1.0 / s_beta;
+    for (int k = threadIdx.x; k < N + i; k += kBlock) P.hp[k] = cscale(tvs[k], ib);
+    if (threadIdx.x == 0) P.hp[N + i] = cscale(csub(tvs[N + 2 * i + 1], s_st), ib * ib);
 }
 
 // One sweep over [C, Q_i]:  q_i = (u - Q_i s) / beta  (stored as column N+i)
-// and u <- z / beta - [C, Q_i] c[0:N+i] - q_i c[N+i]  (in place).
+// and u <- z / beta - [C, Q_i] c[0:N+i] - q_i c[N+i]  (in place).  The grid
+// starts with one column-finishing block per solve (dcgs2_finish_column); a
+// solve that it stops still completes this sweep, whose q_i and u are unused.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_update2(BatchArgs a, int i) {
+__global__ void __launch_bounds__(kBlock, 6) k_update2(BatchArgs a, int i) {
     using V = c2_t<T>;
     using PK = pack_t<T>;
     constexpr int VEC = vec_of<T>();
-    SOLVE_PROLOGUE();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    if ((int)blockIdx.x < a.nsolves) {
+        // blocks 0..nsolves-1: finish column i-1 of solve blockIdx.x (first wave)
+        SolveScal* S = a.S + blockIdx.x;
+        if (!S->in_cycle) return;
+        dcgs2_finish_column<T>(finish_args(a), S, a.P[blockIdx.x], i, true, smraw);
+        return;
+    }
+    const int bsw = blockIdx.x - a.nsolves;
+    const int s = a.blk_solve[bsw];
+    SolveScal* S = a.S + s;
+    const SolvePtrs& P = a.P[s];
+    const int chunk = bsw - P.chunk0;
     if (!S->in_cycle) return;
     const int N = S->N;
     const int K = N + i;
     count_bytes(a, DDG_K_UPDATE, (double)chunk_rows<T>() * ((double)K + 4.0) * sizeof(V));
-    extern __shared__ __align__(16) unsigned char smraw[];
     V* cs = reinterpret_cast<V*>(smraw);      // c, N + i + 1
     V* ss = cs + (N + a.m + 1);               // s, i
     for (int t = threadIdx.x; t < K + 1; t += kBlock) cs[t] = from_d2<V>(P.hp[t]);
     for (int t = threadIdx.x; t < i; t += kBlock) ss[t] = from_d2<V>(P.tv[N + i + t]);
     __syncthreads();
-    const T ib = (T)(1.0 / S->hnorm);
+    const T ib = (T)(1.0 / P.tv[N + 2 * i + 2].x);   // 1 / beta
     const long long ldp = P.ld / VEC;
     const long long p0 = (long long)chunk * kBlock + threadIdx.x;
     const PK* __restrict__ Mp = reinterpret_cast<const PK*>(P.M);
@@ -1218,6 +1289,27 @@ struct Carver {
     }
 };
 
+// Dynamic shared memory of the Arnoldi kernels for restart length m and N
+// augmentation vectors: the Givens staging (column, sines, result, s in the
+// Krylov precision, cosines), k_dots2's reduced coefficients [t | s | alpha |
+// gamma | beta | s^H t], k_update's coefficient vectors.  Sizes above the
+// default 48 KB are opted into per kernel.
+template <typename T>
+static ddg_status dcgs2_smem(int Nreq, int m, size_t& giv, size_t& dots2, size_t& upd) {
+    using V = c2_t<T>;
+    giv = 56 * (size_t)m + 128 + sizeof(V) * (size_t)m;
+    dots2 = std::max(giv, sizeof(double2) * (size_t)(Nreq + 2 * m + 4));
+    upd = std::max(sizeof(V) * (size_t)(Nreq + 2 * m + 2), giv);
+    constexpr size_t kDefault = 48 * 1024;
+    if (dots2 > kDefault)
+        DDG_CHECK_CUDA(cudaFuncSetAttribute(k_dots2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots2));
+    if (upd > kDefault) {
+        DDG_CHECK_CUDA(cudaFuncSetAttribute(k_update2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd));
+        DDG_CHECK_CUDA(cudaFuncSetAttribute(k_update_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd));
+    }
+    return DDG_OK;
+}
+
 template <typename T>
 static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const double* const* b, double* const* x,
                             const double* const* U, int Nreq, double tol, int m, int maxit, double eta,
@@ -1261,7 +1353,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             P.cs = c.take<double>(m);
             P.sn = c.take<double2>(m);
             P.g = c.take<double2>(m + 1);
-            P.hsum = c.take<double2>(KP);
+            P.hsum = c.take<double2>(2 * (size_t)KP);
             P.hp = c.take<double2>(KP);
             P.part = c.take<double2>((size_t)P.nchunks * KP);
             P.Rinv = c.take<double2>(std::max(1, Nreq * Nreq));
@@ -1308,6 +1400,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     args.maxit = maxit;
     args.fallback = ctx->fallback;
     args.aug_cycles = ctx->aug_cycles;
+    args.nsolves = n;
     std::vector<int> hblk(total_ctas);
     for (int s = 0; s < n; ++s)
         for (int c = 0; c < hp[s].nchunks; ++c) hblk[hp[s].chunk0 + c] = s;
@@ -1315,9 +1408,8 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     DDG_CHECK_CUDA(cudaMemcpyAsync(d_blk, hblk.data(), sizeof(int) * total_ctas, cudaMemcpyHostToDevice, st));
 
     const unsigned G = (unsigned)total_ctas;
-    // Givens staging (column, sines, result, cosines) and s in the Krylov precision
-    const size_t giv_smem = 56 * (size_t)m + 128 + sizeof(V) * (size_t)m;
-    const size_t upd_smem = std::max(sizeof(V) * (size_t)(Nreq + 2 * m + 2), giv_smem);
+    size_t giv_smem, dots2_smem, upd_smem;
+    DDG_TRY(dcgs2_smem<T>(Nreq, m, giv_smem, dots2_smem, upd_smem));
     DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_init<<<(n + 127) / 128, 128, 0, st>>>(args, n, Nreq); }));
     if (Nreq > 0) {
         DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_av<T><<<G, kBlock, 0, st>>>(args); }));
@@ -1350,9 +1442,9 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             for (int i = 1; i <= m; ++i) {
                 if (i < m)
                     DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_stencil_u<T><<<G, kBlock, 0, st>>>(args); }));
-                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots2<T><<<G, kBlock, giv_smem, st>>>(args, i); }));
+                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots2<T><<<G, kBlock, dots2_smem, st>>>(args, i); }));
                 if (i < m)
-                    DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update2<T><<<G, kBlock, upd_smem, st>>>(args, i); }));
+                    DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update2<T><<<G + n, kBlock, upd_smem, st>>>(args, i); }));
                 if (i % ctx->poll_every == 0 && i < m) {
                     const int slot = polled & 1;
                     DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 2 + slot, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1527,7 +1619,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
         hp.cs = c.take<double>(m);
         hp.sn = c.take<double2>(m);
         hp.g = c.take<double2>(m + 1);
-        hp.hsum = c.take<double2>(KP);
+        hp.hsum = c.take<double2>(2 * (size_t)KP);
         hp.hp = c.take<double2>(KP);
         hp.part = c.take<double2>((size_t)hp.nchunks * KP);
         hp.Rinv = c.take<double2>(1);
@@ -1579,13 +1671,14 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     args.maxit = maxit;
     args.fallback = 1e300;
     args.aug_cycles = 1;
+    args.nsolves = 1;
     // every launch reads these: the array keeps the previous call's contents
     std::vector<int> hblk(hp.nchunks, 0);
     DDG_CHECK_CUDA(cudaMemcpyAsync(args.P, &hp, sizeof(SolvePtrs), cudaMemcpyHostToDevice, st));
     DDG_CHECK_CUDA(cudaMemcpyAsync(d_blk, hblk.data(), sizeof(int) * hp.nchunks, cudaMemcpyHostToDevice, st));
     const unsigned G = (unsigned)hp.nchunks;
-    const size_t giv_smem = 56 * (size_t)m + 128 + sizeof(V) * (size_t)m;
-    const size_t upd_smem = std::max(sizeof(V) * (size_t)(2 * m + 2), giv_smem);
+    size_t giv_smem, dots2_smem, upd_smem;
+    DDG_TRY(dcgs2_smem<T>(0, m, giv_smem, dots2_smem, upd_smem));
     k_init<<<1, 128, 0, st>>>(args, 1, 0);   // also zeroes the reduction ticket
     DDG_CHECK_LAUNCH("k_init");
     int hc[2] = {0, 0};
@@ -1603,8 +1696,8 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
             DDG_CHECK_LAUNCH("first Arnoldi step");
             for (int i = 1; i <= m; ++i) {
                 if (i < m) k_stencil_u<T><<<G, kBlock, 0, st>>>(args);
-                k_dots2<T><<<G, kBlock, giv_smem, st>>>(args, i);
-                if (i < m) k_update2<T><<<G, kBlock, upd_smem, st>>>(args, i);
+                k_dots2<T><<<G, kBlock, dots2_smem, st>>>(args, i);
+                if (i < m) k_update2<T><<<G + 1, kBlock, upd_smem, st>>>(args, i);
                 DDG_CHECK_LAUNCH("Arnoldi step");
                 if (i % 16 == 0 && i < m) {
                     int in_cycle = 0;
