@@ -39,7 +39,8 @@ typedef enum {
     DDG_ECUDA = 3,       /* a CUDA runtime call failed (message in ddg_last_error) */
     DDG_ENOCONV = 4,     /* iteration cap reached before the tolerance; x holds the best iterate */
     DDG_EBREAKDOWN = 5,  /* reserved: unrecoverable Arnoldi breakdown */
-    DDG_ETIMEOUT = 6,    /* reserved: device watchdog expired */
+    DDG_ETIMEOUT = 6,    /* a bounded device wait gave up (a bulk copy into shared memory did not
+                            complete within 1 s); the solve's outputs are not valid */
     DDG_ESINGULAR = 7    /* a small dense factorisation failed */
 } ddg_status;
 

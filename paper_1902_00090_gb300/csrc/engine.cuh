@@ -130,7 +130,8 @@ struct BatchArgs {
     SolvePtrs* P;
     SolveScal* S;
     const int* blk_solve;
-    int* counts;       // [0] solves inside an Arnoldi loop, [1] solves still active
+    int* counts;       // [0] solves inside an Arnoldi loop, [1] solves still active,
+                       // [4] a bounded wait gave up (kept for the whole solve call)
     int m;             // restart length
     int KP;            // stride of coefficient vectors (>= Nmax + m + 2)
     int nmax;          // leading dimension of B (= kMaxAug)

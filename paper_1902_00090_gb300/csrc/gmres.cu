@@ -27,6 +27,7 @@
 #include <mutex>
 #include <vector>
 
+#include "bulk.cuh"
 #include "engine.cuh"
 
 namespace ddg {
@@ -787,14 +788,26 @@ __device__ __noinline__ void dcgs2_finish_column(FinishArgs a, SolveScal* S, con
 // Iteration i >= 1 holds u = u_i (one Gram-Schmidt pass applied, not yet
 // normalised) and z = A u.  One reduction gives
 //   t = [C Q_i]^H z,  s = Q_i^H u,  alpha = u^H u,  gamma = u^H z
-// (at i = m only s and alpha).  The last CTA then
-//   * finalises column i-1: H[0:i, i-1] = h1 + s, beta = sqrt(alpha - |s|^2)
-//     (Pythagoras: q_i = (u - Q_i s) / beta), B[:, i-1] = h1_C, Givens, stop test;
-//   * forms the first-pass coefficients of column i without touching w_i = A q_i:
-//     with A Q_i s = [C Q_{i+1}] Hs, Hs = [B; H][:, 0:i] s,
-//       h1_C = (t_C - Hs_C)/beta,  h1_Q = (t_Q - Hs_Q)/beta,
-//       h1_i = (gamma - s^H t_Q)/beta^2 - Hs_i/beta,
-//     and c = Hs/beta + h1 for the update u_{i+1} = z/beta - [C Q_{i+1}] c.
+// (at i = m only s and alpha).  The last CTA of a solve then forms
+// beta = sqrt(alpha - |s|^2) (Pythagoras: q_i = (u - Q_i s) / beta) and the
+// coefficients of the next sweep u_{i+1} = z / beta - [C Q_{i+1}] c without
+// touching w_i = A q_i: with A q_i = (z - A Q_i s) / beta and
+// A Q_i s = [C Q_{i+1}] Hs, the first-pass coefficients are
+//   h1 = (t - Hs) / beta (rows < N+i),  h1_i = (gamma - s^H t_Q) / beta^2 - Hs_i / beta,
+// so c = Hs / beta + h1 = t / beta and c_i = (gamma - s^H t_Q) / beta^2.
+// Column i-1 (H = h1 + s, its Givens rotation, the stop test) and h1 itself are
+// finished by dcgs2_finish_column.
+//
+// The columns stream through shared memory: a ring of kRing stages of
+// kRingCols column chunks, filled by bulk copies (one thread issues them
+// kRing - 1 stages ahead) and completed on one mbarrier per stage.
+constexpr int kRing = 3;
+constexpr int kRingCols = 4;
+constexpr int kColBytes = kBlock * 16;                          // one column chunk
+constexpr int kRingBytes = kRing * kRingCols * kColBytes;       // 48 KB
+static_assert(chunk_rows<float>() * 8 == kColBytes && chunk_rows<double>() * 16 == kColBytes,
+              "a column chunk is kBlock 16-byte packs");
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
     using V = c2_t<T>;
@@ -807,9 +820,28 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
     const int K = N + i;               // columns [C, q_0 .. q_{i-1}]
     const int Ktot = N + 2 * i + 2;    // [t | s | alpha | gamma]
     count_bytes(a, DDG_K_DOTS, (double)chunk_rows<T>() * ((double)(hz ? K : i) + 2.0) * sizeof(V));
-    const long long ldp = P.ld / VEC;
     const long long p0 = (long long)chunk * kBlock + threadIdx.x;
-    const PK* __restrict__ Mp = reinterpret_cast<const PK*>(P.M);
+    extern __shared__ __align__(128) unsigned char smraw2[];
+    __shared__ __align__(8) unsigned long long full[kRing];
+    const int kstart = hz ? 0 : N;     // at i = m the C columns are not needed
+    const int nbat = (K - kstart + kRingCols - 1) / kRingCols;
+    // this chunk's rows of column kstart, and the distance between columns
+    const char* colbase = reinterpret_cast<const char*>(P.M) +
+                          ((long long)kstart * P.ld + (long long)chunk * chunk_rows<T>()) * (long long)sizeof(V);
+    const long long colstride = P.ld * (long long)sizeof(V);
+    auto issue = [&](int b) {          // thread 0: batch b into stage b % kRing
+        const int k = b * kRingCols;
+        const int nv = min(kRingCols, K - kstart - k);
+        unsigned long long* bar = &full[b % kRing];
+        unsigned char* dst = smraw2 + (b % kRing) * (kRingCols * kColBytes);
+        mbar_expect_tx(bar, (unsigned)(nv * kColBytes));
+        for (int w = 0; w < nv; ++w) bulk_g2s(dst + w * kColBytes, colbase + (k + w) * colstride, kColBytes, bar);
+    };
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kRing; ++q) mbar_init(&full[q], 1);
+        mbar_init_fence();
+        for (int b = 0; b < min(kRing - 1, nbat); ++b) issue(b);
+    }
     V u[VEC], z[VEC];
     unpack(reinterpret_cast<const PK*>(P.w[0])[p0], u);
     if (hz) unpack(reinterpret_cast<const PK*>(P.w[1])[p0], z);
@@ -819,59 +851,67 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int vidx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-    __shared__ V red_t[kWarps][64];
-    __shared__ V red_s[kWarps][64];
-    __shared__ double sm[kWarps];
+    __shared__ V red_t[kWarps][32];
+    __shared__ V red_s[kWarps][32];
     __shared__ T smt[kWarps];
     // partial sums stay in the Krylov precision until the last CTA
     V* part = reinterpret_cast<V*>(P.part) + (long long)chunk * a.KP;
-    const int kstart = hz ? 0 : N;     // at i = m the C columns are not needed
-    // 4 columns per batch; their t- and s-partials share one 8-value butterfly
-    for (int k0 = kstart; k0 < K; k0 += 64) {
-        const int kt = min(64, K - k0);
-        for (int kk = 0; kk < kt; kk += 4) {
-            const int nv = min(4, kt - kk);
-            const PK* col = Mp + (long long)(k0 + kk) * ldp + p0;
-            PK m[4];
-            if (nv == 4) {
+    bool ok = true;
+    // 4 columns per batch; their t- and s-partials share one 8-value butterfly;
+    // cross-warp sums every 8 batches (32 columns)
+    for (int b = 0; b < nbat; ++b) {
+        const int kk = (b & 7) * kRingCols;
+        const int nv = min(kRingCols, K - kstart - b * kRingCols);
+        __syncthreads();               // stage (b - 1) % kRing has been read by every warp
+        if (threadIdx.x == 0 && b + kRing - 1 < nbat) {
+            fence_proxy_async_smem();
+            issue(b + kRing - 1);
+        }
+        if (!mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u)) ok = false;
+        const PK* stg = reinterpret_cast<const PK*>(smraw2 + (b % kRing) * (kRingCols * kColBytes));
+        PK m[kRingCols];
 #pragma unroll
-                for (int w = 0; w < 4; ++w) m[w] = col[(long long)w * ldp];
-            } else {
+        for (int w = 0; w < kRingCols; ++w) m[w] = (w < nv) ? stg[w * kBlock + threadIdx.x] : zero_pack<T>();
+        V acc[8];
 #pragma unroll
-                for (int w = 0; w < 4; ++w) m[w] = (w < nv) ? col[(long long)w * ldp] : zero_pack<T>();
+        for (int w = 0; w < 4; ++w) {
+            V mv[VEC];
+            unpack(m[w], mv);
+            acc[w] = mk((T)0, (T)0);
+            acc[w + 4] = mk((T)0, (T)0);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                cfmac(acc[w], mv[q], z[q]);
+                cfmac(acc[w + 4], mv[q], u[q]);
             }
-            V acc[8];
+        }
+        const V r = reduce8(acc, lane);
+        if ((lane & 3) == 0 && (vidx & 3) < nv) {
+            if (vidx < 4) red_t[wid][kk + vidx] = r;
+            else red_s[wid][kk + vidx - 4] = r;
+        }
+        if ((b & 7) == 7 || b == nbat - 1) {
+            __syncthreads();
+            const int k0 = kstart + (b >> 3) * 32;
+            const int kt = min(32, K - k0);
+            for (int t = threadIdx.x; t < kt; t += kBlock) {
+                V st = mk((T)0, (T)0), ss = mk((T)0, (T)0);
 #pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                V mv[VEC];
-                unpack(m[w], mv);
-                acc[w] = mk((T)0, (T)0);
-                acc[w + 4] = mk((T)0, (T)0);
-#pragma unroll
-                for (int q = 0; q < VEC; ++q) {
-                    cfmac(acc[w], mv[q], z[q]);
-                    cfmac(acc[w + 4], mv[q], u[q]);
+                for (int w = 0; w < kWarps; ++w) {
+                    st = cadd(st, red_t[w][t]);
+                    ss = cadd(ss, red_s[w][t]);
                 }
-            }
-            const V r = reduce8(acc, lane);
-            if ((lane & 3) == 0 && (vidx & 3) < nv) {
-                if (vidx < 4) red_t[wid][kk + vidx] = r;
-                else red_s[wid][kk + vidx - 4] = r;
+                const int k = k0 + t;
+                part[k] = st;                              // t_k
+                if (k >= N) part[N + i + (k - N)] = ss;    // s_l, l = k - N
             }
         }
-        __syncthreads();
-        for (int t = threadIdx.x; t < kt; t += kBlock) {
-            V st = mk((T)0, (T)0), ss = mk((T)0, (T)0);
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                st = cadd(st, red_t[w][t]);
-                ss = cadd(ss, red_s[w][t]);
-            }
-            const int k = k0 + t;
-            part[k] = st;                              // t_k
-            if (k >= N) part[N + i + (k - N)] = ss;    // s_l, l = k - N
-        }
-        __syncthreads();
+    }
+    if (!ok) {
+        // a copy did not arrive in time: report it, and give the ring one more
+        // bounded wait so that no copy lands after this CTA has gone
+        atomicExch(a.counts + 4, 1);
+        for (int b = max(0, nbat - kRing); b < nbat; ++b) mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u);
     }
     {
         T al = (T)0;
@@ -896,8 +936,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
     // dcgs2_finish_column, in front of k_update2's sweep.
     double2* tv = P.tv;
     const V* pall = reinterpret_cast<const V*>(P.part);
-    extern __shared__ __align__(16) unsigned char smraw2[];
-    double2* tvs = reinterpret_cast<double2*>(smraw2);   // Ktot entries
+    double2* tvs = reinterpret_cast<double2*>(smraw2);   // Ktot entries (the ring's space)
     const int nch = P.nchunks;
     for (int k = threadIdx.x; k < Ktot; k += kBlock) {
         // one coefficient per thread, chunks in order, 16 loads in flight
@@ -930,6 +969,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
             sti += pr.y;
         }
     }
+    __shared__ double sm[kWarps];
     __shared__ double s_beta;
     __shared__ double2 s_st;
     const double s2 = block_sum_d(s2p, sm);
@@ -1291,22 +1331,19 @@ struct Carver {
 
 // Dynamic shared memory of the Arnoldi kernels for restart length m and N
 // augmentation vectors: the Givens staging (column, sines, result, s in the
-// Krylov precision, cosines), k_dots2's reduced coefficients [t | s | alpha |
-// gamma | beta | s^H t], k_update's coefficient vectors.  Sizes above the
-// default 48 KB are opted into per kernel.
+// Krylov precision, cosines), k_dots2's column ring and, in the same space
+// after it, its reduced coefficients [t | s | alpha | gamma | beta | s^H t],
+// k_update's coefficient vectors.  Each kernel is opted into its size.
 template <typename T>
 static ddg_status dcgs2_smem(int Nreq, int m, size_t& giv, size_t& dots2, size_t& upd) {
     using V = c2_t<T>;
     giv = 56 * (size_t)m + 128 + sizeof(V) * (size_t)m;
-    dots2 = std::max(giv, sizeof(double2) * (size_t)(Nreq + 2 * m + 4));
+    dots2 = std::max({(size_t)kRingBytes, giv, sizeof(double2) * (size_t)(Nreq + 2 * m + 4)});
     upd = std::max(sizeof(V) * (size_t)(Nreq + 2 * m + 2), giv);
-    constexpr size_t kDefault = 48 * 1024;
-    if (dots2 > kDefault)
-        DDG_CHECK_CUDA(cudaFuncSetAttribute(k_dots2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots2));
-    if (upd > kDefault) {
-        DDG_CHECK_CUDA(cudaFuncSetAttribute(k_update2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd));
-        DDG_CHECK_CUDA(cudaFuncSetAttribute(k_update_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd));
-    }
+    // (the default limit covers static and dynamic shared memory together)
+    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_dots2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots2));
+    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_update2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd));
+    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_update_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd));
     return DDG_OK;
 }
 
@@ -1380,7 +1417,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     tail.take<SolvePtrs>(n);
     tail.take<SolveScal>(n);
     tail.take<int>(total_ctas);
-    tail.take<int>(4);
+    tail.take<int>(8);
     DDG_TRY(ctx->reserve(tail.off + 4096, st));
     char* base = reinterpret_cast<char*>(ctx->ws);
     layout(base);
@@ -1390,7 +1427,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     args.S = t2.take<SolveScal>(n);
     int* d_blk = t2.take<int>(total_ctas);
     args.blk_solve = d_blk;
-    args.counts = t2.take<int>(4);
+    args.counts = t2.take<int>(8);
     args.bytes = ctx->prof ? ctx->d_bytes : nullptr;
     args.m = m;
     args.KP = KP;
@@ -1422,6 +1459,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     }
     int* hc = ctx->host_counts;
     const size_t bs_smem = sizeof(double2) * (2 * (size_t)m + kMaxAug);
+    DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 8 * sizeof(int), st));
     for (long long cycle = 0; cycle <= (long long)maxit + 1; ++cycle) {
         DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 4 * sizeof(int), st));
         DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_residual<T><<<G, kBlock, 0, st>>>(args); }));
@@ -1430,7 +1468,12 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_update_r<T><<<G, kBlock, 0, st>>>(args); }));
         }
         DDG_CHECK_CUDA(cudaMemcpyAsync(hc, args.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 4, args.counts + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
         DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (hc[4]) {
+            set_error("gmres: a column copy into shared memory did not complete within its time limit");
+            return DDG_ETIMEOUT;
+        }
         if (hc[1] == 0) break;
         if (hc[0] > 0 && ctx->orth == 1) {
             // delayed reorthogonalisation: first pass of step 0, then one
@@ -1482,8 +1525,13 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_finalize<T><<<G, kBlock, 0, st>>>(args); }));
     std::vector<SolveScal> hs(n);
     DDG_CHECK_CUDA(cudaMemcpyAsync(hs.data(), args.S, sizeof(SolveScal) * n, cudaMemcpyDeviceToHost, st));
+    DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 4, args.counts + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
     DDG_CHECK_CUDA(cudaStreamSynchronize(st));
     ctx->resolve();
+    if (hc[4]) {
+        set_error("gmres: a column copy into shared memory did not complete within its time limit");
+        return DDG_ETIMEOUT;
+    }
     bool all = true;
     for (int s = 0; s < n; ++s) {
         all = all && hs[s].converged;
@@ -1634,7 +1682,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     tail.take<SolvePtrs>(1);
     tail.take<SolveScal>(1);
     tail.take<int>(hp.nchunks);
-    tail.take<int>(4);
+    tail.take<int>(8);
     const size_t need = tail.off;
     if (need > kNoAllocBytes) {
         set_error("gmres_solve_noalloc: this solve needs %zu bytes of scratch, more than the %zu-byte static "
@@ -1661,7 +1709,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     args.S = t2.take<SolveScal>(1);
     int* d_blk = t2.take<int>(hp.nchunks);
     args.blk_solve = d_blk;
-    args.counts = t2.take<int>(4);
+    args.counts = t2.take<int>(8);
     args.bytes = nullptr;
     args.m = m;
     args.KP = KP;
@@ -1681,13 +1729,18 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     DDG_TRY(dcgs2_smem<T>(0, m, giv_smem, dots2_smem, upd_smem));
     k_init<<<1, 128, 0, st>>>(args, 1, 0);   // also zeroes the reduction ticket
     DDG_CHECK_LAUNCH("k_init");
-    int hc[2] = {0, 0};
+    int hc[5] = {0, 0, 0, 0, 0};
+    DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 8 * sizeof(int), st));
     for (long long cycle = 0; cycle <= (long long)maxit + 1; ++cycle) {
         DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 4 * sizeof(int), st));
         k_residual<T><<<G, kBlock, 0, st>>>(args);
         DDG_CHECK_LAUNCH("k_residual");
-        DDG_CHECK_CUDA(cudaMemcpyAsync(hc, args.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DDG_CHECK_CUDA(cudaMemcpyAsync(hc, args.counts, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (hc[4]) {
+            set_error("gmres_solve_noalloc: a column copy into shared memory did not complete within its time limit");
+            return DDG_ETIMEOUT;
+        }
         if (hc[1] == 0) break;
         if (hc[0] > 0) {
             k_step<T><<<G, kBlock, 0, st>>>(args, 0);
@@ -1715,7 +1768,12 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     DDG_CHECK_LAUNCH("k_finalize");
     SolveScal hs;
     DDG_CHECK_CUDA(cudaMemcpyAsync(&hs, args.S, sizeof(SolveScal), cudaMemcpyDeviceToHost, st));
+    DDG_CHECK_CUDA(cudaMemcpyAsync(hc, args.counts, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
     DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (hc[4]) {
+        set_error("gmres_solve_noalloc: a column copy into shared memory did not complete within its time limit");
+        return DDG_ETIMEOUT;
+    }
     if (info) {
         info->iters = hs.iters;
         info->cycles = hs.cycles;
