@@ -477,34 +477,6 @@ __global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
     w[p0] = mkpack(wv);
 }
 
-// Delayed scheme: z = A u for the not yet reorthogonalised, unnormalised u
-// (in w[0]); z goes to w[1].  Rows past D are zero.
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_stencil_u(BatchArgs a) {
-    using V = c2_t<T>;
-    using PK = pack_t<T>;
-    constexpr int VEC = vec_of<T>();
-    SOLVE_PROLOGUE();
-    if (!S->in_cycle) return;
-    const long long D = P.D;
-    count_bytes(a, DDG_K_STEP, (double)chunk_rows<T>() * ((double)sizeof(T) + 2.0 * sizeof(V)));
-    const long long p0 = (long long)chunk * kBlock + threadIdx.x;
-    const long long e0 = p0 * VEC;
-    const V* __restrict__ u = reinterpret_cast<const V*>(P.w[0]);
-    PK* __restrict__ z = reinterpret_cast<PK*>(P.w[1]);
-    const T* eps = reinterpret_cast<const T*>(P.eps_lo);
-    const V* coef = reinterpret_cast<const V*>(P.coef_lo);
-    const T kh2 = (T)P.kh2;
-    auto ld_ = [&](long long idx) { return u[idx]; };
-    V zv[VEC];
-#pragma unroll
-    for (int i = 0; i < VEC; ++i) {
-        const long long e = e0 + i;
-        zv[i] = e < D ? stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld_) : mk((T)0, (T)0);
-    }
-    z[p0] = mkpack(zv);
-}
-
 // ---------------------------------------------------------------- Gram-Schmidt projections
 // h[k] = sum_e conj(M[k ld + e]) w[e] for the columns k < K = N + j + 1 of one
 // solve (mode 0: pass 1, also ||w||^2 -> anorm; mode 1: pass 2).  Columns are
@@ -819,7 +791,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
     const bool hz = i < a.m;           // z exists (no matvec at the last column)
     const int K = N + i;               // columns [C, q_0 .. q_{i-1}]
     const int Ktot = N + 2 * i + 2;    // [t | s | alpha | gamma]
-    count_bytes(a, DDG_K_DOTS, (double)chunk_rows<T>() * ((double)(hz ? K : i) + 2.0) * sizeof(V));
+    // columns, u, and z = A u (written; reads eps) when there is a next step
+    count_bytes(a, DDG_K_DOTS, (double)chunk_rows<T>() * (((double)(hz ? K : i) + 2.0) * sizeof(V) +
+                                                         (hz ? (double)sizeof(T) : 0.0)));
     const long long p0 = (long long)chunk * kBlock + threadIdx.x;
     extern __shared__ __align__(128) unsigned char smraw2[];
     __shared__ __align__(8) unsigned long long full[kRing];
@@ -844,8 +818,22 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
     }
     V u[VEC], z[VEC];
     unpack(reinterpret_cast<const PK*>(P.w[0])[p0], u);
-    if (hz) unpack(reinterpret_cast<const PK*>(P.w[1])[p0], z);
-    else {
+    if (hz) {
+        // z = A u on this chunk's rows (the ring fills meanwhile); the stencil's
+        // neighbours of u come from other chunks through L2
+        const V* __restrict__ uu = reinterpret_cast<const V*>(P.w[0]);
+        const T* eps = reinterpret_cast<const T*>(P.eps_lo);
+        const V* coef = reinterpret_cast<const V*>(P.coef_lo);
+        const T kh2 = (T)P.kh2;
+        const long long D = P.D;
+        auto ld_ = [&](long long idx) { return uu[idx]; };
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            const long long e = p0 * VEC + q;
+            z[q] = e < D ? stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld_) : mk((T)0, (T)0);
+        }
+        reinterpret_cast<PK*>(P.w[1])[p0] = mkpack(z);
+    } else {
 #pragma unroll
         for (int q = 0; q < VEC; ++q) z[q] = mk((T)0, (T)0);
     }
@@ -1125,28 +1113,56 @@ __global__ void __launch_bounds__(128) k_backsub(BatchArgs a) {
     for (int i = threadIdx.x; i < k; i += blockDim.x) P.coefy[N + i] = y[i];
 }
 
-// x += V z + Q y in FP64 (V, Q in the Krylov precision).
+// x += V z + Q y (V, Q in the Krylov precision): the correction is summed in
+// blocks of 8 columns in that precision, the block sums and x in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_update_x(BatchArgs a) {
     using V = c2_t<T>;
+    using PK = pack_t<T>;
     constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     if (!S->pending) return;
-    const long long D = P.D, ld = P.ld;
-    const int N = S->N, k = S->k;
-    count_bytes(a, DDG_K_CYCLE_END, (double)chunk_rows<T>() * ((double)(N + k) * sizeof(V) + 32.0));
-    const V* __restrict__ Vv = reinterpret_cast<const V*>(P.V);
-    const V* __restrict__ Q = reinterpret_cast<const V*>(P.M) + (long long)N * ld;
-    const double2* __restrict__ cy = P.coefy;
-    const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
+    const long long D = P.D, ldp = P.ld / VEC;
+    const int N = S->N, k = S->k, nc = N + k;
+    count_bytes(a, DDG_K_CYCLE_END, (double)chunk_rows<T>() * ((double)nc * sizeof(V) + 32.0));
+    // coefficients [z; y] in the Krylov precision (the correction only has to
+    // meet the inner tolerance; x itself is updated in FP64)
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* cyl = reinterpret_cast<V*>(smraw);
+    for (int c = threadIdx.x; c < nc; c += kBlock) cyl[c] = from_d2<V>(P.coefy[c]);
+    __syncthreads();
+    const long long p0 = (long long)chunk * kBlock + threadIdx.x;
+    const PK* __restrict__ Vp = reinterpret_cast<const PK*>(P.V);
+    const PK* __restrict__ Qp = reinterpret_cast<const PK*>(P.M) + (long long)N * ldp;
+    auto column = [&](int c) { return c < N ? Vp + (long long)c * ldp + p0 : Qp + (long long)(c - N) * ldp + p0; };
+    double2 acc[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) acc[q] = make_double2(0.0, 0.0);
+    // blocks of 8 columns summed in T, the block sums in FP64
+    for (int c0 = 0; c0 < nc; c0 += 8) {
+        const int nb = min(8, nc - c0);
+        PK m[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) m[w] = (w < nb) ? *column(c0 + w) : zero_pack<T>();
+        V part[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) part[q] = mk((T)0, (T)0);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            if (w >= nb) break;
+            V mv[VEC];
+            unpack(m[w], mv);
+            const V cw = cyl[c0 + w];
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) cfma(part[q], mv[q], cw);
+        }
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) acc[q] = cadd(acc[q], to_d2(part[q]));
+    }
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
-        const long long e = e0 + q;
-        if (e >= D) continue;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int n = 0; n < N; ++n) cfma(acc, to_d2(Vv[(long long)n * ld + e]), cy[n]);
-        for (int i = 0; i < k; ++i) cfma(acc, to_d2(Q[(long long)i * ld + e]), cy[N + i]);
-        P.x[e] = cadd(P.x[e], acc);
+        const long long e = p0 * VEC + q;
+        if (e < D) P.x[e] = cadd(P.x[e], acc[q]);
     }
 }
 
@@ -1447,6 +1463,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     const unsigned G = (unsigned)total_ctas;
     size_t giv_smem, dots2_smem, upd_smem;
     DDG_TRY(dcgs2_smem<T>(Nreq, m, giv_smem, dots2_smem, upd_smem));
+    const size_t ux_smem = sizeof(V) * (size_t)(Nreq + m);
     DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_init<<<(n + 127) / 128, 128, 0, st>>>(args, n, Nreq); }));
     if (Nreq > 0) {
         DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_av<T><<<G, kBlock, 0, st>>>(args); }));
@@ -1483,8 +1500,6 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T><<<G, kBlock, upd_smem, st>>>(args, 0, 0); }));
             int polled = 0;
             for (int i = 1; i <= m; ++i) {
-                if (i < m)
-                    DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_stencil_u<T><<<G, kBlock, 0, st>>>(args); }));
                 DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots2<T><<<G, kBlock, dots2_smem, st>>>(args, i); }));
                 if (i < m)
                     DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update2<T><<<G + n, kBlock, upd_smem, st>>>(args, i); }));
@@ -1520,7 +1535,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             }
         }
         DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_backsub<<<n, 128, bs_smem, st>>>(args); }));
-        DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_update_x<T><<<G, kBlock, 0, st>>>(args); }));
+        DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_update_x<T><<<G, kBlock, ux_smem, st>>>(args); }));
     }
     DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_finalize<T><<<G, kBlock, 0, st>>>(args); }));
     std::vector<SolveScal> hs(n);
@@ -1727,6 +1742,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     const unsigned G = (unsigned)hp.nchunks;
     size_t giv_smem, dots2_smem, upd_smem;
     DDG_TRY(dcgs2_smem<T>(0, m, giv_smem, dots2_smem, upd_smem));
+    const size_t ux_smem = sizeof(V) * (size_t)m;
     k_init<<<1, 128, 0, st>>>(args, 1, 0);   // also zeroes the reduction ticket
     DDG_CHECK_LAUNCH("k_init");
     int hc[5] = {0, 0, 0, 0, 0};
@@ -1748,7 +1764,6 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
             k_update_w<T><<<G, kBlock, upd_smem, st>>>(args, 0, 0);
             DDG_CHECK_LAUNCH("first Arnoldi step");
             for (int i = 1; i <= m; ++i) {
-                if (i < m) k_stencil_u<T><<<G, kBlock, 0, st>>>(args);
                 k_dots2<T><<<G, kBlock, dots2_smem, st>>>(args, i);
                 if (i < m) k_update2<T><<<G + 1, kBlock, upd_smem, st>>>(args, i);
                 DDG_CHECK_LAUNCH("Arnoldi step");
@@ -1761,7 +1776,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
             }
         }
         k_backsub<<<1, 128, sizeof(double2) * (2 * (size_t)m + kMaxAug), st>>>(args);
-        k_update_x<T><<<G, kBlock, 0, st>>>(args);
+        k_update_x<T><<<G, kBlock, ux_smem, st>>>(args);
         DDG_CHECK_LAUNCH("cycle end");
     }
     k_finalize<T><<<G, kBlock, 0, st>>>(args);
