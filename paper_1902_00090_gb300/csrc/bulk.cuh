@@ -42,6 +42,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         : "memory");
 }
 
+// Pulls `bytes` (multiple of 16, 16-byte aligned) of global memory into L2.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -68,5 +73,13 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
         else if ((it & 63) == 0 && global_ns() - t0 > limit_ns) return false;
     }
 }
+
+// Programmatic dependent launch: waits until the preceding kernel of the
+// stream has completed and its writes are visible (no-op when this launch did
+// not opt in).  Kernels here never trigger their dependents early: the next
+// launch is staged as this one's blocks exit (an early trigger let the next
+// kernel's prefetches compete with this one's reduction tail, and measured
+// slower).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 }  // namespace ddg

@@ -786,14 +786,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
     using PK = pack_t<T>;
     constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
+    // in_cycle only ever drops to 0 in the preceding launch, so a 0 read before
+    // the dependency wait is final and a 1 is checked again after it
     if (!S->in_cycle) return;
     const int N = S->N;
     const bool hz = i < a.m;           // z exists (no matvec at the last column)
     const int K = N + i;               // columns [C, q_0 .. q_{i-1}]
     const int Ktot = N + 2 * i + 2;    // [t | s | alpha | gamma]
-    // columns, u, and z = A u (written; reads eps) when there is a next step
-    count_bytes(a, DDG_K_DOTS, (double)chunk_rows<T>() * (((double)(hz ? K : i) + 2.0) * sizeof(V) +
-                                                         (hz ? (double)sizeof(T) : 0.0)));
     const long long p0 = (long long)chunk * kBlock + threadIdx.x;
     extern __shared__ __align__(128) unsigned char smraw2[];
     __shared__ __align__(8) unsigned long long full[kRing];
@@ -811,11 +810,29 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
         mbar_expect_tx(bar, (unsigned)(nv * kColBytes));
         for (int w = 0; w < nv; ++w) bulk_g2s(dst + w * kColBytes, colbase + (k + w) * colstride, kColBytes, bar);
     };
+    // Stages holding only columns older than q_{i-1} (the previous launch wrote
+    // q_{i-1} and u) are requested before the dependency wait.
+    const int npre = min(kRing - 1, nbat);
+    int early = 0;
+    while (early < npre && kstart + (early + 1) * kRingCols <= K - 1) ++early;
     if (threadIdx.x == 0) {
         for (int q = 0; q < kRing; ++q) mbar_init(&full[q], 1);
         mbar_init_fence();
-        for (int b = 0; b < min(kRing - 1, nbat); ++b) issue(b);
+        for (int b = 0; b < early; ++b) issue(b);
     }
+    pdl_wait();
+    if (!S->in_cycle) {
+        // stopped by the preceding launch: let the early copies land, then leave
+        if (threadIdx.x == 0)
+            for (int b = 0; b < early; ++b)
+                if (!mbar_wait(&full[b], 0u)) atomicExch(a.counts + 4, 1);
+        return;
+    }
+    // columns, u, and z = A u (written; reads eps) when there is a next step
+    count_bytes(a, DDG_K_DOTS, (double)chunk_rows<T>() * (((double)(hz ? K : i) + 2.0) * sizeof(V) +
+                                                         (hz ? (double)sizeof(T) : 0.0)));
+    if (threadIdx.x == 0)
+        for (int b = early; b < npre; ++b) issue(b);
     V u[VEC], z[VEC];
     unpack(reinterpret_cast<const PK*>(P.w[0])[p0], u);
     if (hz) {
@@ -996,6 +1013,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_update2(BatchArgs a, int i) {
     extern __shared__ __align__(16) unsigned char smraw[];
     if ((int)blockIdx.x < a.nsolves) {
         // blocks 0..nsolves-1: finish column i-1 of solve blockIdx.x (first wave)
+        pdl_wait();
         SolveScal* S = a.S + blockIdx.x;
         if (!S->in_cycle) return;
         dcgs2_finish_column<T>(finish_args(a), S, a.P[blockIdx.x], i, true, smraw);
@@ -1009,6 +1027,18 @@ __global__ void __launch_bounds__(kBlock, 6) k_update2(BatchArgs a, int i) {
     if (!S->in_cycle) return;
     const int N = S->N;
     const int K = N + i;
+    const long long ldp = P.ld / VEC;
+    const long long p0 = (long long)chunk * kBlock + threadIdx.x;
+    const PK* __restrict__ Mp = reinterpret_cast<const PK*>(P.M);
+    PK* __restrict__ up = reinterpret_cast<PK*>(P.w[0]);
+    // u and the columns are not written by k_dots2: u is loaded and the first
+    // 8 column chunks are pulled into L2 before the dependency wait
+    V u[VEC];
+    unpack(up[p0], u);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < min(8, K); ++w)
+            bulk_prefetch_l2(Mp + (long long)w * ldp + (long long)chunk * kBlock, kColBytes);
+    pdl_wait();
     count_bytes(a, DDG_K_UPDATE, (double)chunk_rows<T>() * ((double)K + 4.0) * sizeof(V));
     V* cs = reinterpret_cast<V*>(smraw);      // c, N + i + 1
     V* ss = cs + (N + a.m + 1);               // s, i
@@ -1016,12 +1046,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_update2(BatchArgs a, int i) {
     for (int t = threadIdx.x; t < i; t += kBlock) ss[t] = from_d2<V>(P.tv[N + i + t]);
     __syncthreads();
     const T ib = (T)(1.0 / P.tv[N + 2 * i + 2].x);   // 1 / beta
-    const long long ldp = P.ld / VEC;
-    const long long p0 = (long long)chunk * kBlock + threadIdx.x;
-    const PK* __restrict__ Mp = reinterpret_cast<const PK*>(P.M);
-    PK* __restrict__ up = reinterpret_cast<PK*>(P.w[0]);
-    V u[VEC], nu[VEC];
-    unpack(up[p0], u);
+    V nu[VEC];
     unpack(reinterpret_cast<const PK*>(P.w[1])[p0], nu);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) nu[q] = cscale(nu[q], ib);
@@ -1345,6 +1370,25 @@ struct Carver {
     }
 };
 
+// Launch with programmatic stream serialisation: its blocks may start once the
+// preceding kernel's blocks have exited, before that kernel's completion is
+// signalled; they order themselves after it with pdl_wait() before touching
+// what it writes (and prefetch what it does not).
+template <typename... KArgs, typename... Args>
+static void launch_overlapped(void (*kern)(KArgs...), unsigned grid, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, kern, args...);   // a failure is left for cudaGetLastError
+}
+
 // Dynamic shared memory of the Arnoldi kernels for restart length m and N
 // augmentation vectors: the Givens staging (column, sines, result, s in the
 // Krylov precision, cosines), k_dots2's column ring and, in the same space
@@ -1500,9 +1544,10 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T><<<G, kBlock, upd_smem, st>>>(args, 0, 0); }));
             int polled = 0;
             for (int i = 1; i <= m; ++i) {
-                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots2<T><<<G, kBlock, dots2_smem, st>>>(args, i); }));
+                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { launch_overlapped(k_dots2<T>, G, dots2_smem, st, args, i); }));
                 if (i < m)
-                    DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update2<T><<<G + n, kBlock, upd_smem, st>>>(args, i); }));
+                    DDG_TRY(ctx->launch(DDG_K_UPDATE, st,
+                                        [&] { launch_overlapped(k_update2<T>, G + n, upd_smem, st, args, i); }));
                 if (i % ctx->poll_every == 0 && i < m) {
                     const int slot = polled & 1;
                     DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 2 + slot, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
