@@ -1110,20 +1110,23 @@ __global__ void __launch_bounds__(128) k_backsub(BatchArgs a) {
     extern __shared__ __align__(16) double2 sh[];
     double2* gg = sh;            // k
     double2* y = sh + a.m;       // k
-    double2* xa = sh + 2 * a.m;  // N
-    for (int i = threadIdx.x; i < k; i += blockDim.x) gg[i] = P.g[i];
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        for (int i = k - 1; i >= 0; --i) {
-            const double2* col = P.Rg + (long long)i * ldh;
-            double2 yi = cdiv(gg[i], col[i]);
-            for (int l = lane; l < i; l += 32) gg[l] = csub(gg[l], cmul(col[l], yi));
-            if (lane == 0) y[i] = yi;
-            __syncwarp();
-        }
+    double2* rd = sh + 2 * a.m;  // k: 1 / R_ii
+    double2* xa = sh + 3 * a.m;  // N
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        gg[i] = P.g[i];
+        rd[i] = cdiv(make_double2(1.0, 0.0), P.Rg[(long long)i * ldh + i]);
     }
     __syncthreads();
+    // column-oriented back substitution; every step's update is spread over
+    // the whole block (FP64 issue is the limit, so all four SM quadrants work)
+    for (int i = k - 1; i >= 0; --i) {
+        const double2 yi = cmul(gg[i], rd[i]);
+        const double2* col = P.Rg + (long long)i * ldh;
+        __syncthreads();             // every thread has read gg[i]
+        for (int l = threadIdx.x; l < i; l += blockDim.x) gg[l] = csub(gg[l], cmul(col[l], yi));
+        if (threadIdx.x == 0) y[i] = yi;
+        __syncthreads();
+    }
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
         double2 t = P.cr[n];
         for (int i = 0; i < k; ++i) t = csub(t, cmul(P.B[(long long)i * a.nmax + n], y[i]));
@@ -1519,7 +1522,8 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
         DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_store<T><<<G, kBlock, 0, st>>>(args); }));
     }
     int* hc = ctx->host_counts;
-    const size_t bs_smem = sizeof(double2) * (2 * (size_t)m + kMaxAug);
+    const size_t bs_smem = sizeof(double2) * (3 * (size_t)m + kMaxAug);
+    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_backsub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs_smem));
     DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 8 * sizeof(int), st));
     for (long long cycle = 0; cycle <= (long long)maxit + 1; ++cycle) {
         DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 4 * sizeof(int), st));
@@ -1788,6 +1792,8 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     size_t giv_smem, dots2_smem, upd_smem;
     DDG_TRY(dcgs2_smem<T>(0, m, giv_smem, dots2_smem, upd_smem));
     const size_t ux_smem = sizeof(V) * (size_t)m;
+    const size_t bs_smem = sizeof(double2) * (3 * (size_t)m + kMaxAug);
+    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_backsub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs_smem));
     k_init<<<1, 128, 0, st>>>(args, 1, 0);   // also zeroes the reduction ticket
     DDG_CHECK_LAUNCH("k_init");
     int hc[5] = {0, 0, 0, 0, 0};
@@ -1820,7 +1826,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
                 }
             }
         }
-        k_backsub<<<1, 128, sizeof(double2) * (2 * (size_t)m + kMaxAug), st>>>(args);
+        k_backsub<<<1, 128, bs_smem, st>>>(args);
         k_update_x<T><<<G, kBlock, ux_smem, st>>>(args);
         DDG_CHECK_LAUNCH("cycle end");
     }

@@ -106,6 +106,21 @@ def test_dense_direct_16x16(ctx, prec):
     assert np.linalg.norm(b - A @ host(x)) / np.linalg.norm(b) <= tol
 
 
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_longest_restart(ctx, prec):
+    # restart 1024 (the largest accepted): the Arnoldi kernels' shared memory
+    # (Givens staging, coefficient vectors, back substitution) exceeds 48 KB
+    g, eps, A, b = small(32, npml=6, seed=2)
+    x_ref = spla.spsolve(A.tocsc(), b)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x, info, st = ddg.gmres_solve(ctx, op, dev(b), tol=1e-8, restart=1024, maxit=5000, precision=prec)
+    assert st == 0 and info["converged"] and info["cycles"] <= (2 if prec == "c128" else 3)
+    assert np.linalg.norm(b - A @ host(x)) / np.linalg.norm(b) <= 1e-8
+    assert rel(host(x), x_ref) <= 1e-6
+    xo, io = gmres.plain_gmres(A, b, tol=1e-8, restart=1024, maxit=5000)
+    print(f"restart 1024 {prec}: {info['iters']} GPU iterations, oracle {io.iters}")
+
+
 def test_plain_iterations_match_oracle_c128(ctx):
     # Same algorithm in the same precision: equal Krylov step counts (up to a
     # step at a tolerance crossing) and the same solution.
