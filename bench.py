@@ -52,6 +52,8 @@ def parse():
                    help="Eq. 6 (unsupervised, trained on the right-hand sides) or Eq. 5 (solved fields)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--graphs", default="on", choices=["on", "off"],
+                   help="run each restart cycle's Arnoldi steps as one CUDA graph launch")
     return p.parse_args()
 
 
@@ -143,6 +145,7 @@ def run_ours(args, rank, world):
     g, eps_train, eps_test = problem_set()
     src = (g.i_src, g.sigma_src, g.j_src)
     ctx = ddg.Context()
+    ctx.set_graphs(args.graphs == "on")
 
     def build(eps_set):
         ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device=dev)) for e in eps_set]
@@ -322,7 +325,8 @@ def run_ours(args, rank, world):
                                      "its step, then plain GMRES",
                    "precision": args.precision, "training_fields": len(eps_train),
                    "l2": "no flush: per-step working set (Krylov bases, 64 x 28 MB c64) exceeds L2",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "step_loop": "CUDA graph per restart cycle" if args.graphs == "on" else "host-launched"},
         "cnn": {**summary(infos), "predict_ms_per_step": round(predict_ms, 2), "train_s": round(cnn_s, 2),
                 "loss": "Eq. 6 (residual)" if args.cnn_loss == "residual" else "Eq. 5 (projection)",
                 "train_steps": args.cnn_steps, "batch": args.cnn_batch, "lr": args.cnn_lr,

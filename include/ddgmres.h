@@ -122,6 +122,14 @@ typedef enum {
                             Parallel Computing 112, 2022): 2 passes over the basis per step */
 } ddg_orthogonalization;
 ddg_status ddg_context_set_orthogonalization(ddg_context* ctx, int scheme);
+/* Step loop of the delayed scheme (no paper counterpart): with `enable` (the
+   default) every restart cycle's Arnoldi steps run as one CUDA graph launch,
+   a device-side WHILE loop over [8 x (reduction, sweep), step advance] that
+   ends when every solve has left its cycle or the restart length is reached;
+   otherwise the host launches every step and polls the device every 8 steps.
+   Both give the same results (same kernels, same order).  Per-kernel
+   profiling (ddg_context_profile_enable) uses the host-driven loop. */
+ddg_status ddg_context_set_graphs(ddg_context* ctx, int enable);
 /* Augmented solves: when the V-only relative residual ||b~|| / ||b|| of the first
    cycle (Eq. 6's minimum over V) exceeds `threshold`, the predicted subspace is
    judged to have failed: its least-squares step is kept (x += V R^-1 C^H b) and

@@ -58,6 +58,7 @@ _SIGS = {
     "ddg_context_launches": (C.c_longlong, [_vp]),
     "ddg_context_set_orthogonalization": (C.c_int, [_vp, C.c_int]),
     "ddg_context_set_fallback": (C.c_int, [_vp, C.c_double]),
+    "ddg_context_set_graphs": (C.c_int, [_vp, C.c_int]),
     "ddg_context_set_augmented_cycles": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_enable": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -177,6 +178,10 @@ class Context:
     def set_augmented_cycles(self, cycles: int):
         """Restart cycles of an augmented solve that keep V (later cycles: plain GMRES)."""
         _check(load().ddg_context_set_augmented_cycles(self._h, int(cycles)), "ddg_context_set_augmented_cycles")
+
+    def set_graphs(self, on: bool):
+        """Run each restart cycle's Arnoldi steps as one CUDA graph launch (default) or host-driven."""
+        _check(load().ddg_context_set_graphs(self._h, int(bool(on))), "ddg_context_set_graphs")
 
     def set_fallback(self, threshold: float):
         """V-only relative residual above which an augmented solve continues as plain GMRES."""

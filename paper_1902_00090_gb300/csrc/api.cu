@@ -179,6 +179,12 @@ extern "C" ddg_status ddg_context_set_orthogonalization(ddg_context* ctx, int sc
     return DDG_OK;
 }
 
+extern "C" ddg_status ddg_context_set_graphs(ddg_context* ctx, int enable) {
+    if (!ctx) { set_error("ddg_context_set_graphs: NULL context"); return DDG_EINVAL; }
+    reinterpret_cast<Context*>(ctx)->graphs = enable ? 1 : 0;
+    return DDG_OK;
+}
+
 extern "C" ddg_status ddg_context_set_fallback(ddg_context* ctx, double threshold) {
     if (!ctx || !(threshold > 0.0)) { set_error("ddg_context_set_fallback: threshold must be > 0"); return DDG_EINVAL; }
     reinterpret_cast<Context*>(ctx)->fallback = threshold;

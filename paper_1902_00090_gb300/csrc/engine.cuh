@@ -38,7 +38,8 @@ struct Context {
     int orth = 1;                    // 0: CGS2 (two passes per step), 1: delayed CGS2 (one reduction)
     double fallback = 0.5;           // augmented: V-only residual above this -> plain GMRES after the V step
     int aug_cycles = 1;              // augmented: restart cycles that keep V (later cycles run plain GMRES)
-    int poll_every = 8;              // Arnoldi steps between host polls
+    int poll_every = 8;              // Arnoldi steps between host polls (host-driven loop)
+    int graphs = 1;                  // delayed scheme: step loop as a CUDA graph with a device-side WHILE
     int sm_count = 152;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     // launch accounting and profiling
@@ -131,7 +132,8 @@ struct BatchArgs {
     SolveScal* S;
     const int* blk_solve;
     int* counts;       // [0] solves inside an Arnoldi loop, [1] solves still active,
-                       // [4] a bounded wait gave up (kept for the whole solve call)
+                       // [4] a bounded wait gave up (kept for the whole solve call),
+                       // [5] the graph-driven loop's step counter
     int m;             // restart length
     int KP;            // stride of coefficient vectors (>= Nmax + m + 2)
     int nmax;          // leading dimension of B (= kMaxAug)
@@ -141,6 +143,7 @@ struct BatchArgs {
     int aug_cycles;    // restart cycles of an augmented solve that keep V (0: its least-squares step only)
     int maxit;
     int nsolves;       // solves in the batch (k_update2 puts one block per solve in front of its sweep)
+    int* step;         // Arnoldi step of the graph-driven loop (kernels launched with i <= 0 add it)
 };
 
 // Adds `v` to the class counter once per CTA (thread 0), when profiling.

@@ -781,14 +781,20 @@ static_assert(chunk_rows<float>() * 8 == kColBytes && chunk_rows<double>() * 16 
               "a column chunk is kBlock 16-byte packs");
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
+__global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
     using V = c2_t<T>;
     using PK = pack_t<T>;
     constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
+    const int i = i_arg > 0 ? i_arg : *a.step - i_arg;   // graph-driven loop: device step + offset
     // in_cycle only ever drops to 0 in the preceding launch, so a 0 read before
-    // the dependency wait is final and a 1 is checked again after it
-    if (!S->in_cycle) return;
+    // the dependency wait is final and a 1 is checked again after it.  Block 0
+    // always waits, so that this grid never completes before the preceding one
+    // (later launches rely on that order).
+    if (i > a.m || !S->in_cycle) {       // past the restart length (unrolled graph body), or stopped
+        if (blockIdx.x == 0) pdl_wait();
+        return;
+    }
     const int N = S->N;
     const bool hz = i < a.m;           // z exists (no matvec at the last column)
     const int K = N + i;               // columns [C, q_0 .. q_{i-1}]
@@ -1006,19 +1012,24 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i) {
 // starts with one column-finishing block per solve (dcgs2_finish_column); a
 // solve that it stops still completes this sweep, whose q_i and u are unused.
 template <typename T>
-__global__ void __launch_bounds__(kBlock, 6) k_update2(BatchArgs a, int i) {
+__global__ void __launch_bounds__(kBlock, 6) k_update2(BatchArgs a, int i_arg) {
     using V = c2_t<T>;
     using PK = pack_t<T>;
     constexpr int VEC = vec_of<T>();
+    const int i = i_arg > 0 ? i_arg : *a.step - i_arg;   // graph-driven loop: device step + offset
     extern __shared__ __align__(16) unsigned char smraw[];
     if ((int)blockIdx.x < a.nsolves) {
-        // blocks 0..nsolves-1: finish column i-1 of solve blockIdx.x (first wave)
+        // blocks 0..nsolves-1: finish column i-1 of solve blockIdx.x (first
+        // wave); they always wait, so that this grid never completes before
+        // the preceding one
         pdl_wait();
+        if (i >= a.m) return;             // no sweep after the last column
         SolveScal* S = a.S + blockIdx.x;
         if (!S->in_cycle) return;
         dcgs2_finish_column<T>(finish_args(a), S, a.P[blockIdx.x], i, true, smraw);
         return;
     }
+    if (i >= a.m) return;
     const int bsw = blockIdx.x - a.nsolves;
     const int s = a.blk_solve[bsw];
     SolveScal* S = a.S + s;
@@ -1373,6 +1384,17 @@ struct Carver {
     }
 };
 
+// Graph-driven step loop: advances the step by the body's `unroll` steps and
+// keeps the WHILE loop running while some solve is inside its Arnoldi cycle and
+// the restart length is not exhausted (k_dots2 at step m finishes the last
+// column; launches for steps past m return at once).
+constexpr int kGraphUnroll = 8;
+__global__ void k_advance(BatchArgs a, cudaGraphConditionalHandle loop, int unroll) {
+    const int s = *a.step + unroll;
+    *a.step = s;
+    cudaGraphSetConditional(loop, (s <= a.m && a.counts[0] > 0) ? 1u : 0u);
+}
+
 // Launch with programmatic stream serialisation: its blocks may start once the
 // preceding kernel's blocks have exited, before that kernel's completion is
 // signalled; they order themselves after it with pdl_wait() before touching
@@ -1391,6 +1413,87 @@ static void launch_overlapped(void (*kern)(KArgs...), unsigned grid, size_t smem
     cfg.numAttrs = 1;
     (void)cudaLaunchKernelEx(&cfg, kern, args...);   // a failure is left for cudaGetLastError
 }
+
+// One restart cycle's Arnoldi steps of the delayed scheme as a CUDA graph:
+//   step = 1;  while (cond) { for u < 8: k_dots2(step + u); k_update2(step + u);  k_advance }
+// The body's kernels read the step from device memory and add their offset;
+// k_advance sets the condition, so the cycle runs without host round trips.
+// Consecutive Arnoldi kernels keep their programmatic (overlapped) launch.
+template <typename T>
+static ddg_status build_step_graph(const BatchArgs& args, unsigned G, int n, size_t dots2_smem,
+                                   size_t upd_smem, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphNode_t init = nullptr, loop = nullptr;
+    cudaGraphNodeParams cp = {};
+    const char* what = "cudaGraphCreate";
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess) {
+        what = "cudaGraphConditionalHandleCreate";
+        e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    }
+    if (e == cudaSuccess) {
+        what = "cudaGraphAddMemsetNode";
+        cudaMemsetParams mp = {};
+        mp.dst = args.step;
+        mp.value = 1;
+        mp.elementSize = 4;
+        mp.width = 1;
+        mp.height = 1;
+        e = cudaGraphAddMemsetNode(&init, g, nullptr, 0, &mp);
+    }
+    if (e == cudaSuccess) {
+        what = "cudaGraphAddNode (WHILE)";
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&loop, g, &init, nullptr, 1, &cp);
+    }
+    if (e == cudaSuccess) {
+        what = "cudaStreamCreateWithFlags";
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    }
+    if (e == cudaSuccess) {
+        what = "cudaStreamBeginCaptureToGraph";
+        e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+    }
+    if (e == cudaSuccess) {
+        for (int u = 0; u < kGraphUnroll; ++u) {
+            if (u == 0) k_dots2<T><<<G, kBlock, dots2_smem, cs>>>(args, 0);
+            else launch_overlapped(k_dots2<T>, G, dots2_smem, cs, args, -u);
+            launch_overlapped(k_update2<T>, G + n, upd_smem, cs, args, -u);
+        }
+        k_advance<<<1, 1, 0, cs>>>(args, h, kGraphUnroll);
+        const cudaError_t el = cudaGetLastError();
+        cudaGraph_t body = nullptr;
+        what = "step graph capture";
+        e = cudaStreamEndCapture(cs, &body);
+        if (e == cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) {
+        what = "cudaGraphInstantiate";
+        e = cudaGraphInstantiate(&ex, g, 0);
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        if (ex) cudaGraphExecDestroy(ex);
+        return cuda_status(e, what);
+    }
+    *out = ex;
+    return DDG_OK;
+}
+
+struct GraphExecGuard {
+    cudaGraphExec_t e = nullptr;
+    ~GraphExecGuard() {
+        if (e) cudaGraphExecDestroy(e);   // freed once any launch in flight completes
+    }
+};
 
 // Dynamic shared memory of the Arnoldi kernels for restart length m and N
 // augmentation vectors: the Givens staging (column, sines, result, s in the
@@ -1501,6 +1604,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     args.fallback = ctx->fallback;
     args.aug_cycles = ctx->aug_cycles;
     args.nsolves = n;
+    args.step = args.counts + 5;
     std::vector<int> hblk(total_ctas);
     for (int s = 0; s < n; ++s)
         for (int c = 0; c < hp[s].nchunks; ++c) hblk[hp[s].chunk0 + c] = s;
@@ -1525,6 +1629,21 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     const size_t bs_smem = sizeof(double2) * (3 * (size_t)m + kMaxAug);
     DDG_CHECK_CUDA(cudaFuncSetAttribute(k_backsub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs_smem));
     DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 8 * sizeof(int), st));
+    // delayed scheme: each cycle's step loop as one graph launch (per-launch
+    // profiling needs the host-driven loop)
+    const bool use_graph = ctx->orth == 1 && ctx->graphs && !ctx->prof;
+    GraphExecGuard gexec;
+    bool graph_pending = false;   // a graph launch whose kernels are not yet counted
+    auto count_graph = [&]() {
+        if (!graph_pending) return;
+        // every execution of the WHILE body launches 2 * kGraphUnroll + 1 kernels
+        const long long bodies = std::max(0, hc[5] - 1) / kGraphUnroll;
+        ctx->launches += bodies * (2 * kGraphUnroll + 1);
+        ctx->nlaunch[DDG_K_DOTS] += bodies * kGraphUnroll;
+        ctx->nlaunch[DDG_K_UPDATE] += bodies * kGraphUnroll;
+        ctx->nlaunch[DDG_K_STEP] += bodies;
+        graph_pending = false;
+    };
     for (long long cycle = 0; cycle <= (long long)maxit + 1; ++cycle) {
         DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 4 * sizeof(int), st));
         DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_residual<T><<<G, kBlock, 0, st>>>(args); }));
@@ -1533,8 +1652,9 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_update_r<T><<<G, kBlock, 0, st>>>(args); }));
         }
         DDG_CHECK_CUDA(cudaMemcpyAsync(hc, args.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 4, args.counts + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 4, args.counts + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+        count_graph();
         if (hc[4]) {
             set_error("gmres: a column copy into shared memory did not complete within its time limit");
             return DDG_ETIMEOUT;
@@ -1546,21 +1666,27 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_step<T><<<G, kBlock, 0, st>>>(args, 0); }));
             DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots_w<T><<<G, kBlock, 0, st>>>(args, 0, 0); }));
             DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T><<<G, kBlock, upd_smem, st>>>(args, 0, 0); }));
-            int polled = 0;
-            for (int i = 1; i <= m; ++i) {
-                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { launch_overlapped(k_dots2<T>, G, dots2_smem, st, args, i); }));
-                if (i < m)
-                    DDG_TRY(ctx->launch(DDG_K_UPDATE, st,
-                                        [&] { launch_overlapped(k_update2<T>, G + n, upd_smem, st, args, i); }));
-                if (i % ctx->poll_every == 0 && i < m) {
-                    const int slot = polled & 1;
-                    DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 2 + slot, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
-                    DDG_CHECK_CUDA(cudaEventRecord(ctx->ev[slot], st));
-                    if (polled > 0) {
-                        DDG_CHECK_CUDA(cudaEventSynchronize(ctx->ev[slot ^ 1]));
-                        if (hc[2 + (slot ^ 1)] == 0) break;
+            if (use_graph) {
+                if (!gexec.e) DDG_TRY(build_step_graph<T>(args, G, n, dots2_smem, upd_smem, &gexec.e));
+                DDG_CHECK_CUDA(cudaGraphLaunch(gexec.e, st));
+                graph_pending = true;
+            } else {
+                int polled = 0;
+                for (int i = 1; i <= m; ++i) {
+                    DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { launch_overlapped(k_dots2<T>, G, dots2_smem, st, args, i); }));
+                    if (i < m)
+                        DDG_TRY(ctx->launch(DDG_K_UPDATE, st,
+                                            [&] { launch_overlapped(k_update2<T>, G + n, upd_smem, st, args, i); }));
+                    if (i % ctx->poll_every == 0 && i < m) {
+                        const int slot = polled & 1;
+                        DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 2 + slot, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
+                        DDG_CHECK_CUDA(cudaEventRecord(ctx->ev[slot], st));
+                        if (polled > 0) {
+                            DDG_CHECK_CUDA(cudaEventSynchronize(ctx->ev[slot ^ 1]));
+                            if (hc[2 + (slot ^ 1)] == 0) break;
+                        }
+                        ++polled;
                     }
-                    ++polled;
                 }
             }
         } else if (hc[0] > 0) {
@@ -1589,8 +1715,9 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_finalize<T><<<G, kBlock, 0, st>>>(args); }));
     std::vector<SolveScal> hs(n);
     DDG_CHECK_CUDA(cudaMemcpyAsync(hs.data(), args.S, sizeof(SolveScal) * n, cudaMemcpyDeviceToHost, st));
-    DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 4, args.counts + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 4, args.counts + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+    count_graph();
     ctx->resolve();
     if (hc[4]) {
         set_error("gmres: a column copy into shared memory did not complete within its time limit");
@@ -1784,6 +1911,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     args.fallback = 1e300;
     args.aug_cycles = 1;
     args.nsolves = 1;
+    args.step = args.counts + 5;
     // every launch reads these: the array keeps the previous call's contents
     std::vector<int> hblk(hp.nchunks, 0);
     DDG_CHECK_CUDA(cudaMemcpyAsync(args.P, &hp, sizeof(SolvePtrs), cudaMemcpyHostToDevice, st));

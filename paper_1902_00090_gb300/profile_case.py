@@ -26,6 +26,8 @@ def main():
     p.add_argument("--repeat", type=int, default=1)
     p.add_argument("--orth", default=None, choices=[None, "cgs2", "dcgs2"])
     p.add_argument("--profile", action="store_true", help="print per-kernel-class time and GB/s")
+    p.add_argument("--graphs", default="on", choices=["on", "off"],
+                   help="step loop as a CUDA graph (on) or launched by the host (off)")
     a = p.parse_args()
 
     import torch
@@ -37,6 +39,7 @@ def main():
     ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device="cuda")) for e in eps]
     bs = [ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src) for op in ops]
     ctx = ddg.Context(orthogonalization=a.orth)
+    ctx.set_graphs(a.graphs == "on")
     U = None
     if a.k > 0:
         U = torch.as_tensor(inputs.random_complex(g.D, 7, shape=(a.k, g.D)), device="cuda")

@@ -389,3 +389,28 @@ def test_first_cycle_augmented_then_plain(prec):
     if prec == "c128":
         assert abs(info["iters"] - io.iters) <= 1
         assert rel(host(x), xo) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_graph_step_loop_matches_host_loop(prec):
+    # The graph-driven cycle (device-side WHILE over the same kernels) and the
+    # host-driven one launch the same kernels in the same order: equal fields
+    # bit for bit, equal step and cycle counts, including cycles that end
+    # mid-way (restart 30, several cycles; solves stopping at different steps).
+    g = inputs.grid_for(64, 64)
+    eps = inputs.trajectory_set(g, 2, 3, steps=3)
+    ops = [ddg.fdfd_operator(g, dev(e, torch.float64)) for e in eps]
+    bs = [ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src) for op in ops]
+    U = dev(inputs.random_complex(g.D, 5, shape=(4, g.D)))
+    out = {}
+    for graphs in (True, False):
+        c = ddg.Context()
+        c.set_graphs(graphs)
+        xs, infos, st = ddg.gmres_solve_batched(c, ops, bs, tol=1e-6, restart=30, maxit=4000, precision=prec)
+        xa, infa, sta = ddg.augmented_gmres_solve_batched(c, ops, bs, [U] * len(ops), tol=1e-6, restart=30,
+                                                          maxit=4000, precision=prec)
+        assert st == 0 and sta == 0
+        out[graphs] = (np.stack([host(x) for x in xs + xa]),
+                       [(i["iters"], i["cycles"], i["converged"]) for i in infos + infa])
+    assert out[True][1] == out[False][1]
+    assert np.array_equal(out[True][0], out[False][0])
