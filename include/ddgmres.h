@@ -51,7 +51,13 @@ typedef enum {
                             block, FP64 across blocks); true residual r = b - A x, Givens
                             rotations, Hessenberg least squares and the update of x in FP64.
                             Every restart recomputes r in FP64 (iterative refinement). */
-    DDG_C64_ONLY = 2     /* reserved */
+    DDG_C64_ONLY = 2     /* the Krylov loop as DDG_C64_REFINE, and the residual r = b - A x of
+                            every restart also in complex64 (from the operator's FP32 copy):
+                            no FP64 refinement; a cycle runs until its estimate reaches
+                            tol * ||b||.  For tolerances of about 1e-5 and above (FP32
+                            round-off bounds the attainable residual); the Givens rotations,
+                            the small least-squares problem and the x buffer stay FP64.
+                            Not accepted by gmres_solve_noalloc. */
 } ddg_precision;
 
 /* Problem description (host struct).  Units: metres. */
@@ -268,6 +274,14 @@ ddg_status predictor_destroy(ddg_predictor* P);
 long long predictor_num_params(const ddg_predictor* P);
 /* Kernels launched by this predictor since it was created. */
 long long predictor_launches(const ddg_predictor* P);
+/* Forward 3x3 convolutions on the tensor cores (no paper counterpart; default
+   on): layers whose input and output channel counts are multiples of 16 (and
+   at most 256 outputs) run as implicit GEMMs on tcgen05 (BF16 operands, FP32
+   accumulation in tensor memory); the others, the head and the backward pass
+   use CUDA cores.  Both paths give the same results up to FP32 summation
+   order.  A tensor-core wait that gives up makes the call return
+   DDG_ETIMEOUT. */
+ddg_status predictor_set_tensor_cores(ddg_predictor* P, int enable);
 /* theta: host, n = predictor_num_params floats.  Setting resets the Adam state. */
 ddg_status predictor_set_params(ddg_predictor* P, const float* theta, long long n);
 ddg_status predictor_get_params(const ddg_predictor* P, float* theta, long long n);

@@ -17,7 +17,8 @@ _LIB = None
 
 DDG_C128 = 0
 DDG_C64_REFINE = 1
-PRECISIONS = {"c128": DDG_C128, "c64": DDG_C64_REFINE, "c64_refine": DDG_C64_REFINE}
+DDG_C64_ONLY = 2
+PRECISIONS = {"c128": DDG_C128, "c64": DDG_C64_REFINE, "c64_refine": DDG_C64_REFINE, "c64_only": DDG_C64_ONLY}
 
 KERNEL_CLASSES = ("step", "dots", "update", "residual", "cycle_end", "setup")
 
@@ -80,6 +81,7 @@ _SIGS = {
     "predictor_destroy": (C.c_int, [_vp]),
     "predictor_num_params": (C.c_longlong, [_vp]),
     "predictor_launches": (C.c_longlong, [_vp]),
+    "predictor_set_tensor_cores": (C.c_int, [_vp, C.c_int]),
     "predictor_set_params": (C.c_int, [_vp, _vp, C.c_longlong]),
     "predictor_get_params": (C.c_int, [_vp, _vp, C.c_longlong]),
     "predictor_forward": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_double, C.c_double, _vp, _vp]),
@@ -450,6 +452,10 @@ class Predictor:
     def launches(self) -> int:
         """Kernels launched by this predictor (predictor_launches)."""
         return int(load().predictor_launches(self._h))
+
+    def set_tensor_cores(self, on: bool):
+        """Forward 3x3 convolutions on tcgen05 tensor cores (default) or CUDA cores."""
+        _check(load().predictor_set_tensor_cores(self._h, int(bool(on))), "predictor_set_tensor_cores")
 
     def set_params(self, theta):
         import numpy as np

@@ -12,6 +12,9 @@
 //
 // Precision: FP32 master weights and Adam moments; BF16 copies of the weights
 // and BF16 activations in the forward pass; FP32 accumulation; FP32 gradients.
+// The forward 3x3 convolutions whose channel counts are multiples of 16 run on
+// the 5th-generation tensor cores (tcgen05, accumulators in tensor memory);
+// the first layer, the 1x1 head and the backward pass run on CUDA cores.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -21,6 +24,7 @@
 #include <new>
 #include <vector>
 
+#include "bulk.cuh"
 #include "engine.cuh"
 
 using bf16 = __nv_bfloat16;
@@ -145,6 +149,189 @@ __global__ void __launch_bounds__(256) k_conv3(LD ld, int B, int H, int W, int C
             store_out(o + co, v);
         }
     }
+}
+
+// ---------------------------------------------------------------- 3x3 convolution on tensor cores
+// Implicit GEMM: D[p, co] = sum_k A[p, k] Wt[co, k], k = tap * Ci + ci (tap =
+// 3 dy + dx), A[p, k] = in[b, y + dy - 1, x + dx - 1, ci] (zero outside the
+// grid; the input may be the concatenation of a nearest-upsampled x1 and x2).
+// One CTA: 128 consecutive pixels (M = 128) x all Co output channels (N = Co).
+// K streams through two shared-memory stages of 64: all 128 threads gather the
+// im2col tile and the weight tile with 16-byte loads into the K-major
+// no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix, core
+// matrices adjacent in K 128 bytes apart, 8-row groups 1024 bytes apart); one
+// thread issues tcgen05.mma (BF16 x BF16 -> FP32 in tensor memory, K = 16 per
+// instruction) and commits each stage to an mbarrier, so the gather of the
+// next stage overlaps the MMAs of this one.  Epilogue: tcgen05.ld of each
+// warp's 32 accumulator rows, bias, ReLU, BF16 NHWC stores.
+namespace tc {
+constexpr int kM = 128;
+constexpr int kKC = 64;
+constexpr int kStages = 2;
+constexpr int kThreads = 128;
+constexpr uint32_t kLBO = 128;               // core matrices adjacent in K
+constexpr uint32_t kSBO = (kKC / 8) * 128;   // adjacent 8-row groups
+constexpr uint32_t kABytes = kM * kKC * 2;
+
+__host__ __device__ constexpr size_t smem_bytes(int co) { return (size_t)kStages * (kABytes + (size_t)co * kKC * 2); }
+__host__ __device__ constexpr uint32_t tmem_cols(int co) { return co <= 32 ? 32u : co <= 64 ? 64u : co <= 128 ? 128u : 256u; }
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (8-row group) byte offsets in 16-byte units, descriptor version 1, no
+// swizzle, base offset 0.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((kLBO >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((kSBO >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = n (multiple of 16), M = 128.
+__host__ __device__ constexpr uint32_t idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+}  // namespace tc
+
+__global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(LoadCat ld, int B, int H, int W, int Ci, int Co,
+                                                           const bf16* __restrict__ wt, const float* __restrict__ bias,
+                                                           int relu, bf16* __restrict__ out, int* __restrict__ err) {
+    using namespace tc;
+    extern __shared__ __align__(128) unsigned char smt[];
+    __shared__ __align__(8) unsigned long long done[kStages];
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long P = (long long)B * H * W;
+    const long long p0 = (long long)blockIdx.x * kM;
+    const int K = 9 * Ci;
+    const int nch = (K + kKC - 1) / kKC;
+    const uint32_t ncols = tmem_cols(Co);
+    const uint32_t st_bytes = kABytes + (uint32_t)Co * kKC * 2;
+    if (tid == 0) {
+        for (int q = 0; q < kStages; ++q) mbar_init(&done[q], 1);
+        mbar_init_fence();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_tmem;
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+        const int s = c % kStages;
+        unsigned char* As = smt + s * st_bytes;
+        unsigned char* Bs = As + kABytes;
+        // the MMAs that last read this stage are complete
+        if (c >= kStages && !mbar_wait(&done[s], (unsigned)((c - kStages) / kStages) & 1u)) ok = false;
+        for (int q = tid; q < kM * 8; q += kThreads) {
+            const int r = q >> 3, kg = q & 7;
+            const int k0 = c * kKC + kg * 8;
+            const long long p = p0 + r;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (k0 < K && p < P) {
+                const int tap = k0 / Ci, ci = k0 - tap * Ci;
+                const int x = (int)(p % W);
+                const long long t = p / W;
+                const int y = (int)(t % H), b = (int)(t / H);
+                const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+                if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                    const bf16* src;
+                    if (ci < ld.c1)
+                        src = ld.up1 ? ld.x1 + ((((long long)b * ld.h1 + (yy >> 1)) * ld.w1 + (xx >> 1)) * ld.c1 + ci)
+                                     : ld.x1 + ((((long long)b * H + yy) * W + xx) * ld.c1 + ci);
+                    else
+                        src = ld.x2 + ((((long long)b * H + yy) * W + xx) * ld.c2 + (ci - ld.c1));
+                    v = *reinterpret_cast<const uint4*>(src);
+                }
+            }
+            *reinterpret_cast<uint4*>(As + (r >> 3) * kSBO + kg * kLBO + (r & 7) * 16) = v;
+        }
+        for (int q = tid; q < Co * 8; q += kThreads) {
+            const int n = q >> 3, kg = q & 7;
+            const int k0 = c * kKC + kg * 8;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (k0 < K) v = *reinterpret_cast<const uint4*>(wt + (long long)n * K + k0);
+            *reinterpret_cast<uint4*>(Bs + (n >> 3) * kSBO + kg * kLBO + (n & 7) * 16) = v;
+        }
+        fence_proxy_async_smem();   // these shared-memory writes, before the tensor core reads them
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+            for (int ks = 0; ks < kKC / 16; ++ks)
+                mma(tmem, sdesc(a0 + ks * 2 * kLBO), sdesc(b0 + ks * 2 * kLBO), idesc(Co), (c > 0 || ks > 0) ? 1u : 0u);
+            commit(&done[s]);
+        }
+    }
+    // the last commit completes once every MMA issued before it has
+    const int cl = nch - 1;
+    if (!mbar_wait(&done[cl % kStages], (unsigned)(cl / kStages) & 1u)) {
+        ok = false;
+        mbar_wait(&done[cl % kStages], (unsigned)(cl / kStages) & 1u);   // one more bounded wait before freeing
+    }
+    fence_after();
+    const long long p = p0 + warp * 32 + lane;   // accumulator row = tensor-memory lane
+    for (int c0 = 0; c0 < Co; c0 += 8) {
+        uint32_t r[8];
+        ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+        if (p < P) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                v[j] = __uint_as_float(r[j]) + (bias ? bias[c0 + j] : 0.f);
+                if (relu) v[j] = fmaxf(v[j], 0.f);
+            }
+            uint4 o;
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4], v[5]), h3 = __floats2bfloat162_rn(v[6], v[7]);
+            o.x = *reinterpret_cast<uint32_t*>(&h0);
+            o.y = *reinterpret_cast<uint32_t*>(&h1);
+            o.z = *reinterpret_cast<uint32_t*>(&h2);
+            o.w = *reinterpret_cast<uint32_t*>(&h3);
+            *reinterpret_cast<uint4*>(out + p * Co + c0) = o;
+        }
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+// tensor-core weights BF16 [co][ci][9] -> [co][9][ci] (K-major rows, k = tap * Ci + ci)
+__global__ void k_w_tc(const bf16* __restrict__ w, int Co, int Ci, bf16* __restrict__ wt) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)Co * Ci * 9) return;
+    const int co = (int)(idx / (Ci * 9)), ci = (int)((idx / 9) % Ci), tap = (int)(idx % 9);
+    wt[((long long)co * 9 + tap) * Ci + ci] = w[idx];
 }
 
 // Weight gradient of a 3x3 convolution: dW[co][ci][tap] += sum_p g[p, co] in[p + tap, ci],
@@ -593,6 +780,8 @@ struct ddg_predictor {
     void* act = nullptr;
     size_t act_bytes = 0;
     double* d_loss = nullptr;     // per-sample losses
+    int* d_err = nullptr;         // a bounded wait in a tensor-core convolution gave up
+    bool tensor_cores = true;     // forward 3x3 convolutions on tcgen05 where the channels allow
     void* d_desc = nullptr;       // InputDesc / pointer arrays (device)
     size_t desc_bytes = 0;
 };
@@ -685,6 +874,42 @@ static ddg_status conv3(ddg_predictor* P, const LD& ld, int B, int H, int W, int
     return DDG_OK;
 }
 
+// Forward 3x3 convolution of layer li: tensor cores when the channel counts
+// allow 16-byte gathers and N = Co (multiples of 16, Co <= 256), else CUDA cores.
+static ddg_status conv_fwd(ddg_predictor* P, const LoadCat& ld, int B, int H, int W, int li, bf16* out,
+                           cudaStream_t st) {
+    const Layer& Ly = P->layers[li];
+    const bool tcok = P->tensor_cores && Ly.ci % 16 == 0 && Ly.co % 16 == 0 && Ly.co <= 256 && ld.c1 % 8 == 0 &&
+                      ld.c2 % 8 == 0;
+    ++P->launches;
+    if (!tcok) {
+        k_w_fwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
+        return conv3(P, ld, B, H, W, Ly.ci, Ly.co, P->wk, bias32(P, li), 1, out, st);
+    }
+    k_w_tc<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
+    const size_t smem = tc::smem_bytes(Ly.co);
+    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long npx = (long long)B * H * W;
+    ++P->launches;
+    k_conv3_tc<<<(unsigned)((npx + tc::kM - 1) / tc::kM), tc::kThreads, smem, st>>>(
+        ld, B, H, W, Ly.ci, Ly.co, P->wk, bias32(P, li), 1, out, P->d_err);
+    DDG_CHECK_LAUNCH("k_conv3_tc");
+    return DDG_OK;
+}
+
+// Reads and clears the tensor-core convolutions' wait flag (after a stream sync).
+static ddg_status check_tc(ddg_predictor* P, cudaStream_t st) {
+    int h = 0;
+    DDG_CHECK_CUDA(cudaMemcpyAsync(&h, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        DDG_CHECK_CUDA(cudaMemsetAsync(P->d_err, 0, sizeof(int), st));
+        set_error("predictor: a tensor-core convolution's wait did not complete within its time limit");
+        return DDG_ETIMEOUT;
+    }
+    return DDG_OK;
+}
+
 // forward pass for B samples of one grid size; result in A->y
 static ddg_status forward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaStream_t st) {
     const int L = P->levels;
@@ -701,10 +926,8 @@ static ddg_status forward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaSt
         for (int ab = 0; ab < 2; ++ab) {
             const int li = layer_index(P, false, l, ab);
             const Layer& Ly = P->layers[li];
-            ++P->launches;
-            k_w_fwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
             LoadCat ld{ab == 0 ? in : A->ea[l], Ly.ci, 0, Hl, Wl, nullptr, 0};
-            DDG_TRY(conv3(P, ld, B, Hl, Wl, Ly.ci, Ly.co, P->wk, bias32(P, li), 1, ab == 0 ? A->ea[l] : A->eb[l], st));
+            DDG_TRY(conv_fwd(P, ld, B, Hl, Wl, li, ab == 0 ? A->ea[l] : A->eb[l], st));
         }
         h = A->eb[l];
         hc = P->ch[l];
@@ -714,11 +937,9 @@ static ddg_status forward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaSt
         for (int ab = 0; ab < 2; ++ab) {
             const int li = layer_index(P, true, l, ab);
             const Layer& Ly = P->layers[li];
-            ++P->launches;
-            k_w_fwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
             LoadCat ld = ab == 0 ? LoadCat{h, hc, 1, Hl / 2, Wl / 2, A->eb[l], P->ch[l]}
                                  : LoadCat{A->da[l], Ly.ci, 0, Hl, Wl, nullptr, 0};
-            DDG_TRY(conv3(P, ld, B, Hl, Wl, Ly.ci, Ly.co, P->wk, bias32(P, li), 1, ab == 0 ? A->da[l] : A->db[l], st));
+            DDG_TRY(conv_fwd(P, ld, B, Hl, Wl, li, ab == 0 ? A->da[l] : A->db[l], st));
         }
         h = A->db[l];
         hc = P->ch[l];
@@ -884,6 +1105,7 @@ static void free_predictor(ddg_predictor* P) {
     cudaFree(P->wk);
     cudaFree(P->act);
     cudaFree(P->d_loss);
+    cudaFree(P->d_err);
     cudaFree(P->d_desc);
     delete P;
 }
@@ -936,6 +1158,8 @@ extern "C" ddg_status predictor_create(int k, int levels, const int* channels, d
     if (e == cudaSuccess) e = cudaMalloc(&P->adam_v, 4 * n);
     if (e == cudaSuccess) e = cudaMalloc(&P->wk, 2 * maxw);
     if (e == cudaSuccess) e = cudaMalloc(&P->d_loss, sizeof(double) * 4096);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(P->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(P->theta, 0, 4 * n);
     if (e == cudaSuccess) e = cudaMemset(P->theta_bf, 0, 2 * n);
     if (e == cudaSuccess) e = cudaMemset(P->adam_m, 0, 4 * n);
@@ -958,6 +1182,12 @@ extern "C" ddg_status predictor_destroy(ddg_predictor* P) {
 extern "C" long long predictor_num_params(const ddg_predictor* P) { return P ? P->nparams : 0; }
 
 extern "C" long long predictor_launches(const ddg_predictor* P) { return P ? P->launches : 0; }
+
+extern "C" ddg_status predictor_set_tensor_cores(ddg_predictor* P, int enable) {
+    if (!P) { set_error("predictor_set_tensor_cores: NULL predictor"); return DDG_EINVAL; }
+    P->tensor_cores = enable != 0;
+    return DDG_OK;
+}
 
 extern "C" ddg_status predictor_set_params(ddg_predictor* P, const float* theta, long long n) {
     if (!P || !theta || n != P->nparams) { set_error("predictor_set_params: need %lld values", P ? P->nparams : 0LL); return DDG_EINVAL; }
@@ -990,7 +1220,7 @@ extern "C" ddg_status predictor_forward(ddg_predictor* P, int n, const ddg_op* c
     DDG_TRY(build_input(P, n, A, i_src, sigma, j_c, &acts, st));
     DDG_TRY(forward(P, n, H, W, &acts, st));
     DDG_CHECK_CUDA(cudaMemcpyAsync(y, acts.y, sizeof(float) * (size_t)n * H * W * 2 * P->k, cudaMemcpyDeviceToDevice, st));
-    return DDG_OK;
+    return check_tc(P, st);
 }
 
 extern "C" ddg_status subspace_predict(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
@@ -1011,8 +1241,7 @@ extern "C" ddg_status subspace_predict(ddg_predictor* P, int n, const ddg_op* co
     k_to_complex<<<nblk((long long)n * H * W * P->k), 256, 0, st>>>(acts.y, H * W, P->k,
                                                                     reinterpret_cast<double2* const*>(slots), n);
     DDG_CHECK_LAUNCH("k_to_complex");
-    DDG_CHECK_CUDA(cudaStreamSynchronize(st));
-    return DDG_OK;
+    return check_tc(P, st);
 }
 
 extern "C" ddg_status predictor_loss_grad(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
@@ -1058,7 +1287,7 @@ extern "C" ddg_status predictor_loss_grad(ddg_predictor* P, int n, const ddg_op*
     std::vector<double> hl(n);
     DDG_CHECK_CUDA(cudaMemcpyAsync(hl.data(), P->d_loss, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
     if (grad) DDG_CHECK_CUDA(cudaMemcpyAsync(grad, P->grad, 4 * (size_t)P->nparams, cudaMemcpyDeviceToDevice, st));
-    DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+    DDG_TRY(check_tc(P, st));
     double tot = 0.0;
     for (double v : hl) tot += v;
     if (loss) *loss = tot / n;

@@ -144,6 +144,7 @@ struct BatchArgs {
     int maxit;
     int nsolves;       // solves in the batch (k_update2 puts one block per solve in front of its sweep)
     int* step;         // Arnoldi step of the graph-driven loop (kernels launched with i <= 0 add it)
+    int low_res;       // DDG_C64_ONLY: the restart residual r = b - A x in the Krylov precision
 };
 
 // Adds `v` to the class counter once per CTA (thread 0), when profiling.

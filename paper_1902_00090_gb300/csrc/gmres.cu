@@ -264,23 +264,48 @@ __global__ void __launch_bounds__(kBlock) k_residual(BatchArgs a) {
     if (!S->active) return;
     const long long D = P.D;
     const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
-    count_bytes(a, DDG_K_RESIDUAL, (double)min((long long)chunk_rows<T>(), D - (long long)chunk * chunk_rows<T>()) * 56.0);
+    // x, b read and r written (16 B each), eps (8 B, or 4 B in the Krylov precision)
+    count_bytes(a, DDG_K_RESIDUAL, (double)min((long long)chunk_rows<T>(), D - (long long)chunk * chunk_rows<T>()) *
+                                       (a.low_res ? 52.0 : 56.0));
     __shared__ double sm[kWarps];
     const double2* __restrict__ x = P.x;
     double accr = 0.0, accb = 0.0;
-    auto ld = [&](long long idx) { return x[idx]; };
+    if (a.low_res) {
+        // DDG_C64_ONLY: the residual in the Krylov precision, from the operator's
+        // low-precision copy (no FP64 refinement)
+        using V = c2_t<T>;
+        const T* eps = reinterpret_cast<const T*>(P.eps_lo);
+        const V* coef = reinterpret_cast<const V*>(P.coef_lo);
+        const T kh2 = (T)P.kh2;
+        auto ldl = [&](long long idx) { return from_d2<V>(x[idx]); };
 #pragma unroll
-    for (int q = 0; q < VEC; ++q) {
-        const long long e = e0 + q;
-        double2 rv = make_double2(0.0, 0.0);
-        if (e < D) {
-            double2 ax = stencil(e, P.nx, P.ny, P.coef_d, P.kh2 * P.eps_d[e], ld);
-            double2 bv = P.b[e];
-            rv = csub(bv, ax);
-            accr += cabs2(rv);
-            accb += cabs2(bv);
+        for (int q = 0; q < VEC; ++q) {
+            const long long e = e0 + q;
+            V rv = mk((T)0, (T)0);
+            if (e < D) {
+                const V ax = stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ldl);
+                const V bv = from_d2<V>(P.b[e]);
+                rv = csub(bv, ax);
+                accr += cabs2(rv);
+                accb += cabs2(bv);
+            }
+            P.r[e] = to_d2(rv);
         }
-        P.r[e] = rv;
+    } else {
+        auto ld = [&](long long idx) { return x[idx]; };
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            const long long e = e0 + q;
+            double2 rv = make_double2(0.0, 0.0);
+            if (e < D) {
+                double2 ax = stencil(e, P.nx, P.ny, P.coef_d, P.kh2 * P.eps_d[e], ld);
+                double2 bv = P.b[e];
+                rv = csub(bv, ax);
+                accr += cabs2(rv);
+                accb += cabs2(bv);
+            }
+            P.r[e] = rv;
+        }
     }
     double tr = block_sum_d(accr, sm);
     double tb = block_sum_d(accb, sm);
@@ -1516,7 +1541,7 @@ static ddg_status dcgs2_smem(int Nreq, int m, size_t& giv, size_t& dots2, size_t
 template <typename T>
 static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const double* const* b, double* const* x,
                             const double* const* U, int Nreq, double tol, int m, int maxit, double eta,
-                            ddg_info* info, cudaStream_t st) {
+                            ddg_info* info, cudaStream_t st, bool low_res = false) {
     using V = c2_t<T>;
     const long long CH = chunk_rows<T>();
     int KP = std::max(kMaxAug + 2 * m + 4, Nreq * Nreq);
@@ -1605,6 +1630,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     args.aug_cycles = ctx->aug_cycles;
     args.nsolves = n;
     args.step = args.counts + 5;
+    args.low_res = low_res ? 1 : 0;
     std::vector<int> hblk(total_ctas);
     for (int s = 0; s < n; ++s)
         for (int c = 0; c < hp[s].nchunks; ++c) hblk[hp[s].chunk0 + c] = s;
@@ -1747,7 +1773,10 @@ static ddg_status solve_entry(ddg_context* cptr, int n, const ddg_op* const* A, 
     if (!(tol > 0.0 && tol < 1.0)) { set_error("%s: tol=%g outside (0,1)", who, tol); return DDG_EINVAL; }
     if (restart < 1 || restart > kMaxRestart) { set_error("%s: restart=%d outside [1,%d]", who, restart, kMaxRestart); return DDG_EINVAL; }
     if (maxit < 1) { set_error("%s: maxit=%d < 1", who, maxit); return DDG_EINVAL; }
-    if (prec != DDG_C128 && prec != DDG_C64_REFINE) { set_error("%s: unsupported precision %d", who, (int)prec); return DDG_EINVAL; }
+    if (prec != DDG_C128 && prec != DDG_C64_REFINE && prec != DDG_C64_ONLY) {
+        set_error("%s: unsupported precision %d", who, (int)prec);
+        return DDG_EINVAL;
+    }
     if (U && (k < 1 || k > kMaxAug)) { set_error("%s: k=%d outside [1,%d]", who, k, kMaxAug); return DDG_EINVAL; }
     for (int s = 0; s < n; ++s) {
         if (!A[s] || !b[s] || !x[s]) { set_error("%s: NULL operator/b/x at %d", who, s); return DDG_EINVAL; }
@@ -1759,6 +1788,8 @@ static ddg_status solve_entry(ddg_context* cptr, int n, const ddg_op* const* A, 
     const int Nreq = U ? k : 0;
     if (prec == DDG_C128)
         return run_batch<double>(ctx, n, A, b, x, U, Nreq, tol, restart, maxit, 0.0, info, st);
+    if (prec == DDG_C64_ONLY)   // cycles run to tol * ||b||; residual in FP32
+        return run_batch<float>(ctx, n, A, b, x, U, Nreq, tol, restart, maxit, 0.0, info, st, true);
     return run_batch<float>(ctx, n, A, b, x, U, Nreq, tol, restart, maxit, ctx->inner_tol, info, st);
 }
 
@@ -1912,6 +1943,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     args.aug_cycles = 1;
     args.nsolves = 1;
     args.step = args.counts + 5;
+    args.low_res = 0;
     // every launch reads these: the array keeps the previous call's contents
     std::vector<int> hblk(hp.nchunks, 0);
     DDG_CHECK_CUDA(cudaMemcpyAsync(args.P, &hp, sizeof(SolvePtrs), cudaMemcpyHostToDevice, st));

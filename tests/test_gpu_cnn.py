@@ -227,3 +227,41 @@ def test_residual_loss_and_gradient_match_oracle():
     lo, go = ocnn.batch_residual_loss_and_grad(cfg, theta, x, As, rhs)
     assert abs(loss - lo) <= 2e-2 * max(lo, 1e-2)
     assert gg @ go / (np.linalg.norm(gg) * np.linalg.norm(go)) >= 0.98
+
+
+TC = dict(k=2, channels=(16, 32, 48))   # every 3x3 layer but the first takes the tensor-core path
+
+
+def test_tensor_core_convolutions_match_oracle():
+    # channel counts that are multiples of 16: the forward 3x3 convolutions run
+    # on tcgen05 (BF16 x BF16, FP32 in tensor memory); same bars as the CUDA-core
+    # forward against the bfloat16-emulated and the fp64 oracle
+    g, eps, ops = small_problems(n=3)
+    P = ddg.Predictor(**TC)
+    P.init_he(seed=11)
+    theta = P.get_params().astype(np.float64)
+    y = P.forward(ops, (g.i_src, g.sigma_src, g.j_src)).cpu().numpy()
+    cfg = ocnn.CNNConfig(cin=4, channels=TC["channels"], k=TC["k"])
+    x = oracle_inputs(g, eps)
+    yb = ocnn.forward(cfg, ocnn.round_weights(cfg, theta, ocnn.bf16_round), ocnn.bf16_round(x),
+                      store=ocnn.bf16_round)
+    assert rel(y, yb) <= 2e-3
+    assert rel(y, ocnn.forward(cfg, theta, x)) <= 3e-2
+
+
+def test_tensor_core_forward_equals_cuda_core_forward():
+    # the full-size network at 128x128 on both convolution paths: equal up to
+    # FP32 summation order (and the BF16 roundings it flips)
+    g = inputs.grid_128()
+    eps = inputs.trajectory_set(g, 2, 1, steps=3)
+    ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device="cuda")) for e in eps]
+    P = ddg.Predictor(k=8)
+    P.init_he(seed=2)
+    src = (g.i_src, g.sigma_src, g.j_src)
+    y_tc = P.forward(ops, src).cpu().numpy()
+    P.set_tensor_cores(False)
+    y_cc = P.forward(ops, src).cpu().numpy()
+    P.set_tensor_cores(True)
+    y_tc2 = P.forward(ops, src).cpu().numpy()
+    assert np.array_equal(y_tc, y_tc2)          # deterministic
+    assert rel(y_tc, y_cc) <= 1e-2

@@ -164,6 +164,40 @@ def rand_V(D, N, seed):
     return inputs.random_complex(D, seed, shape=(N, D))
 
 
+def test_fp32_only_to_1e4(ctx, config1):
+    # DDG_C64_ONLY: no FP64 refinement; the solver judges convergence on an FP32
+    # residual, so the FP64 residual recomputed by the oracle meets the
+    # tolerance up to FP32 round-off, and the field is within the measured
+    # forward-error factor (3.6 at 1e-6 on this problem) times the tolerance.
+    g, eps, A, b, xd = config1
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x, info, st = ddg.gmres_solve(ctx, op, dev(b), tol=1e-4, restart=200, maxit=5000, precision="c64_only")
+    assert st == 0 and info["converged"]
+    xh = host(x)
+    r = np.linalg.norm(b - A @ xh) / np.linalg.norm(b)
+    assert r <= 1.02e-4
+    assert abs(r - info["true_rel_residual"]) <= 2e-6
+    assert rel(xh, xd) <= 1e-3
+    # the same problem through the refinement path stops at the same tolerance
+    x2, info2, st2 = ddg.gmres_solve(ctx, op, dev(b), tol=1e-4, restart=200, maxit=5000, precision="c64")
+    assert st2 == 0 and abs(info2["iters"] - info["iters"]) <= 0.1 * info["iters"] + 5
+
+
+def test_fp32_only_augmented(ctx):
+    # augmented path in DDG_C64_ONLY with a subspace holding a nearby solution
+    g, eps, A, b = small(48, npml=6, seed=5)
+    # the subspace: the solution of a nearby problem (eps perturbed) and noise
+    eps2 = eps + 0.05 * np.random.default_rng(6).random(eps.shape)
+    x2 = spla.spsolve(fdfd.operator_for(g, eps2).tocsc(), b)
+    V = np.stack([x2, inputs.random_complex(g.D, 41)])
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x, info, st = ddg.augmented_gmres_solve(ctx, op, dev(b), dev(V), tol=1e-4, restart=60, maxit=5000,
+                                            precision="c64_only")
+    assert st == 0 and info["converged"]
+    assert np.linalg.norm(b - A @ host(x)) / np.linalg.norm(b) <= 1.02e-4
+    assert info["first_step_rel_residual"] < 0.5
+
+
 def test_augmented_matches_oracle_c128(ctx):
     g, eps, A, b = small(24, npml=4, seed=9)
     V = rand_V(g.D, 4, 9)

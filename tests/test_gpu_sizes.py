@@ -79,3 +79,24 @@ def test_large_grid_1024_properties():
     r = relres(A, x.cpu().numpy(), b)
     assert abs(r - info["true_rel_residual"]) <= 1e-10
     assert r < 1.0
+
+
+def test_large_grid_1024_fp32_only_capped():
+    # The large grid in DDG_C64_ONLY (the restart residual in FP32), capped at
+    # 2000 steps: restarted GMRES(200) alone stagnates on this 1M-unknown
+    # indefinite problem long before 1e-4.  The FP32 residual the solver reports
+    # must agree with the oracle's FP64 recomputation to FP32 round-off, and
+    # must have fallen.
+    g = inputs.grid_1024()
+    eps = inputs.trajectory_eps(g, 5, 0, steps=1)[0]
+    A = fdfd.operator_for(g, eps)
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    b = fdfd.source_for(g)
+    bd = ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src)
+    ctx = ddg.Context()
+    x, info, st = ddg.gmres_solve(ctx, op, bd, tol=1e-4, restart=200, maxit=2000, precision="c64_only")
+    assert st == 4 and info["iters"] == 2000
+    r = relres(A, x.cpu().numpy(), b)
+    print(f"1024^2 FP32-only: residual {r:.3e} after {info['iters']} steps")
+    assert abs(r - info["true_rel_residual"]) <= 2e-6 + 1e-4 * r
+    assert r < 0.5
