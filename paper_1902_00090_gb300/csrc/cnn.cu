@@ -156,34 +156,44 @@ __global__ void __launch_bounds__(256) k_conv3(LD ld, int B, int H, int W, int C
 // 3 dy + dx), A[p, k] = in[b, y + dy - 1, x + dx - 1, ci] (zero outside the
 // grid; the input may be the concatenation of a nearest-upsampled x1 and x2).
 // One CTA: 128 consecutive pixels (M = 128) x all Co output channels (N = Co).
-// K streams through two shared-memory stages of 64: all 128 threads gather the
-// im2col tile and the weight tile with 16-byte loads into the K-major
-// no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix, core
-// matrices adjacent in K 128 bytes apart, 8-row groups 1024 bytes apart); one
+// K streams through two shared-memory stages of 64: all 256 threads gather the
+// im2col tile and the weight tile with 16-byte loads into the K-major layout
+// with 128-byte swizzle (one 128-byte row of 64 K values per pixel / output
+// channel, its 16-byte chunks permuted by XOR with row % 8, 8-row atoms of
+// 1024 bytes), so that the 8 threads writing one row fill one line; one
 // thread issues tcgen05.mma (BF16 x BF16 -> FP32 in tensor memory, K = 16 per
-// instruction) and commits each stage to an mbarrier, so the gather of the
-// next stage overlaps the MMAs of this one.  Epilogue: tcgen05.ld of each
-// warp's 32 accumulator rows, bias, ReLU, BF16 NHWC stores.
+// instruction, the descriptor advanced 32 bytes per step) and commits each
+// stage to an mbarrier, so the gather of the next stage overlaps the MMAs of
+// this one.  Epilogue: tcgen05.ld of the accumulator rows, bias, ReLU, BF16
+// NHWC stores.
 namespace tc {
 constexpr int kM = 128;
 constexpr int kKC = 64;
 constexpr int kStages = 2;
-constexpr int kThreads = 128;
-constexpr uint32_t kLBO = 128;               // core matrices adjacent in K
-constexpr uint32_t kSBO = (kKC / 8) * 128;   // adjacent 8-row groups
+constexpr int kThreads = 256;
+constexpr uint32_t kRowBytes = kKC * 2;      // one swizzled row: 64 BF16 = 128 bytes
+constexpr uint32_t kSBO = 8 * kRowBytes;     // adjacent 8-row atoms (1024 bytes)
 constexpr uint32_t kABytes = kM * kKC * 2;
+static_assert(kRowBytes == 128, "one K stage is one 128-byte swizzle row");
 
-__host__ __device__ constexpr size_t smem_bytes(int co) { return (size_t)kStages * (kABytes + (size_t)co * kKC * 2); }
+// stages (1024-byte aligned atoms: the dynamic base is rounded up in the kernel)
+__host__ __device__ constexpr size_t smem_bytes(int co) { return (size_t)kStages * (kABytes + (size_t)co * kKC * 2) + 1024; }
+// byte offset of 16-byte chunk `kg` of row `r` in a swizzled K-major tile
+__device__ __forceinline__ uint32_t swz(int r, int kg) {
+    return (uint32_t)(r >> 3) * kSBO + (uint32_t)(r & 7) * kRowBytes + ((uint32_t)(kg ^ (r & 7)) << 4);
+}
 __host__ __device__ constexpr uint32_t tmem_cols(int co) { return co <= 32 ? 32u : co <= 64 ? 64u : co <= 128 ? 128u : 256u; }
 
-// Shared-memory matrix descriptor: start address, leading (K) and stride
-// (8-row group) byte offsets in 16-byte units, descriptor version 1, no
-// swizzle, base offset 0.
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// start address, leading byte offset (unused for this layout, 16 bytes),
+// stride byte offset between 8-row atoms (1024), descriptor version 1, base
+// offset 0 (atoms 1024-byte aligned), layout type 2 (128-byte swizzle).
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
     uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((kLBO >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)1 << 16;
     d |= (uint64_t)((kSBO >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
@@ -217,16 +227,34 @@ __global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(LoadCat ld, int B, in
                                                            const bf16* __restrict__ wt, const float* __restrict__ bias,
                                                            int relu, bf16* __restrict__ out, int* __restrict__ err) {
     using namespace tc;
-    extern __shared__ __align__(128) unsigned char smt[];
+    constexpr int kRowsPerThread = kM * 8 / kThreads;   // A rows gathered by one thread (fixed K group)
+    extern __shared__ __align__(128) unsigned char smraw_tc[];
     __shared__ __align__(8) unsigned long long done[kStages];
     __shared__ uint32_t s_tmem;
+    // swizzle atoms must start on 1024-byte boundaries
+    unsigned char* smt = smraw_tc + ((1024u - (smem_u32(smraw_tc) & 1023u)) & 1023u);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long P = (long long)B * H * W;
-    const long long p0 = (long long)blockIdx.x * kM;
+    const int P = B * H * W;
+    const int p0 = blockIdx.x * kM;
     const int K = 9 * Ci;
     const int nch = (K + kKC - 1) / kKC;
     const uint32_t ncols = tmem_cols(Co);
     const uint32_t st_bytes = kABytes + (uint32_t)Co * kKC * 2;
+    // this thread's K group and rows: row r = tid / 8 + (kThreads / 8) j
+    const int kg = tid & 7, r0 = tid >> 3;
+    int rb[kRowsPerThread], ryx[kRowsPerThread];   // image, and (y << 16 | x); b < 0: past the end
+#pragma unroll
+    for (int j = 0; j < kRowsPerThread; ++j) {
+        const int p = p0 + r0 + (kThreads / 8) * j;
+        if (p < P) {
+            const int x = p % W, t = p / W;
+            rb[j] = t / H;
+            ryx[j] = ((t % H) << 16) | x;
+        } else {
+            rb[j] = -1;
+            ryx[j] = 0;
+        }
+    }
     if (tid == 0) {
         for (int q = 0; q < kStages; ++q) mbar_init(&done[q], 1);
         mbar_init_fence();
@@ -248,35 +276,37 @@ __global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(LoadCat ld, int B, in
         unsigned char* Bs = As + kABytes;
         // the MMAs that last read this stage are complete
         if (c >= kStages && !mbar_wait(&done[s], (unsigned)((c - kStages) / kStages) & 1u)) ok = false;
-        for (int q = tid; q < kM * 8; q += kThreads) {
-            const int r = q >> 3, kg = q & 7;
-            const int k0 = c * kKC + kg * 8;
-            const long long p = p0 + r;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (k0 < K && p < P) {
-                const int tap = k0 / Ci, ci = k0 - tap * Ci;
-                const int x = (int)(p % W);
-                const long long t = p / W;
-                const int y = (int)(t % H), b = (int)(t / H);
-                const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-                if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-                    const bf16* src;
-                    if (ci < ld.c1)
-                        src = ld.up1 ? ld.x1 + ((((long long)b * ld.h1 + (yy >> 1)) * ld.w1 + (xx >> 1)) * ld.c1 + ci)
-                                     : ld.x1 + ((((long long)b * H + yy) * W + xx) * ld.c1 + ci);
-                    else
-                        src = ld.x2 + ((((long long)b * H + yy) * W + xx) * ld.c2 + (ci - ld.c1));
-                    v = *reinterpret_cast<const uint4*>(src);
-                }
-            }
-            *reinterpret_cast<uint4*>(As + (r >> 3) * kSBO + kg * kLBO + (r & 7) * 16) = v;
+        const int k0 = c * kKC + kg * 8;
+        const bool kin = k0 < K;
+        int ci = 0, dy = 0, dx = 0;
+        if (kin) {
+            const int tap = k0 / Ci;
+            ci = k0 - tap * Ci;
+            dy = tap / 3 - 1;
+            dx = tap - 3 * (tap / 3) - 1;
         }
-        for (int q = tid; q < Co * 8; q += kThreads) {
-            const int n = q >> 3, kg = q & 7;
-            const int k0 = c * kKC + kg * 8;
+        const bool first = ci < ld.c1;
+#pragma unroll
+        for (int j = 0; j < kRowsPerThread; ++j) {
+            const int r = r0 + (kThreads / 8) * j;
+            const int b = rb[j];
+            const int yy = (ryx[j] >> 16) + dy, xx = (ryx[j] & 0xFFFF) + dx;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (k0 < K) v = *reinterpret_cast<const uint4*>(wt + (long long)n * K + k0);
-            *reinterpret_cast<uint4*>(Bs + (n >> 3) * kSBO + kg * kLBO + (n & 7) * 16) = v;
+            if (kin && b >= 0 && yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                const bf16* src;
+                if (first)
+                    src = ld.up1 ? ld.x1 + ((((long long)b * ld.h1 + (yy >> 1)) * ld.w1 + (xx >> 1)) * ld.c1 + ci)
+                                 : ld.x1 + ((((long long)b * H + yy) * W + xx) * ld.c1 + ci);
+                else
+                    src = ld.x2 + ((((long long)b * H + yy) * W + xx) * ld.c2 + (ci - ld.c1));
+                v = *reinterpret_cast<const uint4*>(src);
+            }
+            *reinterpret_cast<uint4*>(As + swz(r, kg)) = v;
+        }
+        for (int n = r0; n < Co; n += kThreads / 8) {
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (kin) v = *reinterpret_cast<const uint4*>(wt + (long long)n * K + k0);
+            *reinterpret_cast<uint4*>(Bs + swz(n, kg)) = v;
         }
         fence_proxy_async_smem();   // these shared-memory writes, before the tensor core reads them
         __syncthreads();
@@ -285,7 +315,7 @@ __global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(LoadCat ld, int B, in
             const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
 #pragma unroll
             for (int ks = 0; ks < kKC / 16; ++ks)
-                mma(tmem, sdesc(a0 + ks * 2 * kLBO), sdesc(b0 + ks * 2 * kLBO), idesc(Co), (c > 0 || ks > 0) ? 1u : 0u);
+                mma(tmem, sdesc(a0 + ks * 32), sdesc(b0 + ks * 32), idesc(Co), (c > 0 || ks > 0) ? 1u : 0u);
             commit(&done[s]);
         }
     }
@@ -296,15 +326,18 @@ __global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(LoadCat ld, int B, in
         mbar_wait(&done[cl % kStages], (unsigned)(cl / kStages) & 1u);   // one more bounded wait before freeing
     }
     fence_after();
-    const long long p = p0 + warp * 32 + lane;   // accumulator row = tensor-memory lane
-    for (int c0 = 0; c0 < Co; c0 += 8) {
-        uint32_t r[8];
-        ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+    // warp w reads tensor-memory lanes 32 (w % 4) .. +31 (accumulator rows),
+    // columns [half, half + Co/2) with half = (w / 4) Co/2
+    const int quarter = warp & 3, chalf = (warp >> 2) * (Co / 2);
+    const int p = p0 + quarter * 32 + lane;
+    for (int c0 = chalf; c0 < chalf + Co / 2; c0 += 8) {
+        uint32_t rr[8];
+        ld8(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, rr);
         if (p < P) {
             float v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                v[j] = __uint_as_float(r[j]) + (bias ? bias[c0 + j] : 0.f);
+                v[j] = __uint_as_float(rr[j]) + (bias ? bias[c0 + j] : 0.f);
                 if (relu) v[j] = fmaxf(v[j], 0.f);
             }
             uint4 o;
@@ -314,7 +347,7 @@ __global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(LoadCat ld, int B, in
             o.y = *reinterpret_cast<uint32_t*>(&h1);
             o.z = *reinterpret_cast<uint32_t*>(&h2);
             o.w = *reinterpret_cast<uint32_t*>(&h3);
-            *reinterpret_cast<uint4*>(out + p * Co + c0) = o;
+            *reinterpret_cast<uint4*>(out + (long long)p * Co + c0) = o;
         }
     }
     if (!ok && tid == 0) atomicExch(err, 1);
