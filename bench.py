@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--graphs", default="on", choices=["on", "off"],
                    help="run each restart cycle's Arnoldi steps as one CUDA graph launch")
+    p.add_argument("--basis", default="f16", choices=["f32", "f16"],
+                   help="storage of the Krylov basis (arithmetic stays FP32, the true residual FP64)")
     return p.parse_args()
 
 
@@ -146,6 +148,7 @@ def run_ours(args, rank, world):
     src = (g.i_src, g.sigma_src, g.j_src)
     ctx = ddg.Context()
     ctx.set_graphs(args.graphs == "on")
+    ctx.set_basis_storage(args.basis)
 
     def build(eps_set):
         ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device=dev)) for e in eps_set]
@@ -326,7 +329,9 @@ def run_ours(args, rank, world):
                    "precision": args.precision, "training_fields": len(eps_train),
                    "l2": "no flush: per-step working set (Krylov bases, 64 x 28 MB c64) exceeds L2",
                    "parallelism": f"replicas x{world}",
-                   "step_loop": "CUDA graph per restart cycle" if args.graphs == "on" else "host-launched"},
+                   "step_loop": "CUDA graph per restart cycle" if args.graphs == "on" else "host-launched",
+                   "krylov_basis_storage": {"f32": "FP32", "f16": "IEEE half (arithmetic FP32, true residual FP64)"}[
+                       args.basis]},
         "cnn": {**summary(infos), "predict_ms_per_step": round(predict_ms, 2), "train_s": round(cnn_s, 2),
                 "loss": "Eq. 6 (residual)" if args.cnn_loss == "residual" else "Eq. 5 (projection)",
                 "train_steps": args.cnn_steps, "batch": args.cnn_batch, "lr": args.cnn_lr,

@@ -136,6 +136,17 @@ ddg_status ddg_context_set_orthogonalization(ddg_context* ctx, int scheme);
    Both give the same results (same kernels, same order).  Per-kernel
    profiling (ddg_context_profile_enable) uses the host-driven loop. */
 ddg_status ddg_context_set_graphs(ddg_context* ctx, int enable);
+/* Storage of the Krylov basis [C | Q] in complex64 solves (no paper
+   counterpart; compressed-basis GMRES, Aliaga et al., Int. J. High Perform.
+   Comput. Appl. 36, 2022): with `half` the basis vectors are stored in IEEE
+   half (4 bytes per complex value) and read back into FP32 for every product
+   and sum; everything else is unchanged (FP32 arithmetic, FP64 true residual
+   judging convergence, so the tolerance is met as before).  It halves the
+   bytes of the Gram-Schmidt passes, which dominate the solve; the Arnoldi
+   relation then holds to half precision (~5e-4), which can add Krylov steps
+   when a restart cycle reduces the residual a lot.  Default 0 (the basis in
+   FP32).  Ignored for DDG_C128. */
+ddg_status ddg_context_set_basis_storage(ddg_context* ctx, int half);
 /* Augmented solves: when the V-only relative residual ||b~|| / ||b|| of the first
    cycle (Eq. 6's minimum over V) exceeds `threshold`, the predicted subspace is
    judged to have failed: its least-squares step is kept (x += V R^-1 C^H b) and

@@ -60,6 +60,7 @@ _SIGS = {
     "ddg_context_set_orthogonalization": (C.c_int, [_vp, C.c_int]),
     "ddg_context_set_fallback": (C.c_int, [_vp, C.c_double]),
     "ddg_context_set_graphs": (C.c_int, [_vp, C.c_int]),
+    "ddg_context_set_basis_storage": (C.c_int, [_vp, C.c_int]),
     "ddg_context_set_augmented_cycles": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_enable": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -184,6 +185,11 @@ class Context:
     def set_graphs(self, on: bool):
         """Run each restart cycle's Arnoldi steps as one CUDA graph launch (default) or host-driven."""
         _check(load().ddg_context_set_graphs(self._h, int(bool(on))), "ddg_context_set_graphs")
+
+    def set_basis_storage(self, storage: str):
+        """Krylov basis of complex64 solves stored in 'f32' (default) or 'f16' (IEEE half)."""
+        code = {"f32": 0, "f16": 1}[storage]
+        _check(load().ddg_context_set_basis_storage(self._h, code), "ddg_context_set_basis_storage")
 
     def set_fallback(self, threshold: float):
         """V-only relative residual above which an augmented solve continues as plain GMRES."""

@@ -185,6 +185,12 @@ extern "C" ddg_status ddg_context_set_graphs(ddg_context* ctx, int enable) {
     return DDG_OK;
 }
 
+extern "C" ddg_status ddg_context_set_basis_storage(ddg_context* ctx, int half) {
+    if (!ctx) { set_error("ddg_context_set_basis_storage: NULL context"); return DDG_EINVAL; }
+    reinterpret_cast<Context*>(ctx)->half_basis = half ? 1 : 0;
+    return DDG_OK;
+}
+
 extern "C" ddg_status ddg_context_set_fallback(ddg_context* ctx, double threshold) {
     if (!ctx || !(threshold > 0.0)) { set_error("ddg_context_set_fallback: threshold must be > 0"); return DDG_EINVAL; }
     reinterpret_cast<Context*>(ctx)->fallback = threshold;

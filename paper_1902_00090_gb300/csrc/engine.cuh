@@ -2,6 +2,8 @@
 #pragma once
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace ddg {
@@ -28,6 +30,47 @@ __device__ __forceinline__ void unpack(const double2& p, double2 (&v)[1]) { v[0]
 __device__ __forceinline__ float4 mkpack(const float2 (&v)[2]) { return make_float4(v[0].x, v[0].y, v[1].x, v[1].y); }
 __device__ __forceinline__ double2 mkpack(const double2 (&v)[1]) { return v[0]; }
 
+// Storage of the Krylov basis [C | Q] (and nothing else): the arithmetic type,
+// or, for complex64 arithmetic, IEEE half (values only: every product and sum
+// stays FP32, the true residual FP64).  `round` gives the value a stored
+// element will read back as, so that the columns used in dot products, updates
+// and the stencil are the same numbers.
+template <typename T, bool HB> struct Bstore {
+    using V = c2_t<T>;
+    static constexpr int VEC = PackOf<T>::VEC;
+    using pack = pack_t<T>;                      // one thread's VEC elements
+    static constexpr int ebytes = sizeof(V);     // bytes per complex element
+    __device__ static __forceinline__ void load(const pack& p, V (&v)[VEC]) { unpack(p, v); }
+    __device__ static __forceinline__ pack store(const V (&v)[VEC]) { return mkpack(v); }
+    __device__ static __forceinline__ V round(V x) { return x; }
+    __device__ static __forceinline__ V get(const void* base, long long i) { return reinterpret_cast<const V*>(base)[i]; }
+    __device__ static __forceinline__ void set(void* base, long long i, V x) { reinterpret_cast<V*>(base)[i] = x; }
+};
+template <> struct Bstore<float, true> {
+    using V = float2;
+    static constexpr int VEC = 2;
+    using pack = uint2;                          // two complex as two __half2
+    static constexpr int ebytes = 4;
+    __device__ static __forceinline__ float2 h2f(unsigned u) {
+        __half2 h = *reinterpret_cast<const __half2*>(&u);
+        return __half22float2(h);
+    }
+    __device__ static __forceinline__ unsigned f2h(float2 x) {
+        __half2 h = __float22half2_rn(x);
+        return *reinterpret_cast<const unsigned*>(&h);
+    }
+    __device__ static __forceinline__ void load(const pack& p, V (&v)[2]) {
+        v[0] = h2f(p.x);
+        v[1] = h2f(p.y);
+    }
+    __device__ static __forceinline__ pack store(const V (&v)[2]) { return make_uint2(f2h(v[0]), f2h(v[1])); }
+    __device__ static __forceinline__ V round(V x) { return h2f(f2h(x)); }
+    __device__ static __forceinline__ V get(const void* base, long long i) {
+        return h2f(reinterpret_cast<const unsigned*>(base)[i]);
+    }
+    __device__ static __forceinline__ void set(void* base, long long i, V x) { reinterpret_cast<unsigned*>(base)[i] = f2h(x); }
+};
+
 // Solver context: device workspace (grow-only) and tuning.
 struct Context {
     int device = 0;
@@ -40,6 +83,7 @@ struct Context {
     int aug_cycles = 1;              // augmented: restart cycles that keep V (later cycles run plain GMRES)
     int poll_every = 8;              // Arnoldi steps between host polls (host-driven loop)
     int graphs = 1;                  // delayed scheme: step loop as a CUDA graph with a device-side WHILE
+    int half_basis = 0;              // complex64 solves: Krylov basis stored in IEEE half
     int sm_count = 152;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     // launch accounting and profiling

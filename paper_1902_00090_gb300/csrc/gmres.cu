@@ -358,17 +358,17 @@ __global__ void __launch_bounds__(kBlock) k_residual(BatchArgs a) {
 }
 
 // c_r = C^H r (FP64 r, C in the Krylov precision), one warp reduction per column.
-template <typename T>
+template <typename T, bool HB>
 __global__ void __launch_bounds__(kBlock) k_dots_r(BatchArgs a) {
     using V = c2_t<T>;
+    using BS = Bstore<T, HB>;
     constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     const int N = S->N;
     if (!S->pending || S->in_cycle || N == 0) return;
     const long long ld = P.ld;
     const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
-    count_bytes(a, DDG_K_RESIDUAL, (double)chunk_rows<T>() * ((double)N * sizeof(V) + 16.0));
-    const V* __restrict__ C = reinterpret_cast<const V*>(P.M);
+    count_bytes(a, DDG_K_RESIDUAL, (double)chunk_rows<T>() * ((double)N * BS::ebytes + 16.0));
     double2 rv[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) rv[q] = P.r[e0 + q];
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kBlock) k_dots_r(BatchArgs a) {
     for (int n = 0; n < N; ++n) {
         double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) cfmac(acc, to_d2(C[(long long)n * ld + e0 + q]), rv[q]);
+        for (int q = 0; q < VEC; ++q) cfmac(acc, to_d2(BS::get(P.M, (long long)n * ld + e0 + q)), rv[q]);
         acc = warp_sum(acc);
         if (lane == 0) red[wid][n] = acc;
     }
@@ -397,23 +397,23 @@ __global__ void __launch_bounds__(kBlock) k_dots_r(BatchArgs a) {
 }
 
 // r~ = r - C c_r (FP64), beta = ||r~||: start of the Krylov loop on A~ = P_perp A.
-template <typename T>
+template <typename T, bool HB>
 __global__ void __launch_bounds__(kBlock) k_update_r(BatchArgs a) {
     using V = c2_t<T>;
+    using BS = Bstore<T, HB>;
     constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     const int N = S->N;
     if (!S->pending || S->in_cycle || N == 0) return;
     const long long ld = P.ld;
     const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
-    count_bytes(a, DDG_K_RESIDUAL, (double)chunk_rows<T>() * ((double)N * sizeof(V) + 32.0));
-    const V* __restrict__ C = reinterpret_cast<const V*>(P.M);
+    count_bytes(a, DDG_K_RESIDUAL, (double)chunk_rows<T>() * ((double)N * BS::ebytes + 32.0));
     __shared__ double sm[kWarps];
     double acc = 0.0;
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
         double2 v = P.r[e0 + q];
-        for (int n = 0; n < N; ++n) cfms(v, to_d2(C[(long long)n * ld + e0 + q]), P.cr[n]);
+        for (int n = 0; n < N; ++n) cfms(v, to_d2(BS::get(P.M, (long long)n * ld + e0 + q)), P.cr[n]);
         P.r[e0 + q] = v;
         acc += cabs2(v);
     }
@@ -449,20 +449,23 @@ __global__ void __launch_bounds__(kBlock) k_update_r(BatchArgs a) {
 // Column j of Q is the previous (unnormalised) vector scaled by 1/h_{j,j-1}
 // (for j = 0: the cycle's start vector r scaled by 1/beta); w = A q_j uses the
 // same rounded values of q_j as the stored column.  Rows past D are zero.
-template <typename T>
+template <typename T, bool HB>
 __global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
     using V = c2_t<T>;
     using PK = pack_t<T>;
+    using BS = Bstore<T, HB>;
+    using BP = typename BS::pack;
     constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     if (!S->in_cycle) return;
     const long long D = P.D, ld = P.ld;
     const int N = S->N;
-    count_bytes(a, DDG_K_STEP, (double)chunk_rows<T>() * ((j == 0 ? 16.0 : (double)sizeof(V)) + sizeof(T) + 2.0 * sizeof(V)));
+    count_bytes(a, DDG_K_STEP, (double)chunk_rows<T>() * ((j == 0 ? 16.0 : (double)sizeof(V)) + sizeof(T) + sizeof(V) +
+                                                     BS::ebytes));
     const double inv = 1.0 / S->hnorm;
     const long long p0 = (long long)chunk * kBlock + threadIdx.x;
     const long long e0 = p0 * VEC;
-    PK* __restrict__ q = reinterpret_cast<PK*>(reinterpret_cast<V*>(P.M) + (long long)(N + j) * ld);
+    BP* __restrict__ q = reinterpret_cast<BP*>(static_cast<char*>(P.M) + (long long)(N + j) * ld * BS::ebytes);
     PK* __restrict__ w = reinterpret_cast<PK*>(P.w[j & 1]);
     const T* eps = reinterpret_cast<const T*>(P.eps_lo);
     const V* coef = reinterpret_cast<const V*>(P.coef_lo);
@@ -470,7 +473,8 @@ __global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
     V qv[VEC], wv[VEC];
     if (j == 0) {
         const double2* __restrict__ src = P.r;
-        auto ld_ = [&](long long idx) { return from_d2<V>(cscale(src[idx], inv)); };
+        // the stencil sees q_0 as it is stored
+        auto ld_ = [&](long long idx) { return BS::round(from_d2<V>(cscale(src[idx], inv))); };
 #pragma unroll
         for (int i = 0; i < VEC; ++i) {
             const long long e = e0 + i;
@@ -485,7 +489,7 @@ __global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
     } else {
         const V* __restrict__ src = reinterpret_cast<const V*>(P.w[(j - 1) & 1]);
         const T tinv = (T)inv;
-        auto ld_ = [&](long long idx) { return cscale(src[idx], tinv); };
+        auto ld_ = [&](long long idx) { return BS::round(cscale(src[idx], tinv)); };
 #pragma unroll
         for (int i = 0; i < VEC; ++i) {
             const long long e = e0 + i;
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
             }
         }
     }
-    q[p0] = mkpack(qv);
+    q[p0] = BS::store(qv);
     w[p0] = mkpack(wv);
 }
 
@@ -506,19 +510,21 @@ __global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
 // h[k] = sum_e conj(M[k ld + e]) w[e] for the columns k < K = N + j + 1 of one
 // solve (mode 0: pass 1, also ||w||^2 -> anorm; mode 1: pass 2).  Columns are
 // read in batches of 8 (8 independent 16-byte loads per thread in flight).
-template <typename T>
+template <typename T, bool HB>
 __global__ void __launch_bounds__(kBlock) k_dots_w(BatchArgs a, int j, int mode) {
     using V = c2_t<T>;
     using PK = pack_t<T>;
+    using BS = Bstore<T, HB>;
+    using BP = typename BS::pack;
     constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     if (!S->in_cycle) return;
     const int N = S->N;
     const int K = N + j + 1;
-    count_bytes(a, DDG_K_DOTS, (double)chunk_rows<T>() * ((double)K + 1.0) * sizeof(V));
+    count_bytes(a, DDG_K_DOTS, (double)chunk_rows<T>() * ((double)K * BS::ebytes + sizeof(V)));
     const long long ldp = P.ld / VEC;
     const long long p0 = (long long)chunk * kBlock + threadIdx.x;
-    const PK* __restrict__ Mp = reinterpret_cast<const PK*>(P.M);
+    const BP* __restrict__ Mp = reinterpret_cast<const BP*>(P.M);
     V v[VEC];
     unpack(reinterpret_cast<const PK*>(P.w[j & 1])[p0], v);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -531,20 +537,20 @@ __global__ void __launch_bounds__(kBlock) k_dots_w(BatchArgs a, int j, int mode)
         const int kt = min(64, K - k0);
         for (int kk = 0; kk < kt; kk += 8) {
             const int nv = min(8, kt - kk);
-            const PK* col = Mp + (long long)(k0 + kk) * ldp + p0;
-            PK m[8];
+            const BP* col = Mp + (long long)(k0 + kk) * ldp + p0;
+            BP m[8];
             if (nv == 8) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) m[u] = col[(long long)u * ldp];
             } else {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) m[u] = (u < nv) ? col[(long long)u * ldp] : zero_pack<T>();
+                for (int u = 0; u < 8; ++u) m[u] = (u < nv) ? col[(long long)u * ldp] : BP{};
             }
             V acc[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 V mv[VEC];
-                unpack(m[u], mv);
+                BS::load(m[u], mv);
                 acc[u] = mk((T)0, (T)0);
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) cfmac(acc[u], mv[i], v[i]);
@@ -588,36 +594,38 @@ __global__ void __launch_bounds__(kBlock) k_dots_w(BatchArgs a, int j, int mode)
 // w -= [C Q_j] h (coefficients staged in shared memory).
 //   mode 0: Arnoldi pass 1
 //   mode 1: Arnoldi pass 2, then ||w||, Hessenberg column, Givens, stop test
-template <typename T>
+template <typename T, bool HB>
 __global__ void __launch_bounds__(kBlock) k_update_w(BatchArgs a, int j, int mode) {
     using V = c2_t<T>;
     using PK = pack_t<T>;
+    using BS = Bstore<T, HB>;
+    using BP = typename BS::pack;
     constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     if (!S->in_cycle) return;
     const int N = S->N;
     const int K = N + j + 1;
-    count_bytes(a, DDG_K_UPDATE, (double)chunk_rows<T>() * ((double)K + 2.0) * sizeof(V));
+    count_bytes(a, DDG_K_UPDATE, (double)chunk_rows<T>() * ((double)K * BS::ebytes + 2.0 * sizeof(V)));
     extern __shared__ __align__(16) unsigned char smraw[];
     V* hs = reinterpret_cast<V*>(smraw);
     for (int t = threadIdx.x; t < K; t += kBlock) hs[t] = from_d2<V>(P.hp[t]);
     __syncthreads();
     const long long ldp = P.ld / VEC;
     const long long p0 = (long long)chunk * kBlock + threadIdx.x;
-    const PK* __restrict__ Mp = reinterpret_cast<const PK*>(P.M);
+    const BP* __restrict__ Mp = reinterpret_cast<const BP*>(P.M);
     PK* __restrict__ wp = reinterpret_cast<PK*>(P.w[j & 1]);
     V v[VEC];
     unpack(wp[p0], v);
     int k = 0;
     for (; k + 8 <= K; k += 8) {
-        const PK* col = Mp + (long long)k * ldp + p0;
-        PK m[8];
+        const BP* col = Mp + (long long)k * ldp + p0;
+        BP m[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) m[u] = col[(long long)u * ldp];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             V mv[VEC];
-            unpack(m[u], mv);
+            BS::load(m[u], mv);
             const V c = hs[k + u];
 #pragma unroll
             for (int i = 0; i < VEC; ++i) cfms(v[i], mv[i], c);
@@ -625,7 +633,7 @@ __global__ void __launch_bounds__(kBlock) k_update_w(BatchArgs a, int j, int mod
     }
     for (; k < K; ++k) {
         V mv[VEC];
-        unpack(Mp[(long long)k * ldp + p0], mv);
+        BS::load(Mp[(long long)k * ldp + p0], mv);
         const V c = hs[k];
 #pragma unroll
         for (int i = 0; i < VEC; ++i) cfms(v[i], mv[i], c);
@@ -795,21 +803,29 @@ __device__ __noinline__ void dcgs2_finish_column(FinishArgs a, SolveScal* S, con
 // Column i-1 (H = h1 + s, its Givens rotation, the stop test) and h1 itself are
 // finished by dcgs2_finish_column.
 //
-// The columns stream through shared memory: a ring of kRing stages of
-// kRingCols column chunks, filled by bulk copies (one thread issues them
-// kRing - 1 stages ahead) and completed on one mbarrier per stage.
-constexpr int kRing = 3;
+// The columns stream through shared memory: a ring of stages of kRingCols
+// column chunks (48 KB in all), filled by bulk copies (one thread issues them
+// ring - 1 stages ahead) and completed on one mbarrier per stage.  A column
+// chunk is kBlock packs of one thread's elements: 4 KB in the arithmetic type,
+// 2 KB in half (then 6 stages instead of 3: the same bytes in flight).
 constexpr int kRingCols = 4;
-constexpr int kColBytes = kBlock * 16;                          // one column chunk
-constexpr int kRingBytes = kRing * kRingCols * kColBytes;       // 48 KB
-static_assert(chunk_rows<float>() * 8 == kColBytes && chunk_rows<double>() * 16 == kColBytes,
-              "a column chunk is kBlock 16-byte packs");
+constexpr int kRingBytes = 48 * 1024;
+template <typename T, bool HB> struct Ring {
+    static constexpr int col_bytes = kBlock * (int)sizeof(typename Bstore<T, HB>::pack);
+    static constexpr int stages = kRingBytes / (kRingCols * col_bytes);
+};
+static_assert(Ring<float, false>::stages == 3 && Ring<double, false>::stages == 3 && Ring<float, true>::stages == 6,
+              "ring geometry");
 
-template <typename T>
+template <typename T, bool HB>
 __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
     using V = c2_t<T>;
     using PK = pack_t<T>;
+    using BS = Bstore<T, HB>;
+    using BP = typename BS::pack;
     constexpr int VEC = vec_of<T>();
+    constexpr int kRing = Ring<T, HB>::stages;
+    constexpr int kColBytes = Ring<T, HB>::col_bytes;
     SOLVE_PROLOGUE();
     const int i = i_arg > 0 ? i_arg : *a.step - i_arg;   // graph-driven loop: device step + offset
     // in_cycle only ever drops to 0 in the preceding launch, so a 0 read before
@@ -831,8 +847,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
     const int nbat = (K - kstart + kRingCols - 1) / kRingCols;
     // this chunk's rows of column kstart, and the distance between columns
     const char* colbase = reinterpret_cast<const char*>(P.M) +
-                          ((long long)kstart * P.ld + (long long)chunk * chunk_rows<T>()) * (long long)sizeof(V);
-    const long long colstride = P.ld * (long long)sizeof(V);
+                          ((long long)kstart * P.ld + (long long)chunk * chunk_rows<T>()) * (long long)BS::ebytes;
+    const long long colstride = P.ld * (long long)BS::ebytes;
     auto issue = [&](int b) {          // thread 0: batch b into stage b % kRing
         const int k = b * kRingCols;
         const int nv = min(kRingCols, K - kstart - k);
@@ -860,7 +876,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
         return;
     }
     // columns, u, and z = A u (written; reads eps) when there is a next step
-    count_bytes(a, DDG_K_DOTS, (double)chunk_rows<T>() * (((double)(hz ? K : i) + 2.0) * sizeof(V) +
+    count_bytes(a, DDG_K_DOTS, (double)chunk_rows<T>() * ((double)(hz ? K : i) * BS::ebytes + 2.0 * sizeof(V) +
                                                          (hz ? (double)sizeof(T) : 0.0)));
     if (threadIdx.x == 0)
         for (int b = early; b < npre; ++b) issue(b);
@@ -904,15 +920,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
             issue(b + kRing - 1);
         }
         if (!mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u)) ok = false;
-        const PK* stg = reinterpret_cast<const PK*>(smraw2 + (b % kRing) * (kRingCols * kColBytes));
-        PK m[kRingCols];
+        const BP* stg = reinterpret_cast<const BP*>(smraw2 + (b % kRing) * (kRingCols * kColBytes));
+        BP m[kRingCols];
 #pragma unroll
-        for (int w = 0; w < kRingCols; ++w) m[w] = (w < nv) ? stg[w * kBlock + threadIdx.x] : zero_pack<T>();
+        for (int w = 0; w < kRingCols; ++w) m[w] = (w < nv) ? stg[w * kBlock + threadIdx.x] : BP{};
         V acc[8];
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
             V mv[VEC];
-            unpack(m[w], mv);
+            BS::load(m[w], mv);
             acc[w] = mk((T)0, (T)0);
             acc[w + 4] = mk((T)0, (T)0);
 #pragma unroll
@@ -1036,10 +1052,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
 // and u <- z / beta - [C, Q_i] c[0:N+i] - q_i c[N+i]  (in place).  The grid
 // starts with one column-finishing block per solve (dcgs2_finish_column); a
 // solve that it stops still completes this sweep, whose q_i and u are unused.
-template <typename T>
+template <typename T, bool HB>
 __global__ void __launch_bounds__(kBlock, 6) k_update2(BatchArgs a, int i_arg) {
     using V = c2_t<T>;
     using PK = pack_t<T>;
+    using BS = Bstore<T, HB>;
+    using BP = typename BS::pack;
     constexpr int VEC = vec_of<T>();
     const int i = i_arg > 0 ? i_arg : *a.step - i_arg;   // graph-driven loop: device step + offset
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1065,7 +1083,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_update2(BatchArgs a, int i_arg) {
     const int K = N + i;
     const long long ldp = P.ld / VEC;
     const long long p0 = (long long)chunk * kBlock + threadIdx.x;
-    const PK* __restrict__ Mp = reinterpret_cast<const PK*>(P.M);
+    const BP* __restrict__ Mp = reinterpret_cast<const BP*>(P.M);
     PK* __restrict__ up = reinterpret_cast<PK*>(P.w[0]);
     // u and the columns are not written by k_dots2: u is loaded and the first
     // 8 column chunks are pulled into L2 before the dependency wait
@@ -1073,9 +1091,9 @@ __global__ void __launch_bounds__(kBlock, 6) k_update2(BatchArgs a, int i_arg) {
     unpack(up[p0], u);
     if (threadIdx.x == 0)
         for (int w = 0; w < min(8, K); ++w)
-            bulk_prefetch_l2(Mp + (long long)w * ldp + (long long)chunk * kBlock, kColBytes);
+            bulk_prefetch_l2(Mp + (long long)w * ldp + (long long)chunk * kBlock, Ring<T, HB>::col_bytes);
     pdl_wait();
-    count_bytes(a, DDG_K_UPDATE, (double)chunk_rows<T>() * ((double)K + 4.0) * sizeof(V));
+    count_bytes(a, DDG_K_UPDATE, (double)chunk_rows<T>() * ((double)(K + 1) * BS::ebytes + 3.0 * sizeof(V)));
     V* cs = reinterpret_cast<V*>(smraw);      // c, N + i + 1
     V* ss = cs + (N + a.m + 1);               // s, i
     for (int t = threadIdx.x; t < K + 1; t += kBlock) cs[t] = from_d2<V>(P.hp[t]);
@@ -1090,21 +1108,21 @@ __global__ void __launch_bounds__(kBlock, 6) k_update2(BatchArgs a, int i_arg) {
     // C columns: only the new vector
     for (; k < N; ++k) {
         V mv[VEC];
-        unpack(Mp[(long long)k * ldp + p0], mv);
+        BS::load(Mp[(long long)k * ldp + p0], mv);
         const V c = cs[k];
 #pragma unroll
         for (int q = 0; q < VEC; ++q) cfms(nu[q], mv[q], c);
     }
     // Q columns, 8 at a time: both vectors
     for (; k + 8 <= K; k += 8) {
-        const PK* col = Mp + (long long)k * ldp + p0;
-        PK m[8];
+        const BP* col = Mp + (long long)k * ldp + p0;
+        BP m[8];
 #pragma unroll
         for (int w = 0; w < 8; ++w) m[w] = col[(long long)w * ldp];
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
             V mv[VEC];
-            unpack(m[w], mv);
+            BS::load(m[w], mv);
             const V c = cs[k + w], sl = ss[k + w - N];
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
@@ -1115,7 +1133,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_update2(BatchArgs a, int i_arg) {
     }
     for (; k < K; ++k) {
         V mv[VEC];
-        unpack(Mp[(long long)k * ldp + p0], mv);
+        BS::load(Mp[(long long)k * ldp + p0], mv);
         const V c = cs[k], sl = ss[k - N];
 #pragma unroll
         for (int q = 0; q < VEC; ++q) {
@@ -1127,10 +1145,10 @@ __global__ void __launch_bounds__(kBlock, 6) k_update2(BatchArgs a, int i_arg) {
     const V cl = cs[K];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
-        qi[q] = cscale(u[q], ib);
+        qi[q] = BS::round(cscale(u[q], ib));   // q_i as stored: later steps read it back
         cfms(nu[q], qi[q], cl);
     }
-    reinterpret_cast<PK*>(reinterpret_cast<V*>(P.M) + (long long)K * P.ld)[p0] = mkpack(qi);
+    reinterpret_cast<BP*>(static_cast<char*>(P.M) + (long long)K * P.ld * BS::ebytes)[p0] = BS::store(qi);
     up[p0] = mkpack(nu);
 }
 
@@ -1179,16 +1197,18 @@ __global__ void __launch_bounds__(128) k_backsub(BatchArgs a) {
 
 // x += V z + Q y (V, Q in the Krylov precision): the correction is summed in
 // blocks of 8 columns in that precision, the block sums and x in FP64.
-template <typename T>
+template <typename T, bool HB>
 __global__ void __launch_bounds__(kBlock) k_update_x(BatchArgs a) {
     using V = c2_t<T>;
     using PK = pack_t<T>;
+    using BS = Bstore<T, HB>;
+    using BP = typename BS::pack;
     constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     if (!S->pending) return;
     const long long D = P.D, ldp = P.ld / VEC;
     const int N = S->N, k = S->k, nc = N + k;
-    count_bytes(a, DDG_K_CYCLE_END, (double)chunk_rows<T>() * ((double)nc * sizeof(V) + 32.0));
+    count_bytes(a, DDG_K_CYCLE_END, (double)chunk_rows<T>() * ((double)N * sizeof(V) + (double)k * BS::ebytes + 32.0));
     // coefficients [z; y] in the Krylov precision (the correction only has to
     // meet the inner tolerance; x itself is updated in FP64)
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1196,29 +1216,38 @@ __global__ void __launch_bounds__(kBlock) k_update_x(BatchArgs a) {
     for (int c = threadIdx.x; c < nc; c += kBlock) cyl[c] = from_d2<V>(P.coefy[c]);
     __syncthreads();
     const long long p0 = (long long)chunk * kBlock + threadIdx.x;
+    // V (the predicted vectors, in the arithmetic type) and Q (basis storage)
     const PK* __restrict__ Vp = reinterpret_cast<const PK*>(P.V);
-    const PK* __restrict__ Qp = reinterpret_cast<const PK*>(P.M) + (long long)N * ldp;
-    auto column = [&](int c) { return c < N ? Vp + (long long)c * ldp + p0 : Qp + (long long)(c - N) * ldp + p0; };
+    const BP* __restrict__ Qp = reinterpret_cast<const BP*>(P.M) + (long long)N * ldp;
+    auto column = [&](int c, V (&mv)[VEC]) {
+        if (c < N) unpack(Vp[(long long)c * ldp + p0], mv);
+        else BS::load(Qp[(long long)(c - N) * ldp + p0], mv);
+    };
     double2 acc[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) acc[q] = make_double2(0.0, 0.0);
     // blocks of 8 columns summed in T, the block sums in FP64
     for (int c0 = 0; c0 < nc; c0 += 8) {
         const int nb = min(8, nc - c0);
-        PK m[8];
+        V mv[8][VEC];
 #pragma unroll
-        for (int w = 0; w < 8; ++w) m[w] = (w < nb) ? *column(c0 + w) : zero_pack<T>();
+        for (int w = 0; w < 8; ++w) {
+            if (w < nb) {
+                column(c0 + w, mv[w]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) mv[w][q] = mk((T)0, (T)0);
+            }
+        }
         V part[VEC];
 #pragma unroll
         for (int q = 0; q < VEC; ++q) part[q] = mk((T)0, (T)0);
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
             if (w >= nb) break;
-            V mv[VEC];
-            unpack(m[w], mv);
             const V cw = cyl[c0 + w];
 #pragma unroll
-            for (int q = 0; q < VEC; ++q) cfma(part[q], mv[q], cw);
+            for (int q = 0; q < VEC; ++q) cfma(part[q], mv[w][q], cw);
         }
 #pragma unroll
         for (int q = 0; q < VEC; ++q) acc[q] = cadd(acc[q], to_d2(part[q]));
@@ -1375,22 +1404,22 @@ __global__ void __launch_bounds__(kBlock) k_aug_tri(BatchArgs a, int pass) {
     }
 }
 
-// C and V in the Krylov precision (leading dimension ld, zero past D).
-template <typename T>
+// C in the basis storage, V in the Krylov precision (leading dimension ld, zero past D).
+template <typename T, bool HB>
 __global__ void __launch_bounds__(kBlock) k_aug_store(BatchArgs a) {
     using V = c2_t<T>;
+    using BS = Bstore<T, HB>;
     constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     const int N = S->N;
     const long long D = P.D, ld = P.ld;
-    V* C = reinterpret_cast<V*>(P.M);
     V* Vl = reinterpret_cast<V*>(P.V);
     const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
     for (int n = 0; n < N; ++n)
 #pragma unroll
         for (int t = 0; t < VEC; ++t) {
             const long long e = e0 + t;
-            C[(long long)n * ld + e] = from_d2<V>(P.W[(long long)n * ld + e]);
+            BS::set(P.M, (long long)n * ld + e, from_d2<V>(P.W[(long long)n * ld + e]));
             Vl[(long long)n * ld + e] = e < D ? from_d2<V>(P.U[(long long)n * D + e]) : mk((T)0, (T)0);
         }
 }
@@ -1444,7 +1473,7 @@ static void launch_overlapped(void (*kern)(KArgs...), unsigned grid, size_t smem
 // The body's kernels read the step from device memory and add their offset;
 // k_advance sets the condition, so the cycle runs without host round trips.
 // Consecutive Arnoldi kernels keep their programmatic (overlapped) launch.
-template <typename T>
+template <typename T, bool HB>
 static ddg_status build_step_graph(const BatchArgs& args, unsigned G, int n, size_t dots2_smem,
                                    size_t upd_smem, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
@@ -1488,9 +1517,9 @@ static ddg_status build_step_graph(const BatchArgs& args, unsigned G, int n, siz
     }
     if (e == cudaSuccess) {
         for (int u = 0; u < kGraphUnroll; ++u) {
-            if (u == 0) k_dots2<T><<<G, kBlock, dots2_smem, cs>>>(args, 0);
-            else launch_overlapped(k_dots2<T>, G, dots2_smem, cs, args, -u);
-            launch_overlapped(k_update2<T>, G + n, upd_smem, cs, args, -u);
+            if (u == 0) k_dots2<T, HB><<<G, kBlock, dots2_smem, cs>>>(args, 0);
+            else launch_overlapped(k_dots2<T, HB>, G, dots2_smem, cs, args, -u);
+            launch_overlapped(k_update2<T, HB>, G + n, upd_smem, cs, args, -u);
         }
         k_advance<<<1, 1, 0, cs>>>(args, h, kGraphUnroll);
         const cudaError_t el = cudaGetLastError();
@@ -1525,20 +1554,20 @@ struct GraphExecGuard {
 // Krylov precision, cosines), k_dots2's column ring and, in the same space
 // after it, its reduced coefficients [t | s | alpha | gamma | beta | s^H t],
 // k_update's coefficient vectors.  Each kernel is opted into its size.
-template <typename T>
+template <typename T, bool HB>
 static ddg_status dcgs2_smem(int Nreq, int m, size_t& giv, size_t& dots2, size_t& upd) {
     using V = c2_t<T>;
     giv = 56 * (size_t)m + 128 + sizeof(V) * (size_t)m;
     dots2 = std::max({(size_t)kRingBytes, giv, sizeof(double2) * (size_t)(Nreq + 2 * m + 4)});
     upd = std::max(sizeof(V) * (size_t)(Nreq + 2 * m + 2), giv);
     // (the default limit covers static and dynamic shared memory together)
-    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_dots2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots2));
-    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_update2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd));
-    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_update_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd));
+    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_dots2<T, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots2));
+    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_update2<T, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd));
+    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_update_w<T, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd));
     return DDG_OK;
 }
 
-template <typename T>
+template <typename T, bool HB>
 static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const double* const* b, double* const* x,
                             const double* const* U, int Nreq, double tol, int m, int maxit, double eta,
                             ddg_info* info, cudaStream_t st, bool low_res = false) {
@@ -1561,10 +1590,13 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             const ddg_op* op = A[s];
             SolvePtrs& P = hp[s];
             const long long ld = P.ld;
-            size_t mbytes = sizeof(V) * (size_t)ld * (size_t)(Nreq + m + 1);
+            // basis [C | Q] in its storage type; for complex64 the FP64 set-up
+            // block W (A V, then C) lives in the same allocation behind C
+            constexpr size_t eb = Bstore<T, HB>::ebytes;
+            size_t mbytes = eb * (size_t)ld * (size_t)(Nreq + m + 1);
             size_t woff = 0;
             if (Nreq > 0 && sizeof(T) == 4) {
-                woff = align_up(sizeof(V) * (size_t)ld * Nreq);
+                woff = align_up(eb * (size_t)ld * Nreq);
                 mbytes = std::max(mbytes, woff + sizeof(double2) * (size_t)ld * Nreq);
             }
             char* M = c.take<char>(mbytes);
@@ -1639,7 +1671,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
 
     const unsigned G = (unsigned)total_ctas;
     size_t giv_smem, dots2_smem, upd_smem;
-    DDG_TRY(dcgs2_smem<T>(Nreq, m, giv_smem, dots2_smem, upd_smem));
+    DDG_TRY((dcgs2_smem<T, HB>(Nreq, m, giv_smem, dots2_smem, upd_smem)));
     const size_t ux_smem = sizeof(V) * (size_t)(Nreq + m);
     DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_init<<<(n + 127) / 128, 128, 0, st>>>(args, n, Nreq); }));
     if (Nreq > 0) {
@@ -1649,7 +1681,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_tri<T><<<G, kBlock, 0, st>>>(args, pass); }));
         }
         DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_rinv<<<(n + 63) / 64, 64, 0, st>>>(args, n); }));
-        DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_store<T><<<G, kBlock, 0, st>>>(args); }));
+        DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_store<T, HB><<<G, kBlock, 0, st>>>(args); }));
     }
     int* hc = ctx->host_counts;
     const size_t bs_smem = sizeof(double2) * (3 * (size_t)m + kMaxAug);
@@ -1674,8 +1706,8 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
         DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 4 * sizeof(int), st));
         DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_residual<T><<<G, kBlock, 0, st>>>(args); }));
         if (Nreq > 0) {
-            DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_dots_r<T><<<G, kBlock, 0, st>>>(args); }));
-            DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_update_r<T><<<G, kBlock, 0, st>>>(args); }));
+            DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_dots_r<T, HB><<<G, kBlock, 0, st>>>(args); }));
+            DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_update_r<T, HB><<<G, kBlock, 0, st>>>(args); }));
         }
         DDG_CHECK_CUDA(cudaMemcpyAsync(hc, args.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 4, args.counts + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1689,20 +1721,20 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
         if (hc[0] > 0 && ctx->orth == 1) {
             // delayed reorthogonalisation: first pass of step 0, then one
             // reduction and one sweep per step
-            DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_step<T><<<G, kBlock, 0, st>>>(args, 0); }));
-            DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots_w<T><<<G, kBlock, 0, st>>>(args, 0, 0); }));
-            DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T><<<G, kBlock, upd_smem, st>>>(args, 0, 0); }));
+            DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_step<T, HB><<<G, kBlock, 0, st>>>(args, 0); }));
+            DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots_w<T, HB><<<G, kBlock, 0, st>>>(args, 0, 0); }));
+            DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T, HB><<<G, kBlock, upd_smem, st>>>(args, 0, 0); }));
             if (use_graph) {
-                if (!gexec.e) DDG_TRY(build_step_graph<T>(args, G, n, dots2_smem, upd_smem, &gexec.e));
+                if (!gexec.e) DDG_TRY((build_step_graph<T, HB>(args, G, n, dots2_smem, upd_smem, &gexec.e)));
                 DDG_CHECK_CUDA(cudaGraphLaunch(gexec.e, st));
                 graph_pending = true;
             } else {
                 int polled = 0;
                 for (int i = 1; i <= m; ++i) {
-                    DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { launch_overlapped(k_dots2<T>, G, dots2_smem, st, args, i); }));
+                    DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { launch_overlapped(k_dots2<T, HB>, G, dots2_smem, st, args, i); }));
                     if (i < m)
                         DDG_TRY(ctx->launch(DDG_K_UPDATE, st,
-                                            [&] { launch_overlapped(k_update2<T>, G + n, upd_smem, st, args, i); }));
+                                            [&] { launch_overlapped(k_update2<T, HB>, G + n, upd_smem, st, args, i); }));
                     if (i % ctx->poll_every == 0 && i < m) {
                         const int slot = polled & 1;
                         DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 2 + slot, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1718,11 +1750,11 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
         } else if (hc[0] > 0) {
             int polled = 0;
             for (int j = 0; j < m; ++j) {
-                DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_step<T><<<G, kBlock, 0, st>>>(args, j); }));
-                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots_w<T><<<G, kBlock, 0, st>>>(args, j, 0); }));
-                DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T><<<G, kBlock, upd_smem, st>>>(args, j, 0); }));
-                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots_w<T><<<G, kBlock, 0, st>>>(args, j, 1); }));
-                DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T><<<G, kBlock, upd_smem, st>>>(args, j, 1); }));
+                DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_step<T, HB><<<G, kBlock, 0, st>>>(args, j); }));
+                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots_w<T, HB><<<G, kBlock, 0, st>>>(args, j, 0); }));
+                DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T, HB><<<G, kBlock, upd_smem, st>>>(args, j, 0); }));
+                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots_w<T, HB><<<G, kBlock, 0, st>>>(args, j, 1); }));
+                DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T, HB><<<G, kBlock, upd_smem, st>>>(args, j, 1); }));
                 if ((j + 1) % ctx->poll_every == 0 && j + 1 < m) {
                     const int slot = polled & 1;
                     DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 2 + slot, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1736,7 +1768,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             }
         }
         DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_backsub<<<n, 128, bs_smem, st>>>(args); }));
-        DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_update_x<T><<<G, kBlock, ux_smem, st>>>(args); }));
+        DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_update_x<T, HB><<<G, kBlock, ux_smem, st>>>(args); }));
     }
     DDG_TRY(ctx->launch(DDG_K_CYCLE_END, st, [&] { k_finalize<T><<<G, kBlock, 0, st>>>(args); }));
     std::vector<SolveScal> hs(n);
@@ -1787,10 +1819,12 @@ static ddg_status solve_entry(ddg_context* cptr, int n, const ddg_op* const* A, 
     cudaStream_t st = as_stream(stream);
     const int Nreq = U ? k : 0;
     if (prec == DDG_C128)
-        return run_batch<double>(ctx, n, A, b, x, U, Nreq, tol, restart, maxit, 0.0, info, st);
-    if (prec == DDG_C64_ONLY)   // cycles run to tol * ||b||; residual in FP32
-        return run_batch<float>(ctx, n, A, b, x, U, Nreq, tol, restart, maxit, 0.0, info, st, true);
-    return run_batch<float>(ctx, n, A, b, x, U, Nreq, tol, restart, maxit, ctx->inner_tol, info, st);
+        return run_batch<double, false>(ctx, n, A, b, x, U, Nreq, tol, restart, maxit, 0.0, info, st);
+    const bool lo = prec == DDG_C64_ONLY;   // cycles run to tol * ||b||; residual in FP32
+    const double eta = lo ? 0.0 : ctx->inner_tol;
+    if (ctx->half_basis)
+        return run_batch<float, true>(ctx, n, A, b, x, U, Nreq, tol, restart, maxit, eta, info, st, lo);
+    return run_batch<float, false>(ctx, n, A, b, x, U, Nreq, tol, restart, maxit, eta, info, st, lo);
 }
 
 }  // namespace ddg
@@ -1950,7 +1984,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     DDG_CHECK_CUDA(cudaMemcpyAsync(d_blk, hblk.data(), sizeof(int) * hp.nchunks, cudaMemcpyHostToDevice, st));
     const unsigned G = (unsigned)hp.nchunks;
     size_t giv_smem, dots2_smem, upd_smem;
-    DDG_TRY(dcgs2_smem<T>(0, m, giv_smem, dots2_smem, upd_smem));
+    DDG_TRY((dcgs2_smem<T, false>(0, m, giv_smem, dots2_smem, upd_smem)));
     const size_t ux_smem = sizeof(V) * (size_t)m;
     const size_t bs_smem = sizeof(double2) * (3 * (size_t)m + kMaxAug);
     DDG_CHECK_CUDA(cudaFuncSetAttribute(k_backsub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs_smem));
@@ -1970,13 +2004,13 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
         }
         if (hc[1] == 0) break;
         if (hc[0] > 0) {
-            k_step<T><<<G, kBlock, 0, st>>>(args, 0);
-            k_dots_w<T><<<G, kBlock, 0, st>>>(args, 0, 0);
-            k_update_w<T><<<G, kBlock, upd_smem, st>>>(args, 0, 0);
+            k_step<T, false><<<G, kBlock, 0, st>>>(args, 0);
+            k_dots_w<T, false><<<G, kBlock, 0, st>>>(args, 0, 0);
+            k_update_w<T, false><<<G, kBlock, upd_smem, st>>>(args, 0, 0);
             DDG_CHECK_LAUNCH("first Arnoldi step");
             for (int i = 1; i <= m; ++i) {
-                k_dots2<T><<<G, kBlock, dots2_smem, st>>>(args, i);
-                if (i < m) k_update2<T><<<G + 1, kBlock, upd_smem, st>>>(args, i);
+                k_dots2<T, false><<<G, kBlock, dots2_smem, st>>>(args, i);
+                if (i < m) k_update2<T, false><<<G + 1, kBlock, upd_smem, st>>>(args, i);
                 DDG_CHECK_LAUNCH("Arnoldi step");
                 if (i % 16 == 0 && i < m) {
                     int in_cycle = 0;
@@ -1987,7 +2021,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
             }
         }
         k_backsub<<<1, 128, bs_smem, st>>>(args);
-        k_update_x<T><<<G, kBlock, ux_smem, st>>>(args);
+        k_update_x<T, false><<<G, kBlock, ux_smem, st>>>(args);
         DDG_CHECK_LAUNCH("cycle end");
     }
     k_finalize<T><<<G, kBlock, 0, st>>>(args);

@@ -28,6 +28,7 @@ def main():
     p.add_argument("--profile", action="store_true", help="print per-kernel-class time and GB/s")
     p.add_argument("--graphs", default="on", choices=["on", "off"],
                    help="step loop as a CUDA graph (on) or launched by the host (off)")
+    p.add_argument("--basis", default="f32", choices=["f32", "f16"], help="Krylov basis storage (complex64)")
     a = p.parse_args()
 
     import torch
@@ -40,6 +41,7 @@ def main():
     bs = [ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src) for op in ops]
     ctx = ddg.Context(orthogonalization=a.orth)
     ctx.set_graphs(a.graphs == "on")
+    ctx.set_basis_storage(a.basis)
     U = None
     if a.k > 0:
         U = torch.as_tensor(inputs.random_complex(g.D, 7, shape=(a.k, g.D)), device="cuda")

@@ -448,3 +448,44 @@ def test_graph_step_loop_matches_host_loop(prec):
                        [(i["iters"], i["cycles"], i["converged"]) for i in infos + infa])
     assert out[True][1] == out[False][1]
     assert np.array_equal(out[True][0], out[False][0])
+
+
+@pytest.fixture(scope="module")
+def ctx_f16():
+    c = ddg.Context()
+    c.set_basis_storage("f16")
+    return c
+
+
+def test_half_basis_full_size(ctx_f16, config1):
+    # Krylov basis stored in IEEE half: the FP64 true residual still judges
+    # convergence, so the solution meets the same bars as the FP32 basis
+    g, eps, A, b, xd = config1
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x, info, st = ddg.gmres_solve(ctx_f16, op, dev(b), tol=1e-6, restart=200, maxit=5000, precision="c64")
+    assert st == 0 and info["converged"]
+    xh = host(x)
+    assert np.linalg.norm(b - A @ xh) / np.linalg.norm(b) <= 1e-6
+    assert rel(xh, xd) <= 1e-5
+    x32, info32, _ = ddg.gmres_solve(ddg.Context(), op, dev(b), tol=1e-6, restart=200, maxit=5000, precision="c64")
+    print(f"half basis: {info['iters']} steps, FP32 basis: {info32['iters']} steps")
+    assert info["iters"] <= 1.25 * info32["iters"] + 10
+
+
+def test_half_basis_augmented_and_batched(ctx_f16):
+    # uneven batch, augmented, both cycle policies' first cycle; FP32-only too
+    g = inputs.grid_for(64, 64)
+    eps = inputs.trajectory_set(g, 2, 3, steps=3)
+    ops = [ddg.fdfd_operator(g, dev(e, torch.float64)) for e in eps]
+    bs = [ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src) for op in ops]
+    As = [fdfd.operator_for(g, e) for e in eps]
+    bo = fdfd.source_for(g)
+    x_near = spla.spsolve(As[0].tocsc(), bo)
+    U = dev(np.stack([x_near, inputs.random_complex(g.D, 9)]))
+    for prec, tol in (("c64", 1e-6), ("c64_only", 1e-4)):
+        xs, infos, st = ddg.augmented_gmres_solve_batched(ctx_f16, ops, bs, [U] * len(ops), tol=tol, restart=50,
+                                                          maxit=6000, precision=prec)
+        assert st == 0
+        for A, x, i in zip(As, xs, infos):
+            assert i["converged"]
+            assert np.linalg.norm(bo - A @ host(x)) / np.linalg.norm(bo) <= tol * 1.02
