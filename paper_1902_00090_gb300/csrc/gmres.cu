@@ -688,6 +688,49 @@ cgs2_done:
     for (int t = threadIdx.x; t <= j + 1; t += kBlock) P.Rg[(long long)j * ldh + t] = gout[t];
 }
 
+// ---------------------------------------------------------------- column dot products of the DCGS2 reduction
+// t += conj(m) z and s += conj(m) u over one thread's VEC elements of a column.
+// Complex64: the two elements of a thread are paired in packed two-wide FP32
+// FMAs (fma.rn.f32x2), with z and u pre-split into (x0, x1) / (y0, y1) pairs,
+// then the pair halves added: 8 packed FMAs + 4 adds instead of 16 FMAs.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+template <typename T> struct DotPairs;
+template <> struct DotPairs<float> {
+    float2 zx, zy, nzx, ux, uy, nux;
+    __device__ __forceinline__ DotPairs(const float2 (&z)[2], const float2 (&u)[2])
+        : zx(make_float2(z[0].x, z[1].x)), zy(make_float2(z[0].y, z[1].y)), nzx(make_float2(-z[0].x, -z[1].x)),
+          ux(make_float2(u[0].x, u[1].x)), uy(make_float2(u[0].y, u[1].y)), nux(make_float2(-u[0].x, -u[1].x)) {}
+    __device__ __forceinline__ void dots(const float2 (&m)[2], float2& t, float2& s) const {
+        const float2 mx = make_float2(m[0].x, m[1].x), my = make_float2(m[0].y, m[1].y);
+        const float2 zero = make_float2(0.f, 0.f);
+        const float2 tr = fma2(my, zy, fma2(mx, zx, zero));    // sum of Re(conj(m) z) terms
+        const float2 ti = fma2(my, nzx, fma2(mx, zy, zero));   // sum of Im(conj(m) z) terms
+        const float2 sr = fma2(my, uy, fma2(mx, ux, zero));
+        const float2 si = fma2(my, nux, fma2(mx, uy, zero));
+        t = make_float2(tr.x + tr.y, ti.x + ti.y);
+        s = make_float2(sr.x + sr.y, si.x + si.y);
+    }
+};
+template <> struct DotPairs<double> {
+    double2 z0, u0;
+    __device__ __forceinline__ DotPairs(const double2 (&z)[1], const double2 (&u)[1]) : z0(z[0]), u0(u[0]) {}
+    __device__ __forceinline__ void dots(const double2 (&m)[1], double2& t, double2& s) const {
+        t = make_double2(0.0, 0.0);
+        s = make_double2(0.0, 0.0);
+        cfmac(t, m[0], z0);
+        cfmac(s, m[0], u0);
+    }
+};
+
 // ---------------------------------------------------------------- delayed reorthogonalisation (DCGS2)
 // Finishes Arnoldi column j = i-1 once k_dots2 has reduced s, alpha and beta
 // (tv[N+i ..), tv[N+2i], tv[N+2i+2]):
@@ -803,18 +846,20 @@ __device__ __noinline__ void dcgs2_finish_column(FinishArgs a, SolveScal* S, con
 // Column i-1 (H = h1 + s, its Givens rotation, the stop test) and h1 itself are
 // finished by dcgs2_finish_column.
 //
-// The columns stream through shared memory: a ring of stages of kRingCols
-// column chunks (48 KB in all), filled by bulk copies (one thread issues them
-// ring - 1 stages ahead) and completed on one mbarrier per stage.  A column
-// chunk is kBlock packs of one thread's elements: 4 KB in the arithmetic type,
-// 2 KB in half (then 6 stages instead of 3: the same bytes in flight).
-constexpr int kRingCols = 4;
+// The columns stream through shared memory: a ring of 3 stages of 16 KB
+// (48 KB in all), filled by bulk copies (one thread issues them 2 stages
+// ahead) and completed on one mbarrier per stage.  A column chunk is kBlock
+// packs of one thread's elements: 4 KB in the arithmetic type (4 columns a
+// stage), 2 KB in half (8 columns a stage, so that the per-stage barrier and
+// wait are paid per 16 KB either way).
 constexpr int kRingBytes = 48 * 1024;
 template <typename T, bool HB> struct Ring {
     static constexpr int col_bytes = kBlock * (int)sizeof(typename Bstore<T, HB>::pack);
-    static constexpr int stages = kRingBytes / (kRingCols * col_bytes);
+    static constexpr int cols = 16 * 1024 / col_bytes;
+    static constexpr int stages = kRingBytes / (cols * col_bytes);
 };
-static_assert(Ring<float, false>::stages == 3 && Ring<double, false>::stages == 3 && Ring<float, true>::stages == 6,
+static_assert(Ring<float, false>::cols == 4 && Ring<double, false>::cols == 4 && Ring<float, true>::cols == 8 &&
+                  Ring<float, true>::stages == 3 && Ring<float, false>::stages == 3,
               "ring geometry");
 
 template <typename T, bool HB>
@@ -826,6 +871,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
     constexpr int VEC = vec_of<T>();
     constexpr int kRing = Ring<T, HB>::stages;
     constexpr int kColBytes = Ring<T, HB>::col_bytes;
+    constexpr int kRingCols = Ring<T, HB>::cols;      // columns per stage (a multiple of 4)
+    constexpr int kBatchesPer32 = 32 / kRingCols;     // stages between cross-warp sums
     SOLVE_PROLOGUE();
     const int i = i_arg > 0 ? i_arg : *a.step - i_arg;   // graph-driven loop: device step + offset
     // in_cycle only ever drops to 0 in the preceding launch, so a 0 read before
@@ -901,6 +948,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
 #pragma unroll
         for (int q = 0; q < VEC; ++q) z[q] = mk((T)0, (T)0);
     }
+    const DotPairs<T> dp(z, u);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int vidx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     __shared__ V red_t[kWarps][32];
@@ -909,10 +957,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
     // partial sums stay in the Krylov precision until the last CTA
     V* part = reinterpret_cast<V*>(P.part) + (long long)chunk * a.KP;
     bool ok = true;
-    // 4 columns per batch; their t- and s-partials share one 8-value butterfly;
-    // cross-warp sums every 8 batches (32 columns)
+    // a stage of kRingCols columns; each 4 of them share one 8-value butterfly
+    // of their t- and s-partials; cross-warp sums every 32 columns
     for (int b = 0; b < nbat; ++b) {
-        const int kk = (b & 7) * kRingCols;
+        const int kk = (b % kBatchesPer32) * kRingCols;
         const int nv = min(kRingCols, K - kstart - b * kRingCols);
         __syncthreads();               // stage (b - 1) % kRing has been read by every warp
         if (threadIdx.x == 0 && b + kRing - 1 < nbat) {
@@ -924,27 +972,24 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
         BP m[kRingCols];
 #pragma unroll
         for (int w = 0; w < kRingCols; ++w) m[w] = (w < nv) ? stg[w * kBlock + threadIdx.x] : BP{};
-        V acc[8];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            V mv[VEC];
-            BS::load(m[w], mv);
-            acc[w] = mk((T)0, (T)0);
-            acc[w + 4] = mk((T)0, (T)0);
+        for (int g = 0; g < kRingCols / 4; ++g) {
+            V acc[8];
 #pragma unroll
-            for (int q = 0; q < VEC; ++q) {
-                cfmac(acc[w], mv[q], z[q]);
-                cfmac(acc[w + 4], mv[q], u[q]);
+            for (int w = 0; w < 4; ++w) {
+                V mv[VEC];
+                BS::load(m[4 * g + w], mv);
+                dp.dots(mv, acc[w], acc[w + 4]);
+            }
+            const V r = reduce8(acc, lane);
+            if ((lane & 3) == 0 && 4 * g + (vidx & 3) < nv) {
+                if (vidx < 4) red_t[wid][kk + 4 * g + vidx] = r;
+                else red_s[wid][kk + 4 * g + vidx - 4] = r;
             }
         }
-        const V r = reduce8(acc, lane);
-        if ((lane & 3) == 0 && (vidx & 3) < nv) {
-            if (vidx < 4) red_t[wid][kk + vidx] = r;
-            else red_s[wid][kk + vidx - 4] = r;
-        }
-        if ((b & 7) == 7 || b == nbat - 1) {
+        if ((b + 1) % kBatchesPer32 == 0 || b == nbat - 1) {
             __syncthreads();
-            const int k0 = kstart + (b >> 3) * 32;
+            const int k0 = kstart + (b / kBatchesPer32) * 32;
             const int kt = min(32, K - k0);
             for (int t = threadIdx.x; t < kt; t += kBlock) {
                 V st = mk((T)0, (T)0), ss = mk((T)0, (T)0);
