@@ -688,6 +688,41 @@ cgs2_done:
     for (int t = threadIdx.x; t <= j + 1; t += kBlock) P.Rg[(long long)j * ldh + t] = gout[t];
 }
 
+// ---------------------------------------------------------------- tensor-core projections (half basis)
+// One half2 of the A operand of t = [C Q]^H z, s = Q^H u as a real GEMM over
+// k = 2 row + (0: Re, 1: Im) of the basis columns: component c of a value v
+// split into v_hi + v_lo (two halves, about 22 significant bits):
+//   c = 0: (Re v_hi, Im v_hi)   -> Re(conj(q) v_hi)
+//   c = 1: (Im v_hi, -Re v_hi)  -> Im(conj(q) v_hi)
+//   c = 2, 3: the same for v_lo
+__device__ __forceinline__ unsigned split_pair(float2 v, int c) {
+    const __half hx = __float2half_rn(v.x), hy = __float2half_rn(v.y);
+    const __half lx = __float2half_rn(v.x - __half2float(hx)), ly = __float2half_rn(v.y - __half2float(hy));
+    __half2 r;
+    switch (c) {
+        case 0: r = __halves2half2(hx, hy); break;
+        case 1: r = __halves2half2(hy, __hneg(hx)); break;
+        case 2: r = __halves2half2(lx, ly); break;
+        default: r = __halves2half2(ly, __hneg(lx)); break;
+    }
+    return *reinterpret_cast<const unsigned*>(&r);
+}
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr)
+                 : "memory");
+}
+// D (16 x 8, FP32) += A (16 x 16, half, rows 8..15 zero) B (16 x 8, half)
+__device__ __forceinline__ void mma16816(float& d0, float& d1, float& d2, float& d3, unsigned a0, unsigned a2,
+                                         unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+        : "r"(a0), "r"(0u), "r"(a2), "r"(0u), "r"(b0), "r"(b1));
+}
+
 // ---------------------------------------------------------------- column dot products of the DCGS2 reduction
 // t += conj(m) z and s += conj(m) u over one thread's VEC elements of a column.
 // Complex64: the two elements of a thread are paired in packed two-wide FP32
@@ -857,13 +892,18 @@ template <typename T, bool HB> struct Ring {
     static constexpr int col_bytes = kBlock * (int)sizeof(typename Bstore<T, HB>::pack);
     static constexpr int cols = 16 * 1024 / col_bytes;
     static constexpr int stages = kRingBytes / (cols * col_bytes);
+    // half basis: columns 16 bytes apart beyond their length, so that the 8 rows
+    // of one ldmatrix phase (one per column) fall in different banks
+    static constexpr int col_stride = col_bytes + (HB ? 16 : 0);
+    static constexpr int stage_bytes = cols * col_stride;
+    static constexpr int ring_bytes = stages * stage_bytes;
 };
 static_assert(Ring<float, false>::cols == 4 && Ring<double, false>::cols == 4 && Ring<float, true>::cols == 8 &&
                   Ring<float, true>::stages == 3 && Ring<float, false>::stages == 3,
               "ring geometry");
 
 template <typename T, bool HB>
-__global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
+__global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i_arg) {
     using V = c2_t<T>;
     using PK = pack_t<T>;
     using BS = Bstore<T, HB>;
@@ -873,6 +913,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
     constexpr int kColBytes = Ring<T, HB>::col_bytes;
     constexpr int kRingCols = Ring<T, HB>::cols;      // columns per stage (a multiple of 4)
     constexpr int kBatchesPer32 = 32 / kRingCols;     // stages between cross-warp sums
+    constexpr int kColStride = Ring<T, HB>::col_stride;
+    constexpr int kStageBytes = Ring<T, HB>::stage_bytes;
     SOLVE_PROLOGUE();
     const int i = i_arg > 0 ? i_arg : *a.step - i_arg;   // graph-driven loop: device step + offset
     // in_cycle only ever drops to 0 in the preceding launch, so a 0 read before
@@ -900,9 +942,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
         const int k = b * kRingCols;
         const int nv = min(kRingCols, K - kstart - k);
         unsigned long long* bar = &full[b % kRing];
-        unsigned char* dst = smraw2 + (b % kRing) * (kRingCols * kColBytes);
+        unsigned char* dst = smraw2 + (b % kRing) * kStageBytes;
         mbar_expect_tx(bar, (unsigned)(nv * kColBytes));
-        for (int w = 0; w < nv; ++w) bulk_g2s(dst + w * kColBytes, colbase + (k + w) * colstride, kColBytes, bar);
+        for (int w = 0; w < nv; ++w) bulk_g2s(dst + w * kColStride, colbase + (k + w) * colstride, kColBytes, bar);
     };
     // Stages holding only columns older than q_{i-1} (the previous launch wrote
     // q_{i-1} and u) are requested before the dependency wait.
@@ -948,15 +990,84 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
 #pragma unroll
         for (int q = 0; q < VEC; ++q) z[q] = mk((T)0, (T)0);
     }
-    const DotPairs<T> dp(z, u);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int vidx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-    __shared__ V red_t[kWarps][32];
-    __shared__ V red_s[kWarps][32];
     __shared__ T smt[kWarps];
     // partial sums stay in the Krylov precision until the last CTA
     V* part = reinterpret_cast<V*>(P.part) + (long long)chunk * a.KP;
     bool ok = true;
+    if constexpr (HB) {
+        // Half basis: the projections as real GEMMs on the tensor cores (mma.sync
+        // m16n8k16, half in, FP32 accumulate).  A (16 x 16 per k step): rows
+        // 0..7 = [Re, Im] x [hi, lo] x [z, u] of this warp's 64 rows (see
+        // split_pair), rows 8..15 zero; B (16 x 8): one k step of the stage's 8
+        // columns, read by ldmatrix (a column's interleaved Re/Im halves are its
+        // k order); D (8 x 8 used) per warp and stage, summed across warps every
+        // 32 columns.
+        static_assert(VEC == 2 && kRingCols == 8 && chunk_rows<T>() == 64 * kWarps, "tensor-core tile shape");
+        __shared__ __align__(16) float2 zu[2][kBlock * VEC];
+        __shared__ float redm[kWarps][32][8];
+        __shared__ float comb[32][8];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            zu[0][threadIdx.x * VEC + q] = z[q];
+            zu[1][threadIdx.x * VEC + q] = u[q];
+        }
+        __syncthreads();
+        const int gq = lane >> 2, tg = lane & 3;
+        unsigned afr[8][2];
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) afr[ks][h] = split_pair(zu[gq >> 2][wid * 64 + ks * 8 + tg + 4 * h], gq & 3);
+        for (int b = 0; b < nbat; ++b) {
+            const int kk = (b % kBatchesPer32) * kRingCols;
+            const int nv = min(kRingCols, K - kstart - b * kRingCols);
+            __syncthreads();               // stage (b - 1) % kRing has been read by every warp
+            if (threadIdx.x == 0 && b + kRing - 1 < nbat) {
+                fence_proxy_async_smem();
+                issue(b + kRing - 1);
+            }
+            if (!mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u)) ok = false;
+            const unsigned sbase = smem_u32(smraw2 + (b % kRing) * kStageBytes);
+            float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+#pragma unroll
+            for (int kp = 0; kp < 4; ++kp) {
+                // matrix lane / 8 of the x4 load: halves k = 128 wid + 32 kp + 8 (lane / 8) .. + 7
+                // of column lane % 8
+                unsigned b0, b1, b2, b3;
+                ldsm_x4(sbase + (unsigned)((lane & 7) * kColStride + (wid * 128 + kp * 32 + (lane >> 3) * 8) * 2),
+                        b0, b1, b2, b3);
+                mma16816(d0, d1, d2, d3, afr[2 * kp][0], afr[2 * kp][1], b0, b1);
+                mma16816(d0, d1, d2, d3, afr[2 * kp + 1][0], afr[2 * kp + 1][1], b2, b3);
+            }
+            redm[wid][kk + 2 * tg][gq] = d0;       // D[gq][column 2 tg], D[gq][column 2 tg + 1]
+            redm[wid][kk + 2 * tg + 1][gq] = d1;
+            if ((b + 1) % kBatchesPer32 == 0 || b == nbat - 1) {
+                __syncthreads();
+                const int k0 = kstart + (b / kBatchesPer32) * 32;
+                const int kt = min(32, K - k0);
+                if (threadIdx.x < kt * 8) {
+                    const int cc = threadIdx.x >> 3, mm = threadIdx.x & 7;
+                    float sum = 0.f;
+#pragma unroll
+                    for (int w = 0; w < kWarps; ++w) sum += redm[w][cc][mm];
+                    comb[cc][mm] = sum;
+                }
+                __syncthreads();
+                if (threadIdx.x < kt) {
+                    const float* c8 = comb[threadIdx.x];
+                    const int k = k0 + threadIdx.x;
+                    part[k] = mk(c8[0] + c8[2], c8[1] + c8[3]);                              // t_k
+                    if (k >= N) part[N + i + (k - N)] = mk(c8[4] + c8[6], c8[5] + c8[7]);    // s_l
+                }
+            }
+            (void)nv;
+        }
+    } else {
+    const DotPairs<T> dp(z, u);
+    const int vidx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    __shared__ V red_t[kWarps][32];
+    __shared__ V red_s[kWarps][32];
     // a stage of kRingCols columns; each 4 of them share one 8-value butterfly
     // of their t- and s-partials; cross-warp sums every 32 columns
     for (int b = 0; b < nbat; ++b) {
@@ -1003,6 +1114,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_dots2(BatchArgs a, int i_arg) {
                 if (k >= N) part[N + i + (k - N)] = ss;    // s_l, l = k - N
             }
         }
+    }
     }
     if (!ok) {
         // a copy did not arrive in time: report it, and give the ring one more
@@ -1603,7 +1715,7 @@ template <typename T, bool HB>
 static ddg_status dcgs2_smem(int Nreq, int m, size_t& giv, size_t& dots2, size_t& upd) {
     using V = c2_t<T>;
     giv = 56 * (size_t)m + 128 + sizeof(V) * (size_t)m;
-    dots2 = std::max({(size_t)kRingBytes, giv, sizeof(double2) * (size_t)(Nreq + 2 * m + 4)});
+    dots2 = std::max({(size_t)Ring<T, HB>::ring_bytes, giv, sizeof(double2) * (size_t)(Nreq + 2 * m + 4)});
     upd = std::max(sizeof(V) * (size_t)(Nreq + 2 * m + 2), giv);
     // (the default limit covers static and dynamic shared memory together)
     DDG_CHECK_CUDA(cudaFuncSetAttribute(k_dots2<T, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots2));
