@@ -288,6 +288,34 @@ def run_ours(args, rank, world):
     e2e = {"value": esolved / (ems / 1e3), "unit": "solves/s",
            "h2d_bytes_per_step": int(eps_host.numel() * 8), "d2h_bytes_per_step": int(x_host.numel() * 16)}
 
+    # --- recycling along the design trajectories (the held-out set is 4
+    # trajectories x 16 correlated steps): step t of every trajectory solved
+    # together, with the CNN's vectors plus the previous step's solution as V
+    n_traj = n // 16
+    order = [[j * 16 + t for j in range(n_traj)] for t in range(16)]
+
+    def step_recycle():
+        P.predict(ops, src, U=U_cnn)
+        prev = None
+        infos = [None] * n
+        for t, idx in enumerate(order):
+            if prev is None:
+                Us = [U_cnn[i] for i in idx]
+            else:
+                Us = [torch.cat([U_cnn[i], prev[j].reshape(1, -1)]) for j, i in enumerate(idx)]
+            xr = [torch.zeros_like(bs[i]) for i in idx]
+            xr, inf, st_ = ddg.augmented_gmres_solve_batched(ctx, [ops[i] for i in idx], [bs[i] for i in idx], Us,
+                                                             x=xr, tol=1e-6, restart=args.restart, maxit=5000,
+                                                             precision=args.precision)
+            for j, i in enumerate(idx):
+                infos[i] = inf[j]
+            prev = xr
+        return None, infos, 0
+
+    rms, rinf, _, _, _, rsolved = timed(step_recycle, max(1, K // 2), 1)
+    recycle = {"value": rsolved / (rms / 1e3), "unit": "solves/s", "ms_per_step": rms / max(1, K // 2),
+               "batch": n_traj, "sequential_steps": 16, **summary(rinf)}
+
     # --- roofline of the dominant kernel class (live CUDA events, algorithmic bytes)
     peaks = {}
     try:
@@ -339,6 +367,7 @@ def run_ours(args, rank, world):
                 "train_loss_last": float(np.mean(train_losses[-10:]))},
         "pca": pca,
         "plain": plain,
+        "cnn_recycle": recycle,
         "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
         "pca_speedup_vs_plain": round(pca["value"] / plain["value"], 3) if plain else None,
         "solve_training_fields_s": round(solve_train_s, 2),

@@ -946,9 +946,10 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
         mbar_expect_tx(bar, (unsigned)(nv * kColBytes));
         for (int w = 0; w < nv; ++w) bulk_g2s(dst + w * kColStride, colbase + (k + w) * colstride, kColBytes, bar);
     };
-    // Stages holding only columns older than q_{i-1} (the previous launch wrote
-    // q_{i-1} and u) are requested before the dependency wait.
-    const int npre = min(kRing - 1, nbat);
+    // All kRing stages are requested before the prologue (each later stage once
+    // its slot has been read); those holding only columns older than q_{i-1}
+    // (the previous launch wrote q_{i-1} and u) before the dependency wait.
+    const int npre = min(kRing, nbat);   // every stage is in flight before the prologue's own loads
     int early = 0;
     while (early < npre && kstart + (early + 1) * kRingCols <= K - 1) ++early;
     if (threadIdx.x == 0) {
@@ -1004,26 +1005,38 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
         // k order); D (8 x 8 used) per warp and stage, summed across warps every
         // 32 columns.
         static_assert(VEC == 2 && kRingCols == 8 && chunk_rows<T>() == 64 * kWarps, "tensor-core tile shape");
-        __shared__ __align__(16) float2 zu[2][kBlock * VEC];
+        // split components 0 (hi) and 2 (lo) of z and u per row, once, by the
+        // thread that holds the row; components 1 and 3 are their (Im, -Re) swaps
+        __shared__ unsigned zsplit[4][kBlock * VEC];   // [z hi, z lo, u hi, u lo]
         __shared__ float redm[kWarps][32][8];
         __shared__ float comb[32][8];
 #pragma unroll
         for (int q = 0; q < VEC; ++q) {
-            zu[0][threadIdx.x * VEC + q] = z[q];
-            zu[1][threadIdx.x * VEC + q] = u[q];
+            const int r = threadIdx.x * VEC + q;
+            zsplit[0][r] = split_pair(z[q], 0);
+            zsplit[1][r] = split_pair(z[q], 2);
+            zsplit[2][r] = split_pair(u[q], 0);
+            zsplit[3][r] = split_pair(u[q], 2);
         }
         __syncthreads();
         const int gq = lane >> 2, tg = lane & 3;
+        // row gq of A: vector gq / 4 (z, u), part (gq / 2) & 1 (hi, lo), Re or Im row gq & 1
+        const unsigned* src = zsplit[2 * (gq >> 2) + ((gq >> 1) & 1)];
+        const bool swap = gq & 1;
         unsigned afr[8][2];
 #pragma unroll
         for (int ks = 0; ks < 8; ++ks)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) afr[ks][h] = split_pair(zu[gq >> 2][wid * 64 + ks * 8 + tg + 4 * h], gq & 3);
+            for (int h = 0; h < 2; ++h) {
+                const unsigned w = src[wid * 64 + ks * 8 + tg + 4 * h];
+                // (Re, Im) -> (Im, -Re): swap the halves, flip the sign of the upper one
+                afr[ks][h] = swap ? (((w >> 16) | (w << 16)) ^ 0x80000000u) : w;
+            }
         for (int b = 0; b < nbat; ++b) {
             const int kk = (b % kBatchesPer32) * kRingCols;
             const int nv = min(kRingCols, K - kstart - b * kRingCols);
             __syncthreads();               // stage (b - 1) % kRing has been read by every warp
-            if (threadIdx.x == 0 && b + kRing - 1 < nbat) {
+            if (threadIdx.x == 0 && b >= 1 && b + kRing - 1 < nbat) {
                 fence_proxy_async_smem();
                 issue(b + kRing - 1);
             }
@@ -1074,7 +1087,7 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
         const int kk = (b % kBatchesPer32) * kRingCols;
         const int nv = min(kRingCols, K - kstart - b * kRingCols);
         __syncthreads();               // stage (b - 1) % kRing has been read by every warp
-        if (threadIdx.x == 0 && b + kRing - 1 < nbat) {
+        if (threadIdx.x == 0 && b >= 1 && b + kRing - 1 < nbat) {
             fence_proxy_async_smem();
             issue(b + kRing - 1);
         }
