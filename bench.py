@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--cnn-lr", type=float, default=3e-4)
     p.add_argument("--cnn-loss", default="residual", choices=["residual", "projection"],
                    help="Eq. 6 (unsupervised, trained on the right-hand sides) or Eq. 5 (solved fields)")
+    p.add_argument("--cnn-field", default="none", choices=["none", "background"],
+                   help="extra CNN input: the field of the unpatterned background (one solve per grid)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--graphs", default="on", choices=["on", "off"],
@@ -169,7 +171,17 @@ def run_ours(args, rank, world):
     pca_s = time.time() - t0
     # --- CNN predictor (Sec. III): trained on the same fields with the library's kernels
     t0 = time.time()
-    P = ddg.Predictor(k=args.cnn_k)
+    field = None
+    if args.cnn_field == "background":
+        # the approximate-field input: one solve per grid, the design region
+        # left unpatterned (slab in oxide)
+        from paper_1902_00090_gb300 import inputs
+        op_bg = ddg.fdfd_operator(g, torch.as_tensor(inputs.background_eps(g), device=dev))
+        field, _, _ = ddg.gmres_solve(ctx, op_bg, ddg.fdfd_source(op_bg, *src), tol=1e-8, restart=200, maxit=20000,
+                                      precision="c128")
+    P = ddg.Predictor(k=args.cnn_k, input_field=field is not None)
+    if field is not None:
+        P.set_input_field(field, g.nx, g.ny)
     P.init_he(seed=0)
     P.set_loss(args.cnn_loss)
     targets = bs_tr if args.cnn_loss == "residual" else xs_tr
@@ -351,7 +363,8 @@ def run_ours(args, rank, world):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": "128x128", "dx_nm": 40, "wavelength_nm": 1550,
                    "npml": 10, "restart": args.restart, "tol": 1e-6, "solves_per_step": n,
-                   "predictor": f"cnn k={args.cnn_k} (6 levels, 32-128 channels, bf16, {args.cnn_loss} loss)",
+                   "predictor": f"cnn k={args.cnn_k} (6 levels, 32-128 channels, bf16, {args.cnn_loss} loss"
+                                f"{', background-field input' if args.cnn_field == 'background' else ''})",
                    "restart_policy": "augmented first cycle, then plain GMRES; V-only residual > 0.5 -> "
                                      "its step, then plain GMRES",
                    "precision": args.precision, "training_fields": len(eps_train),

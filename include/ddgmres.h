@@ -281,6 +281,16 @@ ddg_status pca_fit(ddg_context* ctx, const double* F, long long D, int M, int k,
 typedef struct ddg_predictor ddg_predictor;
 /* k complex outputs (1..16); channels: `levels` (1..8) host ints.  Weights start at 0. */
 ddg_status predictor_create(int k, int levels, const int* channels, ddg_predictor** P);
+/* predictor_create_with_field -- the same network with two more input channels:
+   the real and imaginary parts of an approximate field of the grid, normalised
+   to max |f| = 1 (the paper's networks take a cheap approximate field as input,
+   Sec. III and Methods; here e.g. the field of the unpatterned background, one
+   solve per grid and wavelength).  Set it with predictor_set_input_field
+   before any forward or training call on that grid. */
+ddg_status predictor_create_with_field(int k, int levels, const int* channels, ddg_predictor** P);
+/* f: device, ny*nx complex128 (row-major), copied (normalised) into the
+   predictor; DDG_EINVAL for a network created without the field input. */
+ddg_status predictor_set_input_field(ddg_predictor* P, const double* f, int nx, int ny, void* stream);
 ddg_status predictor_destroy(ddg_predictor* P);
 long long predictor_num_params(const ddg_predictor* P);
 /* Kernels launched by this predictor since it was created. */

@@ -288,11 +288,19 @@ def adam_step(theta, g, st: AdamState, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
 
 
 # ---------------------------------------------------------------- inputs
-def input_channels(eps: np.ndarray, wavelength: float, npml: int, src_col: int, sigma: float, j_c: float):
+def input_channels(eps: np.ndarray, wavelength: float, npml: int, src_col: int, sigma: float, j_c: float,
+                   field: np.ndarray = None):
     """Network input (ny, nx, 4): normalised permittivity, wavelength, PML mask,
-    source profile."""
+    source profile; with `field` (an approximate field of the grid, ny*nx
+    complex) two more channels, its real and imaginary parts divided by its
+    largest magnitude (ny, nx, 6)."""
     ny, nx = eps.shape
-    x = np.zeros((ny, nx, 4))
+    x = np.zeros((ny, nx, 4 if field is None else 6))
+    if field is not None:
+        f = np.asarray(field, dtype=np.complex128).reshape(ny, nx)
+        f = f / np.max(np.abs(f))
+        x[..., 4] = f.real
+        x[..., 5] = f.imag
     x[..., 0] = (eps - 2.1) / 10.15
     x[..., 1] = (wavelength - 1.3e-6) / 0.25e-6
     i = np.arange(nx)[None, :]

@@ -83,6 +83,8 @@ _SIGS = {
     "predictor_num_params": (C.c_longlong, [_vp]),
     "predictor_launches": (C.c_longlong, [_vp]),
     "predictor_set_tensor_cores": (C.c_int, [_vp, C.c_int]),
+    "predictor_create_with_field": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp)]),
+    "predictor_set_input_field": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _vp]),
     "predictor_set_params": (C.c_int, [_vp, _vp, C.c_longlong]),
     "predictor_get_params": (C.c_int, [_vp, _vp, C.c_longlong]),
     "predictor_forward": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_double, C.c_double, _vp, _vp]),
@@ -438,21 +440,34 @@ def predictor_layer_shapes(channels, k, cin=4):
 class Predictor:
     """ddg_predictor: the subspace-predicting CNN (weights on the device)."""
 
-    def __init__(self, k=8, channels=(32, 48, 64, 96, 128, 128)):
+    def __init__(self, k=8, channels=(32, 48, 64, 96, 128, 128), input_field=False):
         _torch()
         self.k, self.channels = int(k), tuple(int(c) for c in channels)
+        self.cin = 6 if input_field else 4
         arr = (C.c_int * len(self.channels))(*self.channels)
         h = _vp()
-        _check(load().predictor_create(self.k, len(self.channels), arr, C.byref(h)), "predictor_create")
+        if input_field:
+            _check(load().predictor_create_with_field(self.k, len(self.channels), arr, C.byref(h)),
+                   "predictor_create_with_field")
+        else:
+            _check(load().predictor_create(self.k, len(self.channels), arr, C.byref(h)), "predictor_create")
         self._h = h
         self.nparams = int(load().predictor_num_params(h))
+
+    def set_input_field(self, f, nx, ny, stream=None):
+        """predictor_set_input_field: f a complex128 CUDA tensor of ny*nx values."""
+        torch = _torch()
+        f = f.reshape(-1).to(torch.complex128).contiguous()
+        self._field = f
+        _check(load().predictor_set_input_field(self._h, _vp(f.data_ptr()), int(nx), int(ny), _stream(stream)),
+               "predictor_set_input_field")
 
     @property
     def handle(self):
         return self._h
 
     def layer_shapes(self):
-        return predictor_layer_shapes(self.channels, self.k)
+        return predictor_layer_shapes(self.channels, self.k, self.cin)
 
     @property
     def launches(self) -> int:

@@ -558,7 +558,7 @@ struct InputDesc {
     double wavelength;
 };
 __global__ void k_input(const InputDesc* __restrict__ desc, int B, int H, int W, int i_src, double sigma, double j_c,
-                        bf16* __restrict__ x) {
+                        const float2* __restrict__ field, int cin, bf16* __restrict__ x) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)B * H * W) return;
     const int b = (int)(idx / ((long long)H * W));
@@ -568,11 +568,35 @@ __global__ void k_input(const InputDesc* __restrict__ desc, int B, int H, int W,
     const int L = d.npml;
     const bool inside = i >= L && i < W - L && j >= L && j < H - L;
     const double t = (double)j - j_c;
-    bf16* o = x + idx * 4;
+    bf16* o = x + idx * cin;
     o[0] = __float2bfloat16_rn((float)((d.eps[e] - 2.1) / 10.15));
     o[1] = __float2bfloat16_rn((float)((d.wavelength - 1.3e-6) / 0.25e-6));
     o[2] = __float2bfloat16_rn(inside ? 0.f : 1.f);
     o[3] = __float2bfloat16_rn(i == i_src ? (float)exp(-t * t / (2.0 * sigma * sigma)) : 0.f);
+    if (cin == 6) {
+        // an approximate field of the grid (normalised to max |f| = 1): Re, Im
+        o[4] = __float2bfloat16_rn(field[e].x);
+        o[5] = __float2bfloat16_rn(field[e].y);
+    }
+}
+
+// max |f| over D values (one block), then f / max |f| in FP32
+__global__ void k_field_in(const double2* __restrict__ f, long long D, float2* __restrict__ out) {
+    __shared__ double sm[32];
+    double m = 0.0;
+    for (long long e = threadIdx.x; e < D; e += blockDim.x) m = fmax(m, hypot(f[e].x, f[e].y));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) sm[0] = m;
+    }
+    __syncthreads();
+    const double inv = sm[0] > 0.0 ? 1.0 / sm[0] : 0.0;
+    for (long long e = threadIdx.x; e < D; e += blockDim.x)
+        out[e] = make_float2((float)(f[e].x * inv), (float)(f[e].y * inv));
 }
 
 // Projection loss (Eq. 5) per sample and d loss / d y for the batch mean.
@@ -813,6 +837,8 @@ struct ddg_predictor {
     void* act = nullptr;
     size_t act_bytes = 0;
     double* d_loss = nullptr;     // per-sample losses
+    float2* in_field = nullptr;   // cin = 6: the approximate field of the grid, normalised
+    int field_nx = 0, field_ny = 0;
     int* d_err = nullptr;         // a bounded wait in a tensor-core convolution gave up
     bool tensor_cores = true;     // forward 3x3 convolutions on tcgen05 where the channels allow
     void* d_desc = nullptr;       // InputDesc / pointer arrays (device)
@@ -1086,6 +1112,11 @@ static ddg_status check_batch(const ddg_predictor* P, int n, const ddg_op* const
         set_error("predictor: grid %dx%d not divisible by %d", A[0]->nx, A[0]->ny, div);
         return DDG_EINVAL;
     }
+    if (P->cin == 6 && (!P->in_field || P->field_nx != A[0]->nx || P->field_ny != A[0]->ny)) {
+        set_error("predictor: this network takes an input field of the %dx%d grid (predictor_set_input_field)",
+                  A[0]->nx, A[0]->ny);
+        return DDG_EINVAL;
+    }
     *H = A[0]->ny;
     *W = A[0]->nx;
     return DDG_OK;
@@ -1115,7 +1146,7 @@ static ddg_status build_input(ddg_predictor* P, int n, const ddg_op* const* A, i
     const int H = A[0]->ny, W = A[0]->nx;
     ++P->launches;
     k_input<<<nblk((long long)n * H * W), 256, 0, st>>>(reinterpret_cast<InputDesc*>(P->d_desc), n, H, W, i_src,
-                                                       sigma, j_c, acts->x0);
+                                                       sigma, j_c, P->in_field, P->cin, acts->x0);
     DDG_CHECK_LAUNCH("k_input");
     return DDG_OK;
 }
@@ -1138,6 +1169,7 @@ static void free_predictor(ddg_predictor* P) {
     cudaFree(P->wk);
     cudaFree(P->act);
     cudaFree(P->d_loss);
+    cudaFree(P->in_field);
     cudaFree(P->d_err);
     cudaFree(P->d_desc);
     delete P;
@@ -1149,7 +1181,7 @@ static void free_predictor(ddg_predictor* P) {
 using namespace ddg;
 using namespace ddg::cnn;
 
-extern "C" ddg_status predictor_create(int k, int levels, const int* channels, ddg_predictor** out) {
+static ddg_status create_predictor(int k, int levels, const int* channels, int cin, ddg_predictor** out) {
     if (!out) { set_error("predictor_create: out is NULL"); return DDG_EINVAL; }
     *out = nullptr;
     if (k < 1 || k > 16 || levels < 1 || levels > kMaxLevels || !channels) {
@@ -1158,6 +1190,7 @@ extern "C" ddg_status predictor_create(int k, int levels, const int* channels, d
     }
     ddg_predictor* P = new (std::nothrow) ddg_predictor();
     if (!P) return DDG_ENOMEM;
+    P->cin = cin;
     P->k = k;
     P->levels = levels;
     for (int l = 0; l < levels; ++l) {
@@ -1204,6 +1237,34 @@ extern "C" ddg_status predictor_create(int k, int levels, const int* channels, d
         return DDG_ENOMEM;
     }
     *out = P;
+    return DDG_OK;
+}
+
+extern "C" ddg_status predictor_create(int k, int levels, const int* channels, ddg_predictor** out) {
+    return create_predictor(k, levels, channels, 4, out);
+}
+
+extern "C" ddg_status predictor_create_with_field(int k, int levels, const int* channels, ddg_predictor** out) {
+    return create_predictor(k, levels, channels, 6, out);
+}
+
+extern "C" ddg_status predictor_set_input_field(ddg_predictor* P, const double* f, int nx, int ny, void* stream) {
+    if (!P || !f || nx < 1 || ny < 1) { set_error("predictor_set_input_field: bad arguments"); return DDG_EINVAL; }
+    if (P->cin != 6) { set_error("predictor_set_input_field: network created without an input field"); return DDG_EINVAL; }
+    const long long D = (long long)nx * ny;
+    cudaStream_t st = as_stream(stream);
+    if (P->field_nx * (long long)P->field_ny != D) {
+        cudaFree(P->in_field);
+        P->in_field = nullptr;
+        P->field_nx = P->field_ny = 0;
+        cudaError_t e = cudaMalloc(&P->in_field, sizeof(float2) * D);
+        if (e != cudaSuccess) { cudaGetLastError(); set_error("predictor_set_input_field: cudaMalloc failed"); return DDG_ENOMEM; }
+    }
+    P->field_nx = nx;
+    P->field_ny = ny;
+    ++P->launches;
+    k_field_in<<<1, 1024, 0, st>>>(reinterpret_cast<const double2*>(f), D, P->in_field);
+    DDG_CHECK_LAUNCH("k_field_in");
     return DDG_OK;
 }
 
@@ -1365,7 +1426,7 @@ extern "C" ddg_status predictor_save(const ddg_predictor* P, const char* path) {
     DDG_CHECK_CUDA(cudaMemcpy(buf.data(), P->theta, 4 * n, cudaMemcpyDeviceToHost));
     DDG_CHECK_CUDA(cudaMemcpy(buf.data() + n, P->adam_m, 4 * n, cudaMemcpyDeviceToHost));
     DDG_CHECK_CUDA(cudaMemcpy(buf.data() + 2 * n, P->adam_v, 4 * n, cudaMemcpyDeviceToHost));
-    long long hdr[4 + kMaxLevels] = {0x4444474d50524544LL, 1, P->k, P->levels};
+    long long hdr[4 + kMaxLevels] = {0x4444474d50524544LL, P->cin == 4 ? 1 : 2, P->k, P->levels};
     for (int l = 0; l < kMaxLevels; ++l) hdr[4 + l] = l < P->levels ? P->ch[l] : 0;
     long long tail[2] = {P->nparams, P->step};
     FILE* fp = fopen(path, "wb");
@@ -1390,7 +1451,7 @@ extern "C" ddg_status predictor_load(ddg_predictor* P, const char* path) {
     std::vector<float> buf(3 * n);
     unsigned long long hf = 0;
     bool ok = fread(hdr, sizeof(hdr), 1, fp) == 1 && fread(tail, sizeof(tail), 1, fp) == 1;
-    ok = ok && hdr[0] == 0x4444474d50524544LL && hdr[1] == 1 && hdr[2] == P->k && hdr[3] == P->levels &&
+    ok = ok && hdr[0] == 0x4444474d50524544LL && hdr[1] == (P->cin == 4 ? 1 : 2) && hdr[2] == P->k && hdr[3] == P->levels &&
          tail[0] == P->nparams;
     for (int l = 0; ok && l < P->levels; ++l) ok = hdr[4 + l] == P->ch[l];
     ok = ok && fread(buf.data(), 4, buf.size(), fp) == buf.size() && fread(&hf, sizeof(hf), 1, fp) == 1;

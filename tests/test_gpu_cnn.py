@@ -265,3 +265,32 @@ def test_tensor_core_forward_equals_cuda_core_forward():
     y_tc2 = P.forward(ops, src).cpu().numpy()
     assert np.array_equal(y_tc, y_tc2)          # deterministic
     assert rel(y_tc, y_cc) <= 1e-2
+
+
+def test_input_field_network_matches_oracle():
+    # a network with the approximate-field input (6 channels): forward against
+    # the bfloat16-emulated oracle given the same field; without the field set,
+    # the call is refused
+    g, eps, ops = small_problems()
+    P = ddg.Predictor(input_field=True, **SMALL)
+    P.init_he(seed=12)
+    src = (g.i_src, g.sigma_src, g.j_src)
+    with pytest.raises(ddg.DdgError):
+        P.forward(ops, src)
+    f = inputs.random_complex(g.D, 77)
+    P.set_input_field(torch.as_tensor(f, device="cuda"), g.nx, g.ny)
+    theta = P.get_params().astype(np.float64)
+    y = P.forward(ops, src).cpu().numpy()
+    cfg = ocnn.CNNConfig(cin=6, channels=SMALL["channels"], k=SMALL["k"])
+    assert P.nparams == ocnn.num_params(cfg)
+    x = np.stack([ocnn.input_channels(e, g.wavelength, g.npml, g.i_src, g.sigma_src, g.j_src, field=f) for e in eps])
+    yb = ocnn.forward(cfg, ocnn.round_weights(cfg, theta, ocnn.bf16_round), ocnn.bf16_round(x),
+                      store=ocnn.bf16_round)
+    assert rel(y, yb) <= 2e-3
+    # a checkpoint of this network does not load into one without the field input
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "p.bin")
+        P.save(path)
+        Q = ddg.Predictor(**SMALL)
+        with pytest.raises(ddg.DdgError):
+            Q.load_file(path)

@@ -151,3 +151,17 @@ def test_residual_loss_value_and_gradient():
             dV[r, c] = 1e-7 * part
             fd = (cnn.residual_loss_and_grad(A, V + dV, b)[0] - cnn.residual_loss_and_grad(A, V - dV, b)[0]) / 2e-7
             assert abs(fd - gg[r, c]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_input_field_channels():
+    # the approximate-field input: two more channels, Re and Im of the field
+    # divided by its largest magnitude; the first four unchanged
+    rng = np.random.default_rng(3)
+    eps = 2.1 + 10.15 * rng.random((16, 12))
+    f = rng.standard_normal(16 * 12) + 1j * rng.standard_normal(16 * 12)
+    x4 = cnn.input_channels(eps, 1.55e-6, 2, 3, 2.0, 8.0)
+    x6 = cnn.input_channels(eps, 1.55e-6, 2, 3, 2.0, 8.0, field=f)
+    assert x6.shape == (16, 12, 6) and np.array_equal(x6[..., :4], x4)
+    g = f.reshape(16, 12) / np.max(np.abs(f))
+    assert np.array_equal(x6[..., 4], g.real) and np.array_equal(x6[..., 5], g.imag)
+    assert np.isclose(np.max(np.hypot(x6[..., 4], x6[..., 5])), 1.0)
