@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--cnn-lr", type=float, default=3e-4)
     p.add_argument("--cnn-loss", default="residual", choices=["residual", "projection"],
                    help="Eq. 6 (unsupervised, trained on the right-hand sides) or Eq. 5 (solved fields)")
+    p.add_argument("--cnn-base", default="pca", choices=["none", "pca"],
+                   help="fixed offset of the CNN output: the leading principal components of the training fields")
     p.add_argument("--cnn-field", default="none", choices=["none", "background"],
                    help="extra CNN input: the field of the unpatterned background (one solve per grid)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -183,6 +185,12 @@ def run_ours(args, rank, world):
     if field is not None:
         P.set_input_field(field, g.nx, g.ny)
     P.init_he(seed=0)
+    if args.cnn_base == "pca":
+        # the network learns corrections to the k leading principal components
+        # (scaled to O(1) entries; zero head: training starts from that basis)
+        U_base, _ = ddg.pca_fit(ctx, torch.stack(xs_tr), args.cnn_k)
+        P.set_output_base(U_base, g.nx, g.ny, scale=float(np.sqrt(g.D)))
+        P.zero_head()
     P.set_loss(args.cnn_loss)
     targets = bs_tr if args.cnn_loss == "residual" else xs_tr
     rng = np.random.default_rng(0)
@@ -364,7 +372,8 @@ def run_ours(args, rank, world):
         "config": {"workload": WORKLOAD, "grid": "128x128", "dx_nm": 40, "wavelength_nm": 1550,
                    "npml": 10, "restart": args.restart, "tol": 1e-6, "solves_per_step": n,
                    "predictor": f"cnn k={args.cnn_k} (6 levels, 32-128 channels, bf16, {args.cnn_loss} loss"
-                                f"{', background-field input' if args.cnn_field == 'background' else ''})",
+                                f"{', background-field input' if args.cnn_field == 'background' else ''}"
+                                f"{', output offset = leading PCs of the training fields' if args.cnn_base == 'pca' else ''})",
                    "restart_policy": "augmented first cycle, then plain GMRES; V-only residual > 0.5 -> "
                                      "its step, then plain GMRES",
                    "precision": args.precision, "training_fields": len(eps_train),

@@ -291,6 +291,16 @@ ddg_status predictor_create_with_field(int k, int levels, const int* channels, d
 /* f: device, ny*nx complex128 (row-major), copied (normalised) into the
    predictor; DDG_EINVAL for a network created without the field input. */
 ddg_status predictor_set_input_field(ddg_predictor* P, const double* f, int nx, int ny, void* stream);
+/* predictor_set_output_base -- a fixed offset added to the network's output
+   (no paper counterpart; the paper gives no architecture): the predicted
+   vectors become v_c = scale * U_c + CNN(eps)_c.  With U a data-derived basis
+   (for instance the leading principal components of the training fields,
+   pca_fit) and the head initialised at zero, training starts from that basis
+   and learns permittivity-dependent corrections.  The offset is not trained.
+     U  device, D x k complex128 column-major (column c at U + 2 D c), D = nx ny;
+        NULL removes the offset.
+   Later calls on another grid size are refused (DDG_EINVAL). */
+ddg_status predictor_set_output_base(ddg_predictor* P, const double* U, int nx, int ny, double scale, void* stream);
 ddg_status predictor_destroy(ddg_predictor* P);
 long long predictor_num_params(const ddg_predictor* P);
 /* Kernels launched by this predictor since it was created. */

@@ -85,6 +85,7 @@ _SIGS = {
     "predictor_set_tensor_cores": (C.c_int, [_vp, C.c_int]),
     "predictor_create_with_field": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp)]),
     "predictor_set_input_field": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _vp]),
+    "predictor_set_output_base": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_double, _vp]),
     "predictor_set_params": (C.c_int, [_vp, _vp, C.c_longlong]),
     "predictor_get_params": (C.c_int, [_vp, _vp, C.c_longlong]),
     "predictor_forward": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_double, C.c_double, _vp, _vp]),
@@ -453,6 +454,29 @@ class Predictor:
             _check(load().predictor_create(self.k, len(self.channels), arr, C.byref(h)), "predictor_create")
         self._h = h
         self.nparams = int(load().predictor_num_params(h))
+
+    def set_output_base(self, U, nx, ny, scale=1.0, stream=None):
+        """predictor_set_output_base: U a (k, D) complex128 CUDA tensor (or None to remove)."""
+        torch = _torch()
+        ptr = _vp()
+        if U is not None:
+            U = U.to(torch.complex128).contiguous()
+            self._base = U
+            ptr = _vp(U.data_ptr())
+        _check(load().predictor_set_output_base(self._h, ptr, int(nx), int(ny), float(scale), _stream(stream)),
+               "predictor_set_output_base")
+
+    def zero_head(self):
+        """Sets the 1x1 head's weights and biases to zero (the output is then the output base)."""
+        import numpy as np
+        theta = self.get_params()
+        off = 0
+        for name, co, ci, kk in self.layer_shapes():
+            n = co * ci * kk * kk + co
+            if name == "head":
+                theta[off:off + n] = 0.0
+            off += n
+        self.set_params(theta)
 
     def set_input_field(self, f, nx, ny, stream=None):
         """predictor_set_input_field: f a complex128 CUDA tensor of ny*nx values."""

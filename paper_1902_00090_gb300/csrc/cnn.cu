@@ -735,6 +735,23 @@ __global__ void k_to_bf16(const float* __restrict__ a, bf16* __restrict__ b, lon
 }
 
 // network output (B, D, 2k) FP32 -> U_b (D x k complex128, column-major)
+// base (D x k complex, column c at c * D) scaled, into the output layout [D][2k]
+__global__ void k_base_in(const double2* __restrict__ U, long long D, int k, double scale, float* __restrict__ out) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= D * k) return;
+    const int c = (int)(idx / D);
+    const long long e = idx % D;
+    const double2 u = U[idx];
+    out[e * 2 * k + 2 * c] = (float)(u.x * scale);
+    out[e * 2 * k + 2 * c + 1] = (float)(u.y * scale);
+}
+// y[b] += base for every sample b (n = D * 2k values per sample)
+__global__ void k_add_base(float* __restrict__ y, const float* __restrict__ base, long long n, int B) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * B) return;
+    y[idx] += base[idx % n];
+}
+
 __global__ void k_to_complex(const float* __restrict__ y, int D, int k, double2* const* __restrict__ U, int B) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)B * D * k) return;
@@ -839,6 +856,8 @@ struct ddg_predictor {
     double* d_loss = nullptr;     // per-sample losses
     float2* in_field = nullptr;   // cin = 6: the approximate field of the grid, normalised
     int field_nx = 0, field_ny = 0;
+    float* out_base = nullptr;    // optional fixed output offset (D x 2k, the output layout)
+    int base_nx = 0, base_ny = 0;
     int* d_err = nullptr;         // a bounded wait in a tensor-core convolution gave up
     bool tensor_cores = true;     // forward 3x3 convolutions on tcgen05 where the channels allow
     void* d_desc = nullptr;       // InputDesc / pointer arrays (device)
@@ -1007,6 +1026,11 @@ static ddg_status forward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaSt
     ++P->launches;
     k_head_fwd<<<nblk((long long)B * H * W * 2 * P->k), 256, 0, st>>>(h, (long long)B * H * W, hc, 2 * P->k, wbf(P, lh),
                                                                     bias32(P, lh), A->y);
+    if (P->out_base) {
+        const long long n = (long long)H * W * 2 * P->k;
+        ++P->launches;
+        k_add_base<<<nblk(n * B), 256, 0, st>>>(A->y, P->out_base, n, B);
+    }
     DDG_CHECK_LAUNCH("forward");
     return DDG_OK;
 }
@@ -1112,6 +1136,10 @@ static ddg_status check_batch(const ddg_predictor* P, int n, const ddg_op* const
         set_error("predictor: grid %dx%d not divisible by %d", A[0]->nx, A[0]->ny, div);
         return DDG_EINVAL;
     }
+    if (P->out_base && (P->base_nx != A[0]->nx || P->base_ny != A[0]->ny)) {
+        set_error("predictor: the output base was set for a %dx%d grid", P->base_nx, P->base_ny);
+        return DDG_EINVAL;
+    }
     if (P->cin == 6 && (!P->in_field || P->field_nx != A[0]->nx || P->field_ny != A[0]->ny)) {
         set_error("predictor: this network takes an input field of the %dx%d grid (predictor_set_input_field)",
                   A[0]->nx, A[0]->ny);
@@ -1170,6 +1198,7 @@ static void free_predictor(ddg_predictor* P) {
     cudaFree(P->act);
     cudaFree(P->d_loss);
     cudaFree(P->in_field);
+    cudaFree(P->out_base);
     cudaFree(P->d_err);
     cudaFree(P->d_desc);
     delete P;
@@ -1265,6 +1294,32 @@ extern "C" ddg_status predictor_set_input_field(ddg_predictor* P, const double* 
     ++P->launches;
     k_field_in<<<1, 1024, 0, st>>>(reinterpret_cast<const double2*>(f), D, P->in_field);
     DDG_CHECK_LAUNCH("k_field_in");
+    return DDG_OK;
+}
+
+extern "C" ddg_status predictor_set_output_base(ddg_predictor* P, const double* U, int nx, int ny, double scale,
+                                                void* stream) {
+    if (!P || nx < 1 || ny < 1) { set_error("predictor_set_output_base: bad arguments"); return DDG_EINVAL; }
+    cudaStream_t st = as_stream(stream);
+    if (!U) {   // remove the base
+        cudaFree(P->out_base);
+        P->out_base = nullptr;
+        P->base_nx = P->base_ny = 0;
+        return DDG_OK;
+    }
+    const long long D = (long long)nx * ny;
+    if ((long long)P->base_nx * P->base_ny != D) {
+        cudaFree(P->out_base);
+        P->out_base = nullptr;
+        P->base_nx = P->base_ny = 0;
+        cudaError_t e = cudaMalloc(&P->out_base, sizeof(float) * D * 2 * P->k);
+        if (e != cudaSuccess) { cudaGetLastError(); set_error("predictor_set_output_base: cudaMalloc failed"); return DDG_ENOMEM; }
+    }
+    P->base_nx = nx;
+    P->base_ny = ny;
+    ++P->launches;
+    k_base_in<<<nblk(D * P->k), 256, 0, st>>>(reinterpret_cast<const double2*>(U), D, P->k, scale, P->out_base);
+    DDG_CHECK_LAUNCH("k_base_in");
     return DDG_OK;
 }
 

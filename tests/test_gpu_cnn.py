@@ -294,3 +294,26 @@ def test_input_field_network_matches_oracle():
         Q = ddg.Predictor(**SMALL)
         with pytest.raises(ddg.DdgError):
             Q.load_file(path)
+
+
+def test_output_base_is_added():
+    # the fixed output offset: y = scale * base + network output (output layout
+    # [pixel][2k], channel 2c / 2c + 1 = Re / Im of vector c); with a zero head
+    # the output is the base alone, and removing the base restores the network
+    g, eps, ops = small_problems()
+    P = ddg.Predictor(**SMALL)
+    P.init_he(seed=13)
+    src = (g.i_src, g.sigma_src, g.j_src)
+    y0 = P.forward(ops, src).cpu().numpy()
+    k = SMALL["k"]
+    Uh = inputs.random_complex(g.D, 5, shape=(k, g.D))
+    P.set_output_base(torch.as_tensor(Uh, device="cuda"), g.nx, g.ny, scale=3.0)
+    y1 = P.forward(ops, src).cpu().numpy()
+    base = np.zeros((g.ny, g.nx, 2 * k), dtype=np.float32)
+    base[..., 0::2] = (3.0 * Uh.real.T).reshape(g.ny, g.nx, k)
+    base[..., 1::2] = (3.0 * Uh.imag.T).reshape(g.ny, g.nx, k)
+    assert np.max(np.abs(y1 - (y0 + base[None]))) <= 1e-6 * np.max(np.abs(y0) + np.abs(base))
+    P.zero_head()
+    assert np.array_equal(P.forward(ops, src).cpu().numpy(), np.broadcast_to(base, y1.shape))
+    P.set_output_base(None, g.nx, g.ny)
+    assert not np.any(P.forward(ops, src).cpu().numpy())
