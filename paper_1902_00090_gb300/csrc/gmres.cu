@@ -1386,42 +1386,44 @@ __global__ void __launch_bounds__(kBlock) k_update_x(BatchArgs a) {
     for (int c = threadIdx.x; c < nc; c += kBlock) cyl[c] = from_d2<V>(P.coefy[c]);
     __syncthreads();
     const long long p0 = (long long)chunk * kBlock + threadIdx.x;
-    // V (the predicted vectors, in the arithmetic type) and Q (basis storage)
+    // V (the predicted vectors, in the arithmetic type) then Q (basis storage):
+    // blocks of 8 columns summed in T, the block sums in FP64
     const PK* __restrict__ Vp = reinterpret_cast<const PK*>(P.V);
     const BP* __restrict__ Qp = reinterpret_cast<const BP*>(P.M) + (long long)N * ldp;
-    auto column = [&](int c, V (&mv)[VEC]) {
-        if (c < N) unpack(Vp[(long long)c * ldp + p0], mv);
-        else BS::load(Qp[(long long)(c - N) * ldp + p0], mv);
-    };
     double2 acc[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) acc[q] = make_double2(0.0, 0.0);
-    // blocks of 8 columns summed in T, the block sums in FP64
-    for (int c0 = 0; c0 < nc; c0 += 8) {
-        const int nb = min(8, nc - c0);
-        V mv[8][VEC];
+    auto block = [&](const auto* base, int ncols, int coff) {
+        for (int c0 = 0; c0 < ncols; c0 += 8) {
+            const int nb = min(8, ncols - c0);
+            V mv[8][VEC];
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            if (w < nb) {
-                column(c0 + w, mv[w]);
-            } else {
+            for (int w = 0; w < 8; ++w) {
+                if (w < nb) {
+                    const auto pk = base[(long long)(c0 + w) * ldp + p0];
+                    if constexpr (sizeof(pk) == sizeof(PK)) unpack(pk, mv[w]);
+                    else BS::load(pk, mv[w]);
+                } else {
 #pragma unroll
-                for (int q = 0; q < VEC; ++q) mv[w][q] = mk((T)0, (T)0);
+                    for (int q = 0; q < VEC; ++q) mv[w][q] = mk((T)0, (T)0);
+                }
             }
+            V part[VEC];
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) part[q] = mk((T)0, (T)0);
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                if (w >= nb) break;
+                const V cw = cyl[coff + c0 + w];
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) cfma(part[q], mv[w][q], cw);
+            }
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) acc[q] = cadd(acc[q], to_d2(part[q]));
         }
-        V part[VEC];
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) part[q] = mk((T)0, (T)0);
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            if (w >= nb) break;
-            const V cw = cyl[c0 + w];
-#pragma unroll
-            for (int q = 0; q < VEC; ++q) cfma(part[q], mv[w][q], cw);
-        }
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) acc[q] = cadd(acc[q], to_d2(part[q]));
-    }
+    };
+    if (N > 0) block(Vp, N, 0);
+    block(Qp, k, N);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
         const long long e = p0 * VEC + q;
