@@ -106,13 +106,17 @@ def _cgs(Q: np.ndarray, w: np.ndarray, reorth: bool):
 
 def plain_gmres(A, b: np.ndarray, x0=None, tol: float = 1e-6, restart: int = 200,
                 maxit: int = 5000, reorth: bool = True, breakdown_tol: float = 1e-14,
-                keep_basis: bool = False):
+                keep_basis: bool = False, minv: np.ndarray = None):
     """Restarted GMRES(m) for A f = b (Eq. 2).  A: anything with A @ x.
 
     Stops when the true relative residual ||b - A f|| / ||b|| <= tol (checked at
     the start of every cycle) or after maxit Arnoldi steps.  Inside a cycle the
     Arnoldi loop stops as soon as the least-squares residual |g_{j+1}| is
     <= tol ||b||.  Returns (f, info); with keep_basis, also (Q, H) of the last cycle.
+
+    minv: a diagonal right preconditioner M^-1 (the data-free baseline, e.g. the
+    inverse diagonal of A, Jacobi): GMRES on A M^-1 y = r, f += M^-1 y.  The
+    residuals are those of A f = b, so the stopping rule is unchanged.
     """
     b = np.asarray(b, dtype=np.complex128)
     D = b.shape[0]
@@ -146,7 +150,7 @@ def plain_gmres(A, b: np.ndarray, x0=None, tol: float = 1e-6, restart: int = 200
         k = 0
         est = []
         for j in range(m):
-            w = A @ Q[:, j]
+            w = A @ (Q[:, j] if minv is None else minv * Q[:, j])
             nw = np.linalg.norm(w)
             h, w = _cgs(Q[:, :j + 1], w, reorth)
             H[:j + 1, j] = h
@@ -169,7 +173,8 @@ def plain_gmres(A, b: np.ndarray, x0=None, tol: float = 1e-6, restart: int = 200
             if abs(g[j + 1]) <= tol * nb or info.iters >= maxit:
                 break
         y = back_substitute(R[:k, :k], g[:k])
-        x = x + Q[:, :k] @ y
+        d = Q[:, :k] @ y
+        x = x + (d if minv is None else minv * d)
         info.cycle_estimates.append(est)
         last = (Q[:, :k + 1], H[:k + 1, :k])
     return (x, info, last) if keep_basis else (x, info)

@@ -184,3 +184,26 @@ def test_augmented_first_cycle_then_plain_reading():
     x, info = gmres.augmented_gmres(A, b, V, tol=1e-9, restart=20, maxit=4000, aug_cycles=1)
     assert info.converged and info.iters == i1.iters + ip.iters
     assert np.linalg.norm(x - xp) <= 1e-12 * np.linalg.norm(xp)
+
+
+def test_right_preconditioned_gmres():
+    # The data-free baseline: GMRES on A M^-1 with M = diag(A) (Jacobi).
+    # M = I reproduces the plain solve exactly; Jacobi reaches the direct
+    # solution, and its single cycle minimises ||b - A M^-1 y|| over the
+    # Krylov space of A M^-1 (checked against an explicit basis).
+    g, A, b = small_problem(16, seed=4)
+    x_ref = np.linalg.solve(A.toarray(), b)
+    x0, i0 = gmres.plain_gmres(A, b, tol=1e-10, restart=40, maxit=4000)
+    x1, i1 = gmres.plain_gmres(A, b, tol=1e-10, restart=40, maxit=4000, minv=np.ones(g.D))
+    assert np.array_equal(x0, x1) and i0.iters == i1.iters
+    minv = 1.0 / A.diagonal()
+    xj, ij = gmres.plain_gmres(A, b, tol=1e-10, restart=40, maxit=4000, minv=minv)
+    assert ij.converged and np.linalg.norm(xj - x_ref) / np.linalg.norm(x_ref) <= 1e-8
+    # one cycle of j steps: the residual equals the minimum over the Krylov space of A M^-1
+    j = 12
+    xc, ic = gmres.plain_gmres(A, b, tol=1e-300, restart=j, maxit=j, minv=minv)
+    B = A @ np.diag(minv)
+    K = np.column_stack([np.linalg.matrix_power(B, p) @ b for p in range(j)])
+    Qk, _ = np.linalg.qr(K)
+    y, *_ = np.linalg.lstsq(B @ Qk, b, rcond=None)
+    assert np.isclose(np.linalg.norm(b - A @ xc), np.linalg.norm(b - B @ Qk @ y), rtol=1e-6)
