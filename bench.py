@@ -284,10 +284,16 @@ def run_ours(args, rank, world):
     pca = {"value": psolved / (pms / 1e3), "unit": "solves/s",
            "ms_per_step": pms / sK, "k": args.k, "fit_s": round(pca_s, 2), **summary(pinf)}
     plain = None
+    plain_jacobi = None
     if not args.no_plain:
         qms, qinf, _, _, _, qsolved = timed(step_plain, sK, 1)
         plain = {"value": qsolved / (qms / 1e3), "unit": "solves/s",
                  "ms_per_step": qms / sK, **summary(qinf)}
+        # the data-free baseline: plain GMRES with a Jacobi right preconditioner
+        ctx.set_preconditioner("jacobi")
+        jms, jinf, _, _, _, jsolved = timed(step_plain, 1, 0)
+        ctx.set_preconditioner("none")
+        plain_jacobi = {"value": jsolved / (jms / 1e3), "unit": "solves/s", "ms_per_step": jms, **summary(jinf)}
 
     # --- e2e: host buffers in, host buffers out, through the C ABI
     eps_host = torch.from_numpy(np.ascontiguousarray(eps_test)).pin_memory()
@@ -390,6 +396,7 @@ def run_ours(args, rank, world):
         "pca": pca,
         "plain": plain,
         "cnn_recycle": recycle,
+        "plain_jacobi": plain_jacobi,
         "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
         "pca_speedup_vs_plain": round(pca["value"] / plain["value"], 3) if plain else None,
         "solve_training_fields_s": round(solve_train_s, 2),

@@ -147,6 +147,16 @@ ddg_status ddg_context_set_graphs(ddg_context* ctx, int enable);
    when a restart cycle reduces the residual a lot.  Default 0 (the basis in
    FP32).  Ignored for DDG_C128. */
 ddg_status ddg_context_set_basis_storage(ddg_context* ctx, int half);
+/* Data-free preconditioner, the baseline the data-driven subspace is compared
+   with (Sec. III, the benchmark against data-free preconditioners, and the
+   supplement's section on them): kind 1 = Jacobi, M = D(A), the diagonal of A
+   (the stencil's centre coefficient).  The supplement applies it on the left
+   (D(A)^-1 A); here it is applied on the right: GMRES runs on A M^-1, which is
+   similar to D(A)^-1 A (same spectrum), and x += M^-1 Q y, so the residual
+   minimised, the stopping rule and the augmentation stay those of A f = b.
+   kind 0 (default) = none.  For the indefinite FDFD operator with PML Jacobi
+   slows convergence.  Returns DDG_EINVAL for any other kind. */
+ddg_status ddg_context_set_preconditioner(ddg_context* ctx, int kind);
 /* Augmented solves: when the V-only relative residual ||b~|| / ||b|| of the first
    cycle (Eq. 6's minimum over V) exceeds `threshold`, the predicted subspace is
    judged to have failed: its least-squares step is kept (x += V R^-1 C^H b) and

@@ -61,6 +61,7 @@ _SIGS = {
     "ddg_context_set_fallback": (C.c_int, [_vp, C.c_double]),
     "ddg_context_set_graphs": (C.c_int, [_vp, C.c_int]),
     "ddg_context_set_basis_storage": (C.c_int, [_vp, C.c_int]),
+    "ddg_context_set_preconditioner": (C.c_int, [_vp, C.c_int]),
     "ddg_context_set_augmented_cycles": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_enable": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -193,6 +194,11 @@ class Context:
         """Krylov basis of complex64 solves stored in 'f32' (default) or 'f16' (IEEE half)."""
         code = {"f32": 0, "f16": 1}[storage]
         _check(load().ddg_context_set_basis_storage(self._h, code), "ddg_context_set_basis_storage")
+
+    def set_preconditioner(self, kind: str):
+        """'none' (default) or 'jacobi' (right preconditioner M = diag(A), the data-free baseline)."""
+        code = {"none": 0, "jacobi": 1}[kind]
+        _check(load().ddg_context_set_preconditioner(self._h, code), "ddg_context_set_preconditioner")
 
     def set_fallback(self, threshold: float):
         """V-only relative residual above which an augmented solve continues as plain GMRES."""

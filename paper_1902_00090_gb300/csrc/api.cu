@@ -191,6 +191,12 @@ extern "C" ddg_status ddg_context_set_basis_storage(ddg_context* ctx, int half) 
     return DDG_OK;
 }
 
+extern "C" ddg_status ddg_context_set_preconditioner(ddg_context* ctx, int kind) {
+    if (!ctx || kind < 0 || kind > 1) { set_error("ddg_context_set_preconditioner: bad context or kind %d", kind); return DDG_EINVAL; }
+    reinterpret_cast<Context*>(ctx)->precond = kind;
+    return DDG_OK;
+}
+
 extern "C" ddg_status ddg_context_set_fallback(ddg_context* ctx, double threshold) {
     if (!ctx || !(threshold > 0.0)) { set_error("ddg_context_set_fallback: threshold must be > 0"); return DDG_EINVAL; }
     reinterpret_cast<Context*>(ctx)->fallback = threshold;

@@ -84,6 +84,7 @@ struct Context {
     int poll_every = 8;              // Arnoldi steps between host polls (host-driven loop)
     int graphs = 1;                  // delayed scheme: step loop as a CUDA graph with a device-side WHILE
     int half_basis = 0;              // complex64 solves: Krylov basis stored in IEEE half
+    int precond = 0;                 // 0: none, 1: Jacobi right preconditioner (data-free baseline)
     int sm_count = 152;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     // launch accounting and profiling
@@ -132,6 +133,7 @@ struct SolvePtrs {
     const void* eps_lo;        // float* or double* (precision of the Krylov loop)
     const double2* coef_d;
     const void* coef_lo;       // float2* or double2*
+    const void* dinv;          // right preconditioner M^-1 = 1 / diag(A) in the Krylov precision (ld), or null
     const double2* b;
     double2* x;
     double2* r;                // FP64 residual (ld, zero past D)

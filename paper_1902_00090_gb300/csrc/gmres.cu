@@ -470,17 +470,20 @@ __global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
     const T* eps = reinterpret_cast<const T*>(P.eps_lo);
     const V* coef = reinterpret_cast<const V*>(P.coef_lo);
     const T kh2 = (T)P.kh2;
+    // right preconditioner: w = A M^-1 q (q itself is stored unscaled)
+    const V* __restrict__ dinv = reinterpret_cast<const V*>(P.dinv);
     V qv[VEC], wv[VEC];
     if (j == 0) {
         const double2* __restrict__ src = P.r;
         // the stencil sees q_0 as it is stored
         auto ld_ = [&](long long idx) { return BS::round(from_d2<V>(cscale(src[idx], inv))); };
+        auto ls_ = [&](long long idx) { return dinv ? cmul(ld_(idx), dinv[idx]) : ld_(idx); };
 #pragma unroll
         for (int i = 0; i < VEC; ++i) {
             const long long e = e0 + i;
             if (e < D) {
                 qv[i] = ld_(e);
-                wv[i] = stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld_);
+                wv[i] = stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ls_);
             } else {
                 qv[i] = mk((T)0, (T)0);
                 wv[i] = mk((T)0, (T)0);
@@ -490,12 +493,13 @@ __global__ void __launch_bounds__(kBlock) k_step(BatchArgs a, int j) {
         const V* __restrict__ src = reinterpret_cast<const V*>(P.w[(j - 1) & 1]);
         const T tinv = (T)inv;
         auto ld_ = [&](long long idx) { return BS::round(cscale(src[idx], tinv)); };
+        auto ls_ = [&](long long idx) { return dinv ? cmul(ld_(idx), dinv[idx]) : ld_(idx); };
 #pragma unroll
         for (int i = 0; i < VEC; ++i) {
             const long long e = e0 + i;
             if (e < D) {
                 qv[i] = ld_(e);
-                wv[i] = stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld_);
+                wv[i] = stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ls_);
             } else {
                 qv[i] = mk((T)0, (T)0);
                 wv[i] = mk((T)0, (T)0);
@@ -980,12 +984,20 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
         const V* coef = reinterpret_cast<const V*>(P.coef_lo);
         const T kh2 = (T)P.kh2;
         const long long D = P.D;
-        auto ld_ = [&](long long idx) { return uu[idx]; };
+        auto sweep = [&](const auto& ld_) {
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) {
-            const long long e = p0 * VEC + q;
-            z[q] = e < D ? stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld_) : mk((T)0, (T)0);
-        }
+            for (int q = 0; q < VEC; ++q) {
+                const long long e = p0 * VEC + q;
+                z[q] = e < D ? stencil(e, P.nx, P.ny, coef, kh2 * eps[e], ld_) : mk((T)0, (T)0);
+            }
+        };
+        // right preconditioner: z = A M^-1 u (branch taken once, outside the
+        // loads, so the plain stencil keeps its load batching)
+        const V* __restrict__ dinv = reinterpret_cast<const V*>(P.dinv);
+        if (dinv)
+            sweep([&](long long idx) { return cmul(uu[idx], dinv[idx]); });
+        else
+            sweep([&](long long idx) { return uu[idx]; });
         reinterpret_cast<PK*>(P.w[1])[p0] = mkpack(z);
     } else {
 #pragma unroll
@@ -1423,7 +1435,21 @@ __global__ void __launch_bounds__(kBlock) k_update_x(BatchArgs a) {
         }
     };
     if (N > 0) block(Vp, N, 0);
-    block(Qp, k, N);
+    if (P.dinv) {
+        // right preconditioner: x += V z + M^-1 Q y
+        double2 accv[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            accv[q] = acc[q];
+            acc[q] = make_double2(0.0, 0.0);
+        }
+        block(Qp, k, N);
+        const V* dinv = reinterpret_cast<const V*>(P.dinv);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) acc[q] = cadd(accv[q], cmul(acc[q], to_d2(dinv[p0 * VEC + q])));
+    } else {
+        block(Qp, k, N);
+    }
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
         const long long e = p0 * VEC + q;
@@ -1594,6 +1620,33 @@ __global__ void __launch_bounds__(kBlock) k_aug_store(BatchArgs a) {
             BS::set(P.M, (long long)n * ld + e, from_d2<V>(P.W[(long long)n * ld + e]));
             Vl[(long long)n * ld + e] = e < D ? from_d2<V>(P.U[(long long)n * D + e]) : mk((T)0, (T)0);
         }
+}
+
+// M^-1 = 1 / diag(A) (the stencil's centre coefficient), in the Krylov precision;
+// zero past D.  The data-free baseline of the augmented method: Jacobi.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_dinv(BatchArgs a) {
+    using V = c2_t<T>;
+    constexpr int VEC = vec_of<T>();
+    SOLVE_PROLOGUE();
+    (void)S;
+    const long long D = P.D;
+    const int nx = P.nx, ny = P.ny;
+    V* dv = reinterpret_cast<V*>(const_cast<void*>(P.dinv));
+    const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+        const long long e = e0 + q;
+        V v = mk((T)0, (T)0);
+        if (e < D) {
+            const int j = (int)(e / nx), i = (int)(e - (long long)j * nx);
+            const double2* c = P.coef_d;
+            double2 d = cadd(cadd(c[i], c[nx + i]), cadd(c[2 * nx + j], c[2 * nx + ny + j]));
+            d.x -= P.kh2 * P.eps_d[e];
+            v = from_d2<V>(cdiv(make_double2(1.0, 0.0), d));
+        }
+        dv[e] = v;
+    }
 }
 
 // ---------------------------------------------------------------- host driver
@@ -1793,6 +1846,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             P.cr = c.take<double2>(std::max(1, Nreq));
             P.coefy = c.take<double2>(Nreq + m);
             P.ticket = c.take<unsigned>(1);
+            P.dinv = ctx->precond ? (const void*)c.take<V>(ld) : nullptr;
             P.nx = op->nx;
             P.ny = op->ny;
             P.D = op->D;
@@ -1846,6 +1900,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     DDG_TRY((dcgs2_smem<T, HB>(Nreq, m, giv_smem, dots2_smem, upd_smem)));
     const size_t ux_smem = sizeof(V) * (size_t)(Nreq + m);
     DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_init<<<(n + 127) / 128, 128, 0, st>>>(args, n, Nreq); }));
+    if (ctx->precond) DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_dinv<T><<<G, kBlock, 0, st>>>(args); }));
     if (Nreq > 0) {
         DDG_TRY(ctx->launch(DDG_K_SETUP, st, [&] { k_aug_av<T><<<G, kBlock, 0, st>>>(args); }));
         for (int pass = 0; pass < 2; ++pass) {

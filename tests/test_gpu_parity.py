@@ -489,3 +489,26 @@ def test_half_basis_augmented_and_batched(ctx_f16):
         for A, x, i in zip(As, xs, infos):
             assert i["converged"]
             assert np.linalg.norm(bo - A @ host(x)) / np.linalg.norm(bo) <= tol * 1.02
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_jacobi_preconditioner_matches_oracle(prec):
+    # the data-free baseline: right Jacobi preconditioner, against the oracle's
+    # preconditioned GMRES (same steps and cycles in c128; the solution meets
+    # the tolerance of A f = b in both precisions; augmentation still works)
+    g, eps, A, b = small(32, npml=6, seed=1)
+    tol = 1e-9 if prec == "c128" else 1e-6
+    xo, io = gmres.plain_gmres(A, b, tol=tol, restart=25, maxit=20000, minv=1.0 / A.diagonal())
+    c = ddg.Context()
+    c.set_preconditioner("jacobi")
+    op = ddg.fdfd_operator(g, dev(eps, torch.float64))
+    x, info, st = ddg.gmres_solve(c, op, dev(b), tol=tol, restart=25, maxit=20000, precision=prec)
+    assert st == 0 and info["converged"]
+    assert np.linalg.norm(b - A @ host(x)) / np.linalg.norm(b) <= tol
+    if prec == "c128":
+        assert abs(info["iters"] - io.iters) <= 1 and info["cycles"] == io.cycles
+        assert rel(host(x), xo) <= 1e-6
+    V = np.stack([spla.spsolve(A.tocsc(), b) + 1e-3 * inputs.random_complex(g.D, 3), inputs.random_complex(g.D, 4)])
+    xa, ia, sta = ddg.augmented_gmres_solve(c, op, dev(b), dev(V), tol=tol, restart=25, maxit=20000, precision=prec)
+    assert sta == 0 and ia["converged"]
+    assert np.linalg.norm(b - A @ host(xa)) / np.linalg.norm(b) <= tol
