@@ -885,17 +885,21 @@ __device__ __noinline__ void dcgs2_finish_column(FinishArgs a, SolveScal* S, con
 // Column i-1 (H = h1 + s, its Givens rotation, the stop test) and h1 itself are
 // finished by dcgs2_finish_column.
 //
-// The columns stream through shared memory: a ring of 3 stages of 16 KB
-// (48 KB in all), filled by bulk copies (one thread issues them 2 stages
-// ahead) and completed on one mbarrier per stage.  A column chunk is kBlock
-// packs of one thread's elements: 4 KB in the arithmetic type (4 columns a
-// stage), 2 KB in half (8 columns a stage, so that the per-stage barrier and
-// wait are paid per 16 KB either way).
+// The columns stream through shared memory: a ring of stages of 16 KB, filled
+// by bulk copies and completed on one mbarrier per stage.  The stages requested
+// before the prologue are issued by warp 0, one column per lane (the first
+// copies start sooner); in the stage loop thread 0 requests one stage,
+// stages - 1 ahead (a warp-wide request there costs registers the loop needs).  A column chunk is kBlock packs of
+// one thread's elements: 4 KB in the arithmetic type (4 columns a stage), 2 KB
+// in half (8 columns a stage, so that the per-stage barrier and wait are paid
+// per 16 KB either way).  The copies in flight per CTA set how close a launch
+// comes to the HBM bandwidth: 3 stages (48 KB) at 4 CTAs per SM in the
+// arithmetic type, 4 stages (64 KB) at 3 CTAs per SM in half.
 constexpr int kRingBytes = 48 * 1024;
 template <typename T, bool HB> struct Ring {
     static constexpr int col_bytes = kBlock * (int)sizeof(typename Bstore<T, HB>::pack);
     static constexpr int cols = 16 * 1024 / col_bytes;
-    static constexpr int stages = kRingBytes / (cols * col_bytes);
+    static constexpr int stages = HB ? 4 : kRingBytes / (cols * col_bytes);
     // half basis: columns 16 bytes apart beyond their length, so that the 8 rows
     // of one ldmatrix phase (one per column) fall in different banks
     static constexpr int col_stride = col_bytes + (HB ? 16 : 0);
@@ -903,7 +907,7 @@ template <typename T, bool HB> struct Ring {
     static constexpr int ring_bytes = stages * stage_bytes;
 };
 static_assert(Ring<float, false>::cols == 4 && Ring<double, false>::cols == 4 && Ring<float, true>::cols == 8 &&
-                  Ring<float, true>::stages == 3 && Ring<float, false>::stages == 3,
+                  Ring<float, true>::stages == 4 && Ring<float, false>::stages == 3,
               "ring geometry");
 
 template <typename T, bool HB>
@@ -942,7 +946,19 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
     const char* colbase = reinterpret_cast<const char*>(P.M) +
                           ((long long)kstart * P.ld + (long long)chunk * chunk_rows<T>()) * (long long)BS::ebytes;
     const long long colstride = P.ld * (long long)BS::ebytes;
-    auto issue = [&](int b) {          // thread 0: batch b into stage b % kRing
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // warp 0: batch b into stage b % kRing; lane 0 arms the stage's barrier,
+    // lanes 0..nv-1 copy one column each
+    auto issue = [&](int b) {
+        const int k = b * kRingCols;
+        const int nv = min(kRingCols, K - kstart - k);
+        unsigned long long* bar = &full[b % kRing];
+        unsigned char* dst = smraw2 + (b % kRing) * kStageBytes;
+        if (lane == 0) mbar_expect_tx(bar, (unsigned)(nv * kColBytes));
+        __syncwarp();
+        if (lane < nv) bulk_g2s(dst + lane * kColStride, colbase + (k + lane) * colstride, kColBytes, bar);
+    };
+    auto issue_one = [&](int b) {      // thread 0 alone: batch b into stage b % kRing
         const int k = b * kRingCols;
         const int nv = min(kRingCols, K - kstart - k);
         unsigned long long* bar = &full[b % kRing];
@@ -956,9 +972,12 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
     const int npre = min(kRing, nbat);   // every stage is in flight before the prologue's own loads
     int early = 0;
     while (early < npre && kstart + (early + 1) * kRingCols <= K - 1) ++early;
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < kRing; ++q) mbar_init(&full[q], 1);
-        mbar_init_fence();
+    if (wid == 0) {
+        if (lane == 0) {
+            for (int q = 0; q < kRing; ++q) mbar_init(&full[q], 1);
+            mbar_init_fence();
+        }
+        __syncwarp();
         for (int b = 0; b < early; ++b) issue(b);
     }
     pdl_wait();
@@ -972,7 +991,7 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
     // columns, u, and z = A u (written; reads eps) when there is a next step
     count_bytes(a, DDG_K_DOTS, (double)chunk_rows<T>() * ((double)(hz ? K : i) * BS::ebytes + 2.0 * sizeof(V) +
                                                          (hz ? (double)sizeof(T) : 0.0)));
-    if (threadIdx.x == 0)
+    if (wid == 0)
         for (int b = early; b < npre; ++b) issue(b);
     V u[VEC], z[VEC];
     unpack(reinterpret_cast<const PK*>(P.w[0])[p0], u);
@@ -1003,7 +1022,6 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
 #pragma unroll
         for (int q = 0; q < VEC; ++q) z[q] = mk((T)0, (T)0);
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __shared__ T smt[kWarps];
     // partial sums stay in the Krylov precision until the last CTA
     V* part = reinterpret_cast<V*>(P.part) + (long long)chunk * a.KP;
@@ -1019,9 +1037,12 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
         static_assert(VEC == 2 && kRingCols == 8 && chunk_rows<T>() == 64 * kWarps, "tensor-core tile shape");
         // split components 0 (hi) and 2 (lo) of z and u per row, once, by the
         // thread that holds the row; components 1 and 3 are their (Im, -Re) swaps
-        __shared__ unsigned zsplit[4][kBlock * VEC];   // [z hi, z lo, u hi, u lo]
-        __shared__ float redm[kWarps][32][8];
+        // (zsplit shares its space with redm: the fragments are read before the
+        // first barrier of the stage loop, redm is written after it)
+        __shared__ __align__(16) float redm[kWarps][32][8];
         __shared__ float comb[32][8];
+        static_assert(sizeof(redm) == 4 * kBlock * VEC * sizeof(unsigned), "zsplit fits redm");
+        auto zsplit = reinterpret_cast<unsigned (*)[kBlock * VEC]>(&redm[0][0][0]);   // [z hi, z lo, u hi, u lo]
 #pragma unroll
         for (int q = 0; q < VEC; ++q) {
             const int r = threadIdx.x * VEC + q;
@@ -1050,7 +1071,7 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
             __syncthreads();               // stage (b - 1) % kRing has been read by every warp
             if (threadIdx.x == 0 && b >= 1 && b + kRing - 1 < nbat) {
                 fence_proxy_async_smem();
-                issue(b + kRing - 1);
+                issue_one(b + kRing - 1);
             }
             if (!mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u)) ok = false;
             const unsigned sbase = smem_u32(smraw2 + (b % kRing) * kStageBytes);
@@ -1101,7 +1122,7 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
         __syncthreads();               // stage (b - 1) % kRing has been read by every warp
         if (threadIdx.x == 0 && b >= 1 && b + kRing - 1 < nbat) {
             fence_proxy_async_smem();
-            issue(b + kRing - 1);
+            issue_one(b + kRing - 1);
         }
         if (!mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u)) ok = false;
         const BP* stg = reinterpret_cast<const BP*>(smraw2 + (b % kRing) * (kRingCols * kColBytes));
