@@ -59,3 +59,14 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     g = binding.ddg_grid(2, 2, 1e-8, 1.55e-6, 0, 0, 3.0, 1e-8)
     h = ctypes.c_void_p()
     assert L.fdfd_operator(ctypes.byref(g), ctypes.c_void_p(16), ctypes.byref(h), None) == 1
+
+
+def test_context_setters_reject_null_and_bad_kinds(lib):
+    # the context options added for the data-free baseline and the basis storage
+    L = binding.load()
+    assert L.ddg_context_set_preconditioner(None, 1) == 1
+    assert b"ddg_context_set_preconditioner" in L.ddg_last_error()
+    assert L.ddg_context_set_basis_storage(None, 1) == 1
+    assert L.ddg_context_set_graphs(None, 1) == 1
+    with pytest.raises(KeyError):
+        binding.Context.set_preconditioner(object.__new__(binding.Context), "ilu")
