@@ -56,6 +56,8 @@ def parse():
                    help="extra CNN input: the field of the unpatterned background (one solve per grid)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-queue", action="store_true",
+                   help="skip the solve-queue line (uneven grids, autotuned group width and lanes)")
     p.add_argument("--graphs", default="on", choices=["on", "off"],
                    help="run each restart cycle's Arnoldi steps as one CUDA graph launch")
     p.add_argument("--basis", default="f16", choices=["f32", "f16"],
@@ -342,6 +344,50 @@ def run_ours(args, rank, world):
     recycle = {"value": rsolved / (rms / 1e3), "unit": "solves/s", "ms_per_step": rms / max(1, K // 2),
                "batch": n_traj, "sequential_steps": 16, **summary(rinf)}
 
+    # --- solve queue: the batched-solves workload in small (uneven grids, one
+    # design trajectory of 16 steps per size), plain GMRES, group width and
+    # lanes chosen by the autotuner on the same 64 solves
+    queue = None
+    if not args.no_queue:
+        from paper_1902_00090_gb300 import autotune, inputs
+        qops, qbs = [], []
+        for t, (nx, ny) in enumerate([(128, 128), (192, 192), (256, 256), (384, 256)]):
+            gq = inputs.grid_for(nx, ny)
+            for e in inputs.trajectory_eps(gq, 4, t):
+                qops.append(ddg.fdfd_operator(gq, torch.as_tensor(e, device=dev)))
+                qbs.append(ddg.fdfd_source(qops[-1], gq.i_src, gq.sigma_src, gq.j_src))
+        lanes = []
+        for _ in range(2):
+            c = ddg.Context()
+            c.set_graphs(args.graphs == "on")
+            c.set_basis_storage(args.basis)
+            lanes.append(c)
+        qkw = dict(tol=1e-6, restart=args.restart, maxit=20000, precision=args.precision)
+        # warm-up: each lane's workspace at its largest group
+        ddg.gmres_solve_queue(lanes[:1], qops, qbs, width=64, **qkw)
+        ddg.gmres_solve_queue(lanes, qops, qbs, width=32, **qkw)
+        tune = autotune.tune_queue(lanes, qops, qbs, sample=64, widths=(16, 32, 64), lane_counts=(1, 2),
+                                   basis=args.basis, **qkw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, qinf, _ = ddg.gmres_solve_queue(lanes[:tune["lanes"]], qops, qbs, width=tune["width"], **qkw)
+        torch.cuda.synchronize()
+        qdt = time.perf_counter() - t0
+        single = [t[2] for t in tune["timings"] if t[0] == 64 and t[1] == 1]
+        queue = {"workload": "64 plain GMRES(200) solves, 16 each of 128x128, 192x192, 256x256, 384x256 "
+                             "(one design trajectory per size, queue in that order), c64 + FP64 refinement to 1e-6",
+                 "value": round(sum(i["converged"] for i in qinf) / qdt, 2), "unit": "solves/s",
+                 "tuned": {"width": tune["width"], "lanes": tune["lanes"]},
+                 "single_batch_value": round(single[0], 2) if single else None,
+                 "tuning": [{"width": w, "lanes": l, "solves_per_s": round(v, 2)} for w, l, v in tune["timings"]],
+                 "iters_mean": float(np.mean([i["iters"] for i in qinf])),
+                 "iters_max": int(max(i["iters"] for i in qinf)),
+                 "converged": int(sum(i["converged"] for i in qinf)),
+                 "worst_true_rel_residual": float(max(i["true_rel_residual"] for i in qinf))}
+        for c in lanes:
+            c.close()
+        del qops, qbs
+
     # --- roofline of the dominant kernel class (live CUDA events, algorithmic bytes)
     peaks = {}
     try:
@@ -397,6 +443,7 @@ def run_ours(args, rank, world):
         "plain": plain,
         "cnn_recycle": recycle,
         "plain_jacobi": plain_jacobi,
+        "queue": queue,
         "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
         "pca_speedup_vs_plain": round(pca["value"] / plain["value"], 3) if plain else None,
         "solve_training_fields_s": round(solve_train_s, 2),

@@ -255,6 +255,32 @@ ddg_status augmented_gmres_solve_batched(ddg_context* ctx, int n, const ddg_op* 
                                          void* stream);
 
 /*
+ * gmres_solve_queue -- a queue of n independent solves (the batched-solves
+ * workload: hundreds of correlated solves on uneven grids) run as groups of
+ * `width` consecutive solves, each group one batched solve
+ * (augmented_gmres_solve_batched when U is not NULL, else gmres_solve_batched).
+ * `nlanes` lanes work at once, lane l with context lanes[l] and stream
+ * streams[l] on its own host thread; a lane takes the next group as soon as its
+ * previous group has finished, so one group's slowest solves run beside the
+ * next group's.  Which width and how many lanes suit a workload is found by
+ * timing (the package's autotuner).  Returns when every solve has finished.
+ *   lanes    (host) nlanes distinct contexts, 1 <= nlanes <= 8; their options
+ *            (precision of the basis, graphs, preconditioner) apply per group.
+ *   streams  (host) nlanes streams (distinct when not NULL; NULL entries = the
+ *            legacy default stream), or NULL for all.
+ *   width    >= 1 solves per group.
+ *   A, b, U, x, info: as the batched forms (n entries; U may be NULL).
+ * Returns DDG_ENOCONV if any solve missed the tolerance; on any other error
+ * the lanes stop taking groups and the first error is returned (solves of
+ * groups never taken keep their x and info untouched).
+ */
+ddg_status gmres_solve_queue(ddg_context* const* lanes, void* const* streams, int nlanes,
+                             int width, int n, const ddg_op* const* A,
+                             const double* const* b, const double* const* U, int k,
+                             double* const* x, double tol, int restart, int maxit,
+                             ddg_precision prec, ddg_info* info);
+
+/*
  * pca_fit -- principal components of training fields (Sec. III, "Principal
  * component analysis": an incomplete SVD of the matrix whose columns are the
  * training fields; uncentred, no normalisation).  U receives the k leading left

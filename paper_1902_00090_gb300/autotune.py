@@ -1,0 +1,116 @@
+"""Autotuner for the solve queue (`gmres_solve_queue`): how many solves one
+batched launch covers (the group width) and how many lanes run groups at once.
+
+Wide groups fill the GPU with fewer, larger launches, but a group holds its
+lane until its slowest solve has converged; a second lane lets the next group
+run beside those last solves.  Which balance is best depends on the grid-size
+mix, the subspace size and the precision, so it is measured: every candidate
+(width, lanes) solves the same sample of the workload (drawn from every grid
+size in proportion, so the size mix is kept), the fastest in converged solves
+per second wins, and the choice is cached in a JSON file keyed by the
+workload.  Widths above the sample size are not tried.
+"""
+from __future__ import annotations
+
+import collections
+import json
+import os
+import time
+
+
+def workload_key(A, k: int, precision: str, basis: str) -> str:
+    """Cache key: precision, basis storage, subspace size and the grid-size mix."""
+    mix = sorted(collections.Counter((a.nx, a.ny) for a in A).items())
+    return f"{precision}|{basis}|k{k}|" + ",".join(f"{nx}x{ny}:{c}" for (nx, ny), c in mix)
+
+
+def candidates(n: int, widths=(16, 32, 64, 128, 256), lanes=(1, 2)):
+    """(width, lanes) pairs worth timing on a sample of n solves: a width no
+    larger than the sample, and more lanes only when there are that many groups."""
+    out = []
+    for w in widths:
+        if w > n:
+            continue
+        for nl in lanes:
+            if nl == 1 or (n + w - 1) // w >= nl:
+                out.append((w, nl))
+    if not out:
+        out.append((n, 1))
+    return out
+
+
+def choose(timings):
+    """timings: list of (width, lanes, solves_per_s).  The fastest wins; within
+    1 % of it, fewer lanes and then the wider group (less host work)."""
+    best = max(t[2] for t in timings)
+    near = [t for t in timings if t[2] >= 0.99 * best]
+    near.sort(key=lambda t: (t[1], -t[0]))
+    return near[0]
+
+
+def sample_indices(A, m: int):
+    """About m solves of the queue A with its grid-size mix: each size class
+    contributes in proportion to its count, its solves spread evenly over the
+    class in queue order; returned in queue order."""
+    n = len(A)
+    if m >= n:
+        return list(range(n))
+    classes = collections.defaultdict(list)
+    for i, a in enumerate(A):
+        classes[(a.nx, a.ny)].append(i)
+    out = []
+    for members in classes.values():
+        c = max(1, round(m * len(members) / n))
+        out += [members[int(j * len(members) / c)] for j in range(c)]
+    return sorted(out)
+
+
+def _run_queue(lanes, A, b, U, width, nl, tol, restart, maxit, precision):
+    """Default runner: solves the sample through the library; converged solves per second."""
+    import torch
+    from . import binding
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, infos, _ = binding.gmres_solve_queue(lanes[:nl], A, b, U=U, width=width, tol=tol, restart=restart,
+                                            maxit=maxit, precision=precision)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return sum(1 for i in infos if i["converged"]) / dt
+
+
+def tune_queue(lanes, A, b, U=None, sample: int = 64, widths=(16, 32, 64, 128, 256), lane_counts=(1, 2),
+               tol=1e-6, restart=200, maxit=5000, precision="c64", basis="f16", cache_path=None, run=None):
+    """Returns {"width", "lanes", "solves_per_s", "timings", "key", "cached"}.
+
+    lanes: pre-configured Contexts (at least max(lane_counts)); the first nl of
+    them serve a candidate with nl lanes.  run(lanes, A, b, U, width, nl, tol,
+    restart, maxit, precision) -> converged solves/s may replace the default
+    runner (the library itself).
+    """
+    k = 0 if U is None else int(U[0].shape[0])
+    key = workload_key(A, k, precision, basis)
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+        if key in cache:
+            return dict(cache[key], key=key, cached=True)
+    if len(lanes) < max(lane_counts):
+        raise ValueError(f"{len(lanes)} contexts for up to {max(lane_counts)} lanes")
+    idx = sample_indices(A, sample)
+    As = [A[i] for i in idx]
+    bs = [b[i] for i in idx]
+    Us = None if U is None else [U[i] for i in idx]
+    run = run or _run_queue
+    timings = []
+    for w, nl in candidates(len(idx), widths, lane_counts):
+        timings.append((w, nl, float(run(lanes, As, bs, Us, w, nl, tol, restart, maxit, precision))))
+    w, nl, v = choose(timings)
+    res = {"width": w, "lanes": nl, "solves_per_s": v, "timings": timings}
+    if cache_path:
+        cache[key] = res
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+    return dict(res, key=key, cached=False)

@@ -107,6 +107,10 @@ _SIGS = {
                                                 C.POINTER(_vp), C.c_int, C.POINTER(_vp),
                                                 C.c_double, C.c_int, C.c_int, C.c_int,
                                                 C.POINTER(ddg_info), _vp]),
+    "gmres_solve_queue": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, C.c_int, C.c_int,
+                                    C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.c_int,
+                                    C.POINTER(_vp), C.c_double, C.c_int, C.c_int, C.c_int,
+                                    C.POINTER(ddg_info)]),
 }
 
 
@@ -398,6 +402,46 @@ def augmented_gmres_solve_batched(ctx: Context, A, b, U, x=None, tol=1e-6, resta
         _prec(precision), infos, _stream(stream))
     if st not in (0, 4):
         _check(st, "augmented_gmres_solve_batched")
+    return x, [i.as_dict() for i in infos], st
+
+
+def gmres_solve_queue(lanes, A, b, U=None, x=None, width=64, streams=None, tol=1e-6, restart=200,
+                      maxit=5000, precision="c64"):
+    """A queue of independent solves (A, b, x, U: lists, one entry per solve; U
+    entries (k, D) or U None for plain GMRES) run as groups of `width` batched
+    solves on len(lanes) concurrent lanes (distinct Contexts; one CUDA stream
+    per lane, made here when `streams` is None).  Returns (x list, info list,
+    status).  The call returns once every solve has finished."""
+    torch = _torch()
+    n = len(A)
+    nl = len(lanes)
+    if x is None:
+        x = [torch.zeros_like(bb) for bb in b]
+    if streams is None:
+        streams = [torch.cuda.Stream() for _ in range(nl)]
+    if len(streams) != nl:
+        raise ValueError(f"{len(streams)} streams for {nl} lanes")
+    # the lanes' streams start after the work queued so far on the current stream
+    cur = torch.cuda.current_stream()
+    for s in streams:
+        s.wait_stream(cur)
+    sizes = [a.D for a in A]
+    ha = (_vp * n)(*[a.handle.value for a in A])
+    hl = (_vp * nl)(*[c.handle.value for c in lanes])
+    hs = (_vp * nl)(*[s.cuda_stream for s in streams])
+    k = 0
+    hu = None
+    if U is not None:
+        k = U[0].shape[0]
+        hu = _ptr_array(U, torch.complex128, "U", [k * sz for sz in sizes])
+    infos = (ddg_info * n)()
+    st = load().gmres_solve_queue(hl, hs, nl, int(width), n, ha, _ptr_array(b, torch.complex128, "b", sizes),
+                                  hu, int(k), _ptr_array(x, torch.complex128, "x", sizes), float(tol),
+                                  int(restart), int(maxit), _prec(precision), infos)
+    for s in streams:
+        cur.wait_stream(s)
+    if st not in (0, 4):
+        _check(st, "gmres_solve_queue")
     return x, [i.as_dict() for i in infos], st
 
 

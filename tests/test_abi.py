@@ -70,3 +70,14 @@ def test_context_setters_reject_null_and_bad_kinds(lib):
     assert L.ddg_context_set_graphs(None, 1) == 1
     with pytest.raises(KeyError):
         binding.Context.set_preconditioner(object.__new__(binding.Context), "ilu")
+
+
+def test_queue_rejects_bad_lanes_before_any_cuda_call(lib):
+    L = binding.load()
+    assert L.gmres_solve_queue(None, None, 1, 8, 1, None, None, None, 0, None, 1e-6, 10, 10, 1, None) == 1
+    assert b"gmres_solve_queue" in L.ddg_last_error()
+    two = (ctypes.c_void_p * 2)(16, 16)   # the same context twice
+    A = (ctypes.c_void_p * 1)(16)
+    assert L.gmres_solve_queue(two, None, 2, 8, 1, A, A, None, 0, A, 1e-6, 10, 10, 1, None) == 1
+    assert b"share a context" in L.ddg_last_error()
+    assert L.gmres_solve_queue(two, None, 9, 8, 1, A, A, None, 0, A, 1e-6, 10, 10, 1, None) == 1

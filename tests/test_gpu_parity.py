@@ -512,3 +512,34 @@ def test_jacobi_preconditioner_matches_oracle(prec):
     xa, ia, sta = ddg.augmented_gmres_solve(c, op, dev(b), dev(V), tol=tol, restart=25, maxit=20000, precision=prec)
     assert sta == 0 and ia["converged"]
     assert np.linalg.norm(b - A @ host(xa)) / np.linalg.norm(b) <= tol
+
+
+@pytest.mark.parametrize("augmented", [False, True])
+def test_solve_queue_matches_one_batched_call(augmented):
+    # groups of 2 solves on 2 lanes (3 groups, each lane its own context,
+    # stream and host thread): every solve bitwise equal to the same solve in
+    # one batched call, with the same step count
+    specs = [(16, 3, 0), (37, 5, 1), (64, 8, 2), (24, 4, 3), (16, 3, 4), (30, 4, 5)]
+    ops, bs = [], []
+    for n, L, seed in specs:
+        g = inputs.Grid(nx=n, ny=n + 3, npml=L, i_src=2 * L, sigma_src=n / 8, slab_cells=2)
+        rng = np.random.default_rng(seed)
+        eps = inputs.background_eps(g) + rng.random((g.ny, g.nx))
+        ops.append(ddg.fdfd_operator(g, dev(eps, torch.float64)))
+        bs.append(ddg.fdfd_source(ops[-1], g.i_src, g.sigma_src, g.j_src))
+    U = [dev(inputs.random_complex(o.D, 10 + s, shape=(3, o.D))) for s, o in enumerate(ops)] if augmented else None
+    lanes = [ddg.Context(), ddg.Context()]
+    xq, iq, stq = ddg.gmres_solve_queue(lanes, ops, bs, U=U, width=2, tol=1e-8, restart=40, precision="c64")
+    one = ddg.Context()
+    if augmented:
+        xb, ib, stb = ddg.augmented_gmres_solve_batched(one, ops, bs, U, tol=1e-8, restart=40, precision="c64")
+    else:
+        xb, ib, stb = ddg.gmres_solve_batched(one, ops, bs, tol=1e-8, restart=40, precision="c64")
+    assert stq == 0 and stb == 0
+    for s in range(len(specs)):
+        assert iq[s]["iters"] == ib[s]["iters"] and iq[s]["converged"]
+        assert np.array_equal(host(xq[s]), host(xb[s]))
+    # a cap that no solve meets: every info filled, status DDG_ENOCONV
+    xc, ic, stc = ddg.gmres_solve_queue(lanes, ops, bs, U=U, width=4, tol=1e-12, restart=10, maxit=5,
+                                        precision="c64")
+    assert stc == 4 and all(0 < i["iters"] <= 5 and not i["converged"] for i in ic)
