@@ -255,8 +255,9 @@ ddg_status augmented_gmres_solve_batched(ddg_context* ctx, int n, const ddg_op* 
                                          void* stream);
 
 /*
- * gmres_solve_queue -- a queue of n independent solves (the batched-solves
- * workload: hundreds of correlated solves on uneven grids) run as groups of
+ * gmres_solve_queue -- a queue of n independent solves of Eq. 2 / Eqs. 3-4
+ * (the paper is silent on batching; library plumbing for workloads of hundreds
+ * of correlated solves on uneven grids) run as groups of
  * `width` consecutive solves, each group one batched solve
  * (augmented_gmres_solve_batched when U is not NULL, else gmres_solve_batched).
  * `nlanes` lanes work at once, lane l with context lanes[l] and stream
