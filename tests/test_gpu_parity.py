@@ -543,3 +543,24 @@ def test_solve_queue_matches_one_batched_call(augmented):
     xc, ic, stc = ddg.gmres_solve_queue(lanes, ops, bs, U=U, width=4, tol=1e-12, restart=10, maxit=5,
                                         precision="c64")
     assert stc == 4 and all(0 < i["iters"] <= 5 and not i["converged"] for i in ic)
+
+
+def test_autotuner_times_the_library_and_picks_a_measured_candidate(tmp_path):
+    from paper_1902_00090_gb300 import autotune
+    specs = [(16, 3, 0), (24, 4, 1), (16, 3, 2), (24, 4, 3)]
+    ops, bs = [], []
+    for n, L, seed in specs:
+        g = inputs.Grid(nx=n, ny=n, npml=L, i_src=2 * L, sigma_src=n / 8, slab_cells=2)
+        eps = inputs.background_eps(g) + np.random.default_rng(seed).random((g.ny, g.nx))
+        ops.append(ddg.fdfd_operator(g, dev(eps, torch.float64)))
+        bs.append(ddg.fdfd_source(ops[-1], g.i_src, g.sigma_src, g.j_src))
+    lanes = [ddg.Context(), ddg.Context()]
+    cache = str(tmp_path / "tune.json")
+    r = autotune.tune_queue(lanes, ops, bs, sample=4, widths=(1, 2, 4), tol=1e-8, restart=30,
+                            precision="c64", basis="f32", cache_path=cache)
+    assert not r["cached"] and r["solves_per_s"] > 0
+    assert (r["width"], r["lanes"]) in [(w, l) for w, l, _ in r["timings"]]
+    assert len(r["timings"]) == 5 and all(v > 0 for _, _, v in r["timings"])
+    r2 = autotune.tune_queue(lanes, ops, bs, sample=4, widths=(1, 2, 4), tol=1e-8, restart=30,
+                             precision="c64", basis="f32", cache_path=cache)
+    assert r2["cached"] and (r2["width"], r2["lanes"]) == (r["width"], r["lanes"])
