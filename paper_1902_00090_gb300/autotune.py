@@ -3,7 +3,9 @@ batched launch covers (the group width) and how many lanes run groups at once.
 
 Wide groups fill the GPU with fewer, larger launches, but a group holds its
 lane until its slowest solve has converged; a second lane lets the next group
-run beside those last solves.  Which balance is best depends on the grid-size
+run beside those last solves.  Optionally the restart length is tuned too (no
+longer than the one asked for): a shorter cycle costs less per step (the
+basis grows quadratically per cycle) but may take more steps.  Which balance is best depends on the grid-size
 mix, the subspace size and the precision, so it is measured: every candidate
 (width, lanes) solves the same sample of the workload (drawn from every grid
 size in proportion, so the size mix is kept), the fastest in converged solves
@@ -40,11 +42,12 @@ def candidates(n: int, widths=(16, 32, 64, 128, 256), lanes=(1, 2)):
 
 
 def choose(timings):
-    """timings: list of (width, lanes, solves_per_s).  The fastest wins; within
-    1 % of it, fewer lanes and then the wider group (less host work)."""
+    """timings: list of (width, lanes, solves_per_s[, restart]).  The fastest
+    wins; within 1 % of it, fewer lanes, then the wider group (less host work),
+    then the longer restart."""
     best = max(t[2] for t in timings)
     near = [t for t in timings if t[2] >= 0.99 * best]
-    near.sort(key=lambda t: (t[1], -t[0]))
+    near.sort(key=lambda t: (t[1], -t[0], -(t[3] if len(t) > 3 else 0)))
     return near[0]
 
 
@@ -79,16 +82,23 @@ def _run_queue(lanes, A, b, U, width, nl, tol, restart, maxit, precision):
 
 
 def tune_queue(lanes, A, b, U=None, sample: int = 64, widths=(16, 32, 64, 128, 256), lane_counts=(1, 2),
-               tol=1e-6, restart=200, maxit=5000, precision="c64", basis="f16", cache_path=None, run=None):
-    """Returns {"width", "lanes", "solves_per_s", "timings", "key", "cached"}.
+               tol=1e-6, restart=200, maxit=5000, precision="c64", basis="f16", cache_path=None, run=None,
+               restarts=None):
+    """Returns {"width", "lanes", "restart", "solves_per_s", "timings", "key", "cached"}.
 
     lanes: pre-configured Contexts (at least max(lane_counts)); the first nl of
-    them serve a candidate with nl lanes.  run(lanes, A, b, U, width, nl, tol,
-    restart, maxit, precision) -> converged solves/s may replace the default
-    runner (the library itself).
+    them serve a candidate with nl lanes.  restarts: restart lengths to try as
+    well (each at most `restart`); None keeps `restart`.  run(lanes, A, b, U,
+    width, nl, tol, restart, maxit, precision) -> converged solves/s may
+    replace the default runner (the library itself).
     """
     k = 0 if U is None else int(U[0].shape[0])
+    ms = sorted({int(m) for m in restarts if 1 <= int(m) <= restart}) if restarts else [int(restart)]
+    if not ms:
+        raise ValueError(f"no restart length in {restarts} is within [1, {restart}]")
     key = workload_key(A, k, precision, basis)
+    if restarts:
+        key += f"|tol{tol:g}|m" + ",".join(str(m) for m in ms)
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
@@ -103,10 +113,15 @@ def tune_queue(lanes, A, b, U=None, sample: int = 64, widths=(16, 32, 64, 128, 2
     Us = None if U is None else [U[i] for i in idx]
     run = run or _run_queue
     timings = []
-    for w, nl in candidates(len(idx), widths, lane_counts):
-        timings.append((w, nl, float(run(lanes, As, bs, Us, w, nl, tol, restart, maxit, precision))))
-    w, nl, v = choose(timings)
-    res = {"width": w, "lanes": nl, "solves_per_s": v, "timings": timings}
+    for m in ms:
+        for w, nl in candidates(len(idx), widths, lane_counts):
+            t = (w, nl, float(run(lanes, As, bs, Us, w, nl, tol, m, maxit, precision)))
+            # (width, lanes, solves/s), with the restart length appended when it is tuned
+            timings.append(t + (m,) if restarts else t)
+    best = choose(timings)
+    w, nl, v = best[:3]
+    res = {"width": w, "lanes": nl, "restart": best[3] if restarts else int(restart), "solves_per_s": v,
+           "timings": timings}
     if cache_path:
         cache[key] = res
         tmp = cache_path + ".tmp"

@@ -58,3 +58,23 @@ def test_tune_times_every_candidate_once_and_caches(tmp_path):
     assert r["key"] in stored and stored[r["key"]]["width"] == 16
     r2 = autotune.tune_queue(["c0", "c1"], A, b, sample=64, widths=(16, 32, 64), cache_path=cache, run=run)
     assert r2["cached"] and (r2["width"], r2["lanes"]) == (16, 2) and len(calls) == 5
+
+
+def test_tune_restart_lengths_too(tmp_path):
+    A = [Op(128, 128)] * 32
+    b = list(range(32))
+    seen = []
+
+    def run(lanes, As, bs, Us, w, nl, tol, m, maxit, prec):
+        seen.append((w, nl, m))
+        return {100: 10.0, 150: 12.0, 200: 11.0}[m] + (0.5 if (w, nl) == (16, 2) else 0.0)
+
+    r = autotune.tune_queue(["c0", "c1"], A, b, sample=32, widths=(16, 32), restarts=(100, 150, 200, 300),
+                            restart=200, run=run, cache_path=str(tmp_path / "t.json"))
+    # 300 is above the restart asked for: not tried
+    assert sorted({m for _, _, m in seen}) == [100, 150, 200]
+    assert (r["width"], r["lanes"], r["restart"]) == (16, 2, 150)
+    assert all(len(t) == 4 for t in r["timings"]) and "|m100,150,200" in r["key"]
+    # without restart candidates the timings keep their three fields and the given restart
+    r2 = autotune.tune_queue(["c0", "c1"], A, b, sample=32, widths=(16,), restart=150, run=run)
+    assert all(len(t) == 3 for t in r2["timings"]) and r2["restart"] == 150
