@@ -40,7 +40,8 @@ typedef enum {
     DDG_ENOCONV = 4,     /* iteration cap reached before the tolerance; x holds the best iterate */
     DDG_EBREAKDOWN = 5,  /* reserved: unrecoverable Arnoldi breakdown */
     DDG_ETIMEOUT = 6,    /* a bounded device wait gave up (a bulk copy into shared memory did not
-                            complete within 1 s); the solve's outputs are not valid */
+                            complete within the wait limit, 1 s by default); the solve's outputs
+                            are not valid */
     DDG_ESINGULAR = 7    /* a small dense factorisation failed */
 } ddg_status;
 
@@ -169,6 +170,21 @@ ddg_status ddg_context_set_fallback(ddg_context* ctx, double threshold);
    method for the first cycle); 0 keeps only the least-squares step over V;
    a value >= maxit keeps V in every cycle. */
 ddg_status ddg_context_set_augmented_cycles(ddg_context* ctx, int cycles);
+/* Limit of the bounded device waits of the solver (no paper counterpart): an
+   Arnoldi kernel waits at most `ns` nanoseconds for a bulk copy of basis
+   columns into shared memory (default 1e9, 1 s).  A wait that runs out stops
+   that block's reduction; the block still waits for the copies it issued, at
+   the 1 s default, before it exits, and the call returns DDG_ETIMEOUT (the
+   solve's outputs are not valid; the context stays usable).  A limit of 0
+   tests each copy once without waiting, so that waits run out on purpose
+   (which exercises that path).
+   0 <= ns <= 1e10, else DDG_EINVAL. */
+ddg_status ddg_context_set_wait_limit(ddg_context* ctx, long long ns);
+/* Largest device workspace the context may hold, in bytes (0, the default:
+   no limit).  A call that needs more returns DDG_ENOMEM without allocating
+   (and a workspace above a new limit is freed at once).  Serves callers with
+   a memory budget, and makes the allocation-failure path testable. */
+ddg_status ddg_context_set_workspace_limit(ddg_context* ctx, long long bytes);
 /* Inner-cycle relative tolerance for DDG_C64_REFINE (a cycle ends once its
    least-squares residual falls below eta times the cycle's starting residual).
    Default 1e-5.  Must be in (0, 1). */
@@ -336,10 +352,23 @@ ddg_status predictor_set_input_field(ddg_predictor* P, const double* f, int nx, 
    and learns permittivity-dependent corrections.  The offset is not trained.
      U  device, D x k complex128 column-major (column c at U + 2 D c), D = nx ny;
         NULL removes the offset.
-   Later calls on another grid size are refused (DDG_EINVAL). */
+   The offset serves every problem of that grid size (one offset per grid
+   size; setting it again replaces it).  A forward, prediction or training
+   call with a problem of a grid size that has no offset, while any offset is
+   set, is refused (DDG_EINVAL).  U = NULL removes every offset. */
 ddg_status predictor_set_output_base(ddg_predictor* P, const double* U, int nx, int ny, double scale, void* stream);
+/* predictor_set_output_base_wavelength -- as predictor_set_output_base, for
+   the problems of this grid at one vacuum wavelength (metres, > 0; matched to
+   1e-9 relative).  A problem takes the offset of its grid and wavelength if
+   there is one, else its grid's offset for every wavelength.  Serves one
+   network conditioned on the wavelength with a data-derived basis per
+   wavelength (the fields of one device at two wavelengths differ). */
+ddg_status predictor_set_output_base_wavelength(ddg_predictor* P, const double* U, int nx, int ny,
+                                                double wavelength, double scale, void* stream);
 ddg_status predictor_destroy(ddg_predictor* P);
 long long predictor_num_params(const ddg_predictor* P);
+/* Number k of predicted complex vectors (0 for NULL). */
+int predictor_num_outputs(const ddg_predictor* P);
 /* Kernels launched by this predictor since it was created. */
 long long predictor_launches(const ddg_predictor* P);
 /* Forward 3x3 convolutions on the tensor cores (no paper counterpart; default
@@ -356,8 +385,14 @@ ddg_status predictor_get_params(const ddg_predictor* P, float* theta, long long 
 /* Raw network output for n problems: y device FP32 [n][ny][nx][2k]. */
 ddg_status predictor_forward(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
                              double j_c, float* y, void* stream);
-/* subspace_predict -- the predicted vectors of each problem: U[s] device, D x k
-   complex128 column-major (ready for augmented_gmres_solve).  Synchronises. */
+/* subspace_predict -- the predicted subspace of each problem, orthonormal:
+   the network's k vectors (with the output offset, as predictor_forward)
+   orthonormalised on the device by Cholesky QR applied twice in FP64
+   (G = V^H V = L L^H, V <- V L^-H), so U[s]^H U[s] = I to FP64 round-off and
+   span U[s] = span of the raw output.  A vector whose Cholesky pivot falls
+   below 1e-13 of the largest (already spanned by the vectors before it) is
+   returned as a zero column.  U[s] device, D x k complex128 column-major
+   (ready for augmented_gmres_solve).  Synchronises. */
 ddg_status subspace_predict(ddg_predictor* P, int n, const ddg_op* const* A, int i_src, double sigma,
                             double j_c, double* const* U, void* stream);
 /* Training loss: 0 = projection loss (Eq. 5), the default: f[s] are solved
@@ -384,6 +419,32 @@ ddg_status predictor_save(const ddg_predictor* P, const char* path);
 ddg_status predictor_load(ddg_predictor* P, const char* path);
 
 /*
+ * fdfd_solve_host -- the path of a user who holds permittivities and wants
+ * fields, from and to HOST memory in one call (Eq. 1 set up, Eqs. 3-4 solved;
+ * no paper counterpart beyond that): for each of n problems the permittivity
+ * is copied to the device, the operator (fdfd_operator) and the source
+ * (fdfd_source) are built, the predicted subspace is computed when P is not
+ * NULL (subspace_predict, then augmented_gmres_solve_batched) or plain GMRES
+ * runs (gmres_solve_batched), and the solution is copied back.
+ *   grids     (host) n problem descriptions (with P: one grid size; the
+ *             wavelengths may differ, e.g. one device at two wavelengths).
+ *   eps_host  (host) n pointers to ny*nx doubles, row-major (pinned memory
+ *             lets the copies run asynchronously).
+ *   i_src, sigma, j_c  the source of every problem, as fdfd_source.
+ *   x_host    (host) n pointers to 2*D doubles: the fields (x0 = 0).
+ *   tol, restart, maxit, prec, info: as the batched solves.
+ * The device copies of eps, b, x and the subspace live in a buffer that the
+ * context keeps and grows (about (8 + 32 + 16 k) D bytes per problem).
+ * Returns the solve's status (DDG_ENOCONV: fields copied back, some solve
+ * missed the tolerance); on other errors x_host is not written.
+ * Synchronises `stream`.
+ */
+ddg_status fdfd_solve_host(ddg_context* ctx, ddg_predictor* P, int n, const ddg_grid* grids,
+                           const double* const* eps_host, int i_src, double sigma, double j_c, double tol,
+                           int restart, int maxit, ddg_precision prec, double* const* x_host, ddg_info* info,
+                           void* stream);
+
+/*
  * gmres_solve_noalloc -- gmres_solve without any device allocation.  (The paper
  * has no counterpart: this is a library convenience.)
  *
@@ -394,8 +455,15 @@ ddg_status predictor_load(ddg_predictor* P, const char* path);
  * entry point needs no ddg_context: its whole workspace lives in one static
  * device array of DDG_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads
  * the library holds until the process exits.  It runs one plain restarted
- * GMRES solve with the same kernels as gmres_solve (delayed
- * reorthogonalisation; for DDG_C64_REFINE the inner tolerance is fixed at 1e-5).
+ * GMRES solve with the same Arnoldi kernels as gmres_solve (delayed
+ * reorthogonalisation).  Supported precisions: DDG_C128 and DDG_C64_REFINE
+ * (DDG_C64_ONLY returns DDG_EINVAL).  Having no context, it takes none of a
+ * context's options: the basis is always stored in the arithmetic type (FP32
+ * for DDG_C64_REFINE), there is no preconditioner, the step loop is launched by
+ * the host, and the DDG_C64_REFINE inner tolerance is fixed at 1e-5.  It polls
+ * the solve's state by synchronising the stream every 16 Arnoldi steps (no
+ * pinned buffer, no events), so it trades some speed against gmres_solve for
+ * having no allocation.
  *   - Sizes whose workspace exceeds the array are rejected with DDG_EINVAL
  *     (about (restart + 4) * D * 8 bytes for DDG_C64_REFINE, twice that for
  *     DDG_C128, plus O(restart^2) bytes: D = 128 x 128 fits restart = 200).
@@ -404,7 +472,7 @@ ddg_status predictor_load(ddg_predictor* P, const char* path);
  *   - Every call shares the array and it keeps the last call's contents (the
  *     call initialises what must start at zero).  Calls that overlap on the GPU
  *     (other streams, other host threads) race on it and must be serialised.
- * Arguments and results as gmres_solve; the caller still owns b, x and A.
+ * Other arguments and results as gmres_solve; the caller still owns b, x and A.
  */
 #define DDG_NOALLOC_SCRATCH_BYTES (32LL << 20)
 ddg_status gmres_solve_noalloc(const ddg_op* A, const double* b, double* x, double tol, int restart,

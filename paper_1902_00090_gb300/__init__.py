@@ -8,6 +8,6 @@ nothing; the first binding call loads the library and raises if it is missing.
 from . import inputs  # noqa: F401
 from .binding import (  # noqa: F401
     Context, DdgError, Operator, augmented_gmres_solve, augmented_gmres_solve_batched, gmres_solve_noalloc,
-    ddg_context_create, fdfd_apply, fdfd_apply_c64, fdfd_operator, fdfd_source, gmres_solve,
+    ddg_context_create, fdfd_apply, fdfd_solve_host, fdfd_apply_c64, fdfd_operator, fdfd_source, gmres_solve,
     gmres_solve_batched, gmres_solve_queue, load, make_grid, pca_fit, Predictor, predictor_create,
 )

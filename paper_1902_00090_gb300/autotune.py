@@ -83,22 +83,26 @@ def _run_queue(lanes, A, b, U, width, nl, tol, restart, maxit, precision):
 
 def tune_queue(lanes, A, b, U=None, sample: int = 64, widths=(16, 32, 64, 128, 256), lane_counts=(1, 2),
                tol=1e-6, restart=200, maxit=5000, precision="c64", basis="f16", cache_path=None, run=None,
-               restarts=None):
+               restarts=None, repeats=2):
     """Returns {"width", "lanes", "restart", "solves_per_s", "timings", "key", "cached"}.
 
     lanes: pre-configured Contexts (at least max(lane_counts)); the first nl of
     them serve a candidate with nl lanes.  restarts: restart lengths to try as
     well (each at most `restart`); None keeps `restart`.  run(lanes, A, b, U,
     width, nl, tol, restart, maxit, precision) -> converged solves/s may
-    replace the default runner (the library itself).
+    replace the default runner (the library itself).  Every candidate is timed
+    `repeats` times and keeps its best rate, so that the 1 % choice rule is
+    not decided by one run's noise (about 2 % from run to run).
     """
     k = 0 if U is None else int(U[0].shape[0])
     ms = sorted({int(m) for m in restarts if 1 <= int(m) <= restart}) if restarts else [int(restart)]
     if not ms:
         raise ValueError(f"no restart length in {restarts} is within [1, {restart}]")
-    key = workload_key(A, k, precision, basis)
-    if restarts:
-        key += f"|tol{tol:g}|m" + ",".join(str(m) for m in ms)
+    if repeats < 1:
+        raise ValueError(f"repeats={repeats} < 1")
+    # the tolerance and the restart lengths tried are always part of the key: a
+    # choice made for GMRES(200) must not answer a call that asks for GMRES(100)
+    key = workload_key(A, k, precision, basis) + f"|tol{tol:g}|m" + ",".join(str(m) for m in ms)
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
@@ -115,7 +119,8 @@ def tune_queue(lanes, A, b, U=None, sample: int = 64, widths=(16, 32, 64, 128, 2
     timings = []
     for m in ms:
         for w, nl in candidates(len(idx), widths, lane_counts):
-            t = (w, nl, float(run(lanes, As, bs, Us, w, nl, tol, m, maxit, precision)))
+            t = (w, nl, max(float(run(lanes, As, bs, Us, w, nl, tol, m, maxit, precision))
+                            for _ in range(repeats)))
             # (width, lanes, solves/s), with the restart length appended when it is tuned
             timings.append(t + (m,) if restarts else t)
     best = choose(timings)

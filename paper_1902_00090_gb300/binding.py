@@ -63,6 +63,8 @@ _SIGS = {
     "ddg_context_set_basis_storage": (C.c_int, [_vp, C.c_int]),
     "ddg_context_set_preconditioner": (C.c_int, [_vp, C.c_int]),
     "ddg_context_set_augmented_cycles": (C.c_int, [_vp, C.c_int]),
+    "ddg_context_set_wait_limit": (C.c_int, [_vp, C.c_longlong]),
+    "ddg_context_set_workspace_limit": (C.c_int, [_vp, C.c_longlong]),
     "ddg_context_profile_enable": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_longlong)]),
@@ -87,6 +89,7 @@ _SIGS = {
     "predictor_create_with_field": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp)]),
     "predictor_set_input_field": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _vp]),
     "predictor_set_output_base": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_double, _vp]),
+    "predictor_set_output_base_wavelength": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_double, _vp]),
     "predictor_set_params": (C.c_int, [_vp, _vp, C.c_longlong]),
     "predictor_get_params": (C.c_int, [_vp, _vp, C.c_longlong]),
     "predictor_forward": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int, C.c_double, C.c_double, _vp, _vp]),
@@ -102,6 +105,10 @@ _SIGS = {
     "predictor_load": (C.c_int, [_vp, C.c_char_p]),
     "gmres_solve_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, C.c_int,
                                       C.POINTER(ddg_info), _vp]),
+    "predictor_num_outputs": (C.c_int, [_vp]),
+    "fdfd_solve_host": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(ddg_grid), C.POINTER(_vp), C.c_int, C.c_double,
+                                  C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(_vp),
+                                  C.POINTER(ddg_info), _vp]),
     "pca_fit": (C.c_int, [_vp, _vp, C.c_longlong, C.c_int, C.c_int, _vp, C.POINTER(C.c_double), _vp]),
     "augmented_gmres_solve_batched": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp),
                                                 C.POINTER(_vp), C.c_int, C.POINTER(_vp),
@@ -203,6 +210,14 @@ class Context:
         """'none' (default) or 'jacobi' (right preconditioner M = diag(A), the data-free baseline)."""
         code = {"none": 0, "jacobi": 1}[kind]
         _check(load().ddg_context_set_preconditioner(self._h, code), "ddg_context_set_preconditioner")
+
+    def set_wait_limit(self, ns: int):
+        """Limit (ns) of the solver's bounded device waits; DDG_ETIMEOUT when one runs out."""
+        _check(load().ddg_context_set_wait_limit(self._h, int(ns)), "ddg_context_set_wait_limit")
+
+    def set_workspace_limit(self, nbytes: int):
+        """Largest device workspace this context may allocate (0: no limit); DDG_ENOMEM above it."""
+        _check(load().ddg_context_set_workspace_limit(self._h, int(nbytes)), "ddg_context_set_workspace_limit")
 
     def set_fallback(self, threshold: float):
         """V-only relative residual above which an augmented solve continues as plain GMRES."""
@@ -474,6 +489,36 @@ def gmres_solve_noalloc(A: Operator, b, x=None, tol=1e-6, restart=200, maxit=500
     return x, info.as_dict(), st
 
 
+def fdfd_solve_host(ctx: Context, grids, eps_host, src, x_host, P=None, tol=1e-6, restart=200, maxit=5000,
+                    precision="c64", stream=None):
+    """fdfd_solve_host: grids (one per problem), eps_host (host float64 arrays or
+    CPU tensors of ny*nx values, ideally pinned), src = (i_src, sigma, j_c),
+    x_host (host complex128 arrays or CPU tensors of D values, written).
+    Returns (info list, status)."""
+    n = len(grids)
+    hg = (ddg_grid * n)(*[make_grid(g) for g in grids])
+
+    def hptr(a, what, itemsize, count):
+        if hasattr(a, "data_ptr"):
+            if a.is_cuda or not a.is_contiguous() or a.element_size() * a.numel() != itemsize * count:
+                raise ValueError(f"{what}: need a contiguous host tensor of {count} values")
+            return a.data_ptr()
+        if not a.flags["C_CONTIGUOUS"] or a.nbytes != itemsize * count:
+            raise ValueError(f"{what}: need a contiguous host array of {count} values")
+        return a.ctypes.data
+
+    he = (_vp * n)(*[hptr(e, f"eps[{i}]", 8, g.nx * g.ny) for i, (e, g) in enumerate(zip(eps_host, hg))])
+    hx = (_vp * n)(*[hptr(x, f"x[{i}]", 16, g.nx * g.ny) for i, (x, g) in enumerate(zip(x_host, hg))])
+    i_src, sigma, j_c = src
+    infos = (ddg_info * n)()
+    st = load().fdfd_solve_host(ctx.handle, P.handle if P is not None else None, n, hg, he, int(i_src),
+                                float(sigma), float(j_c), float(tol), int(restart), int(maxit), _prec(precision),
+                                hx, infos, _stream(stream))
+    if st not in (0, 4):
+        _check(st, "fdfd_solve_host")
+    return [i.as_dict() for i in infos], st
+
+
 def predictor_layer_shapes(channels, k, cin=4):
     """(name, Cout, Cin, kernel) per layer in the library's parameter order."""
     L = len(channels)
@@ -505,16 +550,27 @@ class Predictor:
         self._h = h
         self.nparams = int(load().predictor_num_params(h))
 
-    def set_output_base(self, U, nx, ny, scale=1.0, stream=None):
-        """predictor_set_output_base: U a (k, D) complex128 CUDA tensor (or None to remove)."""
+    def set_output_base(self, U, nx, ny, scale=1.0, wavelength=None, stream=None):
+        """predictor_set_output_base (every wavelength of the grid) or, with a
+        wavelength in metres, predictor_set_output_base_wavelength: U a (k, D)
+        complex128 CUDA tensor, or None to remove every offset."""
         torch = _torch()
         ptr = _vp()
         if U is not None:
             U = U.to(torch.complex128).contiguous()
-            self._base = U
             ptr = _vp(U.data_ptr())
-        _check(load().predictor_set_output_base(self._h, ptr, int(nx), int(ny), float(scale), _stream(stream)),
-               "predictor_set_output_base")
+        if wavelength is None or U is None:
+            _check(load().predictor_set_output_base(self._h, ptr, int(nx), int(ny), float(scale), _stream(stream)),
+                   "predictor_set_output_base")
+        else:
+            _check(load().predictor_set_output_base_wavelength(self._h, ptr, int(nx), int(ny), float(wavelength),
+                                                               float(scale), _stream(stream)),
+                   "predictor_set_output_base_wavelength")
+        if U is not None:
+            # the copy into the predictor is stream-ordered: keep U alive until it ran
+            self._bases = getattr(self, "_bases", []) + [U]
+        else:
+            self._bases = []
 
     def zero_head(self):
         """Sets the 1x1 head's weights and biases to zero (the output is then the output base)."""

@@ -2,6 +2,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "common.cuh"
@@ -36,6 +37,14 @@ ddg_status Context::reserve(size_t bytes, cudaStream_t s) {
         ws_bytes = 0;
     }
     size_t want = bytes + bytes / 8;
+    if (ws_limit) {
+        if (bytes > ws_limit) {
+            set_error("workspace: %zu bytes needed, above the context's limit of %zu bytes "
+                      "(ddg_context_set_workspace_limit)", bytes, ws_limit);
+            return DDG_ENOMEM;
+        }
+        want = std::min(want, ws_limit);
+    }
     cudaError_t e = cudaMalloc(&ws, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -118,6 +127,7 @@ extern "C" ddg_status ddg_context_destroy(ddg_context* ctx) {
     if (!ctx) return DDG_OK;
     Context* c = reinterpret_cast<Context*>(ctx);
     cudaFree(c->ws);
+    cudaFree(c->io);
     cudaFreeHost(c->host_counts);
     if (c->ev[0]) cudaEventDestroy(c->ev[0]);
     if (c->ev[1]) cudaEventDestroy(c->ev[1]);
@@ -200,6 +210,29 @@ extern "C" ddg_status ddg_context_set_preconditioner(ddg_context* ctx, int kind)
 extern "C" ddg_status ddg_context_set_fallback(ddg_context* ctx, double threshold) {
     if (!ctx || !(threshold > 0.0)) { set_error("ddg_context_set_fallback: threshold must be > 0"); return DDG_EINVAL; }
     reinterpret_cast<Context*>(ctx)->fallback = threshold;
+    return DDG_OK;
+}
+
+extern "C" ddg_status ddg_context_set_wait_limit(ddg_context* ctx, long long ns) {
+    if (!ctx || ns < 0 || ns > 10000000000LL) {
+        set_error("ddg_context_set_wait_limit: need 0 <= ns <= 1e10");
+        return DDG_EINVAL;
+    }
+    reinterpret_cast<Context*>(ctx)->wait_ns = (unsigned long long)ns;
+    return DDG_OK;
+}
+
+extern "C" ddg_status ddg_context_set_workspace_limit(ddg_context* ctx, long long bytes) {
+    if (!ctx || bytes < 0) { set_error("ddg_context_set_workspace_limit: need bytes >= 0"); return DDG_EINVAL; }
+    Context* c = reinterpret_cast<Context*>(ctx);
+    c->ws_limit = (size_t)bytes;
+    if (bytes && c->ws_bytes > (size_t)bytes) {
+        // give back a workspace above the new limit (the next call allocates within it)
+        DDG_CHECK_CUDA(cudaDeviceSynchronize());
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+    }
     return DDG_OK;
 }
 

@@ -53,10 +53,26 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// Whether the phase of `bar` with parity `parity` has completed (no waiting).
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Waits until the phase of `bar` with parity `parity` has completed.  Gives
-// up after `limit_ns` nanoseconds and returns false.
+// up after `limit_ns` nanoseconds and returns false; a limit of 0 tests once
+// without waiting (mbarrier.try_wait itself suspends the thread for a while,
+// so a short limit could otherwise never run out).
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
                                           unsigned long long limit_ns = 1000000000ull) {
+    if (limit_ns == 0) return mbar_test(bar, parity);
     const unsigned a = smem_u32(bar);
     unsigned long long t0 = 0;
     for (unsigned it = 0;; ++it) {
@@ -70,7 +86,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
             : "memory");
         if (ok) return true;
         if (it == 0) t0 = global_ns();
-        else if ((it & 63) == 0 && global_ns() - t0 > limit_ns) return false;
+        else if (global_ns() - t0 > limit_ns) return false;
     }
 }
 

@@ -745,11 +745,12 @@ __global__ void k_base_in(const double2* __restrict__ U, long long D, int k, dou
     out[e * 2 * k + 2 * c] = (float)(u.x * scale);
     out[e * 2 * k + 2 * c + 1] = (float)(u.y * scale);
 }
-// y[b] += base for every sample b (n = D * 2k values per sample)
-__global__ void k_add_base(float* __restrict__ y, const float* __restrict__ base, long long n, int B) {
+// y[b] += base[b] for every sample b with an offset (n = D * 2k values per sample)
+__global__ void k_add_base(float* __restrict__ y, const float* const* __restrict__ base, long long n, int B) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * B) return;
-    y[idx] += base[idx % n];
+    const float* bs = base[idx / n];
+    if (bs) y[idx] += bs[idx % n];
 }
 
 __global__ void k_to_complex(const float* __restrict__ y, int D, int k, double2* const* __restrict__ U, int B) {
@@ -760,6 +761,160 @@ __global__ void k_to_complex(const float* __restrict__ y, int D, int k, double2*
     const int c = (int)(r / D), e = (int)(r % D);
     const float* ye = y + ((long long)b * D + e) * 2 * k;
     U[b][(long long)c * D + e] = make_double2(ye[2 * c], ye[2 * c + 1]);
+}
+
+// ---------------------------------------------------------------- K13: orthonormal predicted vectors
+// Cholesky QR applied twice, in FP64, to each problem's k predicted vectors
+// (U: D x k column-major): G = U^H U = L L^H, U <- U L^-H.  The span is kept;
+// after two passes U^H U = I to FP64 round-off (times the conditioning left
+// by the first pass).
+constexpr int kOrthRows = 2048;   // rows of one problem per block (Gram and apply)
+constexpr int kOrthTile = 64;     // rows per shared-memory tile of the Gram kernel
+constexpr int kOrthMaxK = 16;
+
+__device__ __forceinline__ void orth_pair(int t, int k, int* i, int* j) {
+    // t-th pair (i, j), i <= j, in row order of the upper triangle
+    int r = 0;
+    while (t >= k - r) { t -= k - r; ++r; }
+    *i = r;
+    *j = r + t;
+}
+
+// Block (c, s): partial Gram of rows [c kOrthRows, (c+1) kOrthRows) of problem
+// s.  Thread groups of np = k(k+1)/2 threads share the block's rows (group g
+// takes tile rows r = g mod ngroups); thread (g, p) owns pair p = (i, j) and
+// sums conj(U_ri) U_rj; the groups' sums are added in a fixed order.
+__global__ void __launch_bounds__(256) k_orth_gram(double2* const* __restrict__ U, int D, int k, int nch,
+                                                   double2* __restrict__ part) {
+    __shared__ double2 tile[kOrthTile][kOrthMaxK];
+    __shared__ double2 red[256];
+    const int s = blockIdx.y, c = blockIdx.x;
+    const double2* u = U[s];
+    const int np = k * (k + 1) / 2;
+    const int ngroups = (int)blockDim.x / np;
+    const int g = (int)threadIdx.x / np, p = (int)threadIdx.x % np;
+    const bool active = g < ngroups;
+    int pi = 0, pj = 0;
+    if (active) orth_pair(p, k, &pi, &pj);
+    double2 acc = make_double2(0.0, 0.0);
+    const long long r0 = (long long)c * kOrthRows;
+    const long long r1 = min((long long)D, r0 + kOrthRows);
+    for (long long t0 = r0; t0 < r1; t0 += kOrthTile) {
+        const int rows = (int)min((long long)kOrthTile, r1 - t0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kOrthTile * k; e += blockDim.x) {
+            const int col = e / kOrthTile, row = e % kOrthTile;
+            tile[row][col] = row < rows ? u[(long long)col * D + t0 + row] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        if (active)
+            for (int r = g; r < rows; r += ngroups) cfmac(acc, tile[r][pi], tile[r][pj]);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < np) {
+        double2 tot = red[threadIdx.x];
+        for (int q = 1; q < ngroups; ++q) tot = cadd(tot, red[q * np + threadIdx.x]);
+        part[((long long)s * nch + c) * np + threadIdx.x] = tot;
+    }
+}
+
+// One block per problem: G from the partial sums (chunk order), G = L L^H by
+// Cholesky, T = L^-H (upper triangular, T[p][j] at p k + j).  A pivot below
+// 1e-13 of the largest diagonal entry marks a direction already spanned by
+// the earlier vectors: that column of T (and row) is zero, so the vector
+// comes out as zero and takes no part in the others.  dropped[s] counts them.
+__global__ void k_orth_factor(const double2* __restrict__ part, int nch, int k, double2* __restrict__ T,
+                              int* __restrict__ dropped) {
+    __shared__ double2 G[kOrthMaxK][kOrthMaxK];
+    const int s = blockIdx.x;
+    const int np = k * (k + 1) / 2;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        double2 tot = make_double2(0.0, 0.0);
+        for (int c = 0; c < nch; ++c) tot = cadd(tot, part[((long long)s * nch + c) * np + p]);
+        int i, j;
+        orth_pair(p, k, &i, &j);
+        G[i][j] = tot;                                  // G_ij = sum conj(U_i) U_j, i <= j
+        G[j][i] = make_double2(tot.x, -tot.y);
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    // one thread factors (k <= 16); its tables live in shared memory, not in
+    // a per-thread stack frame
+    __shared__ double L[kOrthMaxK][kOrthMaxK][2];
+    __shared__ double X[kOrthMaxK][kOrthMaxK][2];
+    bool keep[kOrthMaxK];
+    double gmax = 0.0;
+    for (int i = 0; i < k; ++i) gmax = fmax(gmax, G[i][i].x);
+    int nd = 0;
+    for (int j = 0; j < k; ++j) {
+        double d = G[j][j].x;
+        for (int q = 0; q < j; ++q) d -= L[j][q][0] * L[j][q][0] + L[j][q][1] * L[j][q][1];
+        keep[j] = d > 1e-13 * gmax && gmax > 0.0;
+        if (!keep[j]) {
+            ++nd;
+            for (int i = j; i < k; ++i) L[i][j][0] = L[i][j][1] = 0.0;
+            continue;
+        }
+        const double ljj = sqrt(d);
+        L[j][j][0] = ljj;
+        L[j][j][1] = 0.0;
+        for (int i = j + 1; i < k; ++i) {
+            // L_ij = (G_ij - sum_q L_iq conj(L_jq)) / L_jj, with G_ij = conj(G_ji) for i > j
+            double re = G[i][j].x, im = G[i][j].y;
+            for (int q = 0; q < j; ++q) {
+                re -= L[i][q][0] * L[j][q][0] + L[i][q][1] * L[j][q][1];
+                im -= L[i][q][1] * L[j][q][0] - L[i][q][0] * L[j][q][1];
+            }
+            L[i][j][0] = re / ljj;
+            L[i][j][1] = im / ljj;
+        }
+    }
+    // X = L^-1 (lower) by forward substitution, dropped rows and columns zero
+    for (int j = 0; j < k; ++j) {
+        for (int i = 0; i < k; ++i) X[i][j][0] = X[i][j][1] = 0.0;
+        if (!keep[j]) continue;
+        X[j][j][0] = 1.0 / L[j][j][0];
+        for (int i = j + 1; i < k; ++i) {
+            if (!keep[i]) continue;
+            double re = 0.0, im = 0.0;
+            for (int q = j; q < i; ++q) {
+                re += L[i][q][0] * X[q][j][0] - L[i][q][1] * X[q][j][1];
+                im += L[i][q][0] * X[q][j][1] + L[i][q][1] * X[q][j][0];
+            }
+            X[i][j][0] = -re / L[i][i][0];
+            X[i][j][1] = -im / L[i][i][0];
+        }
+    }
+    double2* Ts = T + (long long)s * k * k;
+    for (int p = 0; p < k; ++p)
+        for (int j = 0; j < k; ++j)   // T = X^H: T_pj = conj(X_jp)
+            Ts[p * k + j] = make_double2(X[j][p][0], -X[j][p][1]);
+    dropped[s] = nd;
+}
+
+// U <- U T in place, one row per thread (T upper triangular).
+__global__ void __launch_bounds__(256) k_orth_apply(double2* const* __restrict__ U, int D, int k,
+                                                    const double2* __restrict__ T) {
+    __shared__ double2 Ts[kOrthMaxK * kOrthMaxK];
+    const int s = blockIdx.y;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) Ts[e] = T[(long long)s * k * k + e];
+    __syncthreads();
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= D) return;
+    double2* u = U[s];
+    double2 v[kOrthMaxK];
+#pragma unroll
+    for (int c = 0; c < kOrthMaxK; ++c)
+        if (c < k) v[c] = u[(long long)c * D + r];
+#pragma unroll
+    for (int j = 0; j < kOrthMaxK; ++j) {
+        if (j >= k) break;
+        double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int p = 0; p <= j; ++p) cfma(acc, v[p], Ts[p * k + j]);
+        u[(long long)j * D + r] = acc;
+    }
 }
 
 // Per-sample operator for the residual loss (FP32 coefficients).
@@ -830,6 +985,12 @@ __global__ void k_adj_post(const FieldOpDesc* __restrict__ ops, float* __restric
 
 inline unsigned nblk(long long n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
 
+struct OutputBase {
+    float* dev;          // D x 2k FP32, the network's output layout
+    int nx, ny;
+    double wavelength;   // metres; 0 = every wavelength of this grid
+};
+
 }  // namespace cnn
 }  // namespace ddg
 
@@ -856,8 +1017,12 @@ struct ddg_predictor {
     double* d_loss = nullptr;     // per-sample losses
     float2* in_field = nullptr;   // cin = 6: the approximate field of the grid, normalised
     int field_nx = 0, field_ny = 0;
-    float* out_base = nullptr;    // optional fixed output offset (D x 2k, the output layout)
-    int base_nx = 0, base_ny = 0;
+    // optional fixed output offsets (D x 2k each, the output layout), keyed by
+    // grid and wavelength (wavelength 0: any wavelength of that grid)
+    std::vector<ddg::cnn::OutputBase> bases;
+    std::vector<const float*> base_ptrs;   // host copy of the last batch's offset pointers
+    double2* orth_ws = nullptr;   // K13: Gram partial sums, factors, dropped counts
+    size_t orth_bytes = 0;
     int* d_err = nullptr;         // a bounded wait in a tensor-core convolution gave up
     bool tensor_cores = true;     // forward 3x3 convolutions on tcgen05 where the channels allow
     void* d_desc = nullptr;       // InputDesc / pointer arrays (device)
@@ -866,6 +1031,8 @@ struct ddg_predictor {
 
 namespace ddg {
 namespace cnn {
+
+static void** base_slots(ddg_predictor* P, int n);
 
 static int layer_index(const ddg_predictor* P, bool dec, int level, int ab) {
     // enc l: 2l + ab ; dec l (l = L-2 .. 0): 2L + 2 (L-2-l) + ab ; head: last
@@ -1026,10 +1193,10 @@ static ddg_status forward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaSt
     ++P->launches;
     k_head_fwd<<<nblk((long long)B * H * W * 2 * P->k), 256, 0, st>>>(h, (long long)B * H * W, hc, 2 * P->k, wbf(P, lh),
                                                                     bias32(P, lh), A->y);
-    if (P->out_base) {
+    if (!P->bases.empty()) {
         const long long n = (long long)H * W * 2 * P->k;
         ++P->launches;
-        k_add_base<<<nblk(n * B), 256, 0, st>>>(A->y, P->out_base, n, B);
+        k_add_base<<<nblk(n * B), 256, 0, st>>>(A->y, reinterpret_cast<const float* const*>(base_slots(P, B)), n, B);
     }
     DDG_CHECK_LAUNCH("forward");
     return DDG_OK;
@@ -1125,6 +1292,20 @@ static ddg_status backward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaS
     return DDG_OK;
 }
 
+static bool same_wavelength(double a, double b) { return fabs(a - b) <= 1e-9 * fmax(fabs(a), fabs(b)); }
+
+// The output offset of one problem: the entry of its grid and wavelength,
+// else the entry of its grid for every wavelength, else none.
+static const OutputBase* find_base(const ddg_predictor* P, const ddg_op* A) {
+    const OutputBase* any = nullptr;
+    for (const OutputBase& b : P->bases) {
+        if (b.nx != A->nx || b.ny != A->ny) continue;
+        if (b.wavelength == 0.0) any = &b;
+        else if (same_wavelength(b.wavelength, A->wavelength)) return &b;
+    }
+    return any;
+}
+
 static ddg_status check_batch(const ddg_predictor* P, int n, const ddg_op* const* A, int* H, int* W) {
     if (!P || n < 1 || !A) { set_error("predictor: bad arguments"); return DDG_EINVAL; }
     for (int s = 0; s < n; ++s) {
@@ -1136,10 +1317,13 @@ static ddg_status check_batch(const ddg_predictor* P, int n, const ddg_op* const
         set_error("predictor: grid %dx%d not divisible by %d", A[0]->nx, A[0]->ny, div);
         return DDG_EINVAL;
     }
-    if (P->out_base && (P->base_nx != A[0]->nx || P->base_ny != A[0]->ny)) {
-        set_error("predictor: the output base was set for a %dx%d grid", P->base_nx, P->base_ny);
-        return DDG_EINVAL;
-    }
+    if (!P->bases.empty())
+        for (int s = 0; s < n; ++s)
+            if (!find_base(P, A[s])) {
+                set_error("predictor: no output base for the %dx%d grid at wavelength %g m (problem %d)", A[s]->nx,
+                          A[s]->ny, A[s]->wavelength, s);
+                return DDG_EINVAL;
+            }
     if (P->cin == 6 && (!P->in_field || P->field_nx != A[0]->nx || P->field_ny != A[0]->ny)) {
         set_error("predictor: this network takes an input field of the %dx%d grid (predictor_set_input_field)",
                   A[0]->nx, A[0]->ny);
@@ -1161,7 +1345,7 @@ static ddg_status build_input(ddg_predictor* P, int n, const ddg_op* const* A, i
         hf[s] = FieldOpDesc{A[s]->eps_f, A[s]->coef_f, A[s]->sb_f, A[s]->nx, A[s]->ny, (float)(A[s]->kh * A[s]->kh)};
     }
     const size_t need = ((sizeof(InputDesc) * n + 15) / 16) * 16 + ((sizeof(FieldOpDesc) * n + 15) / 16) * 16 +
-                        sizeof(void*) * 2 * n + 256;
+                        sizeof(void*) * 3 * n + 256;
     if (need > P->desc_bytes) {
         cudaFree(P->d_desc);
         P->d_desc = nullptr;
@@ -1171,6 +1355,14 @@ static ddg_status build_input(ddg_predictor* P, int n, const ddg_op* const* A, i
     }
     DDG_CHECK_CUDA(cudaMemcpyAsync(P->d_desc, hd.data(), sizeof(InputDesc) * n, cudaMemcpyHostToDevice, st));
     DDG_CHECK_CUDA(cudaMemcpyAsync(field_ops(P, n), hf.data(), sizeof(FieldOpDesc) * n, cudaMemcpyHostToDevice, st));
+    if (!P->bases.empty()) {
+        // per-problem output offsets (checked to exist by check_batch); the
+        // host array must outlive the asynchronous copy
+        P->base_ptrs.assign(n, nullptr);
+        for (int s = 0; s < n; ++s) P->base_ptrs[s] = find_base(P, A[s])->dev;
+        DDG_CHECK_CUDA(cudaMemcpyAsync(base_slots(P, n), P->base_ptrs.data(), sizeof(void*) * n,
+                                       cudaMemcpyHostToDevice, st));
+    }
     const int H = A[0]->ny, W = A[0]->nx;
     ++P->launches;
     k_input<<<nblk((long long)n * H * W), 256, 0, st>>>(reinterpret_cast<InputDesc*>(P->d_desc), n, H, W, i_src,
@@ -1186,6 +1378,8 @@ static void** ptr_slots(ddg_predictor* P, int n) {
     return reinterpret_cast<void**>(reinterpret_cast<char*>(field_ops(P, n)) +
                                     ((sizeof(FieldOpDesc) * n + 15) / 16) * 16);
 }
+// n output-offset pointers behind the 2n pointer slots
+static void** base_slots(ddg_predictor* P, int n) { return ptr_slots(P, n) + 2 * n; }
 
 static void free_predictor(ddg_predictor* P) {
     if (!P) return;
@@ -1198,7 +1392,8 @@ static void free_predictor(ddg_predictor* P) {
     cudaFree(P->act);
     cudaFree(P->d_loss);
     cudaFree(P->in_field);
-    cudaFree(P->out_base);
+    for (auto& b : P->bases) cudaFree(b.dev);
+    cudaFree(P->orth_ws);
     cudaFree(P->d_err);
     cudaFree(P->d_desc);
     delete P;
@@ -1297,30 +1492,45 @@ extern "C" ddg_status predictor_set_input_field(ddg_predictor* P, const double* 
     return DDG_OK;
 }
 
-extern "C" ddg_status predictor_set_output_base(ddg_predictor* P, const double* U, int nx, int ny, double scale,
-                                                void* stream) {
-    if (!P || nx < 1 || ny < 1) { set_error("predictor_set_output_base: bad arguments"); return DDG_EINVAL; }
+static ddg_status set_output_base(ddg_predictor* P, const double* U, int nx, int ny, double wavelength,
+                                  double scale, void* stream, const char* who) {
+    if (!P || nx < 1 || ny < 1 || !(wavelength >= 0.0)) { set_error("%s: bad arguments", who); return DDG_EINVAL; }
     cudaStream_t st = as_stream(stream);
-    if (!U) {   // remove the base
-        cudaFree(P->out_base);
-        P->out_base = nullptr;
-        P->base_nx = P->base_ny = 0;
+    if (!U) {   // remove every offset
+        DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+        for (auto& b : P->bases) cudaFree(b.dev);
+        P->bases.clear();
         return DDG_OK;
     }
     const long long D = (long long)nx * ny;
-    if ((long long)P->base_nx * P->base_ny != D) {
-        cudaFree(P->out_base);
-        P->out_base = nullptr;
-        P->base_nx = P->base_ny = 0;
-        cudaError_t e = cudaMalloc(&P->out_base, sizeof(float) * D * 2 * P->k);
-        if (e != cudaSuccess) { cudaGetLastError(); set_error("predictor_set_output_base: cudaMalloc failed"); return DDG_ENOMEM; }
+    OutputBase* slot = nullptr;
+    for (auto& b : P->bases)
+        if (b.nx == nx && b.ny == ny &&
+            ((wavelength == 0.0 && b.wavelength == 0.0) ||
+             (wavelength > 0.0 && b.wavelength > 0.0 && same_wavelength(b.wavelength, wavelength))))
+            slot = &b;
+    if (!slot) {
+        float* d = nullptr;
+        cudaError_t e = cudaMalloc(&d, sizeof(float) * D * 2 * P->k);
+        if (e != cudaSuccess) { cudaGetLastError(); set_error("%s: cudaMalloc failed", who); return DDG_ENOMEM; }
+        P->bases.push_back(OutputBase{d, nx, ny, wavelength});
+        slot = &P->bases.back();
     }
-    P->base_nx = nx;
-    P->base_ny = ny;
     ++P->launches;
-    k_base_in<<<nblk(D * P->k), 256, 0, st>>>(reinterpret_cast<const double2*>(U), D, P->k, scale, P->out_base);
+    k_base_in<<<nblk(D * P->k), 256, 0, st>>>(reinterpret_cast<const double2*>(U), D, P->k, scale, slot->dev);
     DDG_CHECK_LAUNCH("k_base_in");
     return DDG_OK;
+}
+
+extern "C" ddg_status predictor_set_output_base(ddg_predictor* P, const double* U, int nx, int ny, double scale,
+                                                void* stream) {
+    return set_output_base(P, U, nx, ny, 0.0, scale, stream, "predictor_set_output_base");
+}
+
+extern "C" ddg_status predictor_set_output_base_wavelength(ddg_predictor* P, const double* U, int nx, int ny,
+                                                           double wavelength, double scale, void* stream) {
+    if (!(wavelength > 0.0)) { set_error("predictor_set_output_base_wavelength: wavelength must be > 0"); return DDG_EINVAL; }
+    return set_output_base(P, U, nx, ny, wavelength, scale, stream, "predictor_set_output_base_wavelength");
 }
 
 extern "C" ddg_status predictor_destroy(ddg_predictor* P) {
@@ -1329,6 +1539,8 @@ extern "C" ddg_status predictor_destroy(ddg_predictor* P) {
 }
 
 extern "C" long long predictor_num_params(const ddg_predictor* P) { return P ? P->nparams : 0; }
+
+extern "C" int predictor_num_outputs(const ddg_predictor* P) { return P ? P->k : 0; }
 
 extern "C" long long predictor_launches(const ddg_predictor* P) { return P ? P->launches : 0; }
 
@@ -1390,6 +1602,31 @@ extern "C" ddg_status subspace_predict(ddg_predictor* P, int n, const ddg_op* co
     k_to_complex<<<nblk((long long)n * H * W * P->k), 256, 0, st>>>(acts.y, H * W, P->k,
                                                                     reinterpret_cast<double2* const*>(slots), n);
     DDG_CHECK_LAUNCH("k_to_complex");
+    // K13: Cholesky QR twice (FP64) of each problem's k vectors
+    const int k = P->k, D = H * W, np = k * (k + 1) / 2;
+    const int nch = (D + kOrthRows - 1) / kOrthRows;
+    const size_t part_n = (size_t)n * nch * np, T_n = (size_t)n * k * k;
+    const size_t need = sizeof(double2) * (part_n + T_n) + sizeof(int) * (size_t)n + 256;
+    if (need > P->orth_bytes) {
+        DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+        cudaFree(P->orth_ws);
+        P->orth_ws = nullptr;
+        P->orth_bytes = 0;
+        cudaError_t e = cudaMalloc(&P->orth_ws, need);
+        if (e != cudaSuccess) { cudaGetLastError(); set_error("subspace_predict: cudaMalloc failed"); return DDG_ENOMEM; }
+        P->orth_bytes = need;
+    }
+    double2* part = P->orth_ws;
+    double2* T = part + part_n;
+    int* dropped = reinterpret_cast<int*>(T + T_n);
+    double2* const* Us = reinterpret_cast<double2* const*>(slots);
+    for (int pass = 0; pass < 2; ++pass) {
+        P->launches += 3;
+        k_orth_gram<<<dim3(nch, n), 256, 0, st>>>(Us, D, k, nch, part);
+        k_orth_factor<<<n, 32, 0, st>>>(part, nch, k, T, dropped);
+        k_orth_apply<<<dim3(nblk(D), n), 256, 0, st>>>(Us, D, k, T);
+        DDG_CHECK_LAUNCH("orthonormalisation (K13)");
+    }
     return check_tc(P, st);
 }
 

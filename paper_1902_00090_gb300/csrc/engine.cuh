@@ -12,6 +12,7 @@ constexpr int kBlock = 256;          // threads per CTA of the streaming kernels
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxAug = 32;          // largest augmentation size k
 constexpr int kMaxRestart = 1024;
+constexpr unsigned long long kDefaultWaitNs = 1000000000ull;   // bounded device waits give up after 1 s
 
 // 16-byte packs: every thread of a streaming kernel owns one pack (VEC complex
 // numbers) of each work column; a CTA covers kBlock * VEC consecutive rows.
@@ -85,6 +86,10 @@ struct Context {
     int graphs = 1;                  // delayed scheme: step loop as a CUDA graph with a device-side WHILE
     int half_basis = 0;              // complex64 solves: Krylov basis stored in IEEE half
     int precond = 0;                 // 0: none, 1: Jacobi right preconditioner (data-free baseline)
+    unsigned long long wait_ns = kDefaultWaitNs;   // bounded waits of the Arnoldi kernels
+    size_t ws_limit = 0;             // largest workspace the context may allocate (0: no limit)
+    void* io = nullptr;              // fdfd_solve_host: device copies of the call's inputs and outputs
+    size_t io_bytes = 0;
     int sm_count = 152;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     // launch accounting and profiling
@@ -191,6 +196,7 @@ struct BatchArgs {
     int nsolves;       // solves in the batch (k_update2 puts one block per solve in front of its sweep)
     int* step;         // Arnoldi step of the graph-driven loop (kernels launched with i <= 0 add it)
     int low_res;       // DDG_C64_ONLY: the restart residual r = b - A x in the Krylov precision
+    unsigned long long wait_ns;   // limit of the bounded waits on bulk copies into shared memory
 };
 
 // Adds `v` to the class counter once per CTA (thread 0), when profiling.

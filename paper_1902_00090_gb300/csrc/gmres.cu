@@ -985,7 +985,10 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
         // stopped by the preceding launch: let the early copies land, then leave
         if (threadIdx.x == 0)
             for (int b = 0; b < early; ++b)
-                if (!mbar_wait(&full[b], 0u)) atomicExch(a.counts + 4, 1);
+                if (!mbar_wait(&full[b], 0u, a.wait_ns)) {
+                    atomicExch(a.counts + 4, 1);
+                    mbar_wait(&full[b], 0u);   // one more wait, at the default bound, before leaving
+                }
         return;
     }
     // columns, u, and z = A u (written; reads eps) when there is a next step
@@ -1026,6 +1029,7 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
     // partial sums stay in the Krylov precision until the last CTA
     V* part = reinterpret_cast<V*>(P.part) + (long long)chunk * a.KP;
     bool ok = true;
+    int stop = nbat;     // stages consumed before a wait gave up (nbat: all)
     if constexpr (HB) {
         // Half basis: the projections as real GEMMs on the tensor cores (mma.sync
         // m16n8k16, half in, FP32 accumulate).  A (16 x 16 per k step): rows
@@ -1068,12 +1072,17 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
         for (int b = 0; b < nbat; ++b) {
             const int kk = (b % kBatchesPer32) * kRingCols;
             const int nv = min(kRingCols, K - kstart - b * kRingCols);
-            __syncthreads();               // stage (b - 1) % kRing has been read by every warp
+            // stage (b - 1) % kRing has been read by every warp; a wait that gave
+            // up anywhere in the block stops the loop (before any new request)
+            if (__syncthreads_or(!ok)) {
+                stop = b;
+                break;
+            }
             if (threadIdx.x == 0 && b >= 1 && b + kRing - 1 < nbat) {
                 fence_proxy_async_smem();
                 issue_one(b + kRing - 1);
             }
-            if (!mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u)) ok = false;
+            if (!mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u, a.wait_ns)) ok = false;
             const unsigned sbase = smem_u32(smraw2 + (b % kRing) * kStageBytes);
             float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
 #pragma unroll
@@ -1119,12 +1128,17 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
     for (int b = 0; b < nbat; ++b) {
         const int kk = (b % kBatchesPer32) * kRingCols;
         const int nv = min(kRingCols, K - kstart - b * kRingCols);
-        __syncthreads();               // stage (b - 1) % kRing has been read by every warp
+        // stage (b - 1) % kRing has been read by every warp; a wait that gave
+        // up anywhere in the block stops the loop (before any new request)
+        if (__syncthreads_or(!ok)) {
+            stop = b;
+            break;
+        }
         if (threadIdx.x == 0 && b >= 1 && b + kRing - 1 < nbat) {
             fence_proxy_async_smem();
             issue_one(b + kRing - 1);
         }
-        if (!mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u)) ok = false;
+        if (!mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u, a.wait_ns)) ok = false;
         const BP* stg = reinterpret_cast<const BP*>(smraw2 + (b % kRing) * (kRingCols * kColBytes));
         BP m[kRingCols];
 #pragma unroll
@@ -1162,11 +1176,16 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
         }
     }
     }
-    if (!ok) {
-        // a copy did not arrive in time: report it, and give the ring one more
-        // bounded wait so that no copy lands after this CTA has gone
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) {
+        // a copy did not arrive within the wait limit: report it, and give every
+        // stage still in flight one more wait at the default bound (1 s), so that
+        // no copy lands after this CTA has gone.  Stages [0, issued) were
+        // requested; a slot is re-requested only after every thread has seen
+        // its previous phase complete, so only the latest phase of each slot
+        // can be outstanding.
         atomicExch(a.counts + 4, 1);
-        for (int b = max(0, nbat - kRing); b < nbat; ++b) mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u);
+        const int issued = min(nbat, max(npre, stop + kRing - 1));
+        for (int b = max(0, issued - kRing); b < issued; ++b) mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u);
     }
     {
         T al = (T)0;
@@ -1910,6 +1929,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     args.nsolves = n;
     args.step = args.counts + 5;
     args.low_res = low_res ? 1 : 0;
+    args.wait_ns = ctx->wait_ns;
     std::vector<int> hblk(total_ctas);
     for (int s = 0; s < n; ++s)
         for (int c = 0; c < hp[s].nchunks; ++c) hblk[hp[s].chunk0 + c] = s;
@@ -2179,7 +2199,8 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
         hp.cr = c.take<double2>(1);
         hp.coefy = c.take<double2>(m);
         hp.ticket = c.take<unsigned>(1);
-        return c.off;
+        // the same 4096-byte slack behind the last array as run_batch keeps
+        return c.off + 4096;
     };
     size_t small_off = align_up(layout(nullptr));
     Carver tail{nullptr, small_off};
@@ -2226,6 +2247,7 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     args.nsolves = 1;
     args.step = args.counts + 5;
     args.low_res = 0;
+    args.wait_ns = kDefaultWaitNs;
     // every launch reads these: the array keeps the previous call's contents
     std::vector<int> hblk(hp.nchunks, 0);
     DDG_CHECK_CUDA(cudaMemcpyAsync(args.P, &hp, sizeof(SolvePtrs), cudaMemcpyHostToDevice, st));

@@ -50,14 +50,55 @@ def test_tune_times_every_candidate_once_and_caches(tmp_path):
         return {(16, 1): 10.0, (16, 2): 12.0, (32, 1): 11.0, (32, 2): 11.5, (64, 1): 9.0}[(w, nl)]
 
     cache = str(tmp_path / "tune.json")
-    r = autotune.tune_queue(["c0", "c1"], A, b, sample=64, widths=(16, 32, 64), cache_path=cache, run=run)
+    r = autotune.tune_queue(["c0", "c1"], A, b, sample=64, widths=(16, 32, 64), cache_path=cache, run=run,
+                            repeats=1)
     assert (r["width"], r["lanes"], r["cached"]) == (16, 2, False)
     assert sorted(c[:2] for c in calls) == [(16, 1), (16, 2), (32, 1), (32, 2), (64, 1)]
     assert all(c[2] == 64 for c in calls)
     stored = json.load(open(cache))
     assert r["key"] in stored and stored[r["key"]]["width"] == 16
-    r2 = autotune.tune_queue(["c0", "c1"], A, b, sample=64, widths=(16, 32, 64), cache_path=cache, run=run)
+    r2 = autotune.tune_queue(["c0", "c1"], A, b, sample=64, widths=(16, 32, 64), cache_path=cache, run=run,
+                             repeats=1)
     assert r2["cached"] and (r2["width"], r2["lanes"]) == (16, 2) and len(calls) == 5
+
+
+def test_tune_repeats_each_candidate_and_keeps_its_best_rate():
+    A = [Op(128, 128)] * 32
+    b = list(range(32))
+    noisy = {(16, 1): iter([10.0, 13.0]), (16, 2): iter([12.0, 12.1]), (32, 1): iter([12.5, 9.0])}
+    calls = []
+
+    def run(lanes, As, bs, Us, w, nl, tol, m, maxit, prec):
+        calls.append((w, nl))
+        return next(noisy[(w, nl)])
+
+    r = autotune.tune_queue(["c0", "c1"], A, b, sample=32, widths=(16, 32), run=run, repeats=2)
+    assert len(calls) == 6 and sorted(set(calls)) == [(16, 1), (16, 2), (32, 1)]
+    # best of two: (16, 1) reaches 13.0, above the others' best by more than 1 %
+    assert (r["width"], r["lanes"], r["solves_per_s"]) == (16, 1, 13.0)
+
+
+def test_cache_key_separates_restart_lengths_and_tolerances(tmp_path):
+    A = [Op(128, 128)] * 16
+    b = list(range(16))
+    seen = []
+
+    def run(lanes, As, bs, Us, w, nl, tol, m, maxit, prec):
+        seen.append((m, tol))
+        return 10.0
+
+    cache = str(tmp_path / "t.json")
+    r200 = autotune.tune_queue(["c0"], A, b, sample=16, widths=(16,), lane_counts=(1,), restart=200, run=run,
+                               cache_path=cache, repeats=1)
+    r100 = autotune.tune_queue(["c0"], A, b, sample=16, widths=(16,), lane_counts=(1,), restart=100, run=run,
+                               cache_path=cache, repeats=1)
+    assert not r100["cached"] and r100["restart"] == 100 and r200["restart"] == 200
+    assert r100["key"] != r200["key"] and seen == [(200, 1e-6), (100, 1e-6)]
+    r4 = autotune.tune_queue(["c0"], A, b, sample=16, widths=(16,), lane_counts=(1,), restart=100, tol=1e-4,
+                             run=run, cache_path=cache, repeats=1)
+    assert not r4["cached"] and r4["key"] != r100["key"]
+    assert autotune.tune_queue(["c0"], A, b, sample=16, widths=(16,), lane_counts=(1,), restart=100, run=run,
+                               cache_path=cache, repeats=1)["cached"]
 
 
 def test_tune_restart_lengths_too(tmp_path):

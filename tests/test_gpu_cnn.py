@@ -8,6 +8,7 @@ pure fp64 oracle on the same FP32 weights: output within 3e-2 relative L2,
 loss within 2 %, gradient cosine >= 0.98 (what bfloat16 storage itself gives);
 Adam by its formula applied to the GPU's own gradient (FP32 round-off).
 """
+import dataclasses
 import os
 import tempfile
 
@@ -70,17 +71,52 @@ def test_forward_matches_oracle():
     assert rel(y, yb) <= 2e-3
 
 
-def test_predict_layout():
+def sin_largest_angle(Q, U):
+    """Sine of the largest principal angle between span(Q) and span(U) (Q
+    orthonormal, U orthonormal columns): ||(I - Q Q^H) U||_2."""
+    return np.linalg.norm(U - Q @ (Q.conj().T @ U), 2)
+
+
+def test_predict_is_orthonormal_and_keeps_the_span():
+    # K13: subspace_predict returns the network's k vectors made orthonormal on
+    # the device (Cholesky QR twice, FP64); the span is that of the raw output
     g, eps, ops = small_problems()
     P = ddg.Predictor(**SMALL)
     P.init_he(seed=4)
     src = (g.i_src, g.sigma_src, g.j_src)
     y = P.forward(ops, src).cpu().numpy()
     U = P.predict(ops, src)
+    cfg = ocnn.CNNConfig(cin=4, channels=SMALL["channels"], k=SMALL["k"])
+    theta = P.get_params().astype(np.float64)
+    yb = ocnn.forward(cfg, ocnn.round_weights(cfg, theta, ocnn.bf16_round), ocnn.bf16_round(oracle_inputs(g, eps)),
+                      store=ocnn.bf16_round)
     for s in range(len(ops)):
-        Us = U[s].cpu().numpy()                       # (k, D): row c = v_c
-        V = ocnn.to_complex_fields(y[s:s + 1])[0]     # (D, k)
-        assert np.array_equal(Us.T, V.astype(np.complex128))
+        Us = U[s].cpu().numpy().T                     # (D, k): column c = v_c
+        assert np.max(np.abs(Us.conj().T @ Us - np.eye(SMALL["k"]))) <= 1e-10
+        Q, _ = np.linalg.qr(ocnn.to_complex_fields(y[s:s + 1])[0].astype(np.complex128))
+        assert sin_largest_angle(Q, Us) <= 1e-6
+        # and the span of the oracle's forward pass (same bfloat16 storage)
+        Qo, _ = np.linalg.qr(ocnn.to_complex_fields(yb[s:s + 1])[0])
+        assert sin_largest_angle(Qo, Us) <= 2e-2
+
+
+def test_predict_drops_a_dependent_vector():
+    # with a zero head the output is the offset alone: v_3 = v_1 + v_2 is
+    # spanned by the first two, so it comes out as a zero vector and the
+    # others stay orthonormal with the span of {v_1, v_2}
+    g, eps, ops = small_problems()
+    P = ddg.Predictor(k=3, channels=SMALL["channels"])
+    P.init_he(seed=14)
+    P.zero_head()
+    a, b = inputs.random_complex(g.D, 21), inputs.random_complex(g.D, 22)
+    P.set_output_base(torch.as_tensor(np.stack([a, b, a + b]), device="cuda"), g.nx, g.ny)
+    U = P.predict(ops, (g.i_src, g.sigma_src, g.j_src))
+    Q, _ = np.linalg.qr(np.stack([a, b], axis=1))
+    for Ut in U:
+        Us = Ut.cpu().numpy().T
+        assert not np.any(Us[:, 2])
+        assert np.max(np.abs(Us[:, :2].conj().T @ Us[:, :2] - np.eye(2))) <= 1e-10
+        assert sin_largest_angle(Q, Us[:, :2]) <= 1e-6
 
 
 def test_loss_and_gradient_match_oracle():
@@ -317,3 +353,34 @@ def test_output_base_is_added():
     assert np.array_equal(P.forward(ops, src).cpu().numpy(), np.broadcast_to(base, y1.shape))
     P.set_output_base(None, g.nx, g.ny)
     assert not np.any(P.forward(ops, src).cpu().numpy())
+
+
+def test_output_base_per_wavelength():
+    # offsets keyed by wavelength serve the problems at that wavelength; an
+    # offset for every wavelength serves the rest; a problem with neither is
+    # refused
+    g, eps, _ = small_problems()
+    g2 = dataclasses.replace(g, wavelength=1300e-9)
+    ops = [ddg.fdfd_operator(g, torch.as_tensor(eps[0], device="cuda")),
+           ddg.fdfd_operator(g2, torch.as_tensor(eps[1], device="cuda"))]
+    P = ddg.Predictor(**SMALL)
+    P.init_he(seed=15)
+    P.zero_head()
+    k = SMALL["k"]
+    U13 = inputs.random_complex(g.D, 31, shape=(k, g.D))
+    Uany = inputs.random_complex(g.D, 32, shape=(k, g.D))
+    src = (g.i_src, g.sigma_src, g.j_src)
+    P.set_output_base(torch.as_tensor(U13, device="cuda"), g.nx, g.ny, wavelength=1300e-9)
+    with pytest.raises(ddg.DdgError):
+        P.forward(ops, src)          # the 1550 nm problem has no offset
+    P.set_output_base(torch.as_tensor(Uany, device="cuda"), g.nx, g.ny)
+
+    def layout(Uh):
+        base = np.zeros((g.ny, g.nx, 2 * k), dtype=np.float32)
+        base[..., 0::2] = Uh.real.T.reshape(g.ny, g.nx, k)
+        base[..., 1::2] = Uh.imag.T.reshape(g.ny, g.nx, k)
+        return base
+
+    y = P.forward(ops, src).cpu().numpy()
+    assert np.array_equal(y[0], layout(Uany)) and np.array_equal(y[1], layout(U13))
+
