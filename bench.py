@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="splitter256", choices=["splitter256"])
+    p.add_argument("--workload", default="splitter256", choices=["splitter256", "large1024", "batched"])
     p.add_argument("--precision", default="c64", choices=["c64", "c128"])
     p.add_argument("--restart", type=int, default=200)
     p.add_argument("--maxit", type=int, default=5000)
@@ -85,7 +85,7 @@ def parse():
     p.add_argument("--basis", default="f32", choices=["f32", "f16"],
                    help="storage of the Krylov basis (arithmetic stays FP32, the true residual FP64)")
     # fixed-size runs for kernel profiling (ncu) and quick timing; no JSON line
-    p.add_argument("--case", default=None, choices=["solver", "cnn"],
+    p.add_argument("--case", default=None, choices=["solver", "cnn", "stencil"],
                    help="solver: --solves batched held-out problems with an iteration cap (every launch "
                         "sees the same basis sizes from run to run); cnn: the CNN forward of --solves problems")
     p.add_argument("--solves", type=int, default=64)
@@ -145,6 +145,32 @@ def case_solver(a):
             if n:
                 print(f"  {name:10s} {n:6d} launches {ms:9.2f} ms  {by / max(ms, 1e-9) / 1e6:8.1f} GB/s "
                       f" {ms * 1e3 / n:8.1f} us/launch")
+
+
+def case_stencil(a):
+    """The standalone operator application (fdfd_apply_c64 and fdfd_apply) on
+    one a.n x a.n problem: a.repeat applications between CUDA events, GB/s of
+    algorithmic bytes (x read, eps read, y written: 20 B per cell in complex64,
+    40 B in complex128) against the measured copy bandwidth."""
+    import torch
+    import paper_1902_00090_gb300 as ddg
+    from paper_1902_00090_gb300 import inputs
+
+    g = inputs.grid_for(a.n, a.n, wavelength=a.wavelength)
+    eps = inputs.trajectory_eps(g, SEED_CONFIG, 0, 1)[0]
+    op = ddg.fdfd_operator(g, torch.as_tensor(eps, device="cuda"))
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs") \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    for name, dt, fn, per_cell in (("c64", torch.complex64, ddg.fdfd_apply_c64, 20),
+                                   ("c128", torch.complex128, ddg.fdfd_apply, 40)):
+        x = torch.randn(g.D, dtype=dt, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            fn(op, x, y)
+        _, ms = timed_call(torch, lambda: [fn(op, x, y) for _ in range(a.repeat)])
+        gbs = per_cell * g.D * a.repeat / (ms / 1e3) / 1e9
+        print(f"{name}: {a.n}x{a.n}, {ms * 1e3 / a.repeat:.1f} us per apply, {gbs:.0f} GB/s"
+              + (f" = {gbs / peak:.3f} of the measured {peak:.0f} GB/s" if peak else ""))
 
 
 def case_cnn(a):
@@ -307,6 +333,14 @@ def run_ours(args, rank, world):
     b_of = {lam: ddg.fdfd_source(train_ops[lam][0], *src) for lam in WAVELENGTHS}
     setup_s = time.time() - t0
 
+    # the last training trajectory is kept apart for choosing the restart
+    # policies (neither the PCA fit nor the CNN's training sees it)
+    n_val = TRAJ_STEPS
+    val_ops = [op for lam in WAVELENGTHS for op in train_ops[lam][-n_val:]]
+    val_b = [b_of[lam] for lam in WAVELENGTHS for _ in range(n_val)]
+    for lam in WAVELENGTHS:
+        del train_ops[lam][-n_val:]
+
     # --- PCA bases per wavelength from solved training problems (evenly spread
     # over the training trajectories), the library's own solves
     t0 = time.time()
@@ -335,26 +369,78 @@ def run_ours(args, rank, world):
     del train_ops
 
     n_step = len(test_ops[0])
+    step_lams = [g.wavelength for g in grids for _ in range(n_step // len(grids))]
     xs = [torch.zeros(D, dtype=torch.complex128, device=dev) for _ in range(n_step)]
+    # the headline's subspace per solve: [PCA-20 of its wavelength | CNN-8]
+    # (the PCA rows are fixed, the CNN writes the rest each step)
+    kc = args.k + args.cnn_k
+    U_comb = [torch.empty((kc, D), dtype=torch.complex128, device=dev) for _ in range(n_step)]
+    for u, lam in zip(U_comb, step_lams):
+        u[:args.k].copy_(U_pca[lam])
+    U_cnn_rows = [u[args.k:] for u in U_comb]
     U_cnn = [torch.empty((args.cnn_k, D), dtype=torch.complex128, device=dev) for _ in range(n_step)]
-    step_no = [0]
+    U_pca_step = [U_pca[lam] for lam in step_lams]
+
+    def solve_cnn(ops, bs):
+        for x in xs:
+            x.zero_()
+        P.predict(ops, src, U=U_cnn_rows)
+        return ddg.augmented_gmres_solve_batched(ctx, ops, bs, U_comb, x=xs, **kw)
+
+    def solve_cnn8(ops, bs):
+        for x in xs:
+            x.zero_()
+        P.predict(ops, src, U=U_cnn)
+        return ddg.augmented_gmres_solve_batched(ctx, ops, bs, U_cnn, x=xs, **kw)
+
+    def solve_pca(ops, bs):
+        for x in xs:
+            x.zero_()
+        return ddg.augmented_gmres_solve_batched(ctx, ops, bs, U_pca_step, x=xs, **kw)
+
+    def solve_plain(ops, bs):
+        for x in xs:
+            x.zero_()
+        return ddg.gmres_solve_batched(ctx, ops, bs, x=xs, **kw)
+
+    def set_policy(pol):
+        for lam, (cyc, keep) in pol.items():
+            ctx.set_augmented_policy(cyc, keep, wavelength=lam)
+
+    def tune_policy(solve, candidates):
+        """Per wavelength, the restart policy (cycles with all of V, then the
+        leading `keep` columns) with the fewest Krylov steps on the validation
+        trajectory (a solve that misses the cap counts twice the cap)."""
+        table = []
+        for cand in candidates:
+            set_policy({lam: cand for lam in WAVELENGTHS})
+            _, inf, _ = solve(val_ops, val_b)
+            sc = {}
+            for lam in WAVELENGTHS:
+                its = [i["iters"] if i["converged"] else 2 * args.maxit
+                       for i, l2 in zip(inf, step_lams) if l2 == lam]
+                sc[lam] = float(np.mean(its))
+            table.append((cand, sc))
+        best = {lam: min(table, key=lambda t: t[1][lam])[0] for lam in WAVELENGTHS}
+        report = {f"{int(round(lam * 1e9))}nm": {"chosen": {"cycles": best[lam][0], "keep": best[lam][1]},
+                                                 "steps": {f"{c[0]}/{c[1]}": round(v[lam], 1) for c, v in table}}
+                  for lam in WAVELENGTHS}
+        return best, report
+
+    t0 = time.time()
+    every = 10**6
+    pol_cnn, rep_cnn = tune_policy(solve_cnn, [(1, 0), (1, args.k), (every, kc)])
+    pol_pca, rep_pca = tune_policy(solve_pca, [(1, 0), (every, args.k)])
+    tune_s = time.time() - t0
 
     def step_cnn(t):
-        for x in xs:
-            x.zero_()
-        P.predict(test_ops[t], src, U=U_cnn)
-        return ddg.augmented_gmres_solve_batched(ctx, test_ops[t], test_b[t], U_cnn, x=xs, **kw)
+        return solve_cnn(test_ops[t], test_b[t])
 
     def step_pca(t):
-        for x in xs:
-            x.zero_()
-        Us = [U_pca[g.wavelength] for g in grids for _ in range(n_step // len(grids))]
-        return ddg.augmented_gmres_solve_batched(ctx, test_ops[t], test_b[t], Us, x=xs, **kw)
+        return solve_pca(test_ops[t], test_b[t])
 
     def step_plain(t):
-        for x in xs:
-            x.zero_()
-        return ddg.gmres_solve_batched(ctx, test_ops[t], test_b[t], x=xs, **kw)
+        return solve_plain(test_ops[t], test_b[t])
 
     def timed(step, K, W, start=0, profile=False, clocks=False):
         """W untimed then K timed steps on held-out trajectories start, start+1, ...
@@ -408,6 +494,7 @@ def run_ours(args, rank, world):
         return pass_of(r), r
 
     K, W = args.steps, args.warmup
+    set_policy(pol_cnn)
     head = timed(step_cnn, K, W, start=0, clocks=True)
     value = head["solved"] / (head["ms"] / 1e3)
     # the same step with CUDA events around every launch (they order the
@@ -417,7 +504,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    P.predict(test_ops[0], src, U=U_cnn)
+    P.predict(test_ops[0], src, U=U_cnn_rows)
     e1.record()
     torch.cuda.synchronize()
     predict_ms = e0.elapsed_time(e1)
@@ -425,6 +512,7 @@ def run_ours(args, rank, world):
     # the CNN's pass over the 512 held-out solves: the first 16 timed steps
     # when there are that many (they start at trajectory W mod 16 and go round)
     cnn_pass = pass_of(head) if K >= N_TEST_TRAJ else one_pass(step_cnn)[0]
+    set_policy(pol_pca)
     pca_pass, _ = one_pass(step_pca)
     plain_pass = None
     plain_sample = None
@@ -438,8 +526,18 @@ def run_ours(args, rank, world):
                                               maxit=20000, precision=args.precision)
         plain_sample = {"trajectory": N_TRAIN_TRAJ, "maxit": 20000, **summarize(inf_u, test_wl[0])}
 
-    levers = run_levers(ddg, torch, args, ctx, grids, test_ops, test_b, test_wl, U_pca, P, src, D, kw,
-                        one_pass, step_cnn) if args.levers else None
+    levers = None
+    if args.levers:
+        # what moves the CNN's gain: the CNN's vectors alone (each restart
+        # policy), and the headline's subspace with each fixed policy
+        levers = {}
+        for name, solve, cands in (("cnn8", solve_cnn8, [(1, 0), (every, args.cnn_k)]),
+                                   ("pca20_plus_cnn8", solve_cnn, [(1, 0), (1, args.k), (every, kc)])):
+            for cand in cands:
+                set_policy({lam: cand for lam in WAVELENGTHS})
+                levers[f"{name}_cycles{min(cand[0], 99)}_keep{cand[1]}"] = one_pass(
+                    lambda t, solve=solve: solve(test_ops[t], test_b[t]))[0]
+        set_policy(pol_cnn)
 
     # --- e2e: host permittivities in, host fields out, through fdfd_solve_host
     eps_host = [[torch.from_numpy(np.ascontiguousarray(e)).pin_memory() for e in test_eps[t]]
@@ -447,9 +545,11 @@ def run_ours(args, rank, world):
     x_host = [torch.empty(D, dtype=torch.complex128).pin_memory() for _ in range(n_step)]
     e2e_grids = [g for g in grids for _ in range(n_step // len(grids))]
 
+    set_policy(pol_cnn)
+
     def step_e2e(t):
         ep = [eps_host[t][j] for _ in grids for j in range(n_step // len(grids))]
-        inf, st_ = ddg.fdfd_solve_host(ctx, e2e_grids, ep, src, x_host, P=P, **kw)
+        inf, st_ = ddg.fdfd_solve_host(ctx, e2e_grids, ep, src, x_host, P=P, U_fixed=U_pca_step, **kw)
         return None, inf, st_
 
     eK = max(2, min(K, 4))
@@ -537,29 +637,6 @@ def train_cnn(ddg, args, grids, train_ops, b_of, U_base, src, D, steps=None, n_p
     return P
 
 
-def run_levers(ddg, torch, args, ctx, grids, test_ops, test_b, test_wl, U_pca, P, src, D, kw, one_pass, step_cnn):
-    """What moves the CNN's gain: the restart policy, PCA-20 and CNN-8 as one
-    subspace, and (measured separately) k and the training size."""
-    out = {}
-    ctx.set_augmented_cycles(1)
-    out["cnn_first_cycle_only"], _ = one_pass(step_cnn)
-    ctx.set_augmented_cycles(args.aug_cycles)
-    n_step = len(test_ops[0])
-    U_cnn = [torch.empty((args.cnn_k, D), dtype=torch.complex128, device="cuda") for _ in range(n_step)]
-    xs = [torch.zeros(D, dtype=torch.complex128, device="cuda") for _ in range(n_step)]
-
-    def step_both(t):
-        for x in xs:
-            x.zero_()
-        P.predict(test_ops[t], src, U=U_cnn)
-        Us = [torch.cat([U_pca[g.wavelength], U_cnn[j]]) for j, g in
-              enumerate(g for g in grids for _ in range(n_step // len(grids)))]
-        return ddg.augmented_gmres_solve_batched(ctx, test_ops[t], test_b[t], Us, x=xs, **kw)
-
-    out["pca20_plus_cnn8"], _ = one_pass(step_both)
-    return out
-
-
 def roofline(args, prof):
     peaks = {}
     try:
@@ -588,6 +665,237 @@ def roofline(args, prof):
             "share_of_kernel_time": round(d_ms / total_ms, 4),
             "classes": {c: {"ms": round(v[0], 2), "GBps": round(v[1] / max(v[0], 1e-9) / 1e6, 1),
                             "launches": v[2]} for c, v in prof.items()}}
+
+
+# ------------------------------------------------------------------ other workloads
+def timed_call(torch, fn):
+    """One call between CUDA events on the current stream: (result, ms)."""
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return r, e0.elapsed_time(e1)
+
+
+def run_large(args, rank, world):
+    """The large grid: 1024x1024 at 20 nm (about 1M unknowns), 1550 nm,
+    20-cell PML; 64 held-out solves (4 trajectories x 16 steps, seeds
+    PCG64(5000 + t), t < 4); the CNN (k = 16) trained with the residual loss on
+    256 problems of trajectories 4-19, its output offset the 16 leading PCs of
+    16 approximate training fields (plain GMRES(200), 2000 steps: restarted
+    GMRES does not converge on this grid).  Plain and CNN-augmented GMRES(200)
+    in complex64 + FP64 refinement to 1e-6, and the FP32-only path to 1e-4, all
+    capped at --maxit; a solve that misses its tolerance reports the steps run
+    and the residual reached."""
+    import torch
+    import paper_1902_00090_gb300 as ddg
+    from paper_1902_00090_gb300 import inputs
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    g = inputs.grid_1024()
+    src = (g.i_src, g.sigma_src, g.j_src)
+    k = 16
+    t0 = time.time()
+    test_ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device=dev)) for t in range(4)
+                for e in inputs.trajectory_eps(g, 5, t)]
+    train_ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device=dev)) for t in range(4, 20)
+                 for e in inputs.trajectory_eps(g, 5, t)]
+    b = ddg.fdfd_source(test_ops[0], *src)
+    ctx = ddg.Context()
+    ctx.set_graphs(args.graphs == "on")
+    ctx.set_basis_storage(args.basis)
+    ctx.set_augmented_cycles(args.aug_cycles)
+    pick = list(range(0, len(train_ops), len(train_ops) // 16))[:16]
+    xs, inf_f, _ = ddg.gmres_solve_batched(ctx, [train_ops[i] for i in pick], [b] * len(pick), tol=1e-6,
+                                           restart=200, maxit=2000, precision="c64")
+    U_base, _ = ddg.pca_fit(ctx, torch.stack(xs), k)
+    del xs
+    P = ddg.Predictor(k=k)
+    P.init_he(seed=0)
+    P.set_output_base(U_base, g.nx, g.ny, scale=float(np.sqrt(g.D)))
+    P.zero_head()
+    P.set_loss("residual")
+    rng = np.random.default_rng(0)
+    batch = 4
+    losses = [P.train_step([train_ops[i] for i in rng.choice(len(train_ops), batch, replace=False)], src,
+                           [b] * batch, args.cnn_lr) for _ in range(args.cnn_steps)]
+    setup_s = time.time() - t0
+    n = len(test_ops)
+    bs = [b] * n
+    x = [torch.zeros(g.D, dtype=torch.complex128, device=dev) for _ in range(n)]
+    U = [torch.empty((k, g.D), dtype=torch.complex128, device=dev) for _ in range(n)]
+    out = {}
+    for name, tol, prec in (("c64_refine_1e-6", 1e-6, "c64"), ("fp32_only_1e-4", 1e-4, "c64_only")):
+        for variant in ("plain", "cnn"):
+            for v in x:
+                v.zero_()
+            if variant == "plain":
+                (_, inf, st), ms = timed_call(torch, lambda: ddg.gmres_solve_batched(
+                    ctx, test_ops, bs, x=x, tol=tol, restart=args.restart, maxit=args.maxit, precision=prec))
+            else:
+                def go():
+                    P.predict(test_ops, src, U=U)
+                    return ddg.augmented_gmres_solve_batched(ctx, test_ops, bs, U, x=x, tol=tol,
+                                                             restart=args.restart, maxit=args.maxit, precision=prec)
+                (_, inf, st), ms = timed_call(torch, go)
+            conv = sum(i["converged"] for i in inf)
+            out[f"{variant}_{name}"] = {"value": round(conv / (ms / 1e3), 4), "unit": "solves/s",
+                                        "seconds": round(ms / 1e3, 2), "tol": tol, **summarize(inf)}
+    # HBM fraction of the Arnoldi kernels at this size: a short profiled run
+    ctx.profile_enable(True)
+    for v in x:
+        v.zero_()
+    ddg.gmres_solve_batched(ctx, test_ops, bs, x=x, tol=1e-6, restart=args.restart, maxit=2 * args.restart,
+                            precision="c64")
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    roof = roofline(args, prof)
+    roof["timing"] = "CUDA events around every launch, two restart cycles of the 64 plain solves"
+    return {"metric": METRIC, "workload": "large1024", "value": out["cnn_c64_refine_1e-6"]["value"],
+            "unit": "solves/s", "n_gpus": world, "higher_is_better": True, "dtype": "c64+f64", "data": "synthetic",
+            "config": {"workload": "large1024: 1024x1024 Yee grid at 20 nm (1,048,576 unknowns), 1550 nm, "
+                                   "20-cell PML, 64 held-out solves (4 trajectories x 16), CNN k=16 against plain "
+                                   "GMRES(200); complex64 + FP64 refinement to 1e-6 and FP32-only to 1e-4",
+                       "restart": args.restart, "maxit": args.maxit,
+                       "krylov_basis_storage": args.basis, "basis_bytes": n * (args.restart + 1) * g.D * 8,
+                       "cnn_train_steps": args.cnn_steps, "cnn_batch": batch,
+                       "restart_policy": "predicted subspace kept in every cycle"
+                       if args.aug_cycles >= args.maxit else f"first {args.aug_cycles} cycle(s)"},
+            "runs": out, "offset_fields": summarize(inf_f),
+            "cnn_train_loss_first": round(float(np.mean(losses[:10])), 5),
+            "cnn_train_loss_last": round(float(np.mean(losses[-10:])), 5), "setup_s": round(setup_s, 1),
+            "roofline": roof}
+
+
+BATCH_SIZES = ((128, 128), (192, 192), (256, 256), (384, 256))
+
+
+def run_batched(args, rank, world):
+    """The batched-solves workload: 1024 correlated solves from 64 design
+    trajectories (16 per grid size: 128x128, 192x192, 256x256, 384x256; 40 nm,
+    1550 nm; seeds PCG64(4000 + t), trajectories 32 s + 16 .. 32 s + 31 of size
+    s held out, 32 s .. 32 s + 15 for training), run through the solve queue
+    (group width and lanes autotuned) as three variants: plain GMRES, PCA-20
+    and CNN-8 (PCA and CNN fitted and trained per grid size), plus the CNN
+    with recycling along the trajectories (gmres_solve_trajectories).
+    Complex64 + FP64 refinement to 1e-6, cap --maxit."""
+    import torch
+    import paper_1902_00090_gb300 as ddg
+    from paper_1902_00090_gb300 import autotune, inputs
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    lanes = []
+    for _ in range(2):
+        c = ddg.Context()
+        c.set_graphs(args.graphs == "on")
+        c.set_basis_storage(args.basis)
+        c.set_augmented_cycles(args.aug_cycles)
+        lanes.append(c)
+    ctx = lanes[0]
+    ops, bs, U_pca, U_cnn, per_size = [], [], [], [], {}
+    traj_ops = {}
+    for si, (nx, ny) in enumerate(BATCH_SIZES):
+        g = inputs.grid_for(nx, ny)
+        src = (g.i_src, g.sigma_src, g.j_src)
+        tr_ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device=dev)) for t in range(16)
+                  for e in inputs.trajectory_eps(g, 4, 32 * si + t)]
+        b = ddg.fdfd_source(tr_ops[0], *src)
+        pick = list(range(0, len(tr_ops), len(tr_ops) // args.n_pca))[: args.n_pca]
+        xs, inf, _ = ddg.gmres_solve_batched(ctx, [tr_ops[i] for i in pick], [b] * len(pick), tol=1e-6,
+                                             restart=200, maxit=20000, precision="c64")
+        F = torch.stack(xs)
+        up, _ = ddg.pca_fit(ctx, F, args.k)
+        ub, _ = ddg.pca_fit(ctx, F, args.cnn_k)
+        del F, xs
+        P = ddg.Predictor(k=args.cnn_k)
+        P.init_he(seed=si)
+        P.set_output_base(ub, nx, ny, scale=float(np.sqrt(g.D)))
+        P.zero_head()
+        P.set_loss("residual")
+        rng = np.random.default_rng(si)
+        for _ in range(args.cnn_steps):
+            idx = rng.choice(len(tr_ops), args.cnn_batch, replace=False)
+            P.train_step([tr_ops[i] for i in idx], src, [b] * args.cnn_batch, args.cnn_lr)
+        del tr_ops
+        te = [[ddg.fdfd_operator(g, torch.as_tensor(e, device=dev)) for e in inputs.trajectory_eps(g, 4, 32 * si + 16 + t)]
+              for t in range(16)]
+        traj_ops[(nx, ny)] = (te, b)
+        flat = [op for tr in te for op in tr]
+        ops += flat
+        bs += [b] * len(flat)
+        U_pca += [up] * len(flat)
+        per_size[(nx, ny)] = (P, src, flat)
+    setup_s = time.time() - t0
+    n = len(ops)
+    kw = dict(tol=1e-6, maxit=args.maxit, precision=args.precision)
+
+    def run(ln, A, b, U, w, nl, tol, m, maxit, prec):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _, infos, _ = ddg.gmres_solve_queue(ln[:nl], A, b, U=U, width=w, tol=tol, restart=m, maxit=maxit,
+                                            precision=prec)
+        torch.cuda.synchronize()
+        return sum(1 for i in infos if i["converged"]) / (time.perf_counter() - t1)
+
+    tune = autotune.tune_queue(lanes, ops, bs, sample=64, widths=(32, 64, 128), lane_counts=(1, 2),
+                               restart=args.restart, basis=args.basis, run=run, repeats=1, **kw)
+    width, nl = tune["width"], tune["lanes"]
+    out = {}
+
+    def predict_all():
+        Us = []
+        for (nx, ny), (P, src, flat) in per_size.items():
+            Us += P.predict(flat, src)
+        return Us
+
+    for variant in ("plain", "pca20", "cnn8"):
+        def go():
+            U = None if variant == "plain" else (U_pca if variant == "pca20" else predict_all())
+            return ddg.gmres_solve_queue(lanes[:nl], ops, bs, U=U, width=width, restart=args.restart, **kw)
+        (_, inf, st), ms = timed_call(torch, go)
+        conv = sum(i["converged"] for i in inf)
+        sizes = [f"{o.nx}x{o.ny}" for o in ops]
+        d = {"value": round(conv / (ms / 1e3), 3), "unit": "solves/s", "seconds": round(ms / 1e3, 2),
+             **summarize(inf)}
+        for sz in sorted(set(sizes)):
+            d[sz] = summarize([i for i, z in zip(inf, sizes) if z == sz])
+        out[variant] = d
+
+    # the CNN with recycling along the trajectories: per grid size, step t of
+    # its 16 trajectories batched, subspace [CNN-8 | previous solution]
+    def recycle():
+        infs = []
+        for (nx, ny), (te, b) in traj_ops.items():
+            P, src, flat = per_size[(nx, ny)]
+            Us = P.predict(flat, src)
+            Ut = [Us[16 * r:16 * (r + 1)] for r in range(16)]
+            _, inf, _ = ddg.gmres_solve_trajectories(ctx, te, [[b] * 16 for _ in range(16)], Ut,
+                                                     restart=args.restart, **kw)
+            infs += [i for tr in inf for i in tr]
+        return infs
+    inf_r, ms = timed_call(torch, recycle)
+    out["cnn8_recycle"] = {"value": round(sum(i["converged"] for i in inf_r) / (ms / 1e3), 3), "unit": "solves/s",
+                           "seconds": round(ms / 1e3, 2), **summarize(inf_r),
+                           "note": "per grid size, step t of the 16 trajectories in one batch (16 sequential "
+                                   "batches per size), no queue"}
+    for c in lanes:
+        c.close()
+    return {"metric": METRIC, "workload": "batched", "value": out["cnn8"]["value"], "unit": "solves/s",
+            "n_gpus": world, "higher_is_better": True, "dtype": "c64+f64", "data": "synthetic",
+            "config": {"workload": "batched: 1024 correlated solves from 64 trajectories, 256 each of 128x128, "
+                                   "192x192, 256x256 and 384x256 (40 nm, 1550 nm), through the solve queue; plain, "
+                                   "PCA-20 and CNN-8 (fitted and trained per grid size)",
+                       "restart": args.restart, "maxit": args.maxit, "queue": {"width": width, "lanes": nl},
+                       "tuning": [{"width": t[0], "lanes": t[1], "solves_per_s": round(t[2], 2)}
+                                  for t in tune["timings"]],
+                       "krylov_basis_storage": args.basis, "cnn_train_steps": args.cnn_steps},
+            "variants": out, "speedup_cnn_vs_plain": round(out["cnn8"]["value"] / out["plain"]["value"], 3),
+            "setup_s": round(setup_s, 1)}
 
 
 # ------------------------------------------------------------------ oracle (CPU)
@@ -700,7 +1008,7 @@ def run_reference(args, rank, world):
 def main():
     args = parse()
     if args.case is not None:
-        {"solver": case_solver, "cnn": case_cnn}[args.case](args)
+        {"solver": case_solver, "cnn": case_cnn, "stencil": case_stencil}[args.case](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -713,7 +1021,7 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    line = run_ours(args, rank, world)
+    line = {"splitter256": run_ours, "large1024": run_large, "batched": run_batched}[args.workload](args, rank, world)
     spec = line.pop("_oracle_sample", None)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline and spec is not None:

@@ -170,6 +170,19 @@ ddg_status ddg_context_set_fallback(ddg_context* ctx, double threshold);
    method for the first cycle); 0 keeps only the least-squares step over V;
    a value >= maxit keeps V in every cycle. */
 ddg_status ddg_context_set_augmented_cycles(ddg_context* ctx, int cycles);
+/* Restart policy of augmented solves, in full (no paper counterpart; the
+   paper does not restart): the first `cycles` restart cycles use all k
+   columns of V; later cycles keep the leading `keep` columns (A V = C R is
+   triangular in the column order, so their factors are the leading columns of
+   C and the leading block of R: nothing is recomputed) and keep = 0 continues
+   as plain GMRES.  With wavelength = 0 this sets the default for every solve
+   (ddg_context_set_augmented_cycles sets `cycles` alone); with a wavelength in
+   metres (> 0, matched to 1e-9 relative) the policy of the solves whose
+   operator has that wavelength, which overrides the default (one set of
+   problems, e.g. one device at two wavelengths, may need two policies).
+   Order V so that the vectors worth keeping come first.
+   cycles >= 0, 0 <= keep <= 32, else DDG_EINVAL. */
+ddg_status ddg_context_set_augmented_policy(ddg_context* ctx, double wavelength, int cycles, int keep);
 /* Limit of the bounded device waits of the solver (no paper counterpart): an
    Arnoldi kernel waits at most `ns` nanoseconds for a bulk copy of basis
    columns into shared memory (default 1e9, 1 s).  A wait that runs out stops
@@ -269,6 +282,31 @@ ddg_status augmented_gmres_solve_batched(ddg_context* ctx, int n, const ddg_op* 
                                          int k, double* const* x, double tol, int restart,
                                          int maxit, ddg_precision prec, ddg_info* info,
                                          void* stream);
+
+/*
+ * gmres_solve_trajectories -- Krylov subspace recycling along design
+ * trajectories (Sec. I names recycling across a sequence of related solves as
+ * prior art, and the supplement's update rule is that of GCROT): n_traj
+ * trajectories of n_steps correlated problems each (an optimisation's
+ * successive designs), solved step by step.  Step t of every trajectory runs in
+ * one batched augmented solve (augmented_gmres_solve_batched) whose subspace
+ * is [U (the k predicted vectors of that problem) | x_{t-1} (the same
+ * trajectory's solution of step t-1)]; step 0 uses U alone, or plain GMRES when
+ * U is NULL (k = 0).  Every solve starts from x = 0 (the previous solution
+ * enters through the subspace: its least-squares step already contains it).
+ *   A, b, x, U, info  (host) arrays of n_traj * n_steps entries,
+ *                     trajectory-major (entry r * n_steps + t); a trajectory
+ *                     keeps one grid size; U may be NULL (then k = 0).
+ *   k                 0 <= k <= 31 predicted vectors per problem.
+ *   other arguments   as augmented_gmres_solve_batched (the context's options
+ *                     apply to every step).
+ * The subspaces are assembled in a buffer the context keeps (n_traj (k+1) D
+ * complex128).  Returns DDG_ENOCONV if any solve missed the tolerance.
+ */
+ddg_status gmres_solve_trajectories(ddg_context* ctx, int n_traj, int n_steps, const ddg_op* const* A,
+                                    const double* const* b, const double* const* U, int k, double* const* x,
+                                    double tol, int restart, int maxit, ddg_precision prec, ddg_info* info,
+                                    void* stream);
 
 /*
  * gmres_solve_queue -- a queue of n independent solves of Eq. 2 / Eqs. 3-4
@@ -423,26 +461,34 @@ ddg_status predictor_load(ddg_predictor* P, const char* path);
  * fields, from and to HOST memory in one call (Eq. 1 set up, Eqs. 3-4 solved;
  * no paper counterpart beyond that): for each of n problems the permittivity
  * is copied to the device, the operator (fdfd_operator) and the source
- * (fdfd_source) are built, the predicted subspace is computed when P is not
- * NULL (subspace_predict, then augmented_gmres_solve_batched) or plain GMRES
- * runs (gmres_solve_batched), and the solution is copied back.
+ * (fdfd_source) are built, the subspace [U_fixed[s] | the predictor's k
+ * vectors] is assembled (subspace_predict when P is not NULL) and
+ * augmented_gmres_solve_batched runs, or plain GMRES (gmres_solve_batched)
+ * when there is neither P nor U_fixed; the solution is copied back.
  *   grids     (host) n problem descriptions (with P: one grid size; the
  *             wavelengths may differ, e.g. one device at two wavelengths).
  *   eps_host  (host) n pointers to ny*nx doubles, row-major (pinned memory
  *             lets the copies run asynchronously).
  *   i_src, sigma, j_c  the source of every problem, as fdfd_source.
+ *   U_fixed   NULL, or (host array of) n DEVICE pointers to D x k_fixed
+ *             complex128 column-major bases placed before the predicted
+ *             vectors (e.g. the principal components of each problem's
+ *             wavelength, to be kept across restarts with
+ *             ddg_context_set_augmented_policy); k_fixed = 0 without it, else
+ *             1 <= k_fixed and k_fixed + k <= 32.
  *   x_host    (host) n pointers to 2*D doubles: the fields (x0 = 0).
  *   tol, restart, maxit, prec, info: as the batched solves.
  * The device copies of eps, b, x and the subspace live in a buffer that the
- * context keeps and grows (about (8 + 32 + 16 k) D bytes per problem).
+ * context keeps and grows (about (8 + 32 + 16 (k_fixed + k)) D bytes per
+ * problem).
  * Returns the solve's status (DDG_ENOCONV: fields copied back, some solve
  * missed the tolerance); on other errors x_host is not written.
  * Synchronises `stream`.
  */
 ddg_status fdfd_solve_host(ddg_context* ctx, ddg_predictor* P, int n, const ddg_grid* grids,
-                           const double* const* eps_host, int i_src, double sigma, double j_c, double tol,
-                           int restart, int maxit, ddg_precision prec, double* const* x_host, ddg_info* info,
-                           void* stream);
+                           const double* const* eps_host, int i_src, double sigma, double j_c,
+                           const double* const* U_fixed, int k_fixed, double tol, int restart, int maxit,
+                           ddg_precision prec, double* const* x_host, ddg_info* info, void* stream);
 
 /*
  * gmres_solve_noalloc -- gmres_solve without any device allocation.  (The paper

@@ -203,12 +203,14 @@ def augmentation_setup(A, V: np.ndarray) -> Augmentation:
 def augmented_gmres(A, b: np.ndarray, V: np.ndarray, x0=None, tol: float = 1e-6,
                     restart: int = 200, maxit: int = 5000, reorth: bool = True,
                     breakdown_tol: float = 1e-14, keep_basis: bool = False,
-                    aug_cycles: int | None = None):
+                    aug_cycles: int | None = None, aug_keep: int = 0):
     """Data-driven GMRES (Eq. 3) with the update rule of the supplement.
 
     aug_cycles (restart reading): None keeps V in every cycle; an integer c runs
-    the augmented method in the first max(c, 1) cycles and continues as plain
-    GMRES (Eq. 2) from the current iterate afterwards.
+    the augmented method in the first max(c, 1) cycles and continues from the
+    current iterate afterwards, as plain GMRES (Eq. 2) when aug_keep = 0, else
+    as data-driven GMRES with the leading aug_keep columns of V (their own
+    thin QR, Eq. S1).
 
     Returns (f, info); with keep_basis also a dict holding C, Q, H, B of the last
     cycle for invariant checks (C^H Q = 0, Eq. S3).
@@ -237,9 +239,14 @@ def augmented_gmres(A, b: np.ndarray, V: np.ndarray, x0=None, tol: float = 1e-6,
         if info.iters >= maxit or info.breakdown:
             break
         if aug_cycles is not None and info.cycles >= max(1, aug_cycles):
-            # the augmented cycles are done: plain GMRES from the current iterate
-            xp, ip = plain_gmres(A, b, x0=x, tol=tol, restart=restart, maxit=maxit - info.iters,
-                                 reorth=reorth, breakdown_tol=breakdown_tol)
+            # the augmented cycles are done: plain GMRES, or data-driven GMRES
+            # with the leading aug_keep vectors, from the current iterate
+            if aug_keep > 0:
+                xp, ip = augmented_gmres(A, b, V[:, :aug_keep], x0=x, tol=tol, restart=restart,
+                                         maxit=maxit - info.iters, reorth=reorth, breakdown_tol=breakdown_tol)
+            else:
+                xp, ip = plain_gmres(A, b, x0=x, tol=tol, restart=restart, maxit=maxit - info.iters,
+                                     reorth=reorth, breakdown_tol=breakdown_tol)
             x = xp
             info.iters += ip.iters
             info.cycles += ip.cycles

@@ -64,6 +64,7 @@ _SIGS = {
     "ddg_context_set_preconditioner": (C.c_int, [_vp, C.c_int]),
     "ddg_context_set_augmented_cycles": (C.c_int, [_vp, C.c_int]),
     "ddg_context_set_wait_limit": (C.c_int, [_vp, C.c_longlong]),
+    "ddg_context_set_augmented_policy": (C.c_int, [_vp, C.c_double, C.c_int, C.c_int]),
     "ddg_context_set_workspace_limit": (C.c_int, [_vp, C.c_longlong]),
     "ddg_context_profile_enable": (C.c_int, [_vp, C.c_int]),
     "ddg_context_profile_read": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -106,9 +107,12 @@ _SIGS = {
     "gmres_solve_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, C.c_int,
                                       C.POINTER(ddg_info), _vp]),
     "predictor_num_outputs": (C.c_int, [_vp]),
+    "gmres_solve_trajectories": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),
+                                           C.c_int, C.POINTER(_vp), C.c_double, C.c_int, C.c_int, C.c_int,
+                                           C.POINTER(ddg_info), _vp]),
     "fdfd_solve_host": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(ddg_grid), C.POINTER(_vp), C.c_int, C.c_double,
-                                  C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(_vp),
-                                  C.POINTER(ddg_info), _vp]),
+                                  C.c_double, C.POINTER(_vp), C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
+                                  C.POINTER(_vp), C.POINTER(ddg_info), _vp]),
     "pca_fit": (C.c_int, [_vp, _vp, C.c_longlong, C.c_int, C.c_int, _vp, C.POINTER(C.c_double), _vp]),
     "augmented_gmres_solve_batched": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp),
                                                 C.POINTER(_vp), C.c_int, C.POINTER(_vp),
@@ -210,6 +214,12 @@ class Context:
         """'none' (default) or 'jacobi' (right preconditioner M = diag(A), the data-free baseline)."""
         code = {"none": 0, "jacobi": 1}[kind]
         _check(load().ddg_context_set_preconditioner(self._h, code), "ddg_context_set_preconditioner")
+
+    def set_augmented_policy(self, cycles: int, keep: int = 0, wavelength: float = 0.0):
+        """Cycles that use all of V, then the leading `keep` columns (0: plain);
+        for every solve (wavelength 0) or the solves at one wavelength [m]."""
+        _check(load().ddg_context_set_augmented_policy(self._h, float(wavelength), int(cycles), int(keep)),
+               "ddg_context_set_augmented_policy")
 
     def set_wait_limit(self, ns: int):
         """Limit (ns) of the solver's bounded device waits; DDG_ETIMEOUT when one runs out."""
@@ -420,6 +430,39 @@ def augmented_gmres_solve_batched(ctx: Context, A, b, U, x=None, tol=1e-6, resta
     return x, [i.as_dict() for i in infos], st
 
 
+def gmres_solve_trajectories(ctx: Context, A, b, U=None, x=None, tol=1e-6, restart=200, maxit=5000,
+                             precision="c64", stream=None):
+    """A, b (and U, x): lists of n_traj lists of n_steps entries (one trajectory
+    per inner list); U entries (k, D) complex128 or U None.  Returns (x, info,
+    status) in the same nesting."""
+    torch = _torch()
+    n_traj, n_steps = len(A), len(A[0])
+    if any(len(a) != n_steps for a in A):
+        raise ValueError("every trajectory needs the same number of steps")
+    fa = [a for tr in A for a in tr]
+    fb = [v for tr in b for v in tr]
+    if x is None:
+        x = [[torch.zeros_like(v) for v in tr] for tr in b]
+    fx = [v for tr in x for v in tr]
+    sizes = [a.D for a in fa]
+    k = 0
+    hu = None
+    if U is not None:
+        fu = [u for tr in U for u in tr]
+        k = fu[0].shape[0]
+        hu = _ptr_array(fu, torch.complex128, "U", [k * s for s in sizes])
+    n = len(fa)
+    infos = (ddg_info * n)()
+    st = load().gmres_solve_trajectories(ctx.handle, n_traj, n_steps, (_vp * n)(*[a.handle.value for a in fa]),
+                                         _ptr_array(fb, torch.complex128, "b", sizes), hu, int(k),
+                                         _ptr_array(fx, torch.complex128, "x", sizes), float(tol), int(restart),
+                                         int(maxit), _prec(precision), infos, _stream(stream))
+    if st not in (0, 4):
+        _check(st, "gmres_solve_trajectories")
+    inf = [i.as_dict() for i in infos]
+    return x, [inf[r * n_steps:(r + 1) * n_steps] for r in range(n_traj)], st
+
+
 def gmres_solve_queue(lanes, A, b, U=None, x=None, width=64, streams=None, tol=1e-6, restart=200,
                       maxit=5000, precision="c64"):
     """A queue of independent solves (A, b, x, U: lists, one entry per solve; U
@@ -489,12 +532,13 @@ def gmres_solve_noalloc(A: Operator, b, x=None, tol=1e-6, restart=200, maxit=500
     return x, info.as_dict(), st
 
 
-def fdfd_solve_host(ctx: Context, grids, eps_host, src, x_host, P=None, tol=1e-6, restart=200, maxit=5000,
-                    precision="c64", stream=None):
+def fdfd_solve_host(ctx: Context, grids, eps_host, src, x_host, P=None, U_fixed=None, tol=1e-6, restart=200,
+                    maxit=5000, precision="c64", stream=None):
     """fdfd_solve_host: grids (one per problem), eps_host (host float64 arrays or
     CPU tensors of ny*nx values, ideally pinned), src = (i_src, sigma, j_c),
-    x_host (host complex128 arrays or CPU tensors of D values, written).
-    Returns (info list, status)."""
+    x_host (host complex128 arrays or CPU tensors of D values, written);
+    U_fixed: None or one CUDA complex128 (k_fixed, D) tensor per problem,
+    placed before the predictor's vectors.  Returns (info list, status)."""
     n = len(grids)
     hg = (ddg_grid * n)(*[make_grid(g) for g in grids])
 
@@ -510,10 +554,15 @@ def fdfd_solve_host(ctx: Context, grids, eps_host, src, x_host, P=None, tol=1e-6
     he = (_vp * n)(*[hptr(e, f"eps[{i}]", 8, g.nx * g.ny) for i, (e, g) in enumerate(zip(eps_host, hg))])
     hx = (_vp * n)(*[hptr(x, f"x[{i}]", 16, g.nx * g.ny) for i, (x, g) in enumerate(zip(x_host, hg))])
     i_src, sigma, j_c = src
+    hu, kf = None, 0
+    if U_fixed is not None:
+        import torch
+        kf = int(U_fixed[0].shape[0])
+        hu = _ptr_array(U_fixed, torch.complex128, "U_fixed", [kf * g.nx * g.ny for g in hg])
     infos = (ddg_info * n)()
     st = load().fdfd_solve_host(ctx.handle, P.handle if P is not None else None, n, hg, he, int(i_src),
-                                float(sigma), float(j_c), float(tol), int(restart), int(maxit), _prec(precision),
-                                hx, infos, _stream(stream))
+                                float(sigma), float(j_c), hu, kf, float(tol), int(restart), int(maxit),
+                                _prec(precision), hx, infos, _stream(stream))
     if st not in (0, 4):
         _check(st, "fdfd_solve_host")
     return [i.as_dict() for i in infos], st

@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <cmath>
 #include <new>
 
 #include "common.cuh"
@@ -128,6 +129,7 @@ extern "C" ddg_status ddg_context_destroy(ddg_context* ctx) {
     Context* c = reinterpret_cast<Context*>(ctx);
     cudaFree(c->ws);
     cudaFree(c->io);
+    cudaFree(c->vbuf);
     cudaFreeHost(c->host_counts);
     if (c->ev[0]) cudaEventDestroy(c->ev[0]);
     if (c->ev[1]) cudaEventDestroy(c->ev[1]);
@@ -210,6 +212,27 @@ extern "C" ddg_status ddg_context_set_preconditioner(ddg_context* ctx, int kind)
 extern "C" ddg_status ddg_context_set_fallback(ddg_context* ctx, double threshold) {
     if (!ctx || !(threshold > 0.0)) { set_error("ddg_context_set_fallback: threshold must be > 0"); return DDG_EINVAL; }
     reinterpret_cast<Context*>(ctx)->fallback = threshold;
+    return DDG_OK;
+}
+
+extern "C" ddg_status ddg_context_set_augmented_policy(ddg_context* ctx, double wavelength, int cycles, int keep) {
+    if (!ctx || !(wavelength >= 0.0) || cycles < 0 || keep < 0 || keep > kMaxAug) {
+        set_error("ddg_context_set_augmented_policy: need wavelength >= 0, cycles >= 0, 0 <= keep <= %d", kMaxAug);
+        return DDG_EINVAL;
+    }
+    Context* c = reinterpret_cast<Context*>(ctx);
+    if (wavelength == 0.0) {
+        c->aug_cycles = cycles;
+        c->aug_keep = keep;
+        return DDG_OK;
+    }
+    for (auto& p : c->policies)
+        if (fabs(p.wavelength - wavelength) <= 1e-9 * fmax(p.wavelength, wavelength)) {
+            p.cycles = cycles;
+            p.keep = keep;
+            return DDG_OK;
+        }
+    c->policies.push_back({wavelength, cycles, keep});
     return DDG_OK;
 }
 

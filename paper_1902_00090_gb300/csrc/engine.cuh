@@ -81,7 +81,11 @@ struct Context {
     double inner_tol = 1e-5;         // DDG_C64_REFINE inner-cycle relative tolerance
     int orth = 1;                    // 0: CGS2 (two passes per step), 1: delayed CGS2 (one reduction)
     double fallback = 0.5;           // augmented: V-only residual above this -> plain GMRES after the V step
-    int aug_cycles = 1;              // augmented: restart cycles that keep V (later cycles run plain GMRES)
+    int aug_cycles = 1;              // augmented: restart cycles that keep all of V
+    int aug_keep = 0;                // augmented: leading columns of V kept after those cycles (0: plain GMRES)
+    // per-wavelength policies (cycles, keep) overriding the two above
+    struct Policy { double wavelength; int cycles, keep; };
+    std::vector<Policy> policies;
     int poll_every = 8;              // Arnoldi steps between host polls (host-driven loop)
     int graphs = 1;                  // delayed scheme: step loop as a CUDA graph with a device-side WHILE
     int half_basis = 0;              // complex64 solves: Krylov basis stored in IEEE half
@@ -90,6 +94,8 @@ struct Context {
     size_t ws_limit = 0;             // largest workspace the context may allocate (0: no limit)
     void* io = nullptr;              // fdfd_solve_host: device copies of the call's inputs and outputs
     size_t io_bytes = 0;
+    void* vbuf = nullptr;            // gmres_solve_trajectories: each trajectory's [U | x_{t-1}]
+    size_t vbuf_bytes = 0;
     int sm_count = 152;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     // launch accounting and profiling
@@ -126,6 +132,16 @@ struct Context {
     }
     // Adds the elapsed times of recorded launches (call after a stream sync).
     void resolve();
+    // Restart policy of an augmented solve at this wavelength.
+    void policy_for(double wavelength, int* cycles, int* keep) const {
+        *cycles = aug_cycles;
+        *keep = aug_keep;
+        for (const Policy& p : policies)
+            if (fabs(p.wavelength - wavelength) <= 1e-9 * fmax(p.wavelength, wavelength)) {
+                *cycles = p.cycles;
+                *keep = p.keep;
+            }
+    }
 };
 
 // Per-solve device pointers (read-only during a solve).
@@ -164,6 +180,8 @@ struct SolvePtrs {
     double2* coefy;            // [z = R^-1 x_V (N) | y (k)]
     unsigned* ticket;
     int chunk0, nchunks;
+    int aug_cycles;            // augmented: restart cycles that keep all of V (0: its least-squares step only)
+    int aug_keep;              // augmented: leading columns of V kept after those cycles (0: plain GMRES)
 };
 
 // Per-solve mutable state.
@@ -191,7 +209,6 @@ struct BatchArgs {
     double tol;
     double eta;        // inner relative tolerance (0 for complex128)
     double fallback;   // V-only relative residual above which an augmented solve continues as plain GMRES
-    int aug_cycles;    // restart cycles of an augmented solve that keep V (0: its least-squares step only)
     int maxit;
     int nsolves;       // solves in the batch (k_update2 puts one block per solve in front of its sweep)
     int* step;         // Arnoldi step of the graph-driven loop (kernels launched with i <= 0 add it)

@@ -319,9 +319,19 @@ __global__ void __launch_bounds__(kBlock) k_residual(BatchArgs a) {
         nb2 += t.y;
     }
     if (S->nb < 0.0) S->nb = sqrt(nb2);
-    // after a fallback (or a rank-deficient V), or once the augmented cycles are
-    // done, the solve continues as plain GMRES
-    if (S->fallback || (S->N > 0 && S->cycles >= max(1, a.aug_cycles))) S->N = 0;
+    // after a fallback (or a rank-deficient V) the solve continues as plain
+    // GMRES; once the augmented cycles are done it keeps the leading aug_keep
+    // columns of V (C and R of A V are triangular in the column order, so
+    // those columns of C and the leading block of R^-1 are the factors of the
+    // kept vectors): R^-1 is compacted to the smaller leading dimension
+    if (S->fallback) {
+        S->N = 0;
+    } else if (S->N > 0 && S->cycles >= max(1, P.aug_cycles) && P.aug_keep < S->N) {
+        const int N0 = S->N, N1 = max(0, P.aug_keep);
+        for (int l = 0; l < N1; ++l)
+            for (int n = 0; n < N1; ++n) P.Rinv[l * N1 + n] = P.Rinv[l * N0 + n];   // in place, forward
+        S->N = N1;
+    }
     const double nb = S->nb, rn = sqrt(rn2);
     S->rn = rn;
     S->pending = 0;
@@ -427,7 +437,7 @@ __global__ void __launch_bounds__(kBlock) k_update_r(BatchArgs a) {
     S->beta = nrm;
     if (S->cycles == 1) S->first_res = nrm / S->nb;
     S->k = 0;
-    if (S->cycles == 1 && (nrm > a.fallback * S->nb || a.aug_cycles == 0)) {
+    if (S->cycles == 1 && (nrm > a.fallback * S->nb || P.aug_cycles == 0)) {
         // the predicted subspace fails to cut the residual: keep its least-squares
         // step (x += V R^-1 C^H r at the cycle end) and continue as plain GMRES
         S->fallback = 1;
@@ -1898,6 +1908,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             P.b = reinterpret_cast<const double2*>(b[s]);
             P.x = reinterpret_cast<double2*>(x[s]);
             P.U = (Nreq > 0) ? reinterpret_cast<const double2*>(U[s]) : nullptr;
+            ctx->policy_for(op->wavelength, &P.aug_cycles, &P.aug_keep);
         }
         return c.off + 4096;
     };
@@ -1925,7 +1936,6 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     args.eta = eta;
     args.maxit = maxit;
     args.fallback = ctx->fallback;
-    args.aug_cycles = ctx->aug_cycles;
     args.nsolves = n;
     args.step = args.counts + 5;
     args.low_res = low_res ? 1 : 0;
@@ -2228,6 +2238,8 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     hp.b = reinterpret_cast<const double2*>(b);
     hp.x = reinterpret_cast<double2*>(x);
     hp.U = nullptr;
+    hp.aug_cycles = 1;
+    hp.aug_keep = 0;
     Carver t2{base, small_off};
     BatchArgs args;
     args.P = t2.take<SolvePtrs>(1);
@@ -2243,7 +2255,6 @@ static ddg_status run_single_noalloc(const ddg_op* A, const double* b, double* x
     args.eta = eta;
     args.maxit = maxit;
     args.fallback = 1e300;
-    args.aug_cycles = 1;
     args.nsolves = 1;
     args.step = args.counts + 5;
     args.low_res = 0;

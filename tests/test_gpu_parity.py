@@ -5,6 +5,8 @@ for the complex64 stencil); solves by the true relative residual recomputed
 with the oracle's sparse operator (<= tol) and the relative L2 distance to the
 oracle's direct solution (<= 1e-5 at tol = 1e-6, i.e. forward-error factor 10).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
@@ -46,6 +48,11 @@ GRIDS = [
     inputs.Grid(nx=128, ny=128),
     inputs.Grid(nx=192, ny=64, npml=10, i_src=20),
     inputs.Grid(nx=3, ny=5, npml=1, i_src=1, sigma_src=1.0, slab_cells=1),   # smallest allowed
+    # even widths take the two-cells-per-thread complex64 stencil: a row that
+    # ends inside a warp, the smallest such row, and rows over several blocks
+    inputs.Grid(nx=38, ny=9, npml=3, i_src=5, sigma_src=2.0, slab_cells=2),
+    inputs.Grid(nx=4, ny=5, npml=1, i_src=1, sigma_src=1.0, slab_cells=1),
+    inputs.Grid(nx=1030, ny=6, npml=2, i_src=9, sigma_src=2.0, slab_cells=2),
 ]
 
 
@@ -305,6 +312,7 @@ def test_batched_augmented_uneven(ctx):
         # a useful subspace: the solution of a perturbed problem plus noise
         A2 = fdfd.operator_for(g, eps * 1.01)
         Us.append(dev(np.stack([spla.spsolve(A2.tocsc(), bo), inputs.random_complex(g.D, seed)])))
+    direct = [spla.spsolve(A.tocsc(), bo) for A, bo in zip(As, bos)]
     for prec in ("c128", "c64"):
         xs, infos, st = ddg.augmented_gmres_solve_batched(ctx, ops, bs, Us, tol=1e-7, restart=30,
                                                           precision=prec)
@@ -312,6 +320,8 @@ def test_batched_augmented_uneven(ctx):
         for i in range(len(specs)):
             xh = host(xs[i])
             assert np.linalg.norm(bos[i] - As[i] @ xh) / np.linalg.norm(bos[i]) <= 1e-7
+            # the field: within the forward-error factor 10 of the tolerance of the direct solution
+            assert rel(xh, direct[i]) <= 1e-6
             assert infos[i]["first_step_rel_residual"] < 0.5
 
 
@@ -482,13 +492,16 @@ def test_half_basis_augmented_and_batched(ctx_f16):
     bo = fdfd.source_for(g)
     x_near = spla.spsolve(As[0].tocsc(), bo)
     U = dev(np.stack([x_near, inputs.random_complex(g.D, 9)]))
+    direct = [spla.spsolve(A.tocsc(), bo) for A in As]
     for prec, tol in (("c64", 1e-6), ("c64_only", 1e-4)):
         xs, infos, st = ddg.augmented_gmres_solve_batched(ctx_f16, ops, bs, [U] * len(ops), tol=tol, restart=50,
                                                           maxit=6000, precision=prec)
         assert st == 0
-        for A, x, i in zip(As, xs, infos):
+        for A, x, i, xd in zip(As, xs, infos, direct):
             assert i["converged"]
             assert np.linalg.norm(bo - A @ host(x)) / np.linalg.norm(bo) <= tol * 1.02
+            # the field against the direct solution: the 1e-5 bar at 1e-6 (and 1e-3 at 1e-4)
+            assert rel(host(x), xd) <= 10 * tol
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -564,3 +577,39 @@ def test_autotuner_times_the_library_and_picks_a_measured_candidate(tmp_path):
     r2 = autotune.tune_queue(lanes, ops, bs, sample=4, widths=(1, 2, 4), tol=1e-8, restart=30,
                              precision="c64", basis="f32", cache_path=cache)
     assert r2["cached"] and (r2["width"], r2["lanes"]) == (r["width"], r["lanes"])
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_restart_policy_per_wavelength_matches_oracle(prec):
+    # one batch, one device at two wavelengths, two restart policies: all four
+    # vectors in the first cycle, then the leading two kept (1550 nm, the
+    # default) or plain GMRES (1300 nm); each solve against the oracle with
+    # the same policy (c128: steps +-1 and the solution; c64: the tolerance)
+    ctx = ddg.Context()
+    ctx.set_fallback(2.0)
+    ctx.set_augmented_policy(1, keep=2)
+    ctx.set_augmented_policy(1, keep=0, wavelength=1300e-9)
+    ops, bs, Vs, refs = [], [], [], []
+    for lam, keep in ((1300e-9, 0), (1550e-9, 2)):
+        g0, eps, _, _ = small(24, npml=4, seed=21)
+        g = dataclasses.replace(g0, wavelength=lam)
+        A, b = fdfd.operator_for(g, eps), fdfd.source_for(g)
+        V = rand_V(g.D, 4, 22)
+        xo, io = gmres.augmented_gmres(A, b, V.T, tol=1e-9, restart=20, maxit=4000, aug_cycles=1, aug_keep=keep)
+        assert io.converged
+        ops.append(ddg.fdfd_operator(g, dev(eps, torch.float64)))
+        bs.append(ddg.fdfd_source(ops[-1], g.i_src, g.sigma_src, g.j_src))
+        Vs.append(dev(V))
+        refs.append((A, b, xo, io))
+    tol = 1e-9 if prec == "c128" else 1e-7
+    xs, infos, st = ddg.augmented_gmres_solve_batched(ctx, ops, bs, Vs, tol=tol, restart=20, maxit=4000,
+                                                      precision=prec)
+    assert st == 0
+    for x, info, (A, b, xo, io) in zip(xs, infos, refs):
+        assert np.linalg.norm(b - A @ host(x)) / np.linalg.norm(b) <= tol
+        if prec == "c128":
+            assert abs(info["iters"] - io.iters) <= 1, (info, io.iters)
+            assert rel(host(x), xo) <= 1e-6
+    # the two policies differ on this problem: so the per-wavelength entry was used
+    assert refs[0][3].iters != gmres.augmented_gmres(refs[0][0], refs[0][1], Vs[0].cpu().numpy().T, tol=1e-9,
+                                                     restart=20, maxit=4000, aug_cycles=1, aug_keep=2)[1].iters

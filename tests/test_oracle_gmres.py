@@ -186,6 +186,31 @@ def test_augmented_first_cycle_then_plain_reading():
     assert np.linalg.norm(x - xp) <= 1e-12 * np.linalg.norm(xp)
 
 
+def test_augmented_keeps_leading_columns_after_the_first_cycle():
+    # aug_cycles = 1, aug_keep = j: after the first cycle every cycle minimises
+    # over V[:, :j] + its Krylov space, so its residual is orthogonal to
+    # A V[:, :j] (the least-squares condition), and not to the dropped columns;
+    # keeping every column is the solve that keeps V throughout
+    g, A, b = small_problem(24, npml=4, seed=14)
+    rng = np.random.default_rng(14)
+    V = rng.standard_normal((b.size, 4)) + 1j * rng.standard_normal((b.size, 4))
+    x, info = gmres.augmented_gmres(A, b, V, tol=1e-12, restart=20, maxit=40, aug_cycles=1, aug_keep=2)
+    assert info.cycles == 2 and not info.converged
+    r = b - A @ x
+    C2, _ = np.linalg.qr(A @ V[:, :2])
+    assert np.linalg.norm(C2.conj().T @ r) <= 1e-10 * np.linalg.norm(r)
+    C4, _ = np.linalg.qr(A @ V)
+    assert np.linalg.norm(C4[:, 2:].conj().T @ r) >= 1e-6 * np.linalg.norm(r)
+    xa, ia = gmres.augmented_gmres(A, b, V, tol=1e-9, restart=20, maxit=4000, aug_cycles=1, aug_keep=4)
+    xk, ik = gmres.augmented_gmres(A, b, V, tol=1e-9, restart=20, maxit=4000)
+    assert ia.converged and ia.iters == ik.iters
+    assert np.linalg.norm(xa - xk) <= 1e-8 * np.linalg.norm(xk)
+    # aug_keep = 0 is the first-cycle-then-plain reading
+    x0, i0 = gmres.augmented_gmres(A, b, V, tol=1e-9, restart=20, maxit=4000, aug_cycles=1, aug_keep=0)
+    xp, ip = gmres.augmented_gmres(A, b, V, tol=1e-9, restart=20, maxit=4000, aug_cycles=1)
+    assert np.array_equal(x0, xp) and i0.iters == ip.iters
+
+
 def test_right_preconditioned_gmres():
     # The data-free baseline: GMRES on A M^-1 with M = diag(A) (Jacobi).
     # M = I reproduces the plain solve exactly; Jacobi reaches the direct
