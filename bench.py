@@ -628,6 +628,7 @@ def train_cnn(ddg, args, grids, train_ops, b_of, U_base, src, D, steps=None, n_p
     k = k or args.cnn_k
     P = ddg.Predictor(k=k)
     P.init_he(seed=seed)
+    P.set_tensor_cores(True, backward=True)      # forward and backward convolutions on tcgen05
     for g in grids:
         P.set_output_base(U_base[g.wavelength][:k], g.nx, g.ny, scale=float(np.sqrt(D)), wavelength=g.wavelength)
     P.zero_head()
@@ -723,6 +724,7 @@ def run_large(args, rank, world):
     del xs
     P = ddg.Predictor(k=k)
     P.init_he(seed=0)
+    P.set_tensor_cores(True, backward=True)
     P.set_output_base(U_base, g.nx, g.ny, scale=float(np.sqrt(g.D)))
     P.zero_head()
     P.set_loss("residual")
@@ -747,7 +749,8 @@ def run_large(args, rank, world):
                     ctx, test_ops, bs, x=x, tol=tol, restart=args.restart, maxit=args.maxit, precision=prec))
             else:
                 def go():
-                    P.predict(test_ops, src, U=U)
+                    for c0 in range(0, n, 16):     # prediction in chunks: activations of 16 grids of 1M cells
+                        P.predict(test_ops[c0:c0 + 16], src, U=U[c0:c0 + 16])
                     return ddg.augmented_gmres_solve_batched(ctx, test_ops, bs, U, x=x, tol=tol,
                                                              restart=args.restart, maxit=args.maxit, precision=prec)
                 (_, inf, st), ms = timed_call(torch, go)
@@ -826,6 +829,7 @@ def run_batched(args, rank, world):
         del F, xs
         P = ddg.Predictor(k=args.cnn_k)
         P.init_he(seed=si)
+        P.set_tensor_cores(True, backward=True)
         P.set_output_base(ub, nx, ny, scale=float(np.sqrt(g.D)))
         P.zero_head()
         P.set_loss("residual")

@@ -409,13 +409,19 @@ long long predictor_num_params(const ddg_predictor* P);
 int predictor_num_outputs(const ddg_predictor* P);
 /* Kernels launched by this predictor since it was created. */
 long long predictor_launches(const ddg_predictor* P);
-/* Forward 3x3 convolutions on the tensor cores (no paper counterpart; default
-   on): layers whose input and output channel counts are multiples of 16 (and
-   at most 256 outputs) run as implicit GEMMs on tcgen05 (BF16 operands, FP32
-   accumulation in tensor memory); the others, the head and the backward pass
-   use CUDA cores.  Both paths give the same results up to FP32 summation
-   order.  A tensor-core wait that gives up makes the call return
-   DDG_ETIMEOUT. */
+/* 3x3 convolutions on the tensor cores (no paper counterpart).  `enable` is a
+   set of bits: 1 (the default) = the forward convolutions, 2 = the backward
+   convolutions: the gradient w.r.t. a layer's input (run as a forward
+   convolution from the output to the input channels with flipped taps) and
+   w.r.t. its weights (a GEMM over the pixels: output channels x (tap, input
+   channel)).  Layers whose channel counts are multiples of 16 (at most 256
+   outputs forward and backward-data, at most 128 for the weight gradient)
+   run on tcgen05 (BF16 operands, FP32 accumulation in tensor memory); the
+   others, the head and the bias gradients use CUDA cores.  The forward paths
+   give the same results up to FP32 summation order; with bit 2 the masked
+   output gradient enters both backward products rounded to BF16 (the
+   CUDA-core path keeps it in FP32).  A tensor-core wait that gives up makes
+   the call return DDG_ETIMEOUT.  0 <= enable <= 3, else DDG_EINVAL. */
 ddg_status predictor_set_tensor_cores(ddg_predictor* P, int enable);
 /* theta: host, n = predictor_num_params floats.  Setting resets the Adam state. */
 ddg_status predictor_set_params(ddg_predictor* P, const float* theta, long long n);

@@ -47,17 +47,21 @@ def conv3x3(x, w, b):
     return out + b
 
 
-def conv3x3_backward(x, w, gout):
-    """Gradients of conv3x3 w.r.t. x, w and b given d loss / d out."""
+def conv3x3_backward(x, w, gout, gout_stored=None):
+    """Gradients of conv3x3 w.r.t. x, w and b given d loss / d out.
+    gout_stored (optional) replaces gout in the gradients w.r.t. x and w (a
+    storage emulation, e.g. gout rounded to bfloat16); the bias gradient
+    always sums gout itself."""
     B, H, W, Ci = x.shape
     xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0)))
     gw = np.zeros_like(w)
     gxp = np.zeros_like(xp)
+    gd = gout if gout_stored is None else gout_stored
     for dy in range(3):
         for dx in range(3):
             patch = xp[:, dy:dy + H, dx:dx + W, :]
-            gw[:, :, dy, dx] = np.einsum("bhwo,bhwi->oi", gout, patch)
-            gxp[:, dy:dy + H, dx:dx + W, :] += gout @ w[:, :, dy, dx]
+            gw[:, :, dy, dx] = np.einsum("bhwo,bhwi->oi", gd, patch)
+            gxp[:, dy:dy + H, dx:dx + W, :] += gd @ w[:, :, dy, dx]
     gb = gout.sum(axis=(0, 1, 2))
     return gxp[:, 1:-1, 1:-1, :], gw, gb
 
@@ -192,8 +196,16 @@ def forward(cfg: CNNConfig, theta, x, keep=False, store=None):
     return (y, cache) if keep else y
 
 
-def backward(cfg: CNNConfig, theta, cache, gy):
-    """Gradient of the loss w.r.t. the flat parameter vector given dL/dy."""
+def backward(cfg: CNNConfig, theta, cache, gy, gstore=None):
+    """Gradient of the loss w.r.t. the flat parameter vector given dL/dy.
+    gstore (optional): gstore(layer name, g) is the value of the masked output
+    gradient g that enters that 3x3 layer's input and weight gradients (a
+    storage emulation; the bias gradient always sums g itself)."""
+    gs = gstore if gstore is not None else (lambda name, g: g)
+
+    def conv_back(x, name, g):
+        return conv3x3_backward(x, P[name][0], g, gs(name, g))
+
     P = unpack_params(cfg, theta)
     L = cfg.levels
     grads = {}
@@ -205,10 +217,10 @@ def backward(cfg: CNNConfig, theta, cache, gy):
     # walk the decoder backwards: the forward order was l = L-2 ... 0
     for l in range(0, L - 1):
         gh = gh * (cache[f"out_dec{l}b"] > 0)
-        gx, gw, gb = conv3x3_backward(cache[f"out_dec{l}a"], P[f"dec{l}b"][0], gh)
+        gx, gw, gb = conv_back(cache[f"out_dec{l}a"], f"dec{l}b", gh)
         grads[f"dec{l}b"] = (gw, gb)
         gh = gx * (cache[f"out_dec{l}a"] > 0)
-        gx, gw, gb = conv3x3_backward(cache[f"in_dec{l}a"], P[f"dec{l}a"][0], gh)
+        gx, gw, gb = conv_back(cache[f"in_dec{l}a"], f"dec{l}a", gh)
         grads[f"dec{l}a"] = (gw, gb)
         cu = cfg.channels[l + 1]
         gskips[l] = gx[..., cu:]
@@ -218,10 +230,10 @@ def backward(cfg: CNNConfig, theta, cache, gy):
         if l < L - 1:
             gh = gh + gskips[l]
         gh = gh * (cache[f"out_enc{l}b"] > 0)
-        gx, gw, gb = conv3x3_backward(cache[f"out_enc{l}a"], P[f"enc{l}b"][0], gh)
+        gx, gw, gb = conv_back(cache[f"out_enc{l}a"], f"enc{l}b", gh)
         grads[f"enc{l}b"] = (gw, gb)
         gh = gx * (cache[f"out_enc{l}a"] > 0)
-        gx, gw, gb = conv3x3_backward(cache[f"in_enc{l}a"], P[f"enc{l}a"][0], gh)
+        gx, gw, gb = conv_back(cache[f"in_enc{l}a"], f"enc{l}a", gh)
         grads[f"enc{l}a"] = (gw, gb)
         gh = avgpool2_backward(gx) if l > 0 else gx
     flat = []
@@ -252,7 +264,7 @@ def projection_loss_and_grad(V: np.ndarray, f: np.ndarray):
     return loss, 2.0 * wb.real, 2.0 * wb.imag
 
 
-def batch_loss_and_grad(cfg: CNNConfig, theta, x, fields, store=None):
+def batch_loss_and_grad(cfg: CNNConfig, theta, x, fields, store=None, gstore=None):
     """Mean projection loss over the batch and its gradient w.r.t. theta."""
     y, cache = forward(cfg, theta, x, keep=True, store=store)
     V = to_complex_fields(y)
@@ -266,7 +278,7 @@ def batch_loss_and_grad(cfg: CNNConfig, theta, x, fields, store=None):
         g[:, 0::2] = gr
         g[:, 1::2] = gi
         gy[s] = g.reshape(y.shape[1:]) / B
-    gtheta, _ = backward(cfg, theta, cache, gy)
+    gtheta, _ = backward(cfg, theta, cache, gy, gstore=gstore)
     return tot / B, gtheta
 
 
@@ -324,7 +336,7 @@ def residual_loss_and_grad(A, V: np.ndarray, b: np.ndarray):
     return loss, 2.0 * gv.real, 2.0 * gv.imag
 
 
-def batch_residual_loss_and_grad(cfg: CNNConfig, theta, x, ops, rhs, store=None):
+def batch_residual_loss_and_grad(cfg: CNNConfig, theta, x, ops, rhs, store=None, gstore=None):
     """Mean Eq. 6 loss over the batch (ops: sparse A per sample, rhs: b per
     sample) and its gradient w.r.t. theta."""
     y, cache = forward(cfg, theta, x, keep=True, store=store)
@@ -339,5 +351,5 @@ def batch_residual_loss_and_grad(cfg: CNNConfig, theta, x, ops, rhs, store=None)
         g[:, 0::2] = gr
         g[:, 1::2] = gi
         gy[s] = g.reshape(y.shape[1:]) / B
-    gtheta, _ = backward(cfg, theta, cache, gy)
+    gtheta, _ = backward(cfg, theta, cache, gy, gstore=gstore)
     return tot / B, gtheta

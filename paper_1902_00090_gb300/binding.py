@@ -653,9 +653,11 @@ class Predictor:
         """Kernels launched by this predictor (predictor_launches)."""
         return int(load().predictor_launches(self._h))
 
-    def set_tensor_cores(self, on: bool):
-        """Forward 3x3 convolutions on tcgen05 tensor cores (default) or CUDA cores."""
-        _check(load().predictor_set_tensor_cores(self._h, int(bool(on))), "predictor_set_tensor_cores")
+    def set_tensor_cores(self, on: bool, backward: bool = False):
+        """Forward 3x3 convolutions on tcgen05 tensor cores (default) or CUDA
+        cores; with backward, the backward-data convolutions too."""
+        _check(load().predictor_set_tensor_cores(self._h, (1 if on else 0) | (2 if backward else 0)),
+               "predictor_set_tensor_cores")
 
     def set_params(self, theta):
         import numpy as np

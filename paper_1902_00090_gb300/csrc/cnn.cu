@@ -57,6 +57,16 @@ struct LoadCat {
         }
         return __bfloat162float(x2[(((long long)b * H + y) * W + x) * c2 + (c - c1)]);
     }
+    // channels c .. c + 7 (c % 8 == 0, c1 % 8 == 0) as 8 packed BF16 values
+    __device__ __forceinline__ uint4 load8(int b, int y, int x, int H, int W, int c) const {
+        const bf16* src;
+        if (c < c1)
+            src = up1 ? x1 + ((((long long)b * h1 + (y >> 1)) * w1 + (x >> 1)) * c1 + c)
+                      : x1 + ((((long long)b * H + y) * W + x) * c1 + c);
+        else
+            src = x2 + ((((long long)b * H + y) * W + x) * c2 + (c - c1));
+        return *reinterpret_cast<const uint4*>(src);
+    }
 };
 
 // Gradient input of the backward-data convolution: g masked by ReLU'(out).
@@ -67,6 +77,26 @@ struct LoadGrad {
     __device__ __forceinline__ float operator()(int b, int yy, int x, int H, int W, int c) const {
         const long long i = (((long long)b * H + yy) * W + x) * C + c;
         return __bfloat162float(y[i]) > 0.f ? g[i] : 0.f;
+    }
+    // channels c .. c + 7 (c % 8 == 0, C % 8 == 0) of the masked gradient,
+    // rounded to BF16 (the tensor-core operand type), packed
+    __device__ __forceinline__ uint4 load8(int b, int yy, int x, int H, int W, int c) const {
+        const long long i = (((long long)b * H + yy) * W + x) * C + c;
+        const float4 g0 = *reinterpret_cast<const float4*>(g + i);
+        const float4 g1 = *reinterpret_cast<const float4*>(g + i + 4);
+        const uint4 yv = *reinterpret_cast<const uint4*>(y + i);
+        const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+        const unsigned yw[4] = {yv.x, yv.y, yv.z, yv.w};
+        unsigned o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 yb = *reinterpret_cast<const __nv_bfloat162*>(&yw[q]);
+            const float a = __bfloat162float(yb.x) > 0.f ? gv[2 * q] : 0.f;
+            const float bq = __bfloat162float(yb.y) > 0.f ? gv[2 * q + 1] : 0.f;
+            __nv_bfloat162 h = __floats2bfloat162_rn(a, bq);
+            o[q] = *reinterpret_cast<unsigned*>(&h);
+        }
+        return make_uint4(o[0], o[1], o[2], o[3]);
     }
 };
 
@@ -223,9 +253,14 @@ __device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&r)[8]) {
 }
 }  // namespace tc
 
-__global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(LoadCat ld, int B, int H, int W, int Ci, int Co,
+// The gather G supplies 8 BF16 input channels per 16-byte chunk (LoadCat: the
+// forward's activations; LoadGrad: the backward-data convolution's input, the
+// FP32 gradient masked by ReLU' and rounded to BF16); TOUT is the output type
+// (BF16 activations, or the FP32 input gradient).
+template <class G, typename TOUT>
+__global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(G ld, int B, int H, int W, int Ci, int Co,
                                                            const bf16* __restrict__ wt, const float* __restrict__ bias,
-                                                           int relu, bf16* __restrict__ out, int* __restrict__ err) {
+                                                           int relu, TOUT* __restrict__ out, int* __restrict__ err) {
     using namespace tc;
     constexpr int kRowsPerThread = kM * 8 / kThreads;   // A rows gathered by one thread (fixed K group)
     extern __shared__ __align__(128) unsigned char smraw_tc[];
@@ -285,22 +320,13 @@ __global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(LoadCat ld, int B, in
             dy = tap / 3 - 1;
             dx = tap - 3 * (tap / 3) - 1;
         }
-        const bool first = ci < ld.c1;
 #pragma unroll
         for (int j = 0; j < kRowsPerThread; ++j) {
             const int r = r0 + (kThreads / 8) * j;
             const int b = rb[j];
             const int yy = (ryx[j] >> 16) + dy, xx = (ryx[j] & 0xFFFF) + dx;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (kin && b >= 0 && yy >= 0 && yy < H && xx >= 0 && xx < W) {
-                const bf16* src;
-                if (first)
-                    src = ld.up1 ? ld.x1 + ((((long long)b * ld.h1 + (yy >> 1)) * ld.w1 + (xx >> 1)) * ld.c1 + ci)
-                                 : ld.x1 + ((((long long)b * H + yy) * W + xx) * ld.c1 + ci);
-                else
-                    src = ld.x2 + ((((long long)b * H + yy) * W + xx) * ld.c2 + (ci - ld.c1));
-                v = *reinterpret_cast<const uint4*>(src);
-            }
+            if (kin && b >= 0 && yy >= 0 && yy < H && xx >= 0 && xx < W) v = ld.load8(b, yy, xx, H, W, ci);
             *reinterpret_cast<uint4*>(As + swz(r, kg)) = v;
         }
         for (int n = r0; n < Co; n += kThreads / 8) {
@@ -340,14 +366,20 @@ __global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(LoadCat ld, int B, in
                 v[j] = __uint_as_float(rr[j]) + (bias ? bias[c0 + j] : 0.f);
                 if (relu) v[j] = fmaxf(v[j], 0.f);
             }
-            uint4 o;
-            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4], v[5]), h3 = __floats2bfloat162_rn(v[6], v[7]);
-            o.x = *reinterpret_cast<uint32_t*>(&h0);
-            o.y = *reinterpret_cast<uint32_t*>(&h1);
-            o.z = *reinterpret_cast<uint32_t*>(&h2);
-            o.w = *reinterpret_cast<uint32_t*>(&h3);
-            *reinterpret_cast<uint4*>(out + (long long)p * Co + c0) = o;
+            if constexpr (sizeof(TOUT) == 4) {
+                float4* o4 = reinterpret_cast<float4*>(out + (long long)p * Co + c0);
+                o4[0] = make_float4(v[0], v[1], v[2], v[3]);
+                o4[1] = make_float4(v[4], v[5], v[6], v[7]);
+            } else {
+                uint4 o;
+                __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
+                __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4], v[5]), h3 = __floats2bfloat162_rn(v[6], v[7]);
+                o.x = *reinterpret_cast<uint32_t*>(&h0);
+                o.y = *reinterpret_cast<uint32_t*>(&h1);
+                o.z = *reinterpret_cast<uint32_t*>(&h2);
+                o.w = *reinterpret_cast<uint32_t*>(&h3);
+                *reinterpret_cast<uint4*>(out + (long long)p * Co + c0) = o;
+            }
         }
     }
     if (!ok && tid == 0) atomicExch(err, 1);
@@ -357,6 +389,195 @@ __global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(LoadCat ld, int B, in
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
     }
+}
+
+// ---------------------------------------------------------------- weight gradient on tensor cores
+// dW[co][ci][tap] = sum over pixels p of g'[p][co] x[p + off(tap)][ci], with
+// g' the output gradient masked by ReLU'(out): a GEMM D[m = co, n] = sum_p
+// A[co, p] B[n, p] with n = tap * Ci + ci and K = the pixels.  One CTA: all
+// output channels (M = 128, rows >= Co zero) x a tile of kWN columns n, over a
+// range of pixels in K stages of 64; both operands are gathered as 8-channel
+// 16-byte chunks (g' in BF16 from FP32, x through the layer's input loader)
+// and scattered, one BF16 value per (row, pixel), into the K-major 128-byte
+// swizzled layout of the forward kernel; one thread issues the MMAs and
+// commits each stage; the FP32 accumulators are added to dW with atomics
+// (the CTAs of one n tile split the pixels).  The bias gradient is summed
+// separately (k_bias_grad) from the FP32 g'.
+namespace tcw {
+constexpr int kWN = 128;                       // columns n per CTA
+constexpr uint32_t kTileBytes = tc::kM * tc::kKC * 2;   // 128 rows x 64 K values (A and B alike)
+__host__ __device__ constexpr size_t smem_bytes() { return (size_t)tc::kStages * 2 * kTileBytes + 1024; }
+}  // namespace tcw
+
+template <class LX>
+__global__ void __launch_bounds__(tc::kThreads) k_wgrad_tc(LX lx, const float* __restrict__ g,
+                                                           const bf16* __restrict__ yout, int B, int H, int W, int Ci,
+                                                           int Co, long long pix_per_cta, float* __restrict__ dW,
+                                                           int* __restrict__ err) {
+    using namespace tc;
+    extern __shared__ __align__(128) unsigned char smraw_wg[];
+    __shared__ __align__(8) unsigned long long done[kStages];
+    __shared__ uint32_t s_tmem;
+    unsigned char* smt = smraw_wg + ((1024u - (smem_u32(smraw_wg) & 1023u)) & 1023u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long P = (long long)B * H * W;
+    const int Ntot = 9 * Ci;
+    const int n0 = blockIdx.x * tcw::kWN;
+    const long long p_begin = (long long)blockIdx.y * pix_per_cta;
+    const long long p_end = min(P, p_begin + pix_per_cta);
+    const int nch = p_end > p_begin ? (int)((p_end - p_begin + kKC - 1) / kKC) : 0;
+    // rows co >= Co of A never receive data: zero both stages once
+    for (int q = tid; q < kStages * 2 * (int)tcw::kTileBytes / 16; q += kThreads)
+        reinterpret_cast<uint4*>(smt)[q] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        for (int q = 0; q < kStages; ++q) mbar_init(&done[q], 1);
+        mbar_init_fence();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"((uint32_t)tcw::kWN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_tmem;
+    bool ok = true;
+    const int ncg = Co >> 3;   // 8-channel groups of g'
+    for (int c = 0; c < nch; ++c) {
+        const int s = c % kStages;
+        unsigned char* As = smt + s * 2 * tcw::kTileBytes;
+        unsigned char* Bs = As + tcw::kTileBytes;
+        if (c >= kStages && !mbar_wait(&done[s], (unsigned)((c - kStages) / kStages) & 1u)) ok = false;
+        const long long pc0 = p_begin + (long long)c * kKC;
+        // A: g'[p][co .. co + 7] -> rows co .. co + 7, column p - pc0
+        for (int task = tid; task < kKC * ncg; task += kThreads) {
+            const int pl = task / ncg, cg = task - pl * ncg;
+            const long long p = pc0 + pl;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (p < p_end) {
+                const long long i = p * Co + cg * 8;
+                const float4 g0 = *reinterpret_cast<const float4*>(g + i);
+                const float4 g1 = *reinterpret_cast<const float4*>(g + i + 4);
+                const uint4 yv = *reinterpret_cast<const uint4*>(yout + i);
+                const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+                const unsigned yw[4] = {yv.x, yv.y, yv.z, yv.w};
+                unsigned o[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const __nv_bfloat162 yb = *reinterpret_cast<const __nv_bfloat162*>(&yw[q]);
+                    __nv_bfloat162 h = __floats2bfloat162_rn(__bfloat162float(yb.x) > 0.f ? gv[2 * q] : 0.f,
+                                                             __bfloat162float(yb.y) > 0.f ? gv[2 * q + 1] : 0.f);
+                    o[q] = *reinterpret_cast<unsigned*>(&h);
+                }
+                v = make_uint4(o[0], o[1], o[2], o[3]);
+            }
+            const unsigned short* hv = reinterpret_cast<const unsigned short*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<unsigned short*>(As + swz(cg * 8 + j, pl >> 3) + ((pl & 7) << 1)) = hv[j];
+        }
+        // B: x[p + off(tap)][ci .. ci + 7] -> rows n - n0 .. + 7 (n = tap Ci + ci), column p - pc0
+        for (int task = tid; task < kKC * (tcw::kWN / 8); task += kThreads) {
+            const int pl = task / (tcw::kWN / 8), ng = task - pl * (tcw::kWN / 8);
+            const long long p = pc0 + pl;
+            const int n = n0 + ng * 8;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (p < p_end && n < Ntot) {
+                const int tap = n / Ci, ci = n - tap * Ci;
+                const int x = (int)(p % W);
+                const long long t = p / W;
+                const int y = (int)(t % H), b = (int)(t / H);
+                const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+                if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = lx.load8(b, yy, xx, H, W, ci);
+            }
+            const unsigned short* hv = reinterpret_cast<const unsigned short*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<unsigned short*>(Bs + swz(ng * 8 + j, pl >> 3) + ((pl & 7) << 1)) = hv[j];
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+            for (int ks = 0; ks < kKC / 16; ++ks)
+                mma(tmem, sdesc(a0 + ks * 32), sdesc(b0 + ks * 32), idesc(tcw::kWN), (c > 0 || ks > 0) ? 1u : 0u);
+            commit(&done[s]);
+        }
+    }
+    if (nch > 0) {
+        const int cl = nch - 1;
+        if (!mbar_wait(&done[cl % kStages], (unsigned)(cl / kStages) & 1u)) {
+            ok = false;
+            mbar_wait(&done[cl % kStages], (unsigned)(cl / kStages) & 1u);   // one more bounded wait before freeing
+        }
+        fence_after();
+        // warp w: accumulator rows (co) 32 (w % 4) + lane, columns [half, half + kWN / 2)
+        const int quarter = warp & 3, chalf = (warp >> 2) * (tcw::kWN / 2);
+        const int co = quarter * 32 + lane;
+        for (int c0 = chalf; c0 < chalf + tcw::kWN / 2; c0 += 8) {
+            uint32_t rr[8];
+            ld8(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, rr);
+            if (co < Co) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n < Ntot) {
+                        const int tap = n / Ci, ci = n - tap * Ci;
+                        atomicAdd(dW + ((long long)co * Ci + ci) * 9 + tap, __uint_as_float(rr[j]));
+                    }
+                }
+            }
+        }
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)tcw::kWN)
+                     : "memory");
+    }
+}
+
+// db[co] += sum over pixels of g'[p][co] (FP32), one block per pixel slice
+__global__ void __launch_bounds__(256) k_bias_grad(const float* __restrict__ g, const bf16* __restrict__ yout,
+                                                   long long P, int Co, long long pix_per_block,
+                                                   float* __restrict__ db) {
+    __shared__ float acc[256];
+    const int t = threadIdx.x;
+    const int co = t % Co, lanes = 256 / Co;
+    float sum = 0.f;
+    if (t < lanes * Co) {
+        const long long p0 = (long long)blockIdx.x * pix_per_block;
+        const long long p1 = min(P, p0 + pix_per_block);
+        for (long long p = p0 + t / Co; p < p1; p += lanes) {
+            const long long i = p * Co + co;
+            sum += __bfloat162float(yout[i]) > 0.f ? g[i] : 0.f;
+        }
+    }
+    acc[t] = sum;
+    __syncthreads();
+    if (t < Co) {
+        float tot = 0.f;
+        for (int q = 0; q < lanes; ++q) tot += acc[q * Co + t];
+        atomicAdd(db + t, tot);
+    }
+}
+
+// backward-data weights for the tensor cores: the transposed convolution
+// with flipped taps, as a forward one from Co to Ci channels:
+// wt[ci][tap'][co] = w[co][ci][8 - tap'] (K-major rows, k = tap' * Co + co)
+__global__ void k_w_tc_bwd(const bf16* __restrict__ w, int Co, int Ci, bf16* __restrict__ wt) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)Co * Ci * 9) return;
+    const int co = (int)(idx % Co);
+    const int tap = (int)((idx / Co) % 9);
+    const int ci = (int)(idx / ((long long)Co * 9));
+    wt[idx] = w[((long long)co * Ci + ci) * 9 + (8 - tap)];
 }
 
 // tensor-core weights BF16 [co][ci][9] -> [co][9][ci] (K-major rows, k = tap * Ci + ci)
@@ -1024,7 +1245,9 @@ struct ddg_predictor {
     double2* orth_ws = nullptr;   // K13: Gram partial sums, factors, dropped counts
     size_t orth_bytes = 0;
     int* d_err = nullptr;         // a bounded wait in a tensor-core convolution gave up
-    bool tensor_cores = true;     // forward 3x3 convolutions on tcgen05 where the channels allow
+    int tensor_cores = 1;         // bit 0: forward 3x3 convolutions on tcgen05 where the channels allow;
+                                  // bit 1: the backward convolutions (data and weight gradients) too
+    int sm_count = 152;
     void* d_desc = nullptr;       // InputDesc / pointer arrays (device)
     size_t desc_bytes = 0;
 };
@@ -1058,7 +1281,9 @@ struct Acts {
     float* gskip[kMaxLevels];
 };
 
-static size_t plan_acts(const ddg_predictor* P, int B, int H, int W, char* base, Acts* A) {
+// Activation workspace of one batch; `train` adds the gradient buffers (the
+// forward-only calls, prediction and predictor_forward, need none of them).
+static size_t plan_acts(const ddg_predictor* P, int B, int H, int W, char* base, Acts* A, bool train) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         off = (off + 255) / 256 * 256;
@@ -1077,12 +1302,16 @@ static size_t plan_acts(const ddg_predictor* P, int B, int H, int W, char* base,
         if (l < L - 1) {
             A->da[l] = (bf16*)take(sizeof(bf16) * px * P->ch[l]);
             A->db[l] = (bf16*)take(sizeof(bf16) * px * P->ch[l]);
-            A->gskip[l] = (float*)take(sizeof(float) * px * P->ch[l]);
+            A->gskip[l] = train ? (float*)take(sizeof(float) * px * P->ch[l]) : nullptr;
             maxg = std::max(maxg, px * (size_t)(P->ch[l] + P->ch[l + 1]));
         }
         maxg = std::max(maxg, px * (size_t)std::max(P->ch[l], l > 0 ? P->ch[l - 1] : P->cin));
     }
     A->y = (float*)take(sizeof(float) * (size_t)B * H * W * 2 * P->k);
+    if (!train) {
+        A->gy = A->y2 = A->gy2 = A->g1 = A->g2 = A->g3 = nullptr;
+        return off + 256;
+    }
     A->gy = (float*)take(sizeof(float) * (size_t)B * H * W * 2 * P->k);
     A->y2 = (float*)take(sizeof(float) * (size_t)B * H * W * 2 * P->k);
     A->gy2 = (float*)take(sizeof(float) * (size_t)B * H * W * 2 * P->k);
@@ -1092,8 +1321,8 @@ static size_t plan_acts(const ddg_predictor* P, int B, int H, int W, char* base,
     return off + 256;
 }
 
-static ddg_status ensure_acts(ddg_predictor* P, int B, int H, int W, Acts* A) {
-    const size_t need = plan_acts(P, B, H, W, nullptr, A);
+static ddg_status ensure_acts(ddg_predictor* P, int B, int H, int W, Acts* A, bool train) {
+    const size_t need = plan_acts(P, B, H, W, nullptr, A, train);
     if (need > P->act_bytes) {
         cudaFree(P->act);
         P->act = nullptr;
@@ -1102,7 +1331,7 @@ static ddg_status ensure_acts(ddg_predictor* P, int B, int H, int W, Acts* A) {
         if (e != cudaSuccess) { cudaGetLastError(); set_error("predictor: cudaMalloc of %zu bytes failed", need); return DDG_ENOMEM; }
         P->act_bytes = need;
     }
-    plan_acts(P, B, H, W, reinterpret_cast<char*>(P->act), A);
+    plan_acts(P, B, H, W, reinterpret_cast<char*>(P->act), A, train);
     return DDG_OK;
 }
 
@@ -1124,8 +1353,8 @@ static ddg_status conv3(ddg_predictor* P, const LD& ld, int B, int H, int W, int
 static ddg_status conv_fwd(ddg_predictor* P, const LoadCat& ld, int B, int H, int W, int li, bf16* out,
                            cudaStream_t st) {
     const Layer& Ly = P->layers[li];
-    const bool tcok = P->tensor_cores && Ly.ci % 16 == 0 && Ly.co % 16 == 0 && Ly.co <= 256 && ld.c1 % 8 == 0 &&
-                      ld.c2 % 8 == 0;
+    const bool tcok = (P->tensor_cores & 1) && Ly.ci % 16 == 0 && Ly.co % 16 == 0 && Ly.co <= 256 &&
+                      ld.c1 % 8 == 0 && ld.c2 % 8 == 0;
     ++P->launches;
     if (!tcok) {
         k_w_fwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
@@ -1133,10 +1362,11 @@ static ddg_status conv_fwd(ddg_predictor* P, const LoadCat& ld, int B, int H, in
     }
     k_w_tc<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
     const size_t smem = tc::smem_bytes(Ly.co);
-    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DDG_CHECK_CUDA(cudaFuncSetAttribute(k_conv3_tc<LoadCat, bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
     const long long npx = (long long)B * H * W;
     ++P->launches;
-    k_conv3_tc<<<(unsigned)((npx + tc::kM - 1) / tc::kM), tc::kThreads, smem, st>>>(
+    k_conv3_tc<LoadCat, bf16><<<(unsigned)((npx + tc::kM - 1) / tc::kM), tc::kThreads, smem, st>>>(
         ld, B, H, W, Ly.ci, Ly.co, P->wk, bias32(P, li), 1, out, P->d_err);
     DDG_CHECK_LAUNCH("k_conv3_tc");
     return DDG_OK;
@@ -1211,6 +1441,26 @@ template <class LX>
 static ddg_status wgrad(ddg_predictor* P, const LX& lx, const float* g, const bf16* yout, int B, int H, int W, int li,
                         cudaStream_t st) {
     const Layer& Ly = P->layers[li];
+    if ((P->tensor_cores & 2) && Ly.co % 16 == 0 && Ly.co <= 128 && Ly.ci % 16 == 0) {
+        // on the tensor cores (bit 2): D[co, tap Ci + ci] over the pixels
+        const long long npx = (long long)B * H * W;
+        const int ntn = (9 * Ly.ci + tcw::kWN - 1) / tcw::kWN;
+        const long long want = std::max(1LL, (long long)(2 * P->sm_count + ntn - 1) / ntn);
+        long long per = (npx + want - 1) / want;
+        per = std::max((long long)tc::kKC, (per + tc::kKC - 1) / tc::kKC * tc::kKC);
+        const unsigned slices = (unsigned)((npx + per - 1) / per);
+        const size_t smem = tcw::smem_bytes();
+        DDG_CHECK_CUDA(cudaFuncSetAttribute(k_wgrad_tc<LX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ++P->launches;
+        k_wgrad_tc<LX><<<dim3(ntn, slices), tc::kThreads, smem, st>>>(lx, g, yout, B, H, W, Ly.ci, Ly.co, per,
+                                                                      P->grad + Ly.w_off, P->d_err);
+        DDG_CHECK_LAUNCH("k_wgrad_tc");
+        const long long pb = std::max(1024LL, (npx + 4 * P->sm_count - 1) / (4 * P->sm_count));
+        ++P->launches;
+        k_bias_grad<<<(unsigned)((npx + pb - 1) / pb), 256, 0, st>>>(g, yout, npx, Ly.co, pb, P->grad + Ly.b_off);
+        DDG_CHECK_LAUNCH("k_bias_grad");
+        return DDG_OK;
+    }
     const long long ntiles = (long long)B * ((W + 15) / 16) * ((H + 15) / 16);
     const int gy = ((Ly.co + 15) / 16) * ((Ly.ci + 15) / 16);
     const unsigned sl = wgrad_slices(ntiles, gy);
@@ -1227,10 +1477,25 @@ static ddg_status wgrad(ddg_predictor* P, const LX& lx, const float* g, const bf
 static ddg_status bdata(ddg_predictor* P, const float* g, const bf16* yout, int B, int H, int W, int li, float* gx,
                         cudaStream_t st) {
     const Layer& Ly = P->layers[li];
+    LoadGrad lg{g, yout, Ly.co};
+    if ((P->tensor_cores & 2) && Ly.co % 16 == 0 && Ly.ci % 16 == 0 && Ly.ci <= 256) {
+        // on the tensor cores: a forward convolution from Co to Ci channels
+        // with the flipped taps; the masked gradient enters in BF16
+        ++P->launches;
+        k_w_tc_bwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
+        const size_t smem = tc::smem_bytes(Ly.ci);
+        DDG_CHECK_CUDA(cudaFuncSetAttribute(k_conv3_tc<LoadGrad, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+        const long long npx = (long long)B * H * W;
+        ++P->launches;
+        k_conv3_tc<LoadGrad, float><<<(unsigned)((npx + tc::kM - 1) / tc::kM), tc::kThreads, smem, st>>>(
+            lg, B, H, W, Ly.co, Ly.ci, P->wk, nullptr, 0, gx, P->d_err);
+        DDG_CHECK_LAUNCH("k_conv3_tc (backward data)");
+        return DDG_OK;
+    }
     ++P->launches;
     k_w_bwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
-    LoadGrad ld{g, yout, Ly.co};
-    return conv3(P, ld, B, H, W, Ly.co, Ly.ci, P->wk, (const float*)nullptr, 0, gx, st);
+    return conv3(P, lg, B, H, W, Ly.co, Ly.ci, P->wk, (const float*)nullptr, 0, gx, st);
 }
 
 // backward pass: A->gy holds d loss / d y; accumulates into P->grad
@@ -1422,6 +1687,8 @@ static ddg_status create_predictor(int k, int levels, const int* channels, int c
         P->ch[l] = channels[l];
     }
     cudaGetDevice(&P->device);
+    cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, P->device);
+    if (P->sm_count <= 0) P->sm_count = 152;
     long long off = 0;
     size_t maxw = 0;
     auto add = [&](int co, int ci, int kk) {
@@ -1546,7 +1813,8 @@ extern "C" long long predictor_launches(const ddg_predictor* P) { return P ? P->
 
 extern "C" ddg_status predictor_set_tensor_cores(ddg_predictor* P, int enable) {
     if (!P) { set_error("predictor_set_tensor_cores: NULL predictor"); return DDG_EINVAL; }
-    P->tensor_cores = enable != 0;
+    if (enable < 0 || enable > 3) { set_error("predictor_set_tensor_cores: enable must be 0..3"); return DDG_EINVAL; }
+    P->tensor_cores = enable;
     return DDG_OK;
 }
 
@@ -1577,7 +1845,7 @@ extern "C" ddg_status predictor_forward(ddg_predictor* P, int n, const ddg_op* c
     if (!y) { set_error("predictor_forward: y is NULL"); return DDG_EINVAL; }
     cudaStream_t st = as_stream(stream);
     Acts acts;
-    DDG_TRY(ensure_acts(P, n, H, W, &acts));
+    DDG_TRY(ensure_acts(P, n, H, W, &acts, false));
     DDG_TRY(build_input(P, n, A, i_src, sigma, j_c, &acts, st));
     DDG_TRY(forward(P, n, H, W, &acts, st));
     DDG_CHECK_CUDA(cudaMemcpyAsync(y, acts.y, sizeof(float) * (size_t)n * H * W * 2 * P->k, cudaMemcpyDeviceToDevice, st));
@@ -1593,7 +1861,7 @@ extern "C" ddg_status subspace_predict(ddg_predictor* P, int n, const ddg_op* co
         if (!U[s]) { set_error("subspace_predict: U[%d] is NULL", s); return DDG_EINVAL; }
     cudaStream_t st = as_stream(stream);
     Acts acts;
-    DDG_TRY(ensure_acts(P, n, H, W, &acts));
+    DDG_TRY(ensure_acts(P, n, H, W, &acts, false));
     DDG_TRY(build_input(P, n, A, i_src, sigma, j_c, &acts, st));
     DDG_TRY(forward(P, n, H, W, &acts, st));
     void** slots = ptr_slots(P, n);
@@ -1637,7 +1905,7 @@ extern "C" ddg_status predictor_loss_grad(ddg_predictor* P, int n, const ddg_op*
     if (!f || n > 4096) { set_error("predictor_loss_grad: f is NULL or batch > 4096"); return DDG_EINVAL; }
     cudaStream_t st = as_stream(stream);
     Acts acts;
-    DDG_TRY(ensure_acts(P, n, H, W, &acts));
+    DDG_TRY(ensure_acts(P, n, H, W, &acts, true));
     DDG_TRY(build_input(P, n, A, i_src, sigma, j_c, &acts, st));
     DDG_TRY(forward(P, n, H, W, &acts, st));
     void** slots = ptr_slots(P, n);

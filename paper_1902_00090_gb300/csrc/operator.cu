@@ -90,71 +90,67 @@ __global__ void __launch_bounds__(256) k_apply(int nx, int ny, const T* __restri
 }
 
 // y = A x in complex64 for even nx: two cells per thread with 16-byte loads
-// and stores, marching down a column strip of kApplyRows rows so that every
-// row of x is loaded once per thread (the rows j - 1, j, j + 1 slide through
-// registers).  Thread t of block (bx, by) owns the pair of cells
-// i0 = 2 (bx blockDim.x + t), i0 + 1 in rows by kApplyRows ... + kApplyRows - 1;
-// the x-neighbours i0 - 1 and i0 + 2 come from the neighbouring lanes by
-// shuffles (loaded directly at warp edges and wrapped periodically at the row
-// ends).  Same arithmetic and order per cell as k_apply<float>.
-constexpr int kApplyRows = 8;
+// and stores, the row from blockIdx.y (no index division).  Thread t of row j
+// owns cells i0 = 2 (blockIdx.x blockDim.x + t) and i0 + 1; their x-neighbours
+// i0 - 1 and i0 + 2 come from the neighbouring lanes by shuffles (loaded
+// directly at warp edges and wrapped periodically at the row ends); the rows
+// j - 1 and j + 1 are 16-byte loads of the same two cells (L2 reuse across
+// blocks).  Same arithmetic and order as k_apply<float> per cell.
 __global__ void __launch_bounds__(256) k_apply_c64x2(int nx, int ny, const float* __restrict__ eps,
                                                      const float2* __restrict__ coef, float kh2,
                                                      const float4* __restrict__ x, float4* __restrict__ y) {
+    const int j = blockIdx.y;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;   // pair index in the row
     const int nh = nx >> 1;
     const int lane = threadIdx.x & 31;
     const bool in = h < nh;
     const int hh = in ? h : nh - 1;                         // out-of-row lanes mirror the last pair
+    const long long row = (long long)j * nh;
+    const int jp = (j == ny - 1) ? 0 : j + 1, jm = (j == 0) ? ny - 1 : j - 1;
+    // every load is issued before any shuffle: the lanes at a warp edge or a
+    // row end also fetch the neighbouring pair themselves (no second round)
     const bool ledge = lane == 0 || hh == 0;
     const bool redge = lane == 31 || hh == nh - 1 || h + 1 >= nh;
-    const int hl = hh == 0 ? nh - 1 : hh - 1, hr = hh == nh - 1 ? 0 : hh + 1;
-    const int j0 = blockIdx.y * kApplyRows;
-    const int j1 = min(ny, j0 + kApplyRows);
-    float4 dn = x[(long long)(j0 == 0 ? ny - 1 : j0 - 1) * nh + hh];
-    float4 c = x[(long long)j0 * nh + hh];
-    const float2 axp0 = coef[2 * hh], axp1 = coef[2 * hh + 1];
-    const float2 axm0 = coef[nx + 2 * hh], axm1 = coef[nx + 2 * hh + 1];
-    for (int j = j0; j < j1; ++j) {
-        const long long row = (long long)j * nh;
-        const float4 up = x[(long long)(j == ny - 1 ? 0 : j + 1) * nh + hh];
-        // left neighbour of cell 2hh: the .zw of pair hh - 1; right of 2hh + 1: the .xy of pair hh + 1
-        float lx = __shfl_up_sync(0xffffffffu, c.z, 1), ly = __shfl_up_sync(0xffffffffu, c.w, 1);
-        float rx = __shfl_down_sync(0xffffffffu, c.x, 1), ry = __shfl_down_sync(0xffffffffu, c.y, 1);
-        if (ledge) {
-            const float4 l = x[row + hl];
-            lx = l.z;
-            ly = l.w;
-        }
-        if (redge) {
-            const float4 r = x[row + hr];
-            rx = r.x;
-            ry = r.y;
-        }
-        if (in) {
-            const float2 ayp = coef[2 * nx + j], aym = coef[2 * nx + ny + j];
-            const float2 ev = reinterpret_cast<const float2*>(eps)[row + h];
-            float2 out[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const float2 axp = q == 0 ? axp0 : axp1, axm = q == 0 ? axm0 : axm1;
-                float2 d = cadd(cadd(axp, axm), cadd(ayp, aym));
-                d.x -= kh2 * (q == 0 ? ev.x : ev.y);
-                const float2 xc = q == 0 ? make_float2(c.x, c.y) : make_float2(c.z, c.w);
-                const float2 xr = q == 0 ? make_float2(c.z, c.w) : make_float2(rx, ry);
-                const float2 xl = q == 0 ? make_float2(lx, ly) : make_float2(c.x, c.y);
-                float2 acc = cmul(d, xc);
-                cfms(acc, axp, xr);
-                cfms(acc, axm, xl);
-                cfms(acc, ayp, q == 0 ? make_float2(up.x, up.y) : make_float2(up.z, up.w));
-                cfms(acc, aym, q == 0 ? make_float2(dn.x, dn.y) : make_float2(dn.z, dn.w));
-                out[q] = acc;
-            }
-            y[row + h] = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
-        }
-        dn = c;
-        c = up;
+    const float4 c = x[row + hh];
+    const float4 up = x[(long long)jp * nh + hh];
+    const float4 dn = x[(long long)jm * nh + hh];
+    float4 l = make_float4(0.f, 0.f, 0.f, 0.f), r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ledge) l = x[row + (hh == 0 ? nh - 1 : hh - 1)];
+    if (redge) r = x[row + (hh == nh - 1 ? 0 : hh + 1)];
+    const float2 ev = reinterpret_cast<const float2*>(eps)[row + hh];
+    const float4 axp2 = reinterpret_cast<const float4*>(coef)[hh];        // axp of cells 2hh, 2hh + 1
+    const float4 axm2 = reinterpret_cast<const float4*>(coef + nx)[hh];   // axm of the same cells
+    const float2 ayp = coef[2 * nx + j], aym = coef[2 * nx + ny + j];
+    // left neighbour of cell 2hh: the .zw of pair hh - 1; right of 2hh + 1: the .xy of pair hh + 1
+    float lx = __shfl_up_sync(0xffffffffu, c.z, 1), ly = __shfl_up_sync(0xffffffffu, c.w, 1);
+    float rx = __shfl_down_sync(0xffffffffu, c.x, 1), ry = __shfl_down_sync(0xffffffffu, c.y, 1);
+    if (ledge) {
+        lx = l.z;
+        ly = l.w;
     }
+    if (redge) {
+        rx = r.x;
+        ry = r.y;
+    }
+    if (!in) return;
+    float2 out[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const float2 axp = q == 0 ? make_float2(axp2.x, axp2.y) : make_float2(axp2.z, axp2.w);
+        const float2 axm = q == 0 ? make_float2(axm2.x, axm2.y) : make_float2(axm2.z, axm2.w);
+        float2 d = cadd(cadd(axp, axm), cadd(ayp, aym));
+        d.x -= kh2 * (q == 0 ? ev.x : ev.y);
+        const float2 xc = q == 0 ? make_float2(c.x, c.y) : make_float2(c.z, c.w);
+        const float2 xr = q == 0 ? make_float2(c.z, c.w) : make_float2(rx, ry);
+        const float2 xl = q == 0 ? make_float2(lx, ly) : make_float2(c.x, c.y);
+        float2 acc = cmul(d, xc);
+        cfms(acc, axp, xr);
+        cfms(acc, axm, xl);
+        cfms(acc, ayp, q == 0 ? make_float2(up.x, up.y) : make_float2(up.z, up.w));
+        cfms(acc, aym, q == 0 ? make_float2(dn.x, dn.y) : make_float2(dn.z, dn.w));
+        out[q] = acc;
+    }
+    y[row + h] = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
 }
 
 __global__ void k_source(int nx, int ny, int i_src, double sigma, double j_c, double kh,
@@ -182,7 +178,7 @@ ddg_status launch_apply_d(const ddg_op* A, const double2* x, double2* y, cudaStr
 ddg_status launch_apply_f(const ddg_op* A, const float2* x, float2* y, cudaStream_t s) {
     if ((A->nx & 1) == 0 && A->nx >= 4 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)y & 15) == 0) {
         const int nh = A->nx / 2;
-        dim3 grid((unsigned)((nh + 255) / 256), (unsigned)((A->ny + kApplyRows - 1) / kApplyRows));
+        dim3 grid((unsigned)((nh + 255) / 256), (unsigned)A->ny);
         k_apply_c64x2<<<grid, 256, 0, s>>>(A->nx, A->ny, A->eps_f, A->coef_f, (float)(A->kh * A->kh),
                                            reinterpret_cast<const float4*>(x), reinterpret_cast<float4*>(y));
         DDG_CHECK_LAUNCH("k_apply_c64x2");

@@ -384,3 +384,36 @@ def test_output_base_per_wavelength():
     y = P.forward(ops, src).cpu().numpy()
     assert np.array_equal(y[0], layout(Uany)) and np.array_equal(y[1], layout(U13))
 
+
+
+def test_tensor_core_backward_matches_oracle():
+    # the backward convolutions (data and weight gradients) on tcgen05
+    # (predictor_set_tensor_cores bit 2): the masked output gradient enters
+    # both products in bfloat16.  Against the oracle with the same storage
+    # (activations and, in every layer but the first, whose weight gradient
+    # stays on CUDA cores, the masked gradient rounded to bfloat16), and
+    # against the CUDA-core backward pass of the same network.
+    chans = (16, 32, 32)
+    g, eps, ops = small_problems()
+    P = ddg.Predictor(k=2, channels=chans)
+    P.init_he(seed=17)
+    theta = P.get_params().astype(np.float64)
+    fields = [inputs.random_complex(g.D, 40 + s) for s in range(len(ops))]
+    src = (g.i_src, g.sigma_src, g.j_src)
+    fd = [torch.as_tensor(f, device="cuda") for f in fields]
+    P.set_tensor_cores(True)
+    loss_cc, grad_cc = P.loss_grad(ops, src, fd)
+    P.set_tensor_cores(True, backward=True)
+    loss_tc, grad_tc = P.loss_grad(ops, src, fd)
+    assert loss_tc == loss_cc                       # the forward pass is the same
+    cfg = ocnn.CNNConfig(cin=4, channels=chans, k=2)
+    x = oracle_inputs(g, eps)
+    lb, gb = ocnn.batch_loss_and_grad(cfg, ocnn.round_weights(cfg, theta, ocnn.bf16_round), ocnn.bf16_round(x),
+                                      np.stack(fields), store=ocnn.bf16_round,
+                                      gstore=lambda name, gg: gg if name == "enc0a" else ocnn.bf16_round(gg))
+    gt = grad_tc.cpu().numpy().astype(np.float64)
+    gc = grad_cc.cpu().numpy().astype(np.float64)
+    assert abs(loss_tc - lb) <= 1e-4
+    assert gt @ gb / (np.linalg.norm(gt) * np.linalg.norm(gb)) >= 0.9999
+    assert rel(gt, gb) <= 1e-2
+    assert gt @ gc / (np.linalg.norm(gt) * np.linalg.norm(gc)) >= 0.999

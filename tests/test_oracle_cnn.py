@@ -165,3 +165,33 @@ def test_input_field_channels():
     g = f.reshape(16, 12) / np.max(np.abs(f))
     assert np.array_equal(x6[..., 4], g.real) and np.array_equal(x6[..., 5], g.imag)
     assert np.isclose(np.max(np.hypot(x6[..., 4], x6[..., 5])), 1.0)
+
+
+def test_gradient_storage_hook_replaces_the_product_operand_only():
+    # gstore(name, g) replaces the masked output gradient in that layer's input
+    # and weight gradients, not in its bias gradient: the identity gives the
+    # plain backward pass bitwise; zeroing it at the first layer the backward
+    # pass meets (dec0b) zeroes every gradient below that layer and its own
+    # weights' gradient, and leaves its bias gradient and the head's unchanged
+    cfg = small_cfg()
+    rng = np.random.default_rng(7)
+    theta = rng.standard_normal(cnn.num_params(cfg)) * 0.3
+    x = rng.standard_normal((2, 8, 8, cfg.cin))
+    y, cache = cnn.forward(cfg, theta, x, keep=True)
+    gy = rng.standard_normal(y.shape)
+    g0, _ = cnn.backward(cfg, theta, cache, gy)
+    g1, _ = cnn.backward(cfg, theta, cache, gy, gstore=lambda name, g: g)
+    assert np.array_equal(g0, g1)
+    g2, _ = cnn.backward(cfg, theta, cache, gy,
+                         gstore=lambda name, g: np.zeros_like(g) if name == "dec0b" else g)
+    off = 0
+    for name, co, ci, kk in cnn.layer_shapes(cfg):
+        nw = co * ci * kk * kk
+        if name == "head":
+            assert np.array_equal(g2[off:off + nw + co], g0[off:off + nw + co])
+        elif name == "dec0b":
+            assert not np.any(g2[off:off + nw])
+            assert np.array_equal(g2[off + nw:off + nw + co], g0[off + nw:off + nw + co])
+        else:
+            assert not np.any(g2[off:off + nw + co]), name
+        off += nw + co
