@@ -86,7 +86,7 @@ def parse():
     p.add_argument("--basis", default="f32", choices=["f32", "f16"],
                    help="storage of the Krylov basis (arithmetic stays FP32, the true residual FP64)")
     # fixed-size runs for kernel profiling (ncu) and quick timing; no JSON line
-    p.add_argument("--case", default=None, choices=["solver", "cnn", "stencil"],
+    p.add_argument("--case", default=None, choices=["solver", "cnn", "cnn-train", "stencil"],
                    help="solver: --solves batched held-out problems with an iteration cap (every launch "
                         "sees the same basis sizes from run to run); cnn: the CNN forward of --solves problems")
     p.add_argument("--solves", type=int, default=64)
@@ -172,6 +172,31 @@ def case_stencil(a):
         gbs = per_cell * g.D * a.repeat / (ms / 1e3) / 1e9
         print(f"{name}: {a.n}x{a.n}, {ms * 1e3 / a.repeat:.1f} us per apply, {gbs:.0f} GB/s"
               + (f" = {gbs / peak:.3f} of the measured {peak:.0f} GB/s" if peak else ""))
+
+
+def case_cnn_train(a):
+    """a.repeat residual-loss training steps of the default network (k =
+    a.cnn_k) on a.solves problems of a.n x a.n, with the forward and backward
+    convolutions on tcgen05 (--tensor-cores off: CUDA cores)."""
+    import torch
+    import paper_1902_00090_gb300 as ddg
+
+    g, eps = case_problems(a)
+    ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device="cuda")) for e in eps]
+    b = ddg.fdfd_source(ops[0], g.i_src, g.sigma_src, g.j_src)
+    P = ddg.Predictor(k=a.cnn_k)
+    P.init_he(seed=0)
+    P.set_loss("residual")
+    on = a.tensor_cores == "on"
+    P.set_tensor_cores(on, backward=on)
+    src = (g.i_src, g.sigma_src, g.j_src)
+    for r in range(a.repeat):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        loss = P.train_step(ops, src, [b] * len(ops), a.cnn_lr)
+        torch.cuda.synchronize()
+        print(f"step {r}: {a.solves} problems, {(time.time() - t0) * 1e3:.2f} ms, loss {loss:.5f}, "
+              f"launches {P.launches}")
 
 
 def case_cnn(a):
@@ -1025,7 +1050,7 @@ def run_reference(args, rank, world):
 def main():
     args = parse()
     if args.case is not None:
-        {"solver": case_solver, "cnn": case_cnn, "stencil": case_stencil}[args.case](args)
+        {"solver": case_solver, "cnn": case_cnn, "cnn-train": case_cnn_train, "stencil": case_stencil}[args.case](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
