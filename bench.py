@@ -434,8 +434,11 @@ def run_ours(args, rank, world):
 
     def tune_policy(solve, candidates):
         """Per wavelength, the restart policy (cycles with all of V, then the
-        leading `keep` columns) with the fewest Krylov steps on the validation
-        trajectory (a solve that misses the cap counts twice the cap)."""
+        leading `keep` columns) of least estimated cost on the validation
+        trajectory: mean Krylov steps (a solve that misses the cap counts twice
+        the cap) times the relative bytes of a step, (keep + m/2) / (m/2)
+        (a step streams the kept columns and, over a cycle, m/2 Krylov
+        columns on average)."""
         table = []
         for cand in candidates:
             set_policy({lam: cand for lam in WAVELENGTHS})
@@ -446,16 +449,23 @@ def run_ours(args, rank, world):
                        for i, l2 in zip(inf, step_lams) if l2 == lam]
                 sc[lam] = float(np.mean(its))
             table.append((cand, sc))
-        best = {lam: min(table, key=lambda t: t[1][lam])[0] for lam in WAVELENGTHS}
+        half = args.restart / 2.0
+
+        def cost(c, v, lam):
+            return v[lam] * (c[1] + half) / half      # c[1]: the columns kept after the first cycles
+
+        best = {lam: min(table, key=lambda t: cost(t[0], t[1], lam))[0] for lam in WAVELENGTHS}
         report = {f"{int(round(lam * 1e9))}nm": {"chosen": {"cycles": best[lam][0], "keep": best[lam][1]},
-                                                 "steps": {f"{c[0]}/{c[1]}": round(v[lam], 1) for c, v in table}}
+                                                 "steps": {f"{c[0]}/{c[1]}": round(v[lam], 1) for c, v in table},
+                                                 "cost": {f"{c[0]}/{c[1]}": round(cost(c, v, lam), 1)
+                                                          for c, v in table}}
                   for lam in WAVELENGTHS}
         return best, report
 
     t0 = time.time()
     every = 10**6
-    pol_cnn, rep_cnn = tune_policy(solve_cnn, [(1, 0), (1, args.k), (every, kc)])
-    pol_pca, rep_pca = tune_policy(solve_pca, [(1, 0), (every, args.k)])
+    pol_cnn, rep_cnn = tune_policy(solve_cnn, [(1, 0), (1, 8), (1, args.k), (every, kc)])
+    pol_pca, rep_pca = tune_policy(solve_pca, [(1, 0), (1, 8), (every, args.k)])
     tune_s = time.time() - t0
 
     def step_cnn(t):
@@ -907,24 +917,31 @@ def run_batched(args, rank, world):
             d[sz] = summarize([i for i, z in zip(inf, sizes) if z == sz])
         out[variant] = d
 
-    # the CNN with recycling along the trajectories: per grid size, step t of
-    # its 16 trajectories batched, subspace [CNN-8 | previous solution]
+    # the CNN with recycling along the trajectories (subspace [CNN-8 |
+    # previous solution]) through the queue over trajectories: groups of 8
+    # trajectories of one grid size on 4 lanes
+    rl = lanes + [ddg.Context() for _ in range(2)]
+    for c in rl[2:]:
+        c.set_graphs(args.graphs == "on")
+        c.set_basis_storage(args.basis)
+        c.set_augmented_policy(1, 0)
+
     def recycle():
-        infs = []
+        A, B, Ut = [], [], []
         for (nx, ny), (te, b) in traj_ops.items():
             P, src, flat = per_size[(nx, ny)]
             Us = P.predict(flat, src)
-            Ut = [Us[16 * r:16 * (r + 1)] for r in range(16)]
-            _, inf, _ = ddg.gmres_solve_trajectories(ctx, te, [[b] * 16 for _ in range(16)], Ut,
-                                                     restart=args.restart, **kw)
-            infs += [i for tr in inf for i in tr]
-        return infs
+            A += te
+            B += [[b] * 16 for _ in range(16)]
+            Ut += [Us[16 * r:16 * (r + 1)] for r in range(16)]
+        _, inf, _ = ddg.gmres_solve_queue_trajectories(rl, A, B, Ut, traj_per_group=8, restart=args.restart, **kw)
+        return [i for tr in inf for i in tr]
     inf_r, ms = timed_call(torch, recycle)
     out["cnn8_recycle"] = {"value": round(sum(i["converged"] for i in inf_r) / (ms / 1e3), 3), "unit": "solves/s",
                            "seconds": round(ms / 1e3, 2), **summarize(inf_r),
-                           "note": "per grid size, step t of the 16 trajectories in one batch (16 sequential "
-                                   "batches per size), no queue"}
-    for c in lanes:
+                           "note": "gmres_solve_queue_trajectories: groups of 8 trajectories (one grid size) on 4 "
+                                   "lanes, step t of a group's trajectories in one batch"}
+    for c in rl:
         c.close()
     return {"metric": METRIC, "workload": "batched", "value": out["cnn8"]["value"], "unit": "solves/s",
             "n_gpus": world, "higher_is_better": True, "dtype": "c64+f64", "data": "synthetic",

@@ -336,6 +336,23 @@ ddg_status gmres_solve_queue(ddg_context* const* lanes, void* const* streams, in
                              ddg_precision prec, ddg_info* info);
 
 /*
+ * gmres_solve_queue_trajectories -- the solve queue over design trajectories
+ * with recycling (no paper counterpart beyond gmres_solve_trajectories): the
+ * n_traj trajectories of n_steps problems (host arrays of n_traj * n_steps
+ * entries, trajectory-major, as gmres_solve_trajectories) are taken in groups
+ * of traj_per_group consecutive trajectories by nlanes concurrent lanes, each
+ * group solved by gmres_solve_trajectories on the lane's context and stream
+ * (step t of the group's trajectories in one batch, subspace [U | x_{t-1}]).
+ * Concurrent lanes fill the GPU that one group's per-step batches leave
+ * idle.  Every solve's result is that of gmres_solve_trajectories on its own
+ * trajectory.  Other arguments and the return value as gmres_solve_queue.
+ */
+ddg_status gmres_solve_queue_trajectories(ddg_context* const* lanes, void* const* streams, int nlanes,
+                                          int traj_per_group, int n_traj, int n_steps, const ddg_op* const* A,
+                                          const double* const* b, const double* const* U, int k, double* const* x,
+                                          double tol, int restart, int maxit, ddg_precision prec, ddg_info* info);
+
+/*
  * pca_fit -- principal components of training fields (Sec. III, "Principal
  * component analysis": an incomplete SVD of the matrix whose columns are the
  * training fields; uncentred, no normalisation).  U receives the k leading left

@@ -9,5 +9,5 @@ from . import inputs  # noqa: F401
 from .binding import (  # noqa: F401
     Context, DdgError, Operator, augmented_gmres_solve, augmented_gmres_solve_batched, gmres_solve_noalloc,
     ddg_context_create, fdfd_apply, fdfd_solve_host, fdfd_apply_c64, fdfd_operator, fdfd_source, gmres_solve,
-    gmres_solve_batched, gmres_solve_queue, gmres_solve_trajectories, load, make_grid, pca_fit, Predictor, predictor_create,
+    gmres_solve_batched, gmres_solve_queue, gmres_solve_queue_trajectories, gmres_solve_trajectories, load, make_grid, pca_fit, Predictor, predictor_create,
 )

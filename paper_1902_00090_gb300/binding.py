@@ -107,6 +107,10 @@ _SIGS = {
     "gmres_solve_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, C.c_int,
                                       C.POINTER(ddg_info), _vp]),
     "predictor_num_outputs": (C.c_int, [_vp]),
+    "gmres_solve_queue_trajectories": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, C.c_int, C.c_int, C.c_int,
+                                                 C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.c_int,
+                                                 C.POINTER(_vp), C.c_double, C.c_int, C.c_int, C.c_int,
+                                                 C.POINTER(ddg_info)]),
     "gmres_solve_trajectories": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),
                                            C.c_int, C.POINTER(_vp), C.c_double, C.c_int, C.c_int, C.c_int,
                                            C.POINTER(ddg_info), _vp]),
@@ -459,6 +463,48 @@ def gmres_solve_trajectories(ctx: Context, A, b, U=None, x=None, tol=1e-6, resta
                                          int(maxit), _prec(precision), infos, _stream(stream))
     if st not in (0, 4):
         _check(st, "gmres_solve_trajectories")
+    inf = [i.as_dict() for i in infos]
+    return x, [inf[r * n_steps:(r + 1) * n_steps] for r in range(n_traj)], st
+
+
+def gmres_solve_queue_trajectories(lanes, A, b, U=None, x=None, traj_per_group=16, streams=None, tol=1e-6,
+                                   restart=200, maxit=5000, precision="c64"):
+    """The solve queue over trajectories with recycling: A, b (and U, x) are
+    lists of n_traj lists of n_steps entries; groups of traj_per_group
+    trajectories run gmres_solve_trajectories on len(lanes) concurrent lanes.
+    Returns (x, info, status) nested as A."""
+    torch = _torch()
+    n_traj, n_steps = len(A), len(A[0])
+    if any(len(a) != n_steps for a in A):
+        raise ValueError("every trajectory needs the same number of steps")
+    nl = len(lanes)
+    if streams is None:
+        streams = [torch.cuda.Stream() for _ in range(nl)]
+    cur = torch.cuda.current_stream()
+    for st_ in streams:
+        st_.wait_stream(cur)
+    fa = [a for tr in A for a in tr]
+    fb = [v for tr in b for v in tr]
+    if x is None:
+        x = [[torch.zeros_like(v) for v in tr] for tr in b]
+    fx = [v for tr in x for v in tr]
+    sizes = [a.D for a in fa]
+    k, hu = 0, None
+    if U is not None:
+        fu = [u for tr in U for u in tr]
+        k = fu[0].shape[0]
+        hu = _ptr_array(fu, torch.complex128, "U", [k * s_ for s_ in sizes])
+    n = len(fa)
+    infos = (ddg_info * n)()
+    st = load().gmres_solve_queue_trajectories(
+        (_vp * nl)(*[c.handle.value for c in lanes]), (_vp * nl)(*[s_.cuda_stream for s_ in streams]), nl,
+        int(traj_per_group), n_traj, n_steps, (_vp * n)(*[a.handle.value for a in fa]),
+        _ptr_array(fb, torch.complex128, "b", sizes), hu, int(k), _ptr_array(fx, torch.complex128, "x", sizes),
+        float(tol), int(restart), int(maxit), _prec(precision), infos)
+    for st_ in streams:
+        cur.wait_stream(st_)
+    if st not in (0, 4):
+        _check(st, "gmres_solve_queue_trajectories")
     inf = [i.as_dict() for i in infos]
     return x, [inf[r * n_steps:(r + 1) * n_steps] for r in range(n_traj)], st
 

@@ -23,6 +23,7 @@ struct QueueJob {
     ddg_context* const* lanes;
     void* const* streams;
     int width, n, k, restart, maxit, device;
+    int n_steps = 0;                  // > 0: groups of `width` trajectories of n_steps solves (recycling)
     const ddg_op* const* A;
     const double* const* b;
     const double* const* U;
@@ -49,15 +50,21 @@ static void run_lane(QueueJob* j, int lane) {
         j->stop = true;
         return;
     }
-    const int groups = (j->n + j->width - 1) / j->width;
+    const int units = j->n_steps > 0 ? j->n / j->n_steps : j->n;   // solves, or trajectories
+    const int groups = (units + j->width - 1) / j->width;
     while (!j->stop) {
         const int g = j->next.fetch_add(1);
         if (g >= groups) break;
-        const int s0 = g * j->width;
-        const int cnt = std::min(j->width, j->n - s0);
+        const int u0 = g * j->width;
+        const int cnt = std::min(j->width, units - u0);
+        const int s0 = j->n_steps > 0 ? u0 * j->n_steps : u0;
         ddg_info* inf = j->info ? j->info + s0 : nullptr;
         ddg_status st;
-        if (j->U)
+        if (j->n_steps > 0)
+            st = gmres_solve_trajectories(j->lanes[lane], cnt, j->n_steps, j->A + s0, j->b + s0,
+                                          j->U ? j->U + s0 : nullptr, j->k, j->x + s0, j->tol, j->restart,
+                                          j->maxit, j->prec, inf, j->streams ? j->streams[lane] : nullptr);
+        else if (j->U)
             st = augmented_gmres_solve_batched(j->lanes[lane], cnt, j->A + s0, j->b + s0, j->U + s0, j->k,
                                                j->x + s0, j->tol, j->restart, j->maxit, j->prec, inf,
                                                j->streams ? j->streams[lane] : nullptr);
@@ -81,10 +88,35 @@ static void run_lane(QueueJob* j, int lane) {
 
 using namespace ddg;
 
+static ddg_status run_queue(ddg_context* const* lanes, void* const* streams, int nlanes, int width, int n,
+                            int n_steps, const ddg_op* const* A, const double* const* b, const double* const* U,
+                            int k, double* const* x, double tol, int restart, int maxit, ddg_precision prec,
+                            ddg_info* info);
+
 extern "C" ddg_status gmres_solve_queue(ddg_context* const* lanes, void* const* streams, int nlanes, int width,
                                         int n, const ddg_op* const* A, const double* const* b,
                                         const double* const* U, int k, double* const* x, double tol, int restart,
                                         int maxit, ddg_precision prec, ddg_info* info) {
+    return run_queue(lanes, streams, nlanes, width, n, 0, A, b, U, k, x, tol, restart, maxit, prec, info);
+}
+
+extern "C" ddg_status gmres_solve_queue_trajectories(ddg_context* const* lanes, void* const* streams, int nlanes,
+                                                     int traj_per_group, int n_traj, int n_steps,
+                                                     const ddg_op* const* A, const double* const* b,
+                                                     const double* const* U, int k, double* const* x, double tol,
+                                                     int restart, int maxit, ddg_precision prec, ddg_info* info) {
+    if (n_traj < 1 || n_steps < 1) {
+        set_error("gmres_solve_queue_trajectories: n_traj=%d, n_steps=%d", n_traj, n_steps);
+        return DDG_EINVAL;
+    }
+    return run_queue(lanes, streams, nlanes, traj_per_group, n_traj * n_steps, n_steps, A, b, U, k, x, tol, restart,
+                     maxit, prec, info);
+}
+
+static ddg_status run_queue(ddg_context* const* lanes, void* const* streams, int nlanes, int width, int n,
+                            int n_steps, const ddg_op* const* A, const double* const* b, const double* const* U,
+                            int k, double* const* x, double tol, int restart, int maxit, ddg_precision prec,
+                            ddg_info* info) {
     if (!lanes || nlanes < 1 || nlanes > kMaxLanes) {
         set_error("gmres_solve_queue: lanes NULL or nlanes=%d outside [1,%d]", nlanes, kMaxLanes);
         return DDG_EINVAL;
@@ -116,8 +148,9 @@ extern "C" ddg_status gmres_solve_queue(ddg_context* const* lanes, void* const* 
     j.tol = tol;
     j.prec = prec;
     j.info = info;
+    j.n_steps = n_steps;
     DDG_CHECK_CUDA(cudaGetDevice(&j.device));
-    const int groups = (n + width - 1) / width;
+    const int groups = ((n_steps > 0 ? n / n_steps : n) + width - 1) / width;
     const int used = std::min(nlanes, groups);
     if (used == 1) {
         run_lane(&j, 0);   // no thread for a single lane

@@ -68,3 +68,25 @@ def test_trajectory_recycling_rejects_bad_arguments():
     big = [[dev(inputs.random_complex(G.D, 1, shape=(32, G.D)))]]
     with pytest.raises(ddg.DdgError):
         ddg.gmres_solve_trajectories(ddg.Context(), ops, bs, big)     # k + 1 = 33 columns > 32
+
+
+def test_queue_over_trajectories_equals_one_call():
+    # gmres_solve_queue_trajectories: groups of trajectories on concurrent
+    # lanes, each group solved by gmres_solve_trajectories; every solve's
+    # result is that of its own trajectory, bitwise, in any group
+    n_traj, n_steps = 3, 2
+    eps = [inputs.trajectory_eps(G, 2, 50 + r, steps=n_steps) for r in range(n_traj)]
+    ops = [[ddg.fdfd_operator(G, torch.as_tensor(e, device="cuda")) for e in tr] for tr in eps]
+    bs = [[ddg.fdfd_source(op, G.i_src, G.sigma_src, G.j_src) for op in tr] for tr in ops]
+    U = [[dev(inputs.random_complex(G.D, 200 + 10 * r + t, shape=(2, G.D))) for t in range(n_steps)]
+         for r in range(n_traj)]
+    ctx = ddg.Context()
+    x1, i1, s1 = ddg.gmres_solve_trajectories(ctx, ops, bs, U, tol=1e-7, restart=30, maxit=3000, precision="c64")
+    lanes = [ddg.Context(), ddg.Context()]
+    x2, i2, s2 = ddg.gmres_solve_queue_trajectories(lanes, ops, bs, U, traj_per_group=1, tol=1e-7, restart=30,
+                                                    maxit=3000, precision="c64")
+    assert s1 == s2 == 0
+    for r in range(n_traj):
+        for t in range(n_steps):
+            assert i1[r][t] == i2[r][t]
+            assert torch.equal(x1[r][t], x2[r][t])
