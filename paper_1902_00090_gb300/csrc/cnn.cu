@@ -57,6 +57,16 @@ struct LoadCat {
         }
         return __bfloat162float(x2[(((long long)b * H + y) * W + x) * c2 + (c - c1)]);
     }
+    // channels c, c + 1 (c even, c1 even) as 2 packed BF16 values
+    __device__ __forceinline__ uint32_t load2(int b, int y, int x, int H, int W, int c) const {
+        const bf16* src;
+        if (c < c1)
+            src = up1 ? x1 + ((((long long)b * h1 + (y >> 1)) * w1 + (x >> 1)) * c1 + c)
+                      : x1 + ((((long long)b * H + y) * W + x) * c1 + c);
+        else
+            src = x2 + ((((long long)b * H + y) * W + x) * c2 + (c - c1));
+        return *reinterpret_cast<const uint32_t*>(src);
+    }
     // channels c .. c + 7 (c % 8 == 0, c1 % 8 == 0) as 8 packed BF16 values
     __device__ __forceinline__ uint4 load8(int b, int y, int x, int H, int W, int c) const {
         const bf16* src;
@@ -405,6 +415,16 @@ __global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(G ld, int B, int H, i
 // separately (k_bias_grad) from the FP32 g'.
 namespace tcw {
 constexpr int kWN = 128;                       // columns n per CTA
+}  // namespace tcw
+// Four 8x8 b16 matrices from registers (lane t: row t / 4, elements 2 (t % 4),
+// +1 of each) to shared memory transposed: row i of matrix q (its column i)
+// goes to the 16 bytes at the address held by lane 8 q + i.
+__device__ __forceinline__ void stmatrix_x4_trans(uint32_t addr, const uint32_t (&r)[4]) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3])
+                 : "memory");
+}
+namespace tcw {
 constexpr uint32_t kTileBytes = tc::kM * tc::kKC * 2;   // 128 rows x 64 K values (A and B alike)
 __host__ __device__ constexpr size_t smem_bytes() { return (size_t)tc::kStages * 2 * kTileBytes + 1024; }
 }  // namespace tcw
@@ -451,51 +471,56 @@ __global__ void __launch_bounds__(tc::kThreads) k_wgrad_tc(LX lx, const float* _
         unsigned char* Bs = As + tcw::kTileBytes;
         if (c >= kStages && !mbar_wait(&done[s], (unsigned)((c - kStages) / kStages) & 1u)) ok = false;
         const long long pc0 = p_begin + (long long)c * kKC;
-        // A: g'[p][co .. co + 7] -> rows co .. co + 7, column p - pc0
-        for (int task = tid; task < kKC * ncg; task += kThreads) {
-            const int pl = task / ncg, cg = task - pl * ncg;
-            const long long p = pc0 + pl;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (p < p_end) {
-                const long long i = p * Co + cg * 8;
-                const float4 g0 = *reinterpret_cast<const float4*>(g + i);
-                const float4 g1 = *reinterpret_cast<const float4*>(g + i + 4);
-                const uint4 yv = *reinterpret_cast<const uint4*>(yout + i);
-                const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-                const unsigned yw[4] = {yv.x, yv.y, yv.z, yv.w};
-                unsigned o[4];
+        // Both operands are K-major in the pixels while the data are
+        // pixel-major: each warp stores four 8x8 blocks (8 pixels x 8 rows of
+        // the operand) at a time with stmatrix .trans, which writes every
+        // operand row's 8 pixels as one 16-byte chunk of the swizzled tile.
+        // Block f (x4 group of 4 per warp instruction): lane t holds pixel
+        // 8 pb + t / 4 and the operand rows 8 rb + 2 (t % 4), +1; lane
+        // 8 q + i gives the address of row i of block q.
+        const int nfa = (Co >> 3) * (kKC / 8);          // A blocks: (Co / 8) row blocks x 8 pixel blocks
+        for (int fg = warp; fg < nfa / 4; fg += kThreads / 32) {
+            uint32_t r[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const __nv_bfloat162 yb = *reinterpret_cast<const __nv_bfloat162*>(&yw[q]);
-                    __nv_bfloat162 h = __floats2bfloat162_rn(__bfloat162float(yb.x) > 0.f ? gv[2 * q] : 0.f,
-                                                             __bfloat162float(yb.y) > 0.f ? gv[2 * q + 1] : 0.f);
-                    o[q] = *reinterpret_cast<unsigned*>(&h);
+            for (int q = 0; q < 4; ++q) {
+                const int f = fg * 4 + q, rb = f % (Co >> 3), pb = f / (Co >> 3);
+                const long long p = pc0 + pb * 8 + (lane >> 2);
+                const int co = rb * 8 + 2 * (lane & 3);
+                uint32_t v = 0u;
+                if (p < p_end) {
+                    const long long i = p * Co + co;
+                    const float2 gg = *reinterpret_cast<const float2*>(g + i);
+                    const __nv_bfloat162 yb = *reinterpret_cast<const __nv_bfloat162*>(yout + i);
+                    __nv_bfloat162 h = __floats2bfloat162_rn(__bfloat162float(yb.x) > 0.f ? gg.x : 0.f,
+                                                             __bfloat162float(yb.y) > 0.f ? gg.y : 0.f);
+                    v = *reinterpret_cast<uint32_t*>(&h);
                 }
-                v = make_uint4(o[0], o[1], o[2], o[3]);
+                r[q] = v;
             }
-            const unsigned short* hv = reinterpret_cast<const unsigned short*>(&v);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                *reinterpret_cast<unsigned short*>(As + swz(cg * 8 + j, pl >> 3) + ((pl & 7) << 1)) = hv[j];
+            const int fq = fg * 4 + (lane >> 3), rbq = fq % (Co >> 3), pbq = fq / (Co >> 3);
+            stmatrix_x4_trans(smem_u32(As + swz(rbq * 8 + (lane & 7), pbq)), r);
         }
-        // B: x[p + off(tap)][ci .. ci + 7] -> rows n - n0 .. + 7 (n = tap Ci + ci), column p - pc0
-        for (int task = tid; task < kKC * (tcw::kWN / 8); task += kThreads) {
-            const int pl = task / (tcw::kWN / 8), ng = task - pl * (tcw::kWN / 8);
-            const long long p = pc0 + pl;
-            const int n = n0 + ng * 8;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (p < p_end && n < Ntot) {
-                const int tap = n / Ci, ci = n - tap * Ci;
-                const int x = (int)(p % W);
-                const long long t = p / W;
-                const int y = (int)(t % H), b = (int)(t / H);
-                const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-                if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = lx.load8(b, yy, xx, H, W, ci);
-            }
-            const unsigned short* hv = reinterpret_cast<const unsigned short*>(&v);
+        const int nfb = (tcw::kWN / 8) * (kKC / 8);     // B blocks: 16 column blocks x 8 pixel blocks
+        for (int fg = warp; fg < nfb / 4; fg += kThreads / 32) {
+            uint32_t r[4];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                *reinterpret_cast<unsigned short*>(Bs + swz(ng * 8 + j, pl >> 3) + ((pl & 7) << 1)) = hv[j];
+            for (int q = 0; q < 4; ++q) {
+                const int f = fg * 4 + q, nb = f % (tcw::kWN / 8), pb = f / (tcw::kWN / 8);
+                const long long p = pc0 + pb * 8 + (lane >> 2);
+                const int n = n0 + nb * 8 + 2 * (lane & 3);
+                uint32_t v = 0u;
+                if (p < p_end && n < Ntot) {
+                    const int tap = n / Ci, ci = n - tap * Ci;
+                    const int x = (int)(p % W);
+                    const long long t = p / W;
+                    const int y = (int)(t % H), b = (int)(t / H);
+                    const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+                    if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = lx.load2(b, yy, xx, H, W, ci);
+                }
+                r[q] = v;
+            }
+            const int fq = fg * 4 + (lane >> 3), nbq = fq % (tcw::kWN / 8), pbq = fq / (tcw::kWN / 8);
+            stmatrix_x4_trans(smem_u32(Bs + swz(nbq * 8 + (lane & 7), pbq)), r);
         }
         fence_proxy_async_smem();
         __syncthreads();
