@@ -464,7 +464,17 @@ __global__ void __launch_bounds__(tc::kThreads) k_wgrad_tc(LX lx, const float* _
     fence_after();
     const uint32_t tmem = s_tmem;
     bool ok = true;
-    const int ncg = Co >> 3;   // 8-channel groups of g'
+    // this lane's B columns n = n0 + 8 (4 (warp % 4) + q) + 2 (lane % 4), q < 4,
+    // the same in every stage: input channel, tap offset (-1 for n past 9 Ci)
+    int bci[4], bdy[4], bdx[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int n = n0 + 8 * (4 * (warp & 3) + q) + 2 * (lane & 3);
+        const int tap = n / Ci;
+        bci[q] = n < Ntot ? n - tap * Ci : -1;
+        bdy[q] = tap / 3 - 1;
+        bdx[q] = tap % 3 - 1;
+    }
     for (int c = 0; c < nch; ++c) {
         const int s = c % kStages;
         unsigned char* As = smt + s * 2 * tcw::kTileBytes;
@@ -500,23 +510,28 @@ __global__ void __launch_bounds__(tc::kThreads) k_wgrad_tc(LX lx, const float* _
             const int fq = fg * 4 + (lane >> 3), rbq = fq % (Co >> 3), pbq = fq / (Co >> 3);
             stmatrix_x4_trans(smem_u32(As + swz(rbq * 8 + (lane & 7), pbq)), r);
         }
-        const int nfb = (tcw::kWN / 8) * (kKC / 8);     // B blocks: 16 column blocks x 8 pixel blocks
-        for (int fg = warp; fg < nfb / 4; fg += kThreads / 32) {
+        // B blocks: 16 column blocks x 8 pixel blocks; group fg (4 blocks) has
+        // the pixel block fg / 4 and the column blocks 4 (fg % 4) + q, and
+        // warp w takes fg = w, w + 8, ...: its columns (bcol) are the same in
+        // every group and stage, so only the pixel is decoded per group
+        for (int fg = warp; fg < (tcw::kWN / 8) * (kKC / 8) / 4; fg += kThreads / 32) {
+            const int pb = fg >> 2;
+            const long long p = pc0 + pb * 8 + (lane >> 2);
+            int b = -1, y = 0, x = 0;
+            if (p < p_end) {
+                const int pi = (int)p;               // pixel counts fit in 31 bits (checked at launch)
+                x = pi % W;
+                const int t = pi / W;
+                y = t % H;
+                b = t / H;
+            }
             uint32_t r[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int f = fg * 4 + q, nb = f % (tcw::kWN / 8), pb = f / (tcw::kWN / 8);
-                const long long p = pc0 + pb * 8 + (lane >> 2);
-                const int n = n0 + nb * 8 + 2 * (lane & 3);
                 uint32_t v = 0u;
-                if (p < p_end && n < Ntot) {
-                    const int tap = n / Ci, ci = n - tap * Ci;
-                    const int x = (int)(p % W);
-                    const long long t = p / W;
-                    const int y = (int)(t % H), b = (int)(t / H);
-                    const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-                    if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = lx.load2(b, yy, xx, H, W, ci);
-                }
+                const int yy = y + bdy[q], xx = x + bdx[q];
+                if (b >= 0 && bci[q] >= 0 && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                    v = lx.load2(b, yy, xx, H, W, bci[q]);
                 r[q] = v;
             }
             const int fq = fg * 4 + (lane >> 3), nbq = fq % (tcw::kWN / 8), pbq = fq / (tcw::kWN / 8);
@@ -1466,11 +1481,13 @@ template <class LX>
 static ddg_status wgrad(ddg_predictor* P, const LX& lx, const float* g, const bf16* yout, int B, int H, int W, int li,
                         cudaStream_t st) {
     const Layer& Ly = P->layers[li];
-    if ((P->tensor_cores & 2) && Ly.co % 16 == 0 && Ly.co <= 128 && Ly.ci % 16 == 0) {
+    if ((P->tensor_cores & 2) && Ly.co % 16 == 0 && Ly.co <= 128 && Ly.ci % 16 == 0 &&
+        (long long)B * H * W < (1LL << 31)) {
         // on the tensor cores (bit 2): D[co, tap Ci + ci] over the pixels
         const long long npx = (long long)B * H * W;
         const int ntn = (9 * Ly.ci + tcw::kWN - 1) / tcw::kWN;
-        const long long want = std::max(1LL, (long long)(2 * P->sm_count + ntn - 1) / ntn);
+        // three CTAs fit an SM (66.5 KB of shared memory, 128 tensor-memory columns each)
+        const long long want = std::max(1LL, (long long)(3 * P->sm_count + ntn - 1) / ntn);
         long long per = (npx + want - 1) / want;
         per = std::max((long long)tc::kKC, (per + tc::kKC - 1) / tc::kKC * tc::kKC);
         const unsigned slices = (unsigned)((npx + per - 1) / per);
