@@ -110,3 +110,17 @@ def test_source_profile():
     assert np.argmax(np.abs(col)) == g.ny // 2
     assert np.allclose(np.abs(col[g.ny // 2 - 5]), np.abs(col[g.ny // 2 + 5]))
     assert np.allclose(col.real, 0.0)
+
+
+def test_source_amplitude_and_gaussian_width():
+    # b = -i (k0 h) J (Eq. 1 times h^2 up to mu0 c): at the profile's centre
+    # |b| = k0 h = 2 pi dx / lambda, the phase is -i, and one sigma away the
+    # Gaussian has fallen to exp(-1/2); checked at two wavelengths and sizes
+    from paper_1902_00090_gb300 import inputs
+    for g in (inputs.grid_128(), inputs.grid_for(256, 256, wavelength=1300e-9)):
+        b = fdfd.source_for(g).reshape(g.ny, g.nx)
+        jc = int(g.j_src)
+        kh = 2.0 * np.pi * g.dx / g.wavelength
+        assert abs(b[jc, g.i_src] - (-1j * kh)) <= 1e-15 * kh
+        s = int(g.sigma_src)
+        assert abs(abs(b[jc + s, g.i_src]) / kh - np.exp(-0.5)) <= 1e-14
