@@ -1,5 +1,5 @@
 """Host logic of bench.py that needs no GPU: the clock record taken during the
-timed region (parsing of nvidia-smi samples)."""
+timed region (parsing of nvidia-smi samples) and the restart-policy choice."""
 import os
 import sys
 import threading
@@ -46,3 +46,20 @@ def test_clock_record_flags_throttling_and_missing_samples():
     assert sampler_with([]).stop()["reasons"] == ["no samples"]
     c = bench.ClockSampler(0)
     assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_policy_choice_needs_a_margin_to_keep_more_columns():
+    every = 10**6
+    # mean steps per wavelength as a validation pass reports them
+    table = [((1, 0), {1: 3932.3, 2: 2534.9}), ((1, 8), {1: 4041.4, 2: 3170.2}),
+             ((1, 20), {1: 3371.6, 2: 3210.0}), ((every, 28), {1: 3327.3, 2: 3390.0})]
+    # 1300 nm: 1/20 saves 14 % over 1/0; all 28 kept saves only 1.3 % more
+    assert bench.choose_policy(table, 1) == (1, 20)
+    assert bench.choose_policy(table, 1, margin=0.0) == (every, 28)
+    # 1550 nm: the first-cycle policy has the fewest steps
+    assert bench.choose_policy(table, 2) == (1, 0)
+    # the order of the table does not matter
+    assert bench.choose_policy(table[::-1], 1) == (1, 20)
+    # a large saving still buys more columns
+    big = [((1, 0), {1: 5000.0}), ((every, 20), {1: 3400.0})]
+    assert bench.choose_policy(big, 1) == (every, 20)
