@@ -89,68 +89,90 @@ __global__ void __launch_bounds__(256) k_apply(int nx, int ny, const T* __restri
     y[e] = acc;
 }
 
-// y = A x in complex64 for even nx: two cells per thread with 16-byte loads
-// and stores, the row from blockIdx.y (no index division).  Thread t of row j
-// owns cells i0 = 2 (blockIdx.x blockDim.x + t) and i0 + 1; their x-neighbours
-// i0 - 1 and i0 + 2 come from the neighbouring lanes by shuffles (loaded
-// directly at warp edges and wrapped periodically at the row ends); the rows
-// j - 1 and j + 1 are 16-byte loads of the same two cells (L2 reuse across
-// blocks).  Same arithmetic and order as k_apply<float> per cell.
-__global__ void __launch_bounds__(256) k_apply_c64x2(int nx, int ny, const float* __restrict__ eps,
-                                                     const float2* __restrict__ coef, float kh2,
-                                                     const float4* __restrict__ x, float4* __restrict__ y) {
-    const int j = blockIdx.y;
+// y = A x in complex64 for even nx: two cells and four rows per thread with
+// 16-byte loads and stores.  Thread t of row group blockIdx.y owns cells
+// i0 = 2 (blockIdx.x blockDim.x + t) and i0 + 1 of rows j0 .. j0 + 3
+// (j0 = 4 blockIdx.y).  Every load is issued before any arithmetic: the six
+// rows j0 - 1 .. j0 + 4 of the thread's two cells (each x row is read by
+// 6/4 row groups instead of 3 times, the halo rows from L2), the four eps
+// pairs, and at a warp edge or a row end the neighbouring pair of each row.
+// The x-neighbours i0 - 1 and i0 + 2 come from the neighbouring lanes by
+// shuffles.  eps (read once) and y (written once) bypass L2 retention
+// (evict-first loads, streaming stores) so that L2 keeps the x rows that the
+// next row group reads again.  Rows past ny load a valid row and store
+// nothing.  Same arithmetic and order as k_apply<float> per cell.
+constexpr int kApplyRows = 4;
+__global__ void __launch_bounds__(256) k_apply_c64_rows(int nx, int ny, const float* __restrict__ eps,
+                                                        const float2* __restrict__ coef, float kh2,
+                                                        const float4* __restrict__ x, float4* __restrict__ y) {
+    constexpr int R = kApplyRows;
+    const int j0 = blockIdx.y * R;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;   // pair index in the row
     const int nh = nx >> 1;
     const int lane = threadIdx.x & 31;
     const bool in = h < nh;
     const int hh = in ? h : nh - 1;                         // out-of-row lanes mirror the last pair
-    const long long row = (long long)j * nh;
-    const int jp = (j == ny - 1) ? 0 : j + 1, jm = (j == 0) ? ny - 1 : j - 1;
-    // every load is issued before any shuffle: the lanes at a warp edge or a
-    // row end also fetch the neighbouring pair themselves (no second round)
     const bool ledge = lane == 0 || hh == 0;
     const bool redge = lane == 31 || hh == nh - 1 || h + 1 >= nh;
-    const float4 c = x[row + hh];
-    const float4 up = x[(long long)jp * nh + hh];
-    const float4 dn = x[(long long)jm * nh + hh];
-    float4 l = make_float4(0.f, 0.f, 0.f, 0.f), r = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ledge) l = x[row + (hh == 0 ? nh - 1 : hh - 1)];
-    if (redge) r = x[row + (hh == nh - 1 ? 0 : hh + 1)];
-    const float2 ev = reinterpret_cast<const float2*>(eps)[row + hh];
+    const int hl = hh == 0 ? nh - 1 : hh - 1, hr = hh == nh - 1 ? 0 : hh + 1;   // periodic in x
+    float4 xr[R + 2];                                       // rows j0 - 1 .. j0 + R
+#pragma unroll
+    for (int q = 0; q < R + 2; ++q) {
+        int r = j0 - 1 + q;
+        if (r < 0) r += ny;                                 // periodic in y
+        else if (r >= ny) r = (r == ny) ? 0 : ny - 1;       // row ny wraps; later rows feed no output
+        xr[q] = __ldg(&x[(long long)r * nh + hh]);
+    }
+    float4 lv[R], rv[R];
+    float2 ev[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int r = min(j0 + q, ny - 1);
+        const long long row = (long long)r * nh;
+        lv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rv[q] = lv[q];
+        if (ledge) lv[q] = __ldg(&x[row + hl]);
+        if (redge) rv[q] = __ldg(&x[row + hr]);
+        ev[q] = __ldcs(reinterpret_cast<const float2*>(eps) + row + hh);
+    }
     const float4 axp2 = reinterpret_cast<const float4*>(coef)[hh];        // axp of cells 2hh, 2hh + 1
     const float4 axm2 = reinterpret_cast<const float4*>(coef + nx)[hh];   // axm of the same cells
-    const float2 ayp = coef[2 * nx + j], aym = coef[2 * nx + ny + j];
-    // left neighbour of cell 2hh: the .zw of pair hh - 1; right of 2hh + 1: the .xy of pair hh + 1
-    float lx = __shfl_up_sync(0xffffffffu, c.z, 1), ly = __shfl_up_sync(0xffffffffu, c.w, 1);
-    float rx = __shfl_down_sync(0xffffffffu, c.x, 1), ry = __shfl_down_sync(0xffffffffu, c.y, 1);
-    if (ledge) {
-        lx = l.z;
-        ly = l.w;
-    }
-    if (redge) {
-        rx = r.x;
-        ry = r.y;
-    }
-    if (!in) return;
-    float2 out[2];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const float2 axp = q == 0 ? make_float2(axp2.x, axp2.y) : make_float2(axp2.z, axp2.w);
-        const float2 axm = q == 0 ? make_float2(axm2.x, axm2.y) : make_float2(axm2.z, axm2.w);
-        float2 d = cadd(cadd(axp, axm), cadd(ayp, aym));
-        d.x -= kh2 * (q == 0 ? ev.x : ev.y);
-        const float2 xc = q == 0 ? make_float2(c.x, c.y) : make_float2(c.z, c.w);
-        const float2 xr = q == 0 ? make_float2(c.z, c.w) : make_float2(rx, ry);
-        const float2 xl = q == 0 ? make_float2(lx, ly) : make_float2(c.x, c.y);
-        float2 acc = cmul(d, xc);
-        cfms(acc, axp, xr);
-        cfms(acc, axm, xl);
-        cfms(acc, ayp, q == 0 ? make_float2(up.x, up.y) : make_float2(up.z, up.w));
-        cfms(acc, aym, q == 0 ? make_float2(dn.x, dn.y) : make_float2(dn.z, dn.w));
-        out[q] = acc;
+    for (int q = 0; q < R; ++q) {
+        const int j = j0 + q;
+        const float4 c = xr[q + 1], up = xr[q + 2], dn = xr[q];
+        // left neighbour of cell 2hh: the .zw of pair hh - 1; right of 2hh + 1: the .xy of pair hh + 1
+        float lx = __shfl_up_sync(0xffffffffu, c.z, 1), ly = __shfl_up_sync(0xffffffffu, c.w, 1);
+        float rx = __shfl_down_sync(0xffffffffu, c.x, 1), ry = __shfl_down_sync(0xffffffffu, c.y, 1);
+        if (ledge) {
+            lx = lv[q].z;
+            ly = lv[q].w;
+        }
+        if (redge) {
+            rx = rv[q].x;
+            ry = rv[q].y;
+        }
+        if (!in || j >= ny) continue;                       // after the shuffles: every lane takes part
+        const float2 ayp = coef[2 * nx + j], aym = coef[2 * nx + ny + j];
+        float2 out[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float2 axp = s == 0 ? make_float2(axp2.x, axp2.y) : make_float2(axp2.z, axp2.w);
+            const float2 axm = s == 0 ? make_float2(axm2.x, axm2.y) : make_float2(axm2.z, axm2.w);
+            float2 d = cadd(cadd(axp, axm), cadd(ayp, aym));
+            d.x -= kh2 * (s == 0 ? ev[q].x : ev[q].y);
+            const float2 xc = s == 0 ? make_float2(c.x, c.y) : make_float2(c.z, c.w);
+            const float2 xe = s == 0 ? make_float2(c.z, c.w) : make_float2(rx, ry);
+            const float2 xw = s == 0 ? make_float2(lx, ly) : make_float2(c.x, c.y);
+            float2 acc = cmul(d, xc);
+            cfms(acc, axp, xe);
+            cfms(acc, axm, xw);
+            cfms(acc, ayp, s == 0 ? make_float2(up.x, up.y) : make_float2(up.z, up.w));
+            cfms(acc, aym, s == 0 ? make_float2(dn.x, dn.y) : make_float2(dn.z, dn.w));
+            out[s] = acc;
+        }
+        __stcs(&y[(long long)j * nh + h], make_float4(out[0].x, out[0].y, out[1].x, out[1].y));
     }
-    y[row + h] = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
 }
 
 __global__ void k_source(int nx, int ny, int i_src, double sigma, double j_c, double kh,
@@ -178,10 +200,10 @@ ddg_status launch_apply_d(const ddg_op* A, const double2* x, double2* y, cudaStr
 ddg_status launch_apply_f(const ddg_op* A, const float2* x, float2* y, cudaStream_t s) {
     if ((A->nx & 1) == 0 && A->nx >= 4 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)y & 15) == 0) {
         const int nh = A->nx / 2;
-        dim3 grid((unsigned)((nh + 255) / 256), (unsigned)A->ny);
-        k_apply_c64x2<<<grid, 256, 0, s>>>(A->nx, A->ny, A->eps_f, A->coef_f, (float)(A->kh * A->kh),
-                                           reinterpret_cast<const float4*>(x), reinterpret_cast<float4*>(y));
-        DDG_CHECK_LAUNCH("k_apply_c64x2");
+        dim3 grid((unsigned)((nh + 255) / 256), (unsigned)((A->ny + kApplyRows - 1) / kApplyRows));
+        k_apply_c64_rows<<<grid, 256, 0, s>>>(A->nx, A->ny, A->eps_f, A->coef_f, (float)(A->kh * A->kh),
+                                              reinterpret_cast<const float4*>(x), reinterpret_cast<float4*>(y));
+        DDG_CHECK_LAUNCH("k_apply_c64_rows");
         return DDG_OK;
     }
     unsigned nb = (unsigned)((A->D + 255) / 256);

@@ -53,6 +53,10 @@ GRIDS = [
     inputs.Grid(nx=38, ny=9, npml=3, i_src=5, sigma_src=2.0, slab_cells=2),
     inputs.Grid(nx=4, ny=5, npml=1, i_src=1, sigma_src=1.0, slab_cells=1),
     inputs.Grid(nx=1030, ny=6, npml=2, i_src=9, sigma_src=2.0, slab_cells=2),
+    # the stencil's four-row groups: fewer rows than one group (row ny wraps to
+    # row 0, rows past it feed no output), and a last group with one row
+    inputs.Grid(nx=6, ny=3, npml=1, i_src=1, sigma_src=1.0, slab_cells=1),
+    inputs.Grid(nx=520, ny=13, npml=2, i_src=9, sigma_src=2.0, slab_cells=2),
 ]
 
 

@@ -71,6 +71,8 @@ def test_large_grid_1024_properties():
     y = ddg.fdfd_apply(op, dev(v)).cpu().numpy()
     yo = A @ v
     assert np.max(np.abs(y - yo)) <= 1e-13 * np.max(np.abs(yo))
+    y32 = ddg.fdfd_apply_c64(op, dev(v, torch.complex64)).cpu().numpy()
+    assert np.linalg.norm(y32 - yo) <= 2e-6 * np.linalg.norm(yo)
     b = fdfd.source_for(g)
     bd = ddg.fdfd_source(op, g.i_src, g.sigma_src, g.j_src)
     ctx = ddg.Context()
