@@ -84,7 +84,7 @@ def parse():
     p.add_argument("--levers", action="store_true",
                    help="also measure the levers on the CNN's gain (restart policy, PCA + CNN, k, training size)")
     p.add_argument("--graphs", default="on", choices=["on", "off"],
-                   help="run each restart cycle's Arnoldi steps as one CUDA graph launch")
+                   help="run each batched solve's restart cycles as one CUDA graph launch")
     p.add_argument("--basis", default="f32", choices=["f32", "f16"],
                    help="storage of the Krylov basis (arithmetic stays FP32, the true residual FP64)")
     # fixed-size runs for kernel profiling (ncu) and quick timing; no JSON line
@@ -672,7 +672,8 @@ def run_ours(args, rank, world):
                    "validation_problems": 2 * N_VAL_TRAJ * TRAJ_STEPS,
                    "l2": "no flush: the per-step working set (32 Krylov bases of 105 MB) exceeds the 129 MB L2",
                    "parallelism": f"replicas x{world}",
-                   "step_loop": "CUDA graph per restart cycle" if args.graphs == "on" else "host-launched"},
+                   "solve_loop": ("one CUDA graph launch per batched solve (restart cycles and Arnoldi steps "
+                                  "under device-side WHILE/IF nodes)") if args.graphs == "on" else "host-launched"},
         "cnn": {**summarize(flat, wl), "subspace": f"[PCA-{args.k} of the wavelength | CNN-{args.cnn_k}]",
                 "policy": rep_cnn, "pass": cnn_pass, "predict_ms_per_step": round(predict_ms, 2),
                 "train_s": round(cnn_s, 1), "loss": "Eq. 6 (residual)", "train_steps": args.cnn_steps,

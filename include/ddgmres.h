@@ -129,13 +129,18 @@ typedef enum {
                             Parallel Computing 112, 2022): 2 passes over the basis per step */
 } ddg_orthogonalization;
 ddg_status ddg_context_set_orthogonalization(ddg_context* ctx, int scheme);
-/* Step loop of the delayed scheme (no paper counterpart): with `enable` (the
-   default) every restart cycle's Arnoldi steps run as one CUDA graph launch,
-   a device-side WHILE loop over [8 x (reduction, sweep), step advance] that
-   ends when every solve has left its cycle or the restart length is reached;
-   otherwise the host launches every step and polls the device every 8 steps.
-   Both give the same results (same kernels, same order).  Per-kernel
-   profiling (ddg_context_profile_enable) uses the host-driven loop. */
+/* Solve loop of the delayed scheme (no paper counterpart): with `enable` (the
+   default) a batched solve's restart cycles, after its set-up, run as ONE
+   CUDA graph launch: a device-side WHILE over cycles (cycle-start residual,
+   then an IF for the cycle's Arnoldi steps -- the first step and a nested
+   WHILE over [8 x (reduction, sweep), step advance] that ends when every
+   solve has left its cycle or the restart length is reached -- and an IF for
+   the cycle end), which ends when every solve has converged or stopped, a
+   bounded wait gave up, or maxit + 2 cycles have run; the host reads the
+   results once.  Otherwise the host launches every kernel, reads the counts
+   at every cycle start and polls the device every 8 steps.  Both give the
+   same results (same kernels, same order).  Per-kernel profiling
+   (ddg_context_profile_enable) uses the host-driven loop. */
 ddg_status ddg_context_set_graphs(ddg_context* ctx, int enable);
 /* Storage of the Krylov basis [C | Q] in complex64 solves (no paper
    counterpart; compressed-basis GMRES, Aliaga et al., Int. J. High Perform.

@@ -206,7 +206,7 @@ class Context:
         _check(load().ddg_context_set_augmented_cycles(self._h, int(cycles)), "ddg_context_set_augmented_cycles")
 
     def set_graphs(self, on: bool):
-        """Run each restart cycle's Arnoldi steps as one CUDA graph launch (default) or host-driven."""
+        """Run a batched solve's restart cycles as one CUDA graph launch (default) or host-driven."""
         _check(load().ddg_context_set_graphs(self._h, int(bool(on))), "ddg_context_set_graphs")
 
     def set_basis_storage(self, storage: str):

@@ -111,7 +111,7 @@ extern "C" ddg_status ddg_context_create(ddg_context** out) {
     cudaGetDevice(&c->device);
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
     if (c->sm_count <= 0) c->sm_count = 152;
-    cudaError_t e = cudaMallocHost(&c->host_counts, 8 * sizeof(int));
+    cudaError_t e = cudaMallocHost(&c->host_counts, 16 * sizeof(int));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[1], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_bytes, DDG_K_NCLASSES * sizeof(unsigned long long));

@@ -77,7 +77,7 @@ struct Context {
     int device = 0;
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    int* host_counts = nullptr;      // pinned, polled between launches
+    int* host_counts = nullptr;      // pinned (16 ints), polled between launches
     double inner_tol = 1e-5;         // DDG_C64_REFINE inner-cycle relative tolerance
     int orth = 1;                    // 0: CGS2 (two passes per step), 1: delayed CGS2 (one reduction)
     double fallback = 0.5;           // augmented: V-only residual above this -> plain GMRES after the V step
@@ -202,7 +202,8 @@ struct BatchArgs {
     const int* blk_solve;
     int* counts;       // [0] solves inside an Arnoldi loop, [1] solves still active,
                        // [4] a bounded wait gave up (kept for the whole solve call),
-                       // [5] the graph-driven loop's step counter
+                       // [5] the graph-driven loop's step counter, [6..9] the graph's
+                       // cycles begun, step-loop bodies, Arnoldi cycles, finished cycles
     int m;             // restart length
     int KP;            // stride of coefficient vectors (>= Nmax + m + 2)
     int nmax;          // leading dimension of B (= kMaxAug)

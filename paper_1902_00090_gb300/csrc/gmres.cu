@@ -1713,14 +1713,51 @@ struct Carver {
     }
 };
 
-// Graph-driven step loop: advances the step by the body's `unroll` steps and
-// keeps the WHILE loop running while some solve is inside its Arnoldi cycle and
-// the restart length is not exhausted (k_dots2 at step m finishes the last
-// column; launches for steps past m return at once).
+// Graph-driven solve: every restart cycle of the batch runs inside one CUDA
+// graph launch, under device-side WHILE and IF nodes (no host round trip
+// between cycles or steps).  The graph's small kernels:
+//   k_cycle_begin  clears the per-cycle counts [0..3] (what the host loop's
+//                  memset does);
+//   k_cycle_gate   after the cycle-start residual: continue while some solve
+//                  is active and no bounded wait gave up, at most maxit + 2
+//                  cycles (the host loop's bound); run the Arnoldi steps only
+//                  when some solve is inside a cycle;
+//   k_inner_begin  step = 1 and the step loop's first condition;
+//   k_advance      advances the step by the body's `unroll` steps and keeps the
+//                  step loop running while some solve is inside its Arnoldi
+//                  cycle and the restart length is not exhausted (k_dots2 at
+//                  step m finishes the last column; launches for steps past m
+//                  return at once).
+// Counts [6..9] record cycles begun, step-loop bodies, cycles with Arnoldi
+// steps and cycles that ran to their end, for the launch accounting; every
+// loop is bounded by a counter, never by convergence alone.
 constexpr int kGraphUnroll = 8;
+constexpr int kCounts = 12;          // ints of BatchArgs::counts
+__global__ void k_cycle_begin(BatchArgs a) {
+    a.counts[0] = 0;
+    a.counts[1] = 0;
+    a.counts[2] = 0;
+    a.counts[3] = 0;
+}
+__global__ void k_cycle_gate(BatchArgs a, cudaGraphConditionalHandle outer, cudaGraphConditionalHandle arnoldi,
+                             cudaGraphConditionalHandle finish) {
+    const int c = a.counts[6]++;
+    const bool go = a.counts[1] != 0 && a.counts[4] == 0;
+    const bool ar = go && a.counts[0] > 0;
+    a.counts[8] += ar ? 1 : 0;
+    a.counts[9] += go ? 1 : 0;
+    cudaGraphSetConditional(arnoldi, ar ? 1u : 0u);
+    cudaGraphSetConditional(finish, go ? 1u : 0u);
+    cudaGraphSetConditional(outer, (go && c + 1 <= a.maxit + 1) ? 1u : 0u);
+}
+__global__ void k_inner_begin(BatchArgs a, cudaGraphConditionalHandle loop) {
+    *a.step = 1;
+    cudaGraphSetConditional(loop, (a.m >= 1 && a.counts[0] > 0) ? 1u : 0u);
+}
 __global__ void k_advance(BatchArgs a, cudaGraphConditionalHandle loop, int unroll) {
     const int s = *a.step + unroll;
     *a.step = s;
+    a.counts[7] += 1;
     cudaGraphSetConditional(loop, (s <= a.m && a.counts[0] > 0) ? 1u : 0u);
 }
 
@@ -1743,74 +1780,150 @@ static void launch_overlapped(void (*kern)(KArgs...), unsigned grid, size_t smem
     (void)cudaLaunchKernelEx(&cfg, kern, args...);   // a failure is left for cudaGetLastError
 }
 
-// One restart cycle's Arnoldi steps of the delayed scheme as a CUDA graph:
-//   step = 1;  while (cond) { for u < 8: k_dots2(step + u); k_update2(step + u);  k_advance }
-// The body's kernels read the step from device memory and add their offset;
-// k_advance sets the condition, so the cycle runs without host round trips.
-// Consecutive Arnoldi kernels keep their programmatic (overlapped) launch.
-template <typename T, bool HB>
-static ddg_status build_step_graph(const BatchArgs& args, unsigned G, int n, size_t dots2_smem,
-                                   size_t upd_smem, cudaGraphExec_t* out) {
+// During a stream capture: the graph being captured into.
+static cudaError_t capture_graph(cudaStream_t cs, cudaGraph_t* g) {
+    cudaStreamCaptureStatus status;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &status, nullptr, g, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess && status != cudaStreamCaptureStatusActive) e = cudaErrorStreamCaptureInvalidated;
+    return e;
+}
+
+// During a stream capture: appends a conditional node (IF or WHILE, one body
+// graph) with handle `h` after the capture's current dependencies; later
+// captured work depends on it.  `body` receives the node's body graph.
+static cudaError_t append_conditional(cudaStream_t cs, cudaGraphConditionalHandle h,
+                                      cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+    cudaStreamCaptureStatus status;
     cudaGraph_t g = nullptr;
-    cudaStream_t cs = nullptr;
-    cudaGraphExec_t ex = nullptr;
-    cudaGraphConditionalHandle h = 0;
-    cudaGraphNode_t init = nullptr, loop = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, &deps, &edges, &nd);
+    if (e != cudaSuccess) return e;
+    if (status != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
     cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, g, deps, edges, nd, &cp);
+    if (e != cudaSuccess) return e;
+    *body = cp.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// The delayed scheme's whole batched solve (after the set-up) as one graph:
+//   while (outer) {                                   // one restart cycle per body
+//     k_cycle_begin; k_residual; [k_dots_r; k_update_r]; k_cycle_gate
+//     if (arnoldi) { k_step(0); k_dots_w; k_update_w; k_inner_begin
+//                    while (loop) { for u < 8: k_dots2(step + u); k_update2(step + u);  k_advance } }
+//     if (finish)  { k_backsub; k_update_x }
+//   }
+// Bodies are captured on their own streams into the conditional nodes' body
+// graphs.  The step loop's kernels read the step from device memory and add
+// their offset; consecutive Arnoldi kernels keep their programmatic
+// (overlapped) launch.  Each handle is created on the graph that holds its
+// node and set by a kernel of that graph or of a graph nested in it.
+template <typename T, bool HB>
+static ddg_status build_solve_graph(const BatchArgs& args, unsigned G, int n, int Nreq, size_t dots2_smem,
+                                    size_t upd_smem, size_t bs_smem, size_t ux_smem, cudaGraphExec_t* out) {
+    constexpr cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    cudaGraph_t g = nullptr, cycle_body = nullptr, arn_body = nullptr, fin_body = nullptr, step_body = nullptr;
+    cudaStream_t cs[3] = {nullptr, nullptr, nullptr};
+    bool capturing[3] = {false, false, false};
+    cudaGraphExec_t ex = nullptr;
+    cudaGraphConditionalHandle h_outer = 0, h_arn = 0, h_fin = 0, h_loop = 0;
     const char* what = "cudaGraphCreate";
     cudaError_t e = cudaGraphCreate(&g, 0);
+    auto ok = [&](cudaError_t r, const char* w) {
+        if (e == cudaSuccess && r != cudaSuccess) {
+            e = r;
+            what = w;
+        }
+        return e == cudaSuccess;
+    };
+    auto begin = [&](int i, cudaGraph_t into, const char* w) {
+        if (e != cudaSuccess) return false;
+        capturing[i] = ok(cudaStreamBeginCaptureToGraph(cs[i], into, nullptr, nullptr, 0, mode), w);
+        return capturing[i];
+    };
+    auto end = [&](int i, const char* w) {
+        if (!capturing[i]) return;
+        cudaGraph_t body = nullptr;
+        const cudaError_t el = cudaGetLastError();   // launch errors of this capture
+        const cudaError_t ee = cudaStreamEndCapture(cs[i], &body);
+        capturing[i] = false;
+        ok(el, w);
+        ok(ee, w);
+    };
+    if (e == cudaSuccess) ok(cudaGraphConditionalHandleCreate(&h_outer, g, 1, cudaGraphCondAssignDefault),
+                             "cudaGraphConditionalHandleCreate");
     if (e == cudaSuccess) {
-        what = "cudaGraphConditionalHandleCreate";
-        e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
-    }
-    if (e == cudaSuccess) {
-        what = "cudaGraphAddMemsetNode";
-        cudaMemsetParams mp = {};
-        mp.dst = args.step;
-        mp.value = 1;
-        mp.elementSize = 4;
-        mp.width = 1;
-        mp.height = 1;
-        e = cudaGraphAddMemsetNode(&init, g, nullptr, 0, &mp);
-    }
-    if (e == cudaSuccess) {
-        what = "cudaGraphAddNode (WHILE)";
+        cudaGraphNodeParams cp = {};
         cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
+        cp.conditional.handle = h_outer;
         cp.conditional.type = cudaGraphCondTypeWhile;
         cp.conditional.size = 1;
-        e = cudaGraphAddNode(&loop, g, &init, nullptr, 1, &cp);
+        cudaGraphNode_t node = nullptr;
+        if (ok(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp), "cudaGraphAddNode (cycle loop)"))
+            cycle_body = cp.conditional.phGraph_out[0];
     }
-    if (e == cudaSuccess) {
-        what = "cudaStreamCreateWithFlags";
-        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    }
-    if (e == cudaSuccess) {
-        what = "cudaStreamBeginCaptureToGraph";
-        e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal);
-    }
-    if (e == cudaSuccess) {
-        for (int u = 0; u < kGraphUnroll; ++u) {
-            if (u == 0) k_dots2<T, HB><<<G, kBlock, dots2_smem, cs>>>(args, 0);
-            else launch_overlapped(k_dots2<T, HB>, G, dots2_smem, cs, args, -u);
-            launch_overlapped(k_update2<T, HB>, G + n, upd_smem, cs, args, -u);
+    for (int i = 0; i < 3; ++i)
+        if (e == cudaSuccess) ok(cudaStreamCreateWithFlags(&cs[i], cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+    // one restart cycle
+    if (begin(0, cycle_body, "capture of the cycle")) {
+        k_cycle_begin<<<1, 1, 0, cs[0]>>>(args);
+        k_residual<T><<<G, kBlock, 0, cs[0]>>>(args);
+        if (Nreq > 0) {
+            k_dots_r<T, HB><<<G, kBlock, 0, cs[0]>>>(args);
+            k_update_r<T, HB><<<G, kBlock, 0, cs[0]>>>(args);
         }
-        k_advance<<<1, 1, 0, cs>>>(args, h, kGraphUnroll);
-        const cudaError_t el = cudaGetLastError();
-        cudaGraph_t body = nullptr;
-        what = "step graph capture";
-        e = cudaStreamEndCapture(cs, &body);
-        if (e == cudaSuccess) e = el;
+        cudaGraph_t cg = nullptr;
+        if (ok(capture_graph(cs[0], &cg), "cudaStreamGetCaptureInfo") &&
+            ok(cudaGraphConditionalHandleCreate(&h_arn, cg, 0, 0), "cudaGraphConditionalHandleCreate") &&
+            ok(cudaGraphConditionalHandleCreate(&h_fin, cg, 0, 0), "cudaGraphConditionalHandleCreate")) {
+            k_cycle_gate<<<1, 1, 0, cs[0]>>>(args, h_outer, h_arn, h_fin);
+            if (ok(append_conditional(cs[0], h_arn, cudaGraphCondTypeIf, &arn_body), "Arnoldi IF node"))
+                ok(append_conditional(cs[0], h_fin, cudaGraphCondTypeIf, &fin_body), "cycle-end IF node");
+        }
     }
-    if (e == cudaSuccess) {
-        what = "cudaGraphInstantiate";
-        e = cudaGraphInstantiate(&ex, g, 0);
+    // the cycle's Arnoldi steps: the first step, then the step loop
+    if (begin(1, arn_body, "capture of the Arnoldi steps")) {
+        k_step<T, HB><<<G, kBlock, 0, cs[1]>>>(args, 0);
+        k_dots_w<T, HB><<<G, kBlock, 0, cs[1]>>>(args, 0, 0);
+        k_update_w<T, HB><<<G, kBlock, upd_smem, cs[1]>>>(args, 0, 0);
+        cudaGraph_t cg = nullptr;
+        if (ok(capture_graph(cs[1], &cg), "cudaStreamGetCaptureInfo") &&
+            ok(cudaGraphConditionalHandleCreate(&h_loop, cg, 0, 0), "cudaGraphConditionalHandleCreate")) {
+            k_inner_begin<<<1, 1, 0, cs[1]>>>(args, h_loop);
+            ok(append_conditional(cs[1], h_loop, cudaGraphCondTypeWhile, &step_body), "step WHILE node");
+        }
     }
-    if (cs) cudaStreamDestroy(cs);
+    if (begin(2, step_body, "capture of the step loop")) {
+        for (int u = 0; u < kGraphUnroll; ++u) {
+            if (u == 0) k_dots2<T, HB><<<G, kBlock, dots2_smem, cs[2]>>>(args, 0);
+            else launch_overlapped(k_dots2<T, HB>, G, dots2_smem, cs[2], args, -u);
+            launch_overlapped(k_update2<T, HB>, G + n, upd_smem, cs[2], args, -u);
+        }
+        k_advance<<<1, 1, 0, cs[2]>>>(args, h_loop, kGraphUnroll);
+    }
+    end(2, "capture of the step loop");
+    end(1, "capture of the Arnoldi steps");
+    // the cycle's end
+    if (begin(1, fin_body, "capture of the cycle end")) {
+        k_backsub<<<n, 128, bs_smem, cs[1]>>>(args);
+        k_update_x<T, HB><<<G, kBlock, ux_smem, cs[1]>>>(args);
+    }
+    end(1, "capture of the cycle end");
+    end(0, "capture of the cycle");
+    if (e == cudaSuccess) ok(cudaGraphInstantiate(&ex, g, 0), "cudaGraphInstantiate");
+    for (int i = 0; i < 3; ++i)
+        if (cs[i]) cudaStreamDestroy(cs[i]);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         if (ex) cudaGraphExecDestroy(ex);
+        cudaGetLastError();
         return cuda_status(e, what);
     }
     *out = ex;
@@ -1917,7 +2030,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     tail.take<SolvePtrs>(n);
     tail.take<SolveScal>(n);
     tail.take<int>(total_ctas);
-    tail.take<int>(8);
+    tail.take<int>(kCounts);
     DDG_TRY(ctx->reserve(tail.off + 4096, st));
     char* base = reinterpret_cast<char*>(ctx->ws);
     layout(base);
@@ -1927,7 +2040,7 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     args.S = t2.take<SolveScal>(n);
     int* d_blk = t2.take<int>(total_ctas);
     args.blk_solve = d_blk;
-    args.counts = t2.take<int>(8);
+    args.counts = t2.take<int>(kCounts);
     args.bytes = ctx->prof ? ctx->d_bytes : nullptr;
     args.m = m;
     args.KP = KP;
@@ -1964,23 +2077,34 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     int* hc = ctx->host_counts;
     const size_t bs_smem = sizeof(double2) * (3 * (size_t)m + kMaxAug);
     DDG_CHECK_CUDA(cudaFuncSetAttribute(k_backsub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs_smem));
-    DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 8 * sizeof(int), st));
-    // delayed scheme: each cycle's step loop as one graph launch (per-launch
+    DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, kCounts * sizeof(int), st));
+    // delayed scheme: every restart cycle inside one graph launch (per-launch
     // profiling needs the host-driven loop)
     const bool use_graph = ctx->orth == 1 && ctx->graphs && !ctx->prof;
     GraphExecGuard gexec;
-    bool graph_pending = false;   // a graph launch whose kernels are not yet counted
-    auto count_graph = [&]() {
-        if (!graph_pending) return;
-        // every execution of the WHILE body launches 2 * kGraphUnroll + 1 kernels
-        const long long bodies = std::max(0, hc[5] - 1) / kGraphUnroll;
-        ctx->launches += bodies * (2 * kGraphUnroll + 1);
-        ctx->nlaunch[DDG_K_DOTS] += bodies * kGraphUnroll;
-        ctx->nlaunch[DDG_K_UPDATE] += bodies * kGraphUnroll;
-        ctx->nlaunch[DDG_K_STEP] += bodies;
-        graph_pending = false;
-    };
-    for (long long cycle = 0; cycle <= (long long)maxit + 1; ++cycle) {
+    if (use_graph) {
+        DDG_TRY((build_solve_graph<T, HB>(args, G, n, Nreq, dots2_smem, upd_smem, bs_smem, ux_smem, &gexec.e)));
+        DDG_CHECK_CUDA(cudaGraphLaunch(gexec.e, st));
+        DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 4, args.counts + 4, 6 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DDG_CHECK_CUDA(cudaStreamSynchronize(st));
+        // launches of the graph: per cycle begun k_cycle_begin, k_residual,
+        // [k_dots_r, k_update_r], k_cycle_gate; per cycle with Arnoldi steps
+        // k_step, k_dots_w, k_update_w, k_inner_begin; per step-loop body
+        // 2 kGraphUnroll + 1; per finished cycle k_backsub, k_update_x
+        const long long cycles = hc[6], bodies = hc[7], arn = hc[8], fin = hc[9];
+        const long long res = 1 + (Nreq > 0 ? 2 : 0);
+        ctx->launches += cycles * (res + 2) + arn * 4 + bodies * (2 * kGraphUnroll + 1) + fin * 2;
+        ctx->nlaunch[DDG_K_RESIDUAL] += cycles * res;
+        ctx->nlaunch[DDG_K_STEP] += cycles * 2 + arn * 2 + bodies;
+        ctx->nlaunch[DDG_K_DOTS] += arn + bodies * kGraphUnroll;
+        ctx->nlaunch[DDG_K_UPDATE] += arn + bodies * kGraphUnroll;
+        ctx->nlaunch[DDG_K_CYCLE_END] += fin * 2;
+        if (hc[4]) {
+            set_error("gmres: a column copy into shared memory did not complete within its time limit");
+            return DDG_ETIMEOUT;
+        }
+    }
+    for (long long cycle = 0; !use_graph && cycle <= (long long)maxit + 1; ++cycle) {
         DDG_CHECK_CUDA(cudaMemsetAsync(args.counts, 0, 4 * sizeof(int), st));
         DDG_TRY(ctx->launch(DDG_K_RESIDUAL, st, [&] { k_residual<T><<<G, kBlock, 0, st>>>(args); }));
         if (Nreq > 0) {
@@ -1990,7 +2114,6 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
         DDG_CHECK_CUDA(cudaMemcpyAsync(hc, args.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 4, args.counts + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DDG_CHECK_CUDA(cudaStreamSynchronize(st));
-        count_graph();
         if (hc[4]) {
             set_error("gmres: a column copy into shared memory did not complete within its time limit");
             return DDG_ETIMEOUT;
@@ -2002,27 +2125,21 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
             DDG_TRY(ctx->launch(DDG_K_STEP, st, [&] { k_step<T, HB><<<G, kBlock, 0, st>>>(args, 0); }));
             DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { k_dots_w<T, HB><<<G, kBlock, 0, st>>>(args, 0, 0); }));
             DDG_TRY(ctx->launch(DDG_K_UPDATE, st, [&] { k_update_w<T, HB><<<G, kBlock, upd_smem, st>>>(args, 0, 0); }));
-            if (use_graph) {
-                if (!gexec.e) DDG_TRY((build_step_graph<T, HB>(args, G, n, dots2_smem, upd_smem, &gexec.e)));
-                DDG_CHECK_CUDA(cudaGraphLaunch(gexec.e, st));
-                graph_pending = true;
-            } else {
-                int polled = 0;
-                for (int i = 1; i <= m; ++i) {
-                    DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { launch_overlapped(k_dots2<T, HB>, G, dots2_smem, st, args, i); }));
-                    if (i < m)
-                        DDG_TRY(ctx->launch(DDG_K_UPDATE, st,
-                                            [&] { launch_overlapped(k_update2<T, HB>, G + n, upd_smem, st, args, i); }));
-                    if (i % ctx->poll_every == 0 && i < m) {
-                        const int slot = polled & 1;
-                        DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 2 + slot, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
-                        DDG_CHECK_CUDA(cudaEventRecord(ctx->ev[slot], st));
-                        if (polled > 0) {
-                            DDG_CHECK_CUDA(cudaEventSynchronize(ctx->ev[slot ^ 1]));
-                            if (hc[2 + (slot ^ 1)] == 0) break;
-                        }
-                        ++polled;
+            int polled = 0;
+            for (int i = 1; i <= m; ++i) {
+                DDG_TRY(ctx->launch(DDG_K_DOTS, st, [&] { launch_overlapped(k_dots2<T, HB>, G, dots2_smem, st, args, i); }));
+                if (i < m)
+                    DDG_TRY(ctx->launch(DDG_K_UPDATE, st,
+                                        [&] { launch_overlapped(k_update2<T, HB>, G + n, upd_smem, st, args, i); }));
+                if (i % ctx->poll_every == 0 && i < m) {
+                    const int slot = polled & 1;
+                    DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 2 + slot, args.counts, sizeof(int), cudaMemcpyDeviceToHost, st));
+                    DDG_CHECK_CUDA(cudaEventRecord(ctx->ev[slot], st));
+                    if (polled > 0) {
+                        DDG_CHECK_CUDA(cudaEventSynchronize(ctx->ev[slot ^ 1]));
+                        if (hc[2 + (slot ^ 1)] == 0) break;
                     }
+                    ++polled;
                 }
             }
         } else if (hc[0] > 0) {
@@ -2053,7 +2170,6 @@ static ddg_status run_batch(Context* ctx, int n, const ddg_op* const* A, const d
     DDG_CHECK_CUDA(cudaMemcpyAsync(hs.data(), args.S, sizeof(SolveScal) * n, cudaMemcpyDeviceToHost, st));
     DDG_CHECK_CUDA(cudaMemcpyAsync(hc + 4, args.counts + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     DDG_CHECK_CUDA(cudaStreamSynchronize(st));
-    count_graph();
     ctx->resolve();
     if (hc[4]) {
         set_error("gmres: a column copy into shared memory did not complete within its time limit");

@@ -441,10 +441,12 @@ def test_first_cycle_augmented_then_plain(prec):
 
 @pytest.mark.parametrize("prec", ["c64", "c128"])
 def test_graph_step_loop_matches_host_loop(prec):
-    # The graph-driven cycle (device-side WHILE over the same kernels) and the
-    # host-driven one launch the same kernels in the same order: equal fields
+    # The graph-driven solve (every restart cycle inside one graph launch,
+    # device-side WHILE and IF nodes over the same kernels) and the
+    # host-driven loop launch the same kernels in the same order: equal fields
     # bit for bit, equal step and cycle counts, including cycles that end
-    # mid-way (restart 30, several cycles; solves stopping at different steps).
+    # mid-way (restart 30, several cycles; solves stopping at different steps)
+    # and solves stopped by the iteration cap.
     g = inputs.grid_for(64, 64)
     eps = inputs.trajectory_set(g, 2, 3, steps=3)
     ops = [ddg.fdfd_operator(g, dev(e, torch.float64)) for e in eps]
@@ -457,9 +459,11 @@ def test_graph_step_loop_matches_host_loop(prec):
         xs, infos, st = ddg.gmres_solve_batched(c, ops, bs, tol=1e-6, restart=30, maxit=4000, precision=prec)
         xa, infa, sta = ddg.augmented_gmres_solve_batched(c, ops, bs, [U] * len(ops), tol=1e-6, restart=30,
                                                           maxit=4000, precision=prec)
-        assert st == 0 and sta == 0
-        out[graphs] = (np.stack([host(x) for x in xs + xa]),
-                       [(i["iters"], i["cycles"], i["converged"]) for i in infos + infa])
+        # the iteration cap inside a cycle (the graph's loops end on their counters)
+        xc, infc, stc = ddg.gmres_solve_batched(c, ops, bs, tol=1e-6, restart=30, maxit=45, precision=prec)
+        assert st == 0 and sta == 0 and stc == 4
+        out[graphs] = (np.stack([host(x) for x in xs + xa + xc]),
+                       [(i["iters"], i["cycles"], i["converged"]) for i in infos + infa + infc])
     assert out[True][1] == out[False][1]
     assert np.array_equal(out[True][0], out[False][0])
 
