@@ -694,7 +694,8 @@ def run_ours(args, rank, world):
         "levers": levers,
         "roofline": roof, "e2e": e2e, "gpu_launches": int(head["launches"]), "clocks": head["clocks"],
     }
-    line["_oracle_sample"] = oracle_sample_spec(P, U_base, test_eps, grids, flat, wl, head["infos"])
+    line["_oracle_sample"] = oracle_sample_spec(P, U_base, test_eps, grids, flat, wl, head["infos"],
+                                                U_pca=U_pca, policy=pol_cnn)
     return line
 
 
@@ -1001,36 +1002,47 @@ def run_batched(args, rank, world):
 
 
 # ------------------------------------------------------------------ oracle (CPU)
-def oracle_sample_spec(P, U_base, test_eps, grids, flat, wl, step_infos):
+def oracle_sample_spec(P, U_base, test_eps, grids, flat, wl, step_infos, U_pca=None, policy=None):
     """What the CPU baseline needs from the GPU run: the trained weights, the
-    output offset of 1550 nm, and the GPU's restart cycles for the sampled
-    problem (the first held-out permittivity at 1550 nm) to scale the sample."""
+    output offset of 1550 nm, the headline's PCA rows and restart policy at
+    1550 nm, and the GPU's restart cycles for the sampled problem (the first
+    held-out permittivity at 1550 nm) to scale the sample."""
     lam = WAVELENGTHS[1]
     t0, inf0 = step_infos[0]
     j = len(test_eps[0])          # first 1550 nm solve of the step (the 1300 nm ones come first)
-    return {"theta": P.get_params(), "channels": P.channels, "k": P.k,
+    spec = {"theta": P.get_params(), "channels": P.channels, "k": P.k,
             "base": U_base[lam][: P.k].cpu().numpy(), "eps": test_eps[t0][0], "grid": grids[1],
             "gpu_cycles": int(inf0[j]["cycles"]), "gpu_iters": int(inf0[j]["iters"])}
+    if U_pca is not None:
+        spec["pca"] = U_pca[lam].cpu().numpy()             # (k_pca, D)
+    if policy is not None:
+        spec["policy"] = tuple(int(v) for v in policy[lam])
+    return spec
 
 
 def oracle_cnn_subspace(spec):
-    """The CNN variant's subspace for the sampled problem, computed by the
-    oracle: its fp64 forward pass of the trained weights plus the offset."""
+    """The headline variant's subspace for the sampled problem, computed by the
+    oracle: [PCA-20 rows | its fp64 forward pass of the trained weights plus
+    the offset] (the CNN part alone without PCA rows in the spec)."""
     from oracle import cnn as ocnn
     g = spec["grid"]
     cfg = ocnn.CNNConfig(cin=4, channels=tuple(spec["channels"]), k=spec["k"])
     x = ocnn.input_channels(spec["eps"], g.wavelength, g.npml, g.i_src, g.sigma_src, g.j_src)[None]
     y = ocnn.forward(cfg, spec["theta"].astype(np.float64), x)
     V = ocnn.to_complex_fields(y)[0]                       # (D, k)
-    return V + np.sqrt(g.D) * spec["base"].T
+    V = V + np.sqrt(g.D) * spec["base"].T
+    if "pca" in spec:
+        V = np.concatenate([spec["pca"].T, V], axis=1)
+    return V
 
 
 def cpu_baseline(args, spec, cycles=2):
     """The oracle (numpy/scipy complex128, every host core) on a bounded sample:
-    the first `cycles` restart cycles of one held-out CNN-augmented solve
-    (1550 nm, V kept in every cycle, the oracle's own CNN forward pass of the
-    trained weights), scaled to a whole solve by the restart cycles the GPU
-    needed for that problem."""
+    the first `cycles` restart cycles of one held-out solve of the headline
+    variant (1550 nm: the subspace [PCA-20 | CNN-8] from the oracle's own CNN
+    forward pass of the trained weights, the headline's restart policy at that
+    wavelength), scaled to a whole solve by the restart cycles the GPU needed
+    for that problem."""
     from oracle import fdfd, gmres
     g = spec["grid"]
     A = fdfd.operator_for(g, spec["eps"])
@@ -1038,14 +1050,18 @@ def cpu_baseline(args, spec, cycles=2):
     t0 = time.time()
     V = oracle_cnn_subspace(spec)
     t_pred = time.time() - t0
+    cyc, keep = spec.get("policy", (10**6, V.shape[1]))
     t0 = time.time()
-    x, info = gmres.augmented_gmres(A, b, V, tol=1e-6, restart=args.restart, maxit=cycles * args.restart)
+    x, info = gmres.augmented_gmres(A, b, V, tol=1e-6, restart=args.restart, maxit=cycles * args.restart,
+                                    aug_cycles=cyc, aug_keep=keep)
     t_solve = time.time() - t0
     per_cycle = t_solve / max(1, info.cycles)
     sec_per_solve = t_pred + per_cycle * spec["gpu_cycles"]
+    sub = f"[PCA-{spec['pca'].shape[0]} | CNN-{spec['k']}]" if "pca" in spec else f"CNN-{spec['k']}"
     return {"value": round(1.0 / sec_per_solve, 6), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"1 held-out 256x256 solve at 1550 nm, CNN-augmented GMRES({args.restart}) with the trained "
-                      f"network's fp64 forward pass ({t_pred:.1f} s) and {info.cycles} restart cycles "
+            "sample": f"1 held-out 256x256 solve at 1550 nm, augmented GMRES({args.restart}) with the headline's "
+                      f"subspace {sub} (the trained network's fp64 forward pass, {t_pred:.1f} s) and restart "
+                      f"policy (all columns for {cyc} cycle(s), then {keep} kept), {info.cycles} restart cycles "
                       f"({info.iters} Arnoldi steps, {t_solve:.1f} s, complex128 numpy/scipy), scaled to the "
                       f"{spec['gpu_cycles']} cycles ({spec['gpu_iters']} steps) the GPU solve needed; BLAS threads "
                       f"= os.cpu_count() = {os.cpu_count()}",
