@@ -98,6 +98,8 @@ def parse():
     p.add_argument("--orth", default=None, choices=[None, "cgs2", "dcgs2"])
     p.add_argument("--profile", action="store_true", help="--case solver: per-kernel-class time and GB/s")
     p.add_argument("--tensor-cores", default="on", choices=["on", "off"])
+    p.add_argument("--tma", default="on", choices=["on", "off"],
+                   help="--case cnn|cnn-train: plain-input forward convolutions from TMA tiles")
     return p.parse_args()
 
 
@@ -214,7 +216,7 @@ def case_cnn_train(a):
     P.init_he(seed=0)
     P.set_loss("residual")
     on = a.tensor_cores == "on"
-    P.set_tensor_cores(on, backward=on)
+    P.set_tensor_cores(on, backward=on, tma=a.tma == "on")
     src = (g.i_src, g.sigma_src, g.j_src)
     for r in range(a.repeat):
         torch.cuda.synchronize()
@@ -235,7 +237,7 @@ def case_cnn(a):
     ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device="cuda")) for e in eps]
     P = ddg.Predictor(k=a.cnn_k)
     P.init_he(seed=0)
-    P.set_tensor_cores(a.tensor_cores == "on")
+    P.set_tensor_cores(a.tensor_cores == "on", tma=a.tma == "on")
     src = (g.i_src, g.sigma_src, g.j_src)
     U = [torch.empty((a.cnn_k, g.D), dtype=torch.complex128, device="cuda") for _ in ops]
     for r in range(a.repeat):

@@ -442,8 +442,14 @@ long long predictor_launches(const ddg_predictor* P);
    others, the head and the bias gradients use CUDA cores.  The forward paths
    give the same results up to FP32 summation order; with bit 2 the masked
    output gradient enters both backward products rounded to BF16 (the
-   CUDA-core path keeps it in FP32).  A tensor-core wait that gives up makes
-   the call return DDG_ETIMEOUT.  0 <= enable <= 3, else DDG_EINVAL. */
+   CUDA-core path keeps it in FP32).  Bit 4 (with bit 1; the default is
+   1 | 4): a forward convolution whose input is one plain tensor (not the
+   decoder's upsampled concatenation), on a grid that is a multiple of 16 x 8
+   pixels and whose weights and two 18 x 10 halo tiles fit in shared memory,
+   loads its input tiles by TMA (cp.async.bulk.tensor) and reads the nine taps
+   as descriptor offsets into the loaded tile, with no gather on the SM; same
+   K order and results as the gather.  A tensor-core wait that gives up makes
+   the call return DDG_ETIMEOUT.  0 <= enable <= 7, else DDG_EINVAL. */
 ddg_status predictor_set_tensor_cores(ddg_predictor* P, int enable);
 /* theta: host, n = predictor_num_params floats.  Setting resets the Adam state. */
 ddg_status predictor_set_params(ddg_predictor* P, const float* theta, long long n);

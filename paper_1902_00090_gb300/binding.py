@@ -699,10 +699,12 @@ class Predictor:
         """Kernels launched by this predictor (predictor_launches)."""
         return int(load().predictor_launches(self._h))
 
-    def set_tensor_cores(self, on: bool, backward: bool = False):
+    def set_tensor_cores(self, on: bool, backward: bool = False, tma: bool = True):
         """Forward 3x3 convolutions on tcgen05 tensor cores (default) or CUDA
-        cores; with backward, the backward-data convolutions too."""
-        _check(load().predictor_set_tensor_cores(self._h, (1 if on else 0) | (2 if backward else 0)),
+        cores; with backward, the backward-data convolutions too; with tma (and
+        on), forward ones with a plain input read their tiles by TMA."""
+        _check(load().predictor_set_tensor_cores(
+            self._h, (1 if on else 0) | (2 if backward else 0) | (4 if (tma and on) else 0)),
                "predictor_set_tensor_cores")
 
     def set_params(self, theta):

@@ -15,7 +15,9 @@
 // The forward 3x3 convolutions whose channel counts are multiples of 16 run on
 // the 5th-generation tensor cores (tcgen05, accumulators in tensor memory);
 // the first layer, the 1x1 head and the backward pass run on CUDA cores.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -399,6 +401,208 @@ __global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(G ld, int B, int H, i
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
     }
+}
+
+// ---------------------------------------------------------------- 3x3 convolution from TMA tiles
+// The forward convolutions whose input is one plain NHWC tensor (no
+// upsampled concatenation) as an implicit GEMM without any gather: one output
+// tile of 16 rows x 8 columns = 128 pixels (M = 128) x all Co channels.  Its
+// 18 x 10 halo tile is loaded by TMA (cp.async.bulk.tensor, 4D tensor map
+// over (C, W, H, B), one copy per 8-channel chunk, zeros outside the image =
+// the convolution's padding) into the layout [Ci/8][18][10][8 channels].  In
+// that layout every tap (dy, dx) of the A operand is the same tile seen from
+// another start address: a K-major operand without swizzle whose 8-row core
+// matrices are 8 consecutive pixels of one tile row (16 bytes apart), whose
+// 8-row groups (the tile's rows) are 10 pixels = 160 bytes apart (SBO) and
+// whose 8-channel K groups are one chunk apart (LBO).  So the MMAs read the
+// 9 taps straight from the loaded tile: 9 x Ci/16 tcgen05.mma of K = 16 per
+// tile.  The weights (B, K-major [9 Ci/8][Co][8], k = tap Ci + ci) are loaded
+// once per CTA by a bulk copy and stay in shared memory; each CTA walks the
+// tiles blockIdx.x, + gridDim.x, ... with two input buffers and two tensor-
+// memory accumulators, so the TMA load of tile t + 2 runs while tile t's
+// accumulator is read out (tcgen05.ld, bias, ReLU, BF16 NHWC stores).
+namespace tmc {
+constexpr int TH = 16, TW = 8;                  // output tile: rows x columns (M = 128)
+constexpr int HH = TH + 2, HWD = TW + 2;        // halo tile
+constexpr uint32_t kChunkBytes = HH * HWD * 16; // one 8-channel chunk of a halo tile (2880)
+constexpr uint32_t kChunkStride = 2944;         // chunks 128-byte aligned (TMA destinations)
+constexpr int kBufs = 2;
+constexpr int kThreads = 256;
+static_assert(TH * TW == tc::kM && kChunkStride >= kChunkBytes && kChunkStride % 128 == 0, "tile geometry");
+__host__ __device__ constexpr uint32_t wbytes(int ci, int co) { return 9u * (uint32_t)ci * (uint32_t)co * 2u; }
+__host__ __device__ constexpr uint32_t bufbytes(int ci) { return (uint32_t)(ci / 8) * kChunkStride; }
+__host__ __device__ constexpr size_t smem_bytes(int ci, int co) {
+    return (size_t)wbytes(ci, co) + (size_t)kBufs * bufbytes(ci) + 128;   // + the base's round-up to 128
+}
+// Shared-memory descriptor of a K-major operand without swizzle: start
+// address, leading byte offset (between 8-element K groups), stride byte
+// offset (between 8-row groups), descriptor version 1, layout type 0.
+__device__ __forceinline__ uint64_t desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+// TMA load of one box of a 4D tensor map into shared memory, completing on bar.
+__device__ __forceinline__ void load4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                       unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+}  // namespace tmc
+
+__global__ void __launch_bounds__(tmc::kThreads, 4) k_conv3_tma(const __grid_constant__ CUtensorMap tin, int B, int H,
+                                                             int W, int Ci, int Co, const bf16* __restrict__ wt,
+                                                             const float* __restrict__ bias, int relu,
+                                                             bf16* __restrict__ out, int* __restrict__ err) {
+    using namespace tmc;
+    extern __shared__ __align__(128) unsigned char smraw_tm[];
+    __shared__ __align__(8) unsigned long long wbar, full[kBufs], mdone[kBufs];
+    __shared__ uint32_t s_tmem;
+    unsigned char* sm = smraw_tm + ((128u - (smem_u32(smraw_tm) & 127u)) & 127u);
+    unsigned char* wsm = sm;                        // weights [9 Ci/8][Co][8]
+    unsigned char* ism = sm + wbytes(Ci, Co);       // kBufs halo tiles [Ci/8][18][10][8]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = W / TW, nty = H / TH;
+    const long long ntiles = (long long)B * nty * ntx;
+    const int nmine = ntiles > (long long)blockIdx.x ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    const uint32_t acc_cols = tc::tmem_cols(Co);
+    const uint32_t ncols = 2 * acc_cols;
+    const int nchunk = Ci / 8;
+    auto tile_of = [&](int it, int& b, int& y0, int& x0) {
+        const long long t = (long long)blockIdx.x + (long long)it * gridDim.x;
+        x0 = (int)(t % ntx) * TW;
+        const long long r = t / ntx;
+        y0 = (int)(r % nty) * TH;
+        b = (int)(r / nty);
+    };
+    auto load_tile = [&](int it) {   // thread 0: tile `it` into buffer it % kBufs
+        int b, y0, x0;
+        tile_of(it, b, y0, x0);
+        const int s = it % kBufs;
+        unsigned char* dst = ism + s * bufbytes(Ci);
+        mbar_expect_tx(&full[s], (unsigned)nchunk * kChunkBytes);
+        for (int q = 0; q < nchunk; ++q) load4d(dst + q * kChunkStride, &tin, 8 * q, x0 - 1, y0 - 1, b, &full[s]);
+    };
+    if (tid == 0) {
+        mbar_init(&wbar, 1);
+        for (int q = 0; q < kBufs; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&mdone[q], 1);
+        }
+        mbar_init_fence();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+    int issued = 0;       // tiles whose loads thread 0 requested
+    int committed = 0;    // tiles whose MMAs thread 0 committed
+    bool ok = true;
+    const uint32_t id = tc::idesc(Co);
+    // thread 0: waits for tile t's input (and the weights) and issues its
+    // 9 x Ci/16 MMAs into accumulator t % 2, committed to mdone[t % 2]
+    auto mma_tile = [&](int t) {
+        const int s = t % kBufs;
+        if (!((t > 0 || mbar_wait(&wbar, 0u)) && mbar_wait(&full[s], (unsigned)(t / kBufs) & 1u))) {
+            ok = false;
+            return;
+        }
+        tc::fence_after();
+        const uint32_t in0 = smem_u32(ism + s * bufbytes(Ci)), w0 = smem_u32(wsm);
+        const uint32_t d = tmem + (uint32_t)s * acc_cols;
+        int n = 0;
+        for (int tap = 0; tap < 9; ++tap) {
+            const uint32_t aoff = (uint32_t)((tap / 3) * HWD + tap % 3) * 16u;
+            for (int q = 0; q < Ci / 16; ++q, ++n) {
+                const uint64_t ad = desc(in0 + 2u * (uint32_t)q * kChunkStride + aoff, kChunkStride, HWD * 16u);
+                const uint64_t bd = desc(w0 + (uint32_t)(tap * nchunk + 2 * q) * (uint32_t)Co * 16u,
+                                         (uint32_t)Co * 16u, 128u);
+                tc::mma(d, ad, bd, id, n > 0 ? 1u : 0u);
+            }
+        }
+        tc::commit(&mdone[s]);
+        committed = t + 1;
+    };
+    if (tid == 0 && nmine > 0) {
+        mbar_expect_tx(&wbar, wbytes(Ci, Co));
+        bulk_g2s(wsm, wt, wbytes(Ci, Co), &wbar);
+        for (; issued < min(kBufs, nmine); ++issued) load_tile(issued);
+        mma_tile(0);
+    }
+    const int quarter = warp & 3, chalf = (warp >> 2) * (Co / 2);
+    const int r = quarter * 32 + lane;              // accumulator row = pixel (r / 8, r % 8) of the tile
+    for (int it = 0; it < nmine; ++it) {
+        const int s = it % kBufs;
+        if (__syncthreads_or(!ok)) break;
+        // tile it's MMAs are complete: its accumulator is ready and its input buffer free
+        if (!mbar_wait(&mdone[s], (unsigned)(it / kBufs) & 1u)) ok = false;
+        if (__syncthreads_or(!ok)) break;
+        if (tid == 0) {
+            if (issued < nmine) load_tile(issued++);      // tile it + 2 into the freed buffer
+            if (it + 1 < nmine) mma_tile(it + 1);         // runs on the tensor core during this epilogue
+        }
+        tc::fence_after();
+        int b, y0, x0;
+        tile_of(it, b, y0, x0);
+        bf16* o = out + (((long long)b * H + y0 + (r >> 3)) * W + x0 + (r & 7)) * Co;
+        for (int c0 = chalf; c0 < chalf + Co / 2; c0 += 8) {
+            uint32_t rr[8];
+            tc::ld8(tmem + (uint32_t)s * acc_cols + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, rr);
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                v[j] = __uint_as_float(rr[j]) + (bias ? bias[c0 + j] : 0.f);
+                if (relu) v[j] = fmaxf(v[j], 0.f);
+            }
+            uint4 ov;
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4], v[5]), h3 = __floats2bfloat162_rn(v[6], v[7]);
+            ov.x = *reinterpret_cast<uint32_t*>(&h0);
+            ov.y = *reinterpret_cast<uint32_t*>(&h1);
+            ov.z = *reinterpret_cast<uint32_t*>(&h2);
+            ov.w = *reinterpret_cast<uint32_t*>(&h3);
+            *reinterpret_cast<uint4*>(o + c0) = ov;
+        }
+        // every thread's reads of this accumulator precede the MMAs that
+        // overwrite it (tile it + 2, issued in the next iteration)
+        tc::fence_before();
+    }
+    const bool bad = __syncthreads_or(!ok);   // the loop's exits are block-uniform; ok is per thread
+    if (bad && tid == 0) {
+        // a wait gave up: report it, and let every copy and MMA this CTA
+        // started finish (one more wait each at the default bound) before the
+        // tensor memory is freed and the CTA leaves
+        atomicExch(err, 1);
+        if (issued > 0) mbar_wait(&wbar, 0u);
+        for (int t = max(0, issued - kBufs); t < issued; ++t) mbar_wait(&full[t % kBufs], (unsigned)(t / kBufs) & 1u);
+        if (committed > 0) mbar_wait(&mdone[(committed - 1) % kBufs], (unsigned)((committed - 1) / kBufs) & 1u);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+// TMA-tile weights BF16 [co][ci][9] -> [9 Ci/8][co][8] (k = tap Ci + ci: K group
+// kc = tap Ci/8 + ci/8, then the output channel, then ci % 8)
+__global__ void k_w_tma(const bf16* __restrict__ w, int Co, int Ci, bf16* __restrict__ wt) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)Co * Ci * 9) return;
+    const int co = (int)(idx / (Ci * 9)), ci = (int)((idx / 9) % Ci), tap = (int)(idx % 9);
+    wt[(((long long)(tap * (Ci / 8) + ci / 8) * Co + co) << 3) + (ci & 7)] = w[idx];
 }
 
 // ---------------------------------------------------------------- weight gradient on tensor cores
@@ -1285,8 +1489,9 @@ struct ddg_predictor {
     double2* orth_ws = nullptr;   // K13: Gram partial sums, factors, dropped counts
     size_t orth_bytes = 0;
     int* d_err = nullptr;         // a bounded wait in a tensor-core convolution gave up
-    int tensor_cores = 1;         // bit 0: forward 3x3 convolutions on tcgen05 where the channels allow;
-                                  // bit 1: the backward convolutions (data and weight gradients) too
+    int tensor_cores = 5;         // bit 0: forward 3x3 convolutions on tcgen05 where the channels allow;
+                                  // bit 1: the backward convolutions (data and weight gradients) too;
+                                  // bit 2: forward ones with a plain input from TMA tiles (k_conv3_tma)
     int sm_count = 152;
     void* d_desc = nullptr;       // InputDesc / pointer arrays (device)
     size_t desc_bytes = 0;
@@ -1388,11 +1593,80 @@ static ddg_status conv3(ddg_predictor* P, const LD& ld, int B, int H, int W, int
     return DDG_OK;
 }
 
-// Forward 3x3 convolution of layer li: tensor cores when the channel counts
-// allow 16-byte gathers and N = Co (multiples of 16, Co <= 256), else CUDA cores.
+// cuTensorMapEncodeTiled from the driver (looked up once; null if unavailable).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// The TMA-tile forward convolution (k_conv3_tma) when its conditions hold: a
+// plain input tensor (no upsampled concatenation), Ci and Co multiples of 16
+// (Co <= 256), the grid a multiple of the 16 x 8 tile, the weights and two
+// halo tiles within shared memory, and a tensor map the driver accepts.
+// Returns false (nothing launched) otherwise.
+static bool conv_fwd_tma(ddg_predictor* P, const LoadCat& ld, int B, int H, int W, int li, bf16* out,
+                         cudaStream_t st, ddg_status* status) {
+    const Layer& Ly = P->layers[li];
+    const int Ci = Ly.ci, Co = Ly.co;
+    const size_t smem = tmc::smem_bytes(Ci, Co);
+    if ((P->tensor_cores & 5) != 5 || ld.up1 || ld.c2 != 0 || !ld.x1 || ld.c1 != Ci || Ci % 16 != 0 ||
+        Co % 16 != 0 || Co > 256 || H % tmc::TH != 0 || W % tmc::TW != 0 ||
+        (reinterpret_cast<uintptr_t>(ld.x1) & 15) != 0 || smem > 227 * 1024)
+        return false;
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    CUtensorMap map;
+    const cuuint64_t dims[4] = {(cuuint64_t)Ci, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {(cuuint64_t)Ci * 2, (cuuint64_t)W * Ci * 2, (cuuint64_t)H * W * Ci * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)tmc::HWD, (cuuint32_t)tmc::HH, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(ld.x1), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    *status = DDG_OK;
+    auto fail = [&](cudaError_t e, const char* what) {
+        *status = cuda_status(e, what);
+        return true;
+    };
+    cudaError_t e = cudaFuncSetAttribute(k_conv3_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv3_tma, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return fail(e, "cudaFuncSetAttribute(k_conv3_tma)");
+    // CTAs per SM: registers (<= 64 a thread: 4 CTAs of 256 threads), shared
+    // memory (228 KB an SM, 1 KB of it reserved per CTA) and the 512
+    // tensor-memory columns (two accumulators per CTA)
+    int nb = std::min(4, (int)((228 * 1024) / (smem + 1024)));
+    nb = std::max(1, std::min(nb, (int)(512 / (2 * tc::tmem_cols(Co)))));
+    const long long ntiles = (long long)B * (H / tmc::TH) * (W / tmc::TW);
+    const unsigned grid = (unsigned)std::min<long long>(ntiles, (long long)P->sm_count * nb);
+    P->launches += 2;
+    k_w_tma<<<nblk((long long)Co * Ci * 9), 256, 0, st>>>(wbf(P, li), Co, Ci, P->wk);
+    k_conv3_tma<<<grid, tmc::kThreads, smem, st>>>(map, B, H, W, Ci, Co, P->wk, bias32(P, li), 1, out, P->d_err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(e, "k_conv3_tma");
+    return true;
+}
+
+// Forward 3x3 convolution of layer li: from TMA tiles when k_conv3_tma's
+// conditions hold; else tensor cores with the gather when the channel counts
+// allow 16-byte gathers and N = Co (multiples of 16, Co <= 256); else CUDA cores.
 static ddg_status conv_fwd(ddg_predictor* P, const LoadCat& ld, int B, int H, int W, int li, bf16* out,
                            cudaStream_t st) {
     const Layer& Ly = P->layers[li];
+    ddg_status tst = DDG_OK;
+    if (conv_fwd_tma(P, ld, B, H, W, li, out, st, &tst)) return tst;
     const bool tcok = (P->tensor_cores & 1) && Ly.ci % 16 == 0 && Ly.co % 16 == 0 && Ly.co <= 256 &&
                       ld.c1 % 8 == 0 && ld.c2 % 8 == 0;
     ++P->launches;
@@ -1855,7 +2129,7 @@ extern "C" long long predictor_launches(const ddg_predictor* P) { return P ? P->
 
 extern "C" ddg_status predictor_set_tensor_cores(ddg_predictor* P, int enable) {
     if (!P) { set_error("predictor_set_tensor_cores: NULL predictor"); return DDG_EINVAL; }
-    if (enable < 0 || enable > 3) { set_error("predictor_set_tensor_cores: enable must be 0..3"); return DDG_EINVAL; }
+    if (enable < 0 || enable > 7) { set_error("predictor_set_tensor_cores: enable must be 0..7"); return DDG_EINVAL; }
     P->tensor_cores = enable;
     return DDG_OK;
 }

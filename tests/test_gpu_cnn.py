@@ -303,6 +303,27 @@ def test_tensor_core_forward_equals_cuda_core_forward():
     assert rel(y_tc, y_cc) <= 1e-2
 
 
+def test_tma_tile_forward_equals_gather_forward():
+    # the full-size network at 128x128: the plain-input layers of levels 0-3
+    # (Ci, Co of 32, 48, 64, 96) load their tiles by TMA and read the taps by
+    # descriptor offsets; the others keep the gather.  Same K order as the
+    # gather path, so the same FP32 accumulation up to the tensor core's own
+    # order; checked against the gather-only forward, twice for determinism.
+    g = inputs.grid_128()
+    eps = inputs.trajectory_set(g, 2, 1, steps=5)
+    ops = [ddg.fdfd_operator(g, torch.as_tensor(e, device="cuda")) for e in eps]
+    P = ddg.Predictor(k=8)
+    P.init_he(seed=4)
+    src = (g.i_src, g.sigma_src, g.j_src)
+    y_tma = P.forward(ops, src).cpu().numpy()
+    y_tma2 = P.forward(ops, src).cpu().numpy()
+    P.set_tensor_cores(True, tma=False)
+    y_g = P.forward(ops, src).cpu().numpy()
+    assert np.array_equal(y_tma, y_tma2)
+    print(f"TMA-tile forward vs gather: bitwise equal {np.array_equal(y_tma, y_g)}, rel {rel(y_tma, y_g):.2e}")
+    assert rel(y_tma, y_g) <= 1e-6
+
+
 def test_input_field_network_matches_oracle():
     # a network with the approximate-field input (6 channels): forward against
     # the bfloat16-emulated oracle given the same field; without the field set,
