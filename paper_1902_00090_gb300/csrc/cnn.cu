@@ -418,16 +418,27 @@ __global__ void __launch_bounds__(tc::kThreads) k_conv3_tc(G ld, int B, int H, i
 // 9 taps straight from the loaded tile: 9 x Ci/16 tcgen05.mma of K = 16 per
 // tile.  The weights (B, K-major [9 Ci/8][Co][8], k = tap Ci + ci) are loaded
 // once per CTA by a bulk copy and stay in shared memory; each CTA walks the
-// tiles blockIdx.x, + gridDim.x, ... with two input buffers and two tensor-
-// memory accumulators, so the TMA load of tile t + 2 runs while tile t's
-// accumulator is read out (tcgen05.ld, bias, ReLU, BF16 NHWC stores).
+// tiles blockIdx.x, + gridDim.x, ...
+//
+// Warp roles (no block-wide barrier between tiles): warp 0's lane 0 requests
+// the tiles and issues the MMAs (two input buffers, two tensor-memory
+// accumulators); warps 1-4 (tensor-memory lane quarters 1, 2, 3, 0) read an
+// accumulator out (tcgen05.ld, bias, ReLU, BF16 NHWC stores) and release it.
+//   full[s]    input buffer s loaded (TMA transaction count)
+//   mdone[s]   the MMAs of the tile in buffer / accumulator s complete
+//              (tcgen05.commit): accumulator ready, input buffer free
+//   accfree[s] the 4 epilogue warps have read accumulator s out
+// Every wait is bounded; one that gives up raises the error flag and the
+// abort word, and the CTA waits (at the default bound) for its own copies and
+// MMAs before it frees the tensor memory.
 namespace tmc {
 constexpr int TH = 16, TW = 8;                  // output tile: rows x columns (M = 128)
 constexpr int HH = TH + 2, HWD = TW + 2;        // halo tile
 constexpr uint32_t kChunkBytes = HH * HWD * 16; // one 8-channel chunk of a halo tile (2880)
 constexpr uint32_t kChunkStride = 2944;         // chunks 128-byte aligned (TMA destinations)
-constexpr int kBufs = 2;
-constexpr int kThreads = 256;
+constexpr int kBufs = 2;                        // input buffers = accumulators
+constexpr int kEpiWarps = 4;
+constexpr int kThreads = 32 * (1 + kEpiWarps);
 static_assert(TH * TW == tc::kM && kChunkStride >= kChunkBytes && kChunkStride % 128 == 0, "tile geometry");
 __host__ __device__ constexpr uint32_t wbytes(int ci, int co) { return 9u * (uint32_t)ci * (uint32_t)co * 2u; }
 __host__ __device__ constexpr uint32_t bufbytes(int ci) { return (uint32_t)(ci / 8) * kChunkStride; }
@@ -453,16 +464,31 @@ __device__ __forceinline__ void load4d(void* dst, const CUtensorMap* map, int c0
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
         : "memory");
 }
+__device__ __forceinline__ void arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// 16 consecutive accumulator columns of this warp's 32 lanes (one wait for both halves)
+__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 }  // namespace tmc
 
-__global__ void __launch_bounds__(tmc::kThreads, 4) k_conv3_tma(const __grid_constant__ CUtensorMap tin, int B, int H,
+__global__ void __launch_bounds__(tmc::kThreads) k_conv3_tma(const __grid_constant__ CUtensorMap tin, int B, int H,
                                                              int W, int Ci, int Co, const bf16* __restrict__ wt,
                                                              const float* __restrict__ bias, int relu,
                                                              bf16* __restrict__ out, int* __restrict__ err) {
     using namespace tmc;
     extern __shared__ __align__(128) unsigned char smraw_tm[];
-    __shared__ __align__(8) unsigned long long wbar, full[kBufs], mdone[kBufs];
+    __shared__ __align__(8) unsigned long long wbar, full[kBufs], mdone[kBufs], accfree[kBufs];
     __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
     unsigned char* sm = smraw_tm + ((128u - (smem_u32(smraw_tm) & 127u)) & 127u);
     unsigned char* wsm = sm;                        // weights [9 Ci/8][Co][8]
     unsigned char* ism = sm + wbytes(Ci, Co);       // kBufs halo tiles [Ci/8][18][10][8]
@@ -471,7 +497,7 @@ __global__ void __launch_bounds__(tmc::kThreads, 4) k_conv3_tma(const __grid_con
     const long long ntiles = (long long)B * nty * ntx;
     const int nmine = ntiles > (long long)blockIdx.x ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
     const uint32_t acc_cols = tc::tmem_cols(Co);
-    const uint32_t ncols = 2 * acc_cols;
+    const uint32_t ncols = kBufs * acc_cols;
     const int nchunk = Ci / 8;
     auto tile_of = [&](int it, int& b, int& y0, int& x0) {
         const long long t = (long long)blockIdx.x + (long long)it * gridDim.x;
@@ -480,21 +506,15 @@ __global__ void __launch_bounds__(tmc::kThreads, 4) k_conv3_tma(const __grid_con
         y0 = (int)(r % nty) * TH;
         b = (int)(r / nty);
     };
-    auto load_tile = [&](int it) {   // thread 0: tile `it` into buffer it % kBufs
-        int b, y0, x0;
-        tile_of(it, b, y0, x0);
-        const int s = it % kBufs;
-        unsigned char* dst = ism + s * bufbytes(Ci);
-        mbar_expect_tx(&full[s], (unsigned)nchunk * kChunkBytes);
-        for (int q = 0; q < nchunk; ++q) load4d(dst + q * kChunkStride, &tin, 8 * q, x0 - 1, y0 - 1, b, &full[s]);
-    };
     if (tid == 0) {
         mbar_init(&wbar, 1);
         for (int q = 0; q < kBufs; ++q) {
             mbar_init(&full[q], 1);
             mbar_init(&mdone[q], 1);
+            mbar_init(&accfree[q], kEpiWarps);
         }
         mbar_init_fence();
+        s_abort = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -506,87 +526,103 @@ __global__ void __launch_bounds__(tmc::kThreads, 4) k_conv3_tma(const __grid_con
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = s_tmem;
-    int issued = 0;       // tiles whose loads thread 0 requested
-    int committed = 0;    // tiles whose MMAs thread 0 committed
-    bool ok = true;
-    const uint32_t id = tc::idesc(Co);
-    // thread 0: waits for tile t's input (and the weights) and issues its
-    // 9 x Ci/16 MMAs into accumulator t % 2, committed to mdone[t % 2]
-    auto mma_tile = [&](int t) {
-        const int s = t % kBufs;
-        if (!((t > 0 || mbar_wait(&wbar, 0u)) && mbar_wait(&full[s], (unsigned)(t / kBufs) & 1u))) {
-            ok = false;
-            return;
-        }
-        tc::fence_after();
-        const uint32_t in0 = smem_u32(ism + s * bufbytes(Ci)), w0 = smem_u32(wsm);
-        const uint32_t d = tmem + (uint32_t)s * acc_cols;
-        int n = 0;
-        for (int tap = 0; tap < 9; ++tap) {
-            const uint32_t aoff = (uint32_t)((tap / 3) * HWD + tap % 3) * 16u;
-            for (int q = 0; q < Ci / 16; ++q, ++n) {
-                const uint64_t ad = desc(in0 + 2u * (uint32_t)q * kChunkStride + aoff, kChunkStride, HWD * 16u);
-                const uint64_t bd = desc(w0 + (uint32_t)(tap * nchunk + 2 * q) * (uint32_t)Co * 16u,
-                                         (uint32_t)Co * 16u, 128u);
-                tc::mma(d, ad, bd, id, n > 0 ? 1u : 0u);
-            }
-        }
-        tc::commit(&mdone[s]);
-        committed = t + 1;
+    auto give_up = [&]() {
+        atomicExch(err, 1);
+        s_abort = 1;
     };
     if (tid == 0 && nmine > 0) {
+        // producer: tiles into the input buffers, MMAs into the accumulators
+        auto load_tile = [&](int t) {
+            int b, y0, x0;
+            tile_of(t, b, y0, x0);
+            const int s = t % kBufs;
+            unsigned char* dst = ism + s * bufbytes(Ci);
+            mbar_expect_tx(&full[s], (unsigned)nchunk * kChunkBytes);
+            for (int q = 0; q < nchunk; ++q) load4d(dst + q * kChunkStride, &tin, 8 * q, x0 - 1, y0 - 1, b, &full[s]);
+        };
         mbar_expect_tx(&wbar, wbytes(Ci, Co));
         bulk_g2s(wsm, wt, wbytes(Ci, Co), &wbar);
+        int issued = 0, committed = 0;
         for (; issued < min(kBufs, nmine); ++issued) load_tile(issued);
-        mma_tile(0);
-    }
-    const int quarter = warp & 3, chalf = (warp >> 2) * (Co / 2);
-    const int r = quarter * 32 + lane;              // accumulator row = pixel (r / 8, r % 8) of the tile
-    for (int it = 0; it < nmine; ++it) {
-        const int s = it % kBufs;
-        if (__syncthreads_or(!ok)) break;
-        // tile it's MMAs are complete: its accumulator is ready and its input buffer free
-        if (!mbar_wait(&mdone[s], (unsigned)(it / kBufs) & 1u)) ok = false;
-        if (__syncthreads_or(!ok)) break;
-        if (tid == 0) {
-            if (issued < nmine) load_tile(issued++);      // tile it + 2 into the freed buffer
-            if (it + 1 < nmine) mma_tile(it + 1);         // runs on the tensor core during this epilogue
-        }
-        tc::fence_after();
-        int b, y0, x0;
-        tile_of(it, b, y0, x0);
-        bf16* o = out + (((long long)b * H + y0 + (r >> 3)) * W + x0 + (r & 7)) * Co;
-        for (int c0 = chalf; c0 < chalf + Co / 2; c0 += 8) {
-            uint32_t rr[8];
-            tc::ld8(tmem + (uint32_t)s * acc_cols + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, rr);
-            float v[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                v[j] = __uint_as_float(rr[j]) + (bias ? bias[c0 + j] : 0.f);
-                if (relu) v[j] = fmaxf(v[j], 0.f);
+        const uint32_t id = tc::idesc(Co);
+        bool ok = mbar_wait(&wbar, 0u);
+        for (int t = 0; ok && t < nmine && !s_abort; ++t) {
+            const int s = t % kBufs;
+            const unsigned par = (unsigned)(t / kBufs) & 1u;
+            // tile t loaded, and accumulator s read out (tile t - 2)
+            if (!mbar_wait(&full[s], par) || (t >= kBufs && !mbar_wait(&accfree[s], par ^ 1u))) {
+                ok = false;
+                break;
             }
-            uint4 ov;
-            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4], v[5]), h3 = __floats2bfloat162_rn(v[6], v[7]);
-            ov.x = *reinterpret_cast<uint32_t*>(&h0);
-            ov.y = *reinterpret_cast<uint32_t*>(&h1);
-            ov.z = *reinterpret_cast<uint32_t*>(&h2);
-            ov.w = *reinterpret_cast<uint32_t*>(&h3);
-            *reinterpret_cast<uint4*>(o + c0) = ov;
+            tc::fence_after();
+            const uint32_t in0 = smem_u32(ism + s * bufbytes(Ci)), w0 = smem_u32(wsm);
+            const uint32_t d = tmem + (uint32_t)s * acc_cols;
+            int n = 0;
+            for (int tap = 0; tap < 9; ++tap) {
+                const uint32_t aoff = (uint32_t)((tap / 3) * HWD + tap % 3) * 16u;
+                for (int q = 0; q < Ci / 16; ++q, ++n) {
+                    const uint64_t ad = desc(in0 + 2u * (uint32_t)q * kChunkStride + aoff, kChunkStride, HWD * 16u);
+                    const uint64_t bd = desc(w0 + (uint32_t)(tap * nchunk + 2 * q) * (uint32_t)Co * 16u,
+                                             (uint32_t)Co * 16u, 128u);
+                    tc::mma(d, ad, bd, id, n > 0 ? 1u : 0u);
+                }
+            }
+            tc::commit(&mdone[s]);
+            committed = t + 1;
+            // tile t + 2 into buffer s once tile t's MMAs have read it
+            if (issued < nmine) {
+                if (!mbar_wait(&mdone[s], par)) {
+                    ok = false;
+                    break;
+                }
+                load_tile(issued++);
+            }
         }
-        // every thread's reads of this accumulator precede the MMAs that
-        // overwrite it (tile it + 2, issued in the next iteration)
-        tc::fence_before();
-    }
-    const bool bad = __syncthreads_or(!ok);   // the loop's exits are block-uniform; ok is per thread
-    if (bad && tid == 0) {
-        // a wait gave up: report it, and let every copy and MMA this CTA
-        // started finish (one more wait each at the default bound) before the
-        // tensor memory is freed and the CTA leaves
-        atomicExch(err, 1);
-        if (issued > 0) mbar_wait(&wbar, 0u);
-        for (int t = max(0, issued - kBufs); t < issued; ++t) mbar_wait(&full[t % kBufs], (unsigned)(t / kBufs) & 1u);
-        if (committed > 0) mbar_wait(&mdone[(committed - 1) % kBufs], (unsigned)((committed - 1) / kBufs) & 1u);
+        if (!ok) {
+            // let every copy and MMA this CTA started finish before leaving
+            give_up();
+            mbar_wait(&wbar, 0u);
+            for (int t = max(0, issued - kBufs); t < issued; ++t)
+                mbar_wait(&full[t % kBufs], (unsigned)(t / kBufs) & 1u);
+            if (committed > 0) mbar_wait(&mdone[(committed - 1) % kBufs], (unsigned)((committed - 1) / kBufs) & 1u);
+        }
+    } else if (warp >= 1) {
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
+        const int quarter = warp & 3;
+        const int r = quarter * 32 + lane;          // accumulator row = pixel (r / 8, r % 8) of the tile
+        for (int t = 0; t < nmine && !s_abort; ++t) {
+            const int s = t % kBufs;
+            if (!mbar_wait(&mdone[s], (unsigned)(t / kBufs) & 1u)) {
+                give_up();
+                break;
+            }
+            tc::fence_after();
+            int b, y0, x0;
+            tile_of(t, b, y0, x0);
+            bf16* o = out + (((long long)b * H + y0 + (r >> 3)) * W + x0 + (r & 7)) * Co;
+            for (int c0 = 0; c0 < Co; c0 += 16) {
+                uint32_t rr[16];
+                ld16(tmem + (uint32_t)s * acc_cols + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, rr);
+                uint32_t pk[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float v0 = __uint_as_float(rr[2 * j]) + (bias ? bias[c0 + 2 * j] : 0.f);
+                    float v1 = __uint_as_float(rr[2 * j + 1]) + (bias ? bias[c0 + 2 * j + 1] : 0.f);
+                    if (relu) {
+                        v0 = fmaxf(v0, 0.f);
+                        v1 = fmaxf(v1, 0.f);
+                    }
+                    __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                    pk[j] = *reinterpret_cast<uint32_t*>(&h);
+                }
+                *reinterpret_cast<uint4*>(o + c0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4*>(o + c0 + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+            // this warp's reads of accumulator s are complete: release it
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) arrive(&accfree[s]);
+        }
     }
     tc::fence_before();
     __syncthreads();
@@ -1644,10 +1680,9 @@ static bool conv_fwd_tma(ddg_predictor* P, const LoadCat& ld, int B, int H, int 
         e = cudaFuncSetAttribute(k_conv3_tma, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return fail(e, "cudaFuncSetAttribute(k_conv3_tma)");
-    // CTAs per SM: registers (<= 64 a thread: 4 CTAs of 256 threads), shared
-    // memory (228 KB an SM, 1 KB of it reserved per CTA) and the 512
-    // tensor-memory columns (two accumulators per CTA)
-    int nb = std::min(4, (int)((228 * 1024) / (smem + 1024)));
+    // CTAs per SM: shared memory (228 KB an SM, 1 KB of it reserved per CTA),
+    // at most 8, and the 512 tensor-memory columns (two accumulators per CTA)
+    int nb = std::min(8, (int)((228 * 1024) / (smem + 1024)));
     nb = std::max(1, std::min(nb, (int)(512 / (2 * tc::tmem_cols(Co)))));
     const long long ntiles = (long long)B * (H / tmc::TH) * (W / tmc::TW);
     const unsigned grid = (unsigned)std::min<long long>(ntiles, (long long)P->sm_count * nb);
