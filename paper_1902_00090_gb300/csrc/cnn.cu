@@ -632,13 +632,15 @@ __global__ void __launch_bounds__(tmc::kThreads) k_conv3_tma(const __grid_consta
     }
 }
 
-// TMA-tile weights BF16 [co][ci][9] -> [9 Ci/8][co][8] (k = tap Ci + ci: K group
-// kc = tap Ci/8 + ci/8, then the output channel, then ci % 8)
-__global__ void k_w_tma(const bf16* __restrict__ w, int Co, int Ci, bf16* __restrict__ wt) {
+// TMA-tile weights BF16 [co][ci][9] (ci < Ci) -> [9 Cp/8][co][8] (k = tap Cp + ci:
+// K group kc = tap Cp/8 + ci/8, then the output channel, then ci % 8), the
+// input channels padded with zero weights to Cp >= Ci
+__global__ void k_w_tma(const bf16* __restrict__ w, int Co, int Ci, int Cp, bf16* __restrict__ wt) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)Co * Ci * 9) return;
-    const int co = (int)(idx / (Ci * 9)), ci = (int)((idx / 9) % Ci), tap = (int)(idx % 9);
-    wt[(((long long)(tap * (Ci / 8) + ci / 8) * Co + co) << 3) + (ci & 7)] = w[idx];
+    if (idx >= (long long)Co * Cp * 9) return;
+    const int co = (int)(idx / (Cp * 9)), ci = (int)((idx / 9) % Cp), tap = (int)(idx % 9);
+    wt[(((long long)(tap * (Cp / 8) + ci / 8) * Co + co) << 3) + (ci & 7)] =
+        ci < Ci ? w[((long long)co * Ci + ci) * 9 + tap] : __float2bfloat16_rn(0.f);
 }
 
 // ---------------------------------------------------------------- weight gradient on tensor cores
@@ -861,11 +863,12 @@ __global__ void k_w_tc_bwd(const bf16* __restrict__ w, int Co, int Ci, bf16* __r
 }
 
 // tensor-core weights BF16 [co][ci][9] -> [co][9][ci] (K-major rows, k = tap * Ci + ci)
-__global__ void k_w_tc(const bf16* __restrict__ w, int Co, int Ci, bf16* __restrict__ wt) {
+// (input channels padded with zero weights to Cp >= Ci: k = tap * Cp + ci)
+__global__ void k_w_tc(const bf16* __restrict__ w, int Co, int Ci, int Cp, bf16* __restrict__ wt) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)Co * Ci * 9) return;
-    const int co = (int)(idx / (Ci * 9)), ci = (int)((idx / 9) % Ci), tap = (int)(idx % 9);
-    wt[((long long)co * 9 + tap) * Ci + ci] = w[idx];
+    if (idx >= (long long)Co * Cp * 9) return;
+    const int co = (int)(idx / (Cp * 9)), ci = (int)((idx / 9) % Cp), tap = (int)(idx % 9);
+    wt[((long long)co * 9 + tap) * Cp + ci] = ci < Ci ? w[((long long)co * Ci + ci) * 9 + tap] : __float2bfloat16_rn(0.f);
 }
 
 // Weight gradient of a 3x3 convolution: dW[co][ci][tap] += sum_p g[p, co] in[p + tap, ci],
@@ -1058,8 +1061,9 @@ struct InputDesc {
     int nx, ny, npml;
     double wavelength;
 };
+constexpr int kInPad = 16;   // channels of the padded input copy
 __global__ void k_input(const InputDesc* __restrict__ desc, int B, int H, int W, int i_src, double sigma, double j_c,
-                        const float2* __restrict__ field, int cin, bf16* __restrict__ x) {
+                        const float2* __restrict__ field, int cin, bf16* __restrict__ x, bf16* __restrict__ xp) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)B * H * W) return;
     const int b = (int)(idx / ((long long)H * W));
@@ -1079,6 +1083,13 @@ __global__ void k_input(const InputDesc* __restrict__ desc, int B, int H, int W,
         o[4] = __float2bfloat16_rn(field[e].x);
         o[5] = __float2bfloat16_rn(field[e].y);
     }
+    // the same channels, zero-padded to kInPad, as two 16-byte stores
+    __align__(16) bf16 pad[kInPad];
+#pragma unroll
+    for (int c = 0; c < kInPad; ++c) pad[c] = c < cin ? o[c] : __float2bfloat16_rn(0.f);
+    uint4* q = reinterpret_cast<uint4*>(xp + idx * kInPad);
+    q[0] = reinterpret_cast<const uint4*>(pad)[0];
+    q[1] = reinterpret_cast<const uint4*>(pad)[1];
 }
 
 // max |f| over D values (one block), then f / max |f| in FP32
@@ -1547,6 +1558,7 @@ static int layer_index(const ddg_predictor* P, bool dec, int level, int ab) {
 struct Acts {
     // device pointers for one batch size / grid
     bf16* x0;
+    bf16* x0p;     // the input with its channels zero-padded to 16 (TMA-tile first layer)
     bf16* ea[kMaxLevels];
     bf16* eb[kMaxLevels];
     bf16* pooled[kMaxLevels];
@@ -1575,6 +1587,7 @@ static size_t plan_acts(const ddg_predictor* P, int B, int H, int W, char* base,
     const int L = P->levels;
     size_t maxg = 0;
     A->x0 = (bf16*)take(sizeof(bf16) * (size_t)B * H * W * P->cin);
+    A->x0p = (bf16*)take(sizeof(bf16) * (size_t)B * H * W * kInPad);
     for (int l = 0; l < L; ++l) {
         const size_t px = (size_t)B * (H >> l) * (W >> l);
         if (l > 0) A->pooled[l] = (bf16*)take(sizeof(bf16) * px * P->ch[l - 1]);
@@ -1649,11 +1662,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // plain input tensor (no upsampled concatenation), Ci and Co multiples of 16
 // (Co <= 256), the grid a multiple of the 16 x 8 tile, the weights and two
 // halo tiles within shared memory, and a tensor map the driver accepts.
-// Returns false (nothing launched) otherwise.
+// ci_pad > 0: the input tensor holds ci_pad >= Ly.ci channels, the ones past
+// Ly.ci zero (the first layer's padded input), and the weights are padded to
+// match.  Returns false (nothing launched) otherwise.
 static bool conv_fwd_tma(ddg_predictor* P, const LoadCat& ld, int B, int H, int W, int li, bf16* out,
-                         cudaStream_t st, ddg_status* status) {
+                         cudaStream_t st, ddg_status* status, int ci_pad = 0) {
     const Layer& Ly = P->layers[li];
-    const int Ci = Ly.ci, Co = Ly.co;
+    const int Ci = ci_pad > 0 ? ci_pad : Ly.ci, Co = Ly.co;
+    if (Ci < Ly.ci) return false;
     const size_t smem = tmc::smem_bytes(Ci, Co);
     if ((P->tensor_cores & 5) != 5 || ld.up1 || ld.c2 != 0 || !ld.x1 || ld.c1 != Ci || Ci % 16 != 0 ||
         Co % 16 != 0 || Co > 256 || H % tmc::TH != 0 || W % tmc::TW != 0 ||
@@ -1687,7 +1703,7 @@ static bool conv_fwd_tma(ddg_predictor* P, const LoadCat& ld, int B, int H, int 
     const long long ntiles = (long long)B * (H / tmc::TH) * (W / tmc::TW);
     const unsigned grid = (unsigned)std::min<long long>(ntiles, (long long)P->sm_count * nb);
     P->launches += 2;
-    k_w_tma<<<nblk((long long)Co * Ci * 9), 256, 0, st>>>(wbf(P, li), Co, Ci, P->wk);
+    k_w_tma<<<nblk((long long)Co * Ci * 9), 256, 0, st>>>(wbf(P, li), Co, Ly.ci, Ci, P->wk);
     k_conv3_tma<<<grid, tmc::kThreads, smem, st>>>(map, B, H, W, Ci, Co, P->wk, bias32(P, li), 1, out, P->d_err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(e, "k_conv3_tma");
@@ -1697,26 +1713,33 @@ static bool conv_fwd_tma(ddg_predictor* P, const LoadCat& ld, int B, int H, int 
 // Forward 3x3 convolution of layer li: from TMA tiles when k_conv3_tma's
 // conditions hold; else tensor cores with the gather when the channel counts
 // allow 16-byte gathers and N = Co (multiples of 16, Co <= 256); else CUDA cores.
+// ci_pad > 0: the input holds ci_pad >= Ly.ci channels, the extra ones zero
+// (tensor-core paths only; the weights are padded with zeros to match).
 static ddg_status conv_fwd(ddg_predictor* P, const LoadCat& ld, int B, int H, int W, int li, bf16* out,
-                           cudaStream_t st) {
+                           cudaStream_t st, int ci_pad = 0) {
     const Layer& Ly = P->layers[li];
     ddg_status tst = DDG_OK;
-    if (conv_fwd_tma(P, ld, B, H, W, li, out, st, &tst)) return tst;
-    const bool tcok = (P->tensor_cores & 1) && Ly.ci % 16 == 0 && Ly.co % 16 == 0 && Ly.co <= 256 &&
+    if (conv_fwd_tma(P, ld, B, H, W, li, out, st, &tst, ci_pad)) return tst;
+    const int Ci = ci_pad > 0 ? ci_pad : Ly.ci;
+    const bool tcok = (P->tensor_cores & 1) && Ci % 16 == 0 && Ly.co % 16 == 0 && Ly.co <= 256 &&
                       ld.c1 % 8 == 0 && ld.c2 % 8 == 0;
     ++P->launches;
     if (!tcok) {
+        if (ci_pad > 0) {
+            set_error("predictor: a padded input needs the tensor-core path");
+            return DDG_EINVAL;
+        }
         k_w_fwd<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
         return conv3(P, ld, B, H, W, Ly.ci, Ly.co, P->wk, bias32(P, li), 1, out, st);
     }
-    k_w_tc<<<nblk((long long)Ly.co * Ly.ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, P->wk);
+    k_w_tc<<<nblk((long long)Ly.co * Ci * 9), 256, 0, st>>>(wbf(P, li), Ly.co, Ly.ci, Ci, P->wk);
     const size_t smem = tc::smem_bytes(Ly.co);
     DDG_CHECK_CUDA(cudaFuncSetAttribute(k_conv3_tc<LoadCat, bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
     const long long npx = (long long)B * H * W;
     ++P->launches;
     k_conv3_tc<LoadCat, bf16><<<(unsigned)((npx + tc::kM - 1) / tc::kM), tc::kThreads, smem, st>>>(
-        ld, B, H, W, Ly.ci, Ly.co, P->wk, bias32(P, li), 1, out, P->d_err);
+        ld, B, H, W, Ci, Ly.co, P->wk, bias32(P, li), 1, out, P->d_err);
     DDG_CHECK_LAUNCH("k_conv3_tc");
     return DDG_OK;
 }
@@ -1750,6 +1773,14 @@ static ddg_status forward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaSt
         for (int ab = 0; ab < 2; ++ab) {
             const int li = layer_index(P, false, l, ab);
             const Layer& Ly = P->layers[li];
+            if (l == 0 && ab == 0 && Ly.ci <= kInPad && (P->tensor_cores & 1) && Ly.co % 16 == 0 &&
+                Ly.co <= 256) {
+                // the first layer on the tensor cores, from the input copy
+                // zero-padded to 16 channels (zero weights for the padding)
+                LoadCat ldp{A->x0p, kInPad, 0, Hl, Wl, nullptr, 0};
+                DDG_TRY(conv_fwd(P, ldp, B, Hl, Wl, li, A->ea[0], st, kInPad));
+                continue;
+            }
             LoadCat ld{ab == 0 ? in : A->ea[l], Ly.ci, 0, Hl, Wl, nullptr, 0};
             DDG_TRY(conv_fwd(P, ld, B, Hl, Wl, li, ab == 0 ? A->ea[l] : A->eb[l], st));
         }
@@ -1982,7 +2013,7 @@ static ddg_status build_input(ddg_predictor* P, int n, const ddg_op* const* A, i
     const int H = A[0]->ny, W = A[0]->nx;
     ++P->launches;
     k_input<<<nblk((long long)n * H * W), 256, 0, st>>>(reinterpret_cast<InputDesc*>(P->d_desc), n, H, W, i_src,
-                                                       sigma, j_c, P->in_field, P->cin, acts->x0);
+                                                       sigma, j_c, P->in_field, P->cin, acts->x0, acts->x0p);
     DDG_CHECK_LAUNCH("k_input");
     return DDG_OK;
 }
@@ -2046,7 +2077,7 @@ static ddg_status create_predictor(int k, int levels, const int* channels, int c
         Layer Ly{co, ci, kk, off, off + (long long)co * ci * kk * kk};
         off = Ly.b_off + co;
         P->layers.push_back(Ly);
-        maxw = std::max(maxw, (size_t)co * ci * kk * kk);
+        maxw = std::max(maxw, (size_t)co * std::max(ci, kk == 3 ? kInPad : 0) * kk * kk);   // padded inputs too
     };
     for (int l = 0; l < levels; ++l) {
         add(P->ch[l], l == 0 ? P->cin : P->ch[l - 1], 3);
