@@ -438,8 +438,10 @@ long long predictor_launches(const ddg_predictor* P);
    w.r.t. its weights (a GEMM over the pixels: output channels x (tap, input
    channel)).  Layers whose channel counts are multiples of 16 (at most 256
    outputs forward and backward-data, at most 128 for the weight gradient)
-   run on tcgen05 (BF16 operands, FP32 accumulation in tensor memory); the
-   others, the head and the bias gradients use CUDA cores.  The forward paths
+   run on tcgen05 (BF16 operands, FP32 accumulation in tensor memory), and so
+   does the first layer's forward (at most 16 input channels, read from a copy
+   of the input zero-padded to 16 channels, with zero weights for the
+   padding); the others, the head and the bias gradients use CUDA cores.  The forward paths
    give the same results up to FP32 summation order; with bit 2 the masked
    output gradient enters both backward products rounded to BF16 (the
    CUDA-core path keeps it in FP32).  Bit 4 (with bit 1; the default is
