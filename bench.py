@@ -437,6 +437,15 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     cnn_s = time.time() - t0
     train_losses = P.train_losses
+    # levers (--levers): a k = 16 network (its offset: the 16 leading PCs of
+    # each wavelength) and the k = 8 network trained on a quarter of the
+    # training problems, with the same steps, batch and learning rate
+    P16 = Pq = None
+    if args.levers:
+        n_all = sum(len(v) for v in train_ops.values())
+        P16 = train_cnn(ddg, args, grids, train_ops, b_of, U_pca, src, D, k=16)
+        Pq = train_cnn(ddg, args, grids, train_ops, b_of, U_base, src, D, n_problems=n_all // 4)
+        Pq.n_problems = n_all // 4
     del train_ops
 
     n_step = len(test_ops[0])
@@ -619,6 +628,45 @@ def run_ours(args, rank, world):
                 set_policy({lam: cand for lam in WAVELENGTHS})
                 levers[f"{name}_cycles{min(cand[0], 99)}_keep{cand[1]}"] = one_pass(
                     lambda t, solve=solve: solve(test_ops[t], test_b[t]))[0]
+        # k = 16: the CNN's 16 vectors alone, and [PCA-16 | CNN-16]
+        U16 = [torch.empty((16, D), dtype=torch.complex128, device=dev) for _ in range(n_step)]
+        U_comb16 = [torch.empty((32, D), dtype=torch.complex128, device=dev) for _ in range(n_step)]
+        for u, lam in zip(U_comb16, step_lams):
+            u[:16].copy_(U_pca[lam][:16])
+
+        def solve_cnn16(ops, bs):
+            for x in xs:
+                x.zero_()
+            P16.predict(ops, src, U=U16)
+            return ddg.augmented_gmres_solve_batched(ctx, ops, bs, U16, x=xs, **kw)
+
+        def solve_pca16_cnn16(ops, bs):
+            for x in xs:
+                x.zero_()
+            P16.predict(ops, src, U=[u[16:] for u in U_comb16])
+            return ddg.augmented_gmres_solve_batched(ctx, ops, bs, U_comb16, x=xs, **kw)
+
+        for name, solve, cands in (("cnn16", solve_cnn16, [(1, 0), (every, 16)]),
+                                   ("pca16_plus_cnn16", solve_pca16_cnn16, [(1, 0), (1, 16)])):
+            for cand in cands:
+                set_policy({lam: cand for lam in WAVELENGTHS})
+                levers[f"{name}_cycles{min(cand[0], 99)}_keep{cand[1]}"] = one_pass(
+                    lambda t, solve=solve: solve(test_ops[t], test_b[t]))[0]
+
+        # training-set size: the headline's subspace and policy with the k = 8
+        # network trained on a quarter of the problems
+        def solve_cnn_quarter(ops, bs):
+            for x in xs:
+                x.zero_()
+            Pq.predict(ops, src, U=U_cnn_rows)
+            return ddg.augmented_gmres_solve_batched(ctx, ops, bs, U_comb, x=xs, **kw)
+
+        set_policy(pol_cnn)
+        levers[f"pca20_plus_cnn8_trained_on_{Pq.n_problems}"] = one_pass(
+            lambda t: solve_cnn_quarter(test_ops[t], test_b[t]))[0]
+        levers["train_loss_last"] = {"cnn8": round(float(np.mean(train_losses[-20:])), 5),
+                                     "cnn16": round(float(np.mean(P16.train_losses[-20:])), 5),
+                                     f"cnn8_{Pq.n_problems}": round(float(np.mean(Pq.train_losses[-20:])), 5)}
         set_policy(pol_cnn)
 
     # --- e2e: host permittivities in, host fields out, through fdfd_solve_host
