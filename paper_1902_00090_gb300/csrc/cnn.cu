@@ -826,6 +826,63 @@ __global__ void __launch_bounds__(tc::kThreads) k_wgrad_tc(LX lx, const float* _
 }
 
 // db[co] += sum over pixels of g'[p][co] (FP32), one block per pixel slice
+// Co % 4 == 0: each thread one group of 4 channels (16-byte gradient and
+// 8-byte output loads), 4 pixels in flight per thread, one atomic per channel
+// and block.
+__global__ void __launch_bounds__(256) k_bias_grad4(const float* __restrict__ g, const bf16* __restrict__ yout,
+                                                    long long P, int Co, long long pix_per_block,
+                                                    float* __restrict__ db) {
+    __shared__ float4 acc4[256];
+    const int t = threadIdx.x;
+    const int cg = Co >> 2, lanes = 256 / cg, c4 = t % cg;
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto add = [&](float4 gv, uint2 yv) {
+        const __nv_bfloat162 y01 = *reinterpret_cast<const __nv_bfloat162*>(&yv.x);
+        const __nv_bfloat162 y23 = *reinterpret_cast<const __nv_bfloat162*>(&yv.y);
+        sum.x += __bfloat162float(y01.x) > 0.f ? gv.x : 0.f;
+        sum.y += __bfloat162float(y01.y) > 0.f ? gv.y : 0.f;
+        sum.z += __bfloat162float(y23.x) > 0.f ? gv.z : 0.f;
+        sum.w += __bfloat162float(y23.y) > 0.f ? gv.w : 0.f;
+    };
+    if (t < lanes * cg) {
+        const long long p0 = (long long)blockIdx.x * pix_per_block;
+        const long long p1 = min(P, p0 + pix_per_block);
+        long long p = p0 + t / cg;
+        for (; p + 3LL * lanes < p1; p += 4LL * lanes) {
+            float4 gv[4];
+            uint2 yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long i = (p + (long long)u * lanes) * Co + 4 * c4;
+                gv[u] = *reinterpret_cast<const float4*>(g + i);
+                yv[u] = *reinterpret_cast<const uint2*>(yout + i);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) add(gv[u], yv[u]);
+        }
+        for (; p < p1; p += lanes) {
+            const long long i = p * Co + 4 * c4;
+            add(*reinterpret_cast<const float4*>(g + i), *reinterpret_cast<const uint2*>(yout + i));
+        }
+    }
+    acc4[t] = sum;
+    __syncthreads();
+    if (t < cg) {
+        float4 tot = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < lanes; ++q) {
+            const float4 v = acc4[q * cg + t];
+            tot.x += v.x;
+            tot.y += v.y;
+            tot.z += v.z;
+            tot.w += v.w;
+        }
+        atomicAdd(db + 4 * t, tot.x);
+        atomicAdd(db + 4 * t + 1, tot.y);
+        atomicAdd(db + 4 * t + 2, tot.z);
+        atomicAdd(db + 4 * t + 3, tot.w);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_bias_grad(const float* __restrict__ g, const bf16* __restrict__ yout,
                                                    long long P, int Co, long long pix_per_block,
                                                    float* __restrict__ db) {
@@ -1036,6 +1093,71 @@ __global__ void k_head_bwd_data(const float* __restrict__ gy, long long P, int C
     for (int o = 0; o < O; ++o) s = fmaf(gy[p * O + o], __bfloat162float(w[(long long)o * C + c]), s);
     gh[idx] = s;
 }
+// The 1x1 head's weight and bias gradients over the pixels in parallel:
+// dW[o][c] += sum_p gy[p, o] h[p, c] (c < C), db[o] += sum_p gy[p, o] (c = C).
+// Each block takes a range of pixels in tiles of kHeadTile staged in shared
+// memory (coalesced loads; h with a column of ones for the bias, padded to a
+// multiple of 4); thread pair (o, c4) accumulates 4 consecutive c of one o;
+// one atomic per output and block.
+constexpr int kHeadTile = 64;
+constexpr int kHeadPairs = 8;          // (o, 4 c) pairs per thread
+__host__ __device__ constexpr int head_cp(int C) { return (C + 1 + 3) / 4 * 4; }
+__global__ void __launch_bounds__(256) k_head_bwd_w4(const float* __restrict__ gy, const bf16* __restrict__ h,
+                                                     long long P, int C, int O, long long pix_per_block,
+                                                     float* __restrict__ dW, float* __restrict__ db) {
+    extern __shared__ __align__(16) float hsm[];
+    const int Cp = head_cp(C), nq = Cp / 4, npair = O * nq;
+    float* gs = hsm;                       // [kHeadTile][O]
+    float* hs = hsm + kHeadTile * O;       // [kHeadTile][Cp]
+    const int t = threadIdx.x;
+    float4 acc[kHeadPairs];
+#pragma unroll
+    for (int j = 0; j < kHeadPairs; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const long long p0 = (long long)blockIdx.x * pix_per_block;
+    const long long p1 = min(P, p0 + pix_per_block);
+    for (long long pt = p0; pt < p1; pt += kHeadTile) {
+        const int np = (int)min((long long)kHeadTile, p1 - pt);
+        __syncthreads();   // the previous tile is consumed
+        for (int idx = t; idx < kHeadTile * O; idx += blockDim.x)
+            gs[idx] = idx / O < np ? gy[pt * O + idx] : 0.f;
+        for (int idx = t; idx < kHeadTile * Cp; idx += blockDim.x) {
+            const int px = idx / Cp, c = idx - px * Cp;
+            float v = 0.f;
+            if (px < np) v = c < C ? __bfloat162float(h[(pt + px) * C + c]) : (c == C ? 1.f : 0.f);
+            hs[idx] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kHeadPairs; ++j) {
+            const int pr = t + j * 256;
+            if (pr >= npair) continue;
+            const int o = pr / nq, q = pr - o * nq;
+            float4 a = acc[j];
+            for (int px = 0; px < kHeadTile; ++px) {
+                const float gv = gs[px * O + o];
+                const float4 hv = *reinterpret_cast<const float4*>(hs + px * Cp + 4 * q);
+                a.x += gv * hv.x;
+                a.y += gv * hv.y;
+                a.z += gv * hv.z;
+                a.w += gv * hv.w;
+            }
+            acc[j] = a;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kHeadPairs; ++j) {
+        const int pr = t + j * 256;
+        if (pr >= npair) continue;
+        const int o = pr / nq, q = pr - o * nq;
+        const float v[4] = {acc[j].x, acc[j].y, acc[j].z, acc[j].w};
+        for (int u = 0; u < 4; ++u) {
+            const int c = 4 * q + u;
+            if (c < C) atomicAdd(dW + (long long)o * C + c, v[u]);
+            else if (c == C) atomicAdd(db + o, v[u]);
+        }
+    }
+}
+
 __global__ void k_head_bwd_w(const float* __restrict__ gy, const bf16* __restrict__ h, long long P, int C, int O,
                              float* __restrict__ dW, float* __restrict__ db) {
     // one CTA per (o, c) pair (+ one row c == C for the bias); block reduction over pixels
@@ -1111,118 +1233,193 @@ __global__ void k_field_in(const double2* __restrict__ f, long long D, float2* _
         out[e] = make_float2((float)(f[e].x * inv), (float)(f[e].y * inv));
 }
 
-// Projection loss (Eq. 5) per sample and d loss / d y for the batch mean.
-// One CTA per sample: a = V^H f, G = V^H V (warp per entry, FP32 sums over
-// the pixels of a lane, FP64 across lanes), Cholesky solve G z = a (FP64,
-// tiny ridge), l = 1 - Re(a^H z)/|f|^2, gy = 2 (Re, Im) of -(f - V z) z^H /(|f|^2 B).
-__global__ void __launch_bounds__(256) k_proj_loss(const float* __restrict__ y, const double2* const* __restrict__ f,
-                                                   int D, int k, int B, double* __restrict__ loss,
-                                                   float* __restrict__ gy) {
-    extern __shared__ double2 sh[];   // a (k), G (k*k), z (k)
-    const int s = blockIdx.x;
-    const float* ys = y + (long long)s * D * 2 * k;
-    const double2* fs = f[s];
-    float* gs = gy + (long long)s * D * 2 * k;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double2* a = sh;
-    double2* G = sh + k;
-    double2* z = sh + k + k * k;
-    __shared__ double sF;
-    // entries: 0..k-1 -> a_c ; k.. -> G(c, d) for c <= d ; last -> |f|^2
-    const int nent = k + k * (k + 1) / 2 + 1;
-    for (int ent = wid; ent < nent; ent += nw) {
-        float sr = 0.f, si = 0.f;
-        if (ent < k) {
-            const int c = ent;
-            for (int e = lane; e < D; e += 32) {
-                const float vr = ys[(long long)e * 2 * k + 2 * c], vi = ys[(long long)e * 2 * k + 2 * c + 1];
-                const double2 fe = fs[e];
-                const float fr = (float)fe.x, fi = (float)fe.y;
-                sr += vr * fr + vi * fi;
-                si += vr * fi - vi * fr;
-            }
-        } else if (ent < nent - 1) {
-            int q = ent - k, c = 0;
-            while (q >= k - c) { q -= k - c; ++c; }
-            const int d = c + q;
-            for (int e = lane; e < D; e += 32) {
-                const float cr = ys[(long long)e * 2 * k + 2 * c], ci = ys[(long long)e * 2 * k + 2 * c + 1];
-                const float dr = ys[(long long)e * 2 * k + 2 * d], di = ys[(long long)e * 2 * k + 2 * d + 1];
-                sr += cr * dr + ci * di;
-                si += cr * di - ci * dr;
-            }
-        } else {
-            for (int e = lane; e < D; e += 32) {
-                const double2 fe = fs[e];
-                sr += (float)(fe.x * fe.x + fe.y * fe.y);
-            }
+// Projection loss (Eq. 5) over the pixels in parallel, three kernels:
+//   k_proj_part   per sample s and block c (a range of 256-pixel tiles staged
+//                 in shared memory): partial sums of a = V^H f, the upper
+//                 triangle of G = V^H V and |f|^2 (FP32 per lane, FP64 across
+//                 the lanes); entry e < k: a_e, then G(c, d) for c <= d in
+//                 row order, last |f|^2
+//   k_proj_solve  per sample: the sums over the blocks in block order (FP64),
+//                 Cholesky solve G z = a (tiny ridge), l = 1 - Re(a^H z)/|f|^2;
+//                 keeps z and |f|^2
+//   k_proj_grad   per pixel: gy = 2 (Re, Im) of -(f - V z) z^H / (|f|^2 B)
+constexpr int kLossTile = 256;
+constexpr int kLossMaxEnt = 20;   // entries per warp: ceil((16 + 136 + 1) / 8) for k <= 16
+__host__ __device__ constexpr int loss_entries(int k) { return k + k * (k + 1) / 2 + 1; }
+__host__ __device__ constexpr size_t loss_smem(int k) {
+    return sizeof(float) * (size_t)kLossTile * (2 * k + 1) + sizeof(float2) * kLossTile +
+           sizeof(int2) * (size_t)loss_entries(k);
+}
+
+__global__ void __launch_bounds__(256) k_proj_part(const float* __restrict__ y, const double2* const* __restrict__ f,
+                                                   int D, int k, int tiles_per_block, double2* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char lsm_raw[];
+    const int s = blockIdx.y, c = blockIdx.x, nch = gridDim.x;
+    const int stride = 2 * k + 1;                 // odd: lanes reading one column hit distinct banks
+    float* ys = reinterpret_cast<float*>(lsm_raw);
+    float2* fsm = reinterpret_cast<float2*>(ys + kLossTile * stride);
+    int2* tab = reinterpret_cast<int2*>(fsm + kLossTile);   // entry -> (c, d); d < 0: a_c; c < 0: |f|^2
+    const int nent = loss_entries(k);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < nent; e += blockDim.x) {
+        int2 cd;
+        if (e < k) cd = make_int2(e, -1);
+        else if (e == nent - 1) cd = make_int2(-1, -1);
+        else {
+            int q = e - k, cc = 0;
+            while (q >= k - cc) { q -= k - cc; ++cc; }
+            cd = make_int2(cc, cc + q);
         }
-        double dr = sr, di = si;
+        tab[e] = cd;
+    }
+    float ar[kLossMaxEnt], ai[kLossMaxEnt];
+#pragma unroll
+    for (int j = 0; j < kLossMaxEnt; ++j) ar[j] = ai[j] = 0.f;
+    const float* yss = y + (long long)s * D * 2 * k;
+    const double2* fs = f[s];
+    const int ntiles = (D + kLossTile - 1) / kLossTile;
+    for (int tt = 0; tt < tiles_per_block; ++tt) {
+        const int tile = c * tiles_per_block + tt;
+        if (tile >= ntiles) break;
+        const int e0 = tile * kLossTile;
+        const int npx = min(kLossTile, D - e0);
+        __syncthreads();   // the previous tile is consumed (and the table written)
+        for (int idx = threadIdx.x; idx < kLossTile * 2 * k; idx += blockDim.x) {
+            const int px = idx / (2 * k), q = idx - px * 2 * k;
+            ys[px * stride + q] = px < npx ? yss[(long long)(e0 + px) * 2 * k + q] : 0.f;
+        }
+        for (int px = threadIdx.x; px < kLossTile; px += blockDim.x) {
+            const double2 fe = px < npx ? fs[e0 + px] : make_double2(0.0, 0.0);
+            fsm[px] = make_float2((float)fe.x, (float)fe.y);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kLossMaxEnt; ++j) {
+            const int ent = wid + 8 * j;
+            if (ent >= nent) continue;
+            const int2 cd = tab[ent];
+            float sr = 0.f, si = 0.f;
+            if (cd.y >= 0) {            // G(c, d) = v_c^H v_d
+                for (int px = lane; px < kLossTile; px += 32) {
+                    const float cr = ys[px * stride + 2 * cd.x], ci = ys[px * stride + 2 * cd.x + 1];
+                    const float dr = ys[px * stride + 2 * cd.y], di = ys[px * stride + 2 * cd.y + 1];
+                    sr += cr * dr + ci * di;
+                    si += cr * di - ci * dr;
+                }
+            } else if (cd.x >= 0) {     // a_c = v_c^H f
+                for (int px = lane; px < kLossTile; px += 32) {
+                    const float vr = ys[px * stride + 2 * cd.x], vi = ys[px * stride + 2 * cd.x + 1];
+                    const float2 fe = fsm[px];
+                    sr += vr * fe.x + vi * fe.y;
+                    si += vr * fe.y - vi * fe.x;
+                }
+            } else {                    // |f|^2
+                for (int px = lane; px < kLossTile; px += 32) {
+                    const float2 fe = fsm[px];
+                    sr += fe.x * fe.x + fe.y * fe.y;
+                }
+            }
+            ar[j] += sr;
+            ai[j] += si;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kLossMaxEnt; ++j) {
+        const int ent = wid + 8 * j;
+        if (ent >= nent) continue;
+        double dr = ar[j], di = ai[j];
         for (int m = 16; m > 0; m >>= 1) {
             dr += __shfl_xor_sync(0xffffffffu, dr, m);
             di += __shfl_xor_sync(0xffffffffu, di, m);
         }
-        if (lane == 0) {
-            if (ent < k) a[ent] = make_double2(dr, di);
-            else if (ent < nent - 1) {
-                int q = ent - k, c = 0;
-                while (q >= k - c) { q -= k - c; ++c; }
-                const int d = c + q;
-                G[d * k + c] = make_double2(dr, di);       // G(c, d)
-                G[c * k + d] = make_double2(dr, -di);      // G(d, c)
-            } else sF = dr;
-        }
+        if (lane == 0) part[((long long)s * nch + c) * nent + ent] = make_double2(dr, di);
+    }
+}
+
+// Sums the blocks' partials (in block order), solves G z = a and writes the
+// loss; zf[s] holds z_0 .. z_{k-1} and (|f|^2, 0).
+__global__ void __launch_bounds__(256) k_proj_solve(const double2* __restrict__ part, int k, int nch,
+                                                    double* __restrict__ loss, double2* __restrict__ zf) {
+    extern __shared__ double2 sh2[];   // entries (nent), G (k*k), z (k)
+    const int s = blockIdx.x;
+    const int nent = loss_entries(k);
+    double2* ent = sh2;
+    double2* G = sh2 + nent;
+    double2* z = G + k * k;
+    for (int e = threadIdx.x; e < nent; e += blockDim.x) {
+        double2 acc = make_double2(0.0, 0.0);
+        const double2* pe = part + (long long)s * nch * nent + e;
+        for (int c = 0; c < nch; ++c) acc = cadd(acc, pe[(long long)c * nent]);
+        ent[e] = acc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // Cholesky G = R^H R (upper R in place, column-major) with a ridge of 1e-6 max diag:
-        // keeps the loss finite when the predicted vectors become dependent
-        double dmax = 0.0;
-        for (int c = 0; c < k; ++c) dmax = fmax(dmax, G[c * k + c].x);
-        for (int c = 0; c < k; ++c) G[c * k + c].x += 1e-6 * dmax + 1e-300;
-        for (int p = 0; p < k; ++p) {
-            double dd = G[p * k + p].x;
-            for (int l = 0; l < p; ++l) dd -= cabs2(G[p * k + l]);
-            const double rpp = sqrt(fmax(dd, 1e-300));
-            G[p * k + p] = make_double2(rpp, 0.0);
-            for (int q = p + 1; q < k; ++q) {
-                double2 tq = G[q * k + p];
-                for (int l = 0; l < p; ++l) tq = csub(tq, cmulc(G[p * k + l], G[q * k + l]));
-                G[q * k + p] = cscale(tq, 1.0 / rpp);
-            }
+    if (threadIdx.x != 0) return;
+    const double2* a = ent;
+    int q = k;
+    for (int c = 0; c < k; ++c)
+        for (int d = c; d < k; ++d, ++q) {
+            G[d * k + c] = ent[q];                                  // G(c, d)
+            G[c * k + d] = make_double2(ent[q].x, -ent[q].y);       // G(d, c)
         }
-        // R^H w = a (forward), R z = w (backward)
-        for (int p = 0; p < k; ++p) {
-            double2 tq = a[p];
-            for (int l = 0; l < p; ++l) tq = csub(tq, cmulc(G[p * k + l], z[l]));
-            z[p] = cscale(tq, 1.0 / G[p * k + p].x);
+    const double sF = ent[nent - 1].x;
+    // Cholesky G = R^H R (upper R in place, column-major) with a ridge of 1e-6 max diag:
+    // keeps the loss finite when the predicted vectors become dependent
+    double dmax = 0.0;
+    for (int c = 0; c < k; ++c) dmax = fmax(dmax, G[c * k + c].x);
+    for (int c = 0; c < k; ++c) G[c * k + c].x += 1e-6 * dmax + 1e-300;
+    for (int p = 0; p < k; ++p) {
+        double dd = G[p * k + p].x;
+        for (int l = 0; l < p; ++l) dd -= cabs2(G[p * k + l]);
+        const double rpp = sqrt(fmax(dd, 1e-300));
+        G[p * k + p] = make_double2(rpp, 0.0);
+        for (int r = p + 1; r < k; ++r) {
+            double2 tq = G[r * k + p];
+            for (int l = 0; l < p; ++l) tq = csub(tq, cmulc(G[p * k + l], G[r * k + l]));
+            G[r * k + p] = cscale(tq, 1.0 / rpp);
         }
-        for (int p = k - 1; p >= 0; --p) {
-            double2 tq = z[p];
-            for (int l = p + 1; l < k; ++l) tq = csub(tq, cmul(G[l * k + p], z[l]));
-            z[p] = cscale(tq, 1.0 / G[p * k + p].x);
-        }
-        double az = 0.0;
-        for (int c = 0; c < k; ++c) az += a[c].x * z[c].x + a[c].y * z[c].y;   // Re(a^H z)
-        loss[s] = 1.0 - az / sF;
     }
-    __syncthreads();
-    const float scale = (float)(-2.0 / (sF * B));
-    for (int e = threadIdx.x; e < D; e += blockDim.x) {
-        const double2 fe = fs[e];
-        float rr = (float)fe.x, ri = (float)fe.y;
-        for (int c = 0; c < k; ++c) {
-            const float vr = ys[(long long)e * 2 * k + 2 * c], vi = ys[(long long)e * 2 * k + 2 * c + 1];
-            const float zr = (float)z[c].x, zi = (float)z[c].y;
-            rr -= vr * zr - vi * zi;
-            ri -= vr * zi + vi * zr;
-        }
-        for (int c = 0; c < k; ++c) {
-            const float zr = (float)z[c].x, zi = (float)z[c].y;
-            // r conj(z_c)
-            gs[(long long)e * 2 * k + 2 * c] = scale * (rr * zr + ri * zi);
-            gs[(long long)e * 2 * k + 2 * c + 1] = scale * (ri * zr - rr * zi);
-        }
+    // R^H w = a (forward), R z = w (backward)
+    for (int p = 0; p < k; ++p) {
+        double2 tq = a[p];
+        for (int l = 0; l < p; ++l) tq = csub(tq, cmulc(G[p * k + l], z[l]));
+        z[p] = cscale(tq, 1.0 / G[p * k + p].x);
+    }
+    for (int p = k - 1; p >= 0; --p) {
+        double2 tq = z[p];
+        for (int l = p + 1; l < k; ++l) tq = csub(tq, cmul(G[l * k + p], z[l]));
+        z[p] = cscale(tq, 1.0 / G[p * k + p].x);
+    }
+    double az = 0.0;
+    for (int c = 0; c < k; ++c) az += a[c].x * z[c].x + a[c].y * z[c].y;   // Re(a^H z)
+    loss[s] = 1.0 - az / sF;
+    for (int c = 0; c < k; ++c) zf[(long long)s * (k + 1) + c] = z[c];
+    zf[(long long)s * (k + 1) + k] = make_double2(sF, 0.0);
+}
+
+// gy[s, e] = 2 (Re, Im) of -(f - V z) conj(z_c) / (|f|^2 B), one pixel per thread.
+__global__ void __launch_bounds__(256) k_proj_grad(const float* __restrict__ y, const double2* const* __restrict__ f,
+                                                   int D, int k, int B, const double2* __restrict__ zf,
+                                                   float* __restrict__ gy) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)B * D) return;
+    const int s = (int)(idx / D), e = (int)(idx - (long long)s * D);
+    const double2* zs = zf + (long long)s * (k + 1);
+    const float scale = (float)(-2.0 / (zs[k].x * B));
+    const float* ys = y + idx * 2 * k;
+    float* gs = gy + idx * 2 * k;
+    const double2 fe = f[s][e];
+    float rr = (float)fe.x, ri = (float)fe.y;
+    for (int c = 0; c < k; ++c) {
+        const float vr = ys[2 * c], vi = ys[2 * c + 1];
+        const float zr = (float)zs[c].x, zi = (float)zs[c].y;
+        rr -= vr * zr - vi * zi;
+        ri -= vr * zi + vi * zr;
+    }
+    for (int c = 0; c < k; ++c) {
+        const float zr = (float)zs[c].x, zi = (float)zs[c].y;
+        // r conj(z_c)
+        gs[2 * c] = scale * (rr * zr + ri * zi);
+        gs[2 * c + 1] = scale * (ri * zr - rr * zi);
     }
 }
 
@@ -1572,7 +1769,16 @@ struct Acts {
     float* g2;
     float* g3;
     float* gskip[kMaxLevels];
+    double2* lpart;   // loss partial sums (train): [B][loss blocks][entries]
+    double2* lz;      // loss solutions (train): [B][k + 1]
 };
+
+// blocks per sample of the loss partial sums, and 256-pixel tiles per block
+static void loss_blocks(int D, int* nch, int* tpb) {
+    const int ntiles = (D + kLossTile - 1) / kLossTile;
+    *nch = std::min(256, ntiles);
+    *tpb = (ntiles + *nch - 1) / *nch;
+}
 
 // Activation workspace of one batch; `train` adds the gradient buffers (the
 // forward-only calls, prediction and predictor_forward, need none of them).
@@ -1604,6 +1810,7 @@ static size_t plan_acts(const ddg_predictor* P, int B, int H, int W, char* base,
     A->y = (float*)take(sizeof(float) * (size_t)B * H * W * 2 * P->k);
     if (!train) {
         A->gy = A->y2 = A->gy2 = A->g1 = A->g2 = A->g3 = nullptr;
+        A->lpart = A->lz = nullptr;
         return off + 256;
     }
     A->gy = (float*)take(sizeof(float) * (size_t)B * H * W * 2 * P->k);
@@ -1612,6 +1819,10 @@ static size_t plan_acts(const ddg_predictor* P, int B, int H, int W, char* base,
     A->g1 = (float*)take(sizeof(float) * maxg);
     A->g2 = (float*)take(sizeof(float) * maxg);
     A->g3 = (float*)take(sizeof(float) * maxg);
+    int nch = 0, tpb = 0;
+    loss_blocks(H * W, &nch, &tpb);
+    A->lpart = (double2*)take(sizeof(double2) * (size_t)B * nch * loss_entries(P->k));
+    A->lz = (double2*)take(sizeof(double2) * (size_t)B * (P->k + 1));
     return off + 256;
 }
 
@@ -1839,7 +2050,12 @@ static ddg_status wgrad(ddg_predictor* P, const LX& lx, const float* g, const bf
         DDG_CHECK_LAUNCH("k_wgrad_tc");
         const long long pb = std::max(1024LL, (npx + 4 * P->sm_count - 1) / (4 * P->sm_count));
         ++P->launches;
-        k_bias_grad<<<(unsigned)((npx + pb - 1) / pb), 256, 0, st>>>(g, yout, npx, Ly.co, pb, P->grad + Ly.b_off);
+        if (Ly.co % 4 == 0 && Ly.co <= 1024)
+            k_bias_grad4<<<(unsigned)((npx + pb - 1) / pb), 256, 0, st>>>(g, yout, npx, Ly.co, pb,
+                                                                          P->grad + Ly.b_off);
+        else
+            k_bias_grad<<<(unsigned)((npx + pb - 1) / pb), 256, 0, st>>>(g, yout, npx, Ly.co, pb,
+                                                                         P->grad + Ly.b_off);
         DDG_CHECK_LAUNCH("k_bias_grad");
         return DDG_OK;
     }
@@ -1888,8 +2104,16 @@ static ddg_status backward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaS
     const int O = 2 * P->k, C0 = P->ch[0];
     const bf16* hin = L > 1 ? A->db[0] : A->eb[0];   // input of the 1x1 head
     ++P->launches;
-    k_head_bwd_w<<<O * (C0 + 1), 256, 0, st>>>(A->gy, hin, px0, C0, O, P->grad + P->layers[lh].w_off,
-                                              P->grad + P->layers[lh].b_off);
+    const size_t hsm = sizeof(float) * (size_t)kHeadTile * (O + head_cp(C0));
+    if (O * (head_cp(C0) / 4) <= 256 * kHeadPairs && hsm <= 48 * 1024) {
+        const long long pb = std::max(1024LL, (px0 + 4 * P->sm_count - 1) / (4 * P->sm_count));
+        k_head_bwd_w4<<<(unsigned)((px0 + pb - 1) / pb), 256, hsm, st>>>(A->gy, hin, px0, C0, O, pb,
+                                                                          P->grad + P->layers[lh].w_off,
+                                                                          P->grad + P->layers[lh].b_off);
+    } else {
+        k_head_bwd_w<<<O * (C0 + 1), 256, 0, st>>>(A->gy, hin, px0, C0, O, P->grad + P->layers[lh].w_off,
+                                                  P->grad + P->layers[lh].b_off);
+    }
     ++P->launches;
     k_head_bwd_data<<<nblk(px0 * C0), 256, 0, st>>>(A->gy, px0, C0, O, wbf(P, lh), A->g1);
     DDG_CHECK_LAUNCH("head backward");
@@ -2294,21 +2518,27 @@ extern "C" ddg_status predictor_loss_grad(ddg_predictor* P, int n, const ddg_op*
     DDG_CHECK_CUDA(cudaMemcpyAsync(slots, f, sizeof(void*) * n, cudaMemcpyHostToDevice, st));
     const int k = P->k;
     const int D = H * W;
-    const size_t smem = sizeof(double2) * (size_t)(2 * k + k * k);
+    const double2* const* fsl = reinterpret_cast<const double2* const*>(slots);
+    int nch = 0, tpb = 0;
+    loss_blocks(D, &nch, &tpb);
+    // Eq. 5 for V = y (projection loss) or V = A y (residual loss) and its gradient in gout
+    auto proj_loss = [&](const float* yv, float* gout) {
+        P->launches += 3;
+        k_proj_part<<<dim3(nch, n), 256, loss_smem(k), st>>>(yv, fsl, D, k, tpb, acts.lpart);
+        k_proj_solve<<<n, 256, sizeof(double2) * (size_t)(loss_entries(k) + k * k + k), st>>>(acts.lpart, k, nch,
+                                                                                             P->d_loss, acts.lz);
+        k_proj_grad<<<nblk((long long)n * D), 256, 0, st>>>(yv, fsl, D, k, n, acts.lz, gout);
+    };
     if (P->loss_kind == 0) {
         // Eq. 5: V against the solved fields f
-        ++P->launches;
-        k_proj_loss<<<n, 256, smem, st>>>(acts.y, reinterpret_cast<const double2* const*>(slots), D, k, n,
-                                          P->d_loss, acts.gy);
+        proj_loss(acts.y, acts.gy);
     } else {
         // Eq. 6: W = A V against the right-hand sides b, then dl/dV = A^H dl/dW
         FieldOpDesc* fo = field_ops(P, n);
         const long long nk = (long long)n * D * k;
         ++P->launches;
         k_fields_apply<<<nblk((long long)n * D), 256, 0, st>>>(fo, acts.y, n, D, k, acts.y2);
-        ++P->launches;
-        k_proj_loss<<<n, 256, smem, st>>>(acts.y2, reinterpret_cast<const double2* const*>(slots), D, k, n,
-                                          P->d_loss, acts.gy2);
+        proj_loss(acts.y2, acts.gy2);
         ++P->launches;
         k_adj_pre<<<nblk(nk), 256, 0, st>>>(fo, acts.gy2, n, D, k, acts.y2);
         ++P->launches;
