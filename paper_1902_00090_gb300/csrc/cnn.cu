@@ -1082,6 +1082,83 @@ __global__ void k_head_fwd(const bf16* __restrict__ h, long long P, int C, int O
     y[idx] = s;
 }
 
+// The 1x1 head, one pixel per thread (C % 8 == 0, C <= 256, O <= 32): the
+// weights in shared memory as [c][o] (every thread reads the same entry, a
+// broadcast), the pixel's input row by 16-byte loads, all O outputs in
+// registers, written as 16-byte stores when O % 4 == 0.
+constexpr int kHeadMaxO = 32;
+__global__ void __launch_bounds__(256) k_head_fwd_px(const bf16* __restrict__ h, long long P, int C, int O,
+                                                     const bf16* __restrict__ w, const float* __restrict__ bias,
+                                                     float* __restrict__ y) {
+    extern __shared__ float wsh[];   // [C][O] then bias [O]
+    for (int i = threadIdx.x; i < C * O; i += blockDim.x) {
+        const int o = i / C, c = i - o * C;
+        wsh[c * O + o] = __bfloat162float(w[i]);
+    }
+    for (int o = threadIdx.x; o < O; o += blockDim.x) wsh[C * O + o] = bias[o];
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    float out[kHeadMaxO];
+#pragma unroll
+    for (int o = 0; o < kHeadMaxO; ++o) out[o] = o < O ? wsh[C * O + o] : 0.f;
+    const uint4* hr = reinterpret_cast<const uint4*>(h + p * C);
+    for (int c8 = 0; c8 < C / 8; ++c8) {
+        const uint4 v = hr[c8];
+        const unsigned wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 b2 = *reinterpret_cast<const __nv_bfloat162*>(&wv[q]);
+            const float h0 = __bfloat162float(b2.x), h1 = __bfloat162float(b2.y);
+            const float* w0 = wsh + (8 * c8 + 2 * q) * O;
+#pragma unroll
+            for (int o = 0; o < kHeadMaxO; ++o)
+                if (o < O) out[o] = fmaf(h1, w0[O + o], fmaf(h0, w0[o], out[o]));
+        }
+    }
+    float* yo = y + p * O;
+    if (O % 4 == 0) {
+#pragma unroll
+        for (int o = 0; o < kHeadMaxO; o += 4)
+            if (o < O) *reinterpret_cast<float4*>(yo + o) = make_float4(out[o], out[o + 1], out[o + 2], out[o + 3]);
+    } else {
+#pragma unroll
+        for (int o = 0; o < kHeadMaxO; ++o)
+            if (o < O) yo[o] = out[o];
+    }
+}
+
+// gh[p, c] = sum_o gy[p, o] w[o][c], one pixel per thread (conditions as
+// k_head_fwd_px): the gradient row in registers, 32 input channels at a time.
+__global__ void __launch_bounds__(256) k_head_bwd_data_px(const float* __restrict__ gy, long long P, int C, int O,
+                                                          const bf16* __restrict__ w, float* __restrict__ gh) {
+    extern __shared__ float wsh[];   // [o][c]
+    for (int i = threadIdx.x; i < C * O; i += blockDim.x) wsh[i] = __bfloat162float(w[i]);
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    float g[kHeadMaxO];
+#pragma unroll
+    for (int o = 0; o < kHeadMaxO; ++o) g[o] = o < O ? gy[p * O + o] : 0.f;
+    float* go = gh + p * C;
+    for (int c0 = 0; c0 < C; c0 += 32) {
+        float acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+#pragma unroll
+        for (int o = 0; o < kHeadMaxO; ++o) {
+            if (o >= O) continue;
+            const float* wr = wsh + o * C + c0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (c0 + j < C) acc[j] = fmaf(g[o], wr[j], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+            if (c0 + j < C) *reinterpret_cast<float4*>(go + c0 + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+    }
+}
+
 // head backward: gh[p, c] = sum_o gy[p, o] w[o][c]; dW[o][c] += sum_p gy[p, o] h[p, c]; db[o] += sum_p gy
 __global__ void k_head_bwd_data(const float* __restrict__ gy, long long P, int C, int O, const bf16* __restrict__ w,
                                 float* __restrict__ gh) {
@@ -2012,8 +2089,12 @@ static ddg_status forward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaSt
     }
     const int lh = (int)P->layers.size() - 1;
     ++P->launches;
-    k_head_fwd<<<nblk((long long)B * H * W * 2 * P->k), 256, 0, st>>>(h, (long long)B * H * W, hc, 2 * P->k, wbf(P, lh),
-                                                                    bias32(P, lh), A->y);
+    if (hc % 8 == 0 && hc <= 256 && 2 * P->k <= kHeadMaxO)
+        k_head_fwd_px<<<nblk((long long)B * H * W), 256, sizeof(float) * (size_t)(hc + 1) * 2 * P->k, st>>>(
+            h, (long long)B * H * W, hc, 2 * P->k, wbf(P, lh), bias32(P, lh), A->y);
+    else
+        k_head_fwd<<<nblk((long long)B * H * W * 2 * P->k), 256, 0, st>>>(h, (long long)B * H * W, hc, 2 * P->k,
+                                                                        wbf(P, lh), bias32(P, lh), A->y);
     if (!P->bases.empty()) {
         const long long n = (long long)H * W * 2 * P->k;
         ++P->launches;
@@ -2115,7 +2196,11 @@ static ddg_status backward(ddg_predictor* P, int B, int H, int W, Acts* A, cudaS
                                                   P->grad + P->layers[lh].b_off);
     }
     ++P->launches;
-    k_head_bwd_data<<<nblk(px0 * C0), 256, 0, st>>>(A->gy, px0, C0, O, wbf(P, lh), A->g1);
+    if (C0 % 8 == 0 && C0 <= 256 && O <= kHeadMaxO)
+        k_head_bwd_data_px<<<nblk(px0), 256, sizeof(float) * (size_t)C0 * O, st>>>(A->gy, px0, C0, O, wbf(P, lh),
+                                                                                   A->g1);
+    else
+        k_head_bwd_data<<<nblk(px0 * C0), 256, 0, st>>>(A->gy, px0, C0, O, wbf(P, lh), A->g1);
     DDG_CHECK_LAUNCH("head backward");
     float* gh = A->g1;      // gradient w.r.t. the current level's output (post-ReLU)
     float* ga = A->g2;
