@@ -438,12 +438,22 @@ constexpr uint32_t kChunkBytes = HH * HWD * 16; // one 8-channel chunk of a halo
 constexpr uint32_t kChunkStride = 2944;         // chunks 128-byte aligned (TMA destinations)
 constexpr int kBufs = 2;                        // input buffers = accumulators
 constexpr int kEpiWarps = 4;
+constexpr int kExpWarps = 4;                    // upsampled inputs: warps that expand the coarse tile
 constexpr int kThreads = 32 * (1 + kEpiWarps);
+constexpr int kThreadsUp = 32 * (1 + kEpiWarps + kExpWarps);
+// upsampled input: the coarse tile under an 18 x 10 fine halo tile (fine row
+// y0 - 1 + hy is coarse row y0/2 - 1 + (hy + 1)/2, the same in x)
+constexpr int CH = HH / 2 + 1, CW = HWD / 2 + 1;   // 10 x 6
+constexpr uint32_t kCoarseBytes = CH * CW * 16;    // one 8-channel chunk (960)
+constexpr uint32_t kCoarseStride = 1024;           // 128-byte aligned (TMA destinations)
 static_assert(TH * TW == tc::kM && kChunkStride >= kChunkBytes && kChunkStride % 128 == 0, "tile geometry");
+static_assert(kCoarseStride >= kCoarseBytes && kCoarseStride % 128 == 0, "coarse tile geometry");
 __host__ __device__ constexpr uint32_t wbytes(int ci, int co) { return 9u * (uint32_t)ci * (uint32_t)co * 2u; }
 __host__ __device__ constexpr uint32_t bufbytes(int ci) { return (uint32_t)(ci / 8) * kChunkStride; }
-__host__ __device__ constexpr size_t smem_bytes(int ci, int co) {
-    return (size_t)wbytes(ci, co) + (size_t)kBufs * bufbytes(ci) + 128;   // + the base's round-up to 128
+__host__ __device__ constexpr uint32_t cbufbytes(int c1) { return (uint32_t)(c1 / 8) * kCoarseStride; }
+__host__ __device__ constexpr size_t smem_bytes(int ci, int co, int c1 = 0) {
+    // + the base's round-up to 128
+    return (size_t)wbytes(ci, co) + (size_t)kBufs * (bufbytes(ci) + cbufbytes(c1)) + 128;
 }
 // Shared-memory descriptor of a K-major operand without swizzle: start
 // address, leading byte offset (between 8-element K groups), stride byte
@@ -480,18 +490,27 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 }  // namespace tmc
 
-__global__ void __launch_bounds__(tmc::kThreads) k_conv3_tma(const __grid_constant__ CUtensorMap tin, int B, int H,
-                                                             int W, int Ci, int Co, const bf16* __restrict__ wt,
-                                                             const float* __restrict__ bias, int relu,
-                                                             bf16* __restrict__ out, int* __restrict__ err) {
+// c1 > 0: the input is [nearest-upsampled x1 (c1 channels, half resolution,
+// tensor map tup) | x2 (Ci - c1 channels, tensor map tin)]: the x2 chunks come
+// by TMA as above, the x1 chunks as a coarse 10 x 6 tile (TMA, zeros outside)
+// that warps 5-8 expand into the fine halo layout (each fine pixel copies its
+// coarse parent), then make visible to the tensor core (proxy fence) and
+// count on the buffer's "loaded" barrier.
+__global__ void __launch_bounds__(tmc::kThreadsUp) k_conv3_tma(const __grid_constant__ CUtensorMap tin,
+                                                               const __grid_constant__ CUtensorMap tup, int c1, int B,
+                                                               int H, int W, int Ci, int Co,
+                                                               const bf16* __restrict__ wt,
+                                                               const float* __restrict__ bias, int relu,
+                                                               bf16* __restrict__ out, int* __restrict__ err) {
     using namespace tmc;
     extern __shared__ __align__(128) unsigned char smraw_tm[];
-    __shared__ __align__(8) unsigned long long wbar, full[kBufs], mdone[kBufs], accfree[kBufs];
+    __shared__ __align__(8) unsigned long long wbar, full[kBufs], mdone[kBufs], accfree[kBufs], cfull[kBufs];
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     unsigned char* sm = smraw_tm + ((128u - (smem_u32(smraw_tm) & 127u)) & 127u);
     unsigned char* wsm = sm;                        // weights [9 Ci/8][Co][8]
     unsigned char* ism = sm + wbytes(Ci, Co);       // kBufs halo tiles [Ci/8][18][10][8]
+    unsigned char* csm = ism + kBufs * bufbytes(Ci); // kBufs coarse tiles [c1/8][10][6][8] (c1 > 0)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntx = W / TW, nty = H / TH;
     const long long ntiles = (long long)B * nty * ntx;
@@ -509,9 +528,10 @@ __global__ void __launch_bounds__(tmc::kThreads) k_conv3_tma(const __grid_consta
     if (tid == 0) {
         mbar_init(&wbar, 1);
         for (int q = 0; q < kBufs; ++q) {
-            mbar_init(&full[q], 1);
+            mbar_init(&full[q], 1 + (c1 > 0 ? kExpWarps : 0));   // the producer, and the expanding warps
             mbar_init(&mdone[q], 1);
             mbar_init(&accfree[q], kEpiWarps);
+            mbar_init(&cfull[q], 1);
         }
         mbar_init_fence();
         s_abort = 0;
@@ -537,8 +557,16 @@ __global__ void __launch_bounds__(tmc::kThreads) k_conv3_tma(const __grid_consta
             tile_of(t, b, y0, x0);
             const int s = t % kBufs;
             unsigned char* dst = ism + s * bufbytes(Ci);
-            mbar_expect_tx(&full[s], (unsigned)nchunk * kChunkBytes);
-            for (int q = 0; q < nchunk; ++q) load4d(dst + q * kChunkStride, &tin, 8 * q, x0 - 1, y0 - 1, b, &full[s]);
+            const int n1 = c1 / 8;     // chunks from the upsampled input (0: a plain input)
+            mbar_expect_tx(&full[s], (unsigned)(nchunk - n1) * kChunkBytes);
+            for (int q = n1; q < nchunk; ++q)
+                load4d(dst + q * kChunkStride, &tin, 8 * (q - n1), x0 - 1, y0 - 1, b, &full[s]);
+            if (n1 > 0) {
+                unsigned char* cdst = csm + s * cbufbytes(c1);
+                mbar_expect_tx(&cfull[s], (unsigned)n1 * kCoarseBytes);
+                for (int q = 0; q < n1; ++q)
+                    load4d(cdst + q * kCoarseStride, &tup, 8 * q, x0 / 2 - 1, y0 / 2 - 1, b, &cfull[s]);
+            }
         };
         mbar_expect_tx(&wbar, wbytes(Ci, Co));
         bulk_g2s(wsm, wt, wbytes(Ci, Co), &wbar);
@@ -585,6 +613,30 @@ __global__ void __launch_bounds__(tmc::kThreads) k_conv3_tma(const __grid_consta
             for (int t = max(0, issued - kBufs); t < issued; ++t)
                 mbar_wait(&full[t % kBufs], (unsigned)(t / kBufs) & 1u);
             if (committed > 0) mbar_wait(&mdone[(committed - 1) % kBufs], (unsigned)((committed - 1) / kBufs) & 1u);
+        }
+    } else if (warp > kEpiWarps) {
+        // expanding warps (c1 > 0 only; the launch has them only then): fine
+        // halo pixel (hy, hx) of chunk q <- coarse pixel ((hy + 1)/2, (hx + 1)/2)
+        const int n1 = c1 / 8;
+        const int et = tid - 32 * (1 + kEpiWarps), ne = 32 * kExpWarps;
+        for (int t = 0; n1 > 0 && t < nmine && !s_abort; ++t) {
+            const int s = t % kBufs;
+            if (!mbar_wait(&cfull[s], (unsigned)(t / kBufs) & 1u)) {
+                give_up();
+                break;
+            }
+            const unsigned char* src = csm + s * cbufbytes(c1);
+            unsigned char* dst = ism + s * bufbytes(Ci);
+            for (int idx = et; idx < n1 * HH * HWD; idx += ne) {
+                const int q = idx / (HH * HWD), rr = idx - q * (HH * HWD);
+                const int hy = rr / HWD, hx = rr - hy * HWD;
+                const uint4 v = *reinterpret_cast<const uint4*>(src + q * kCoarseStride +
+                                                                ((hy + 1) / 2 * CW + (hx + 1) / 2) * 16);
+                *reinterpret_cast<uint4*>(dst + q * kChunkStride + rr * 16) = v;
+            }
+            fence_proxy_async_smem();   // these writes, before the tensor core reads them
+            __syncwarp();
+            if (lane == 0) arrive(&full[s]);
         }
     } else if (warp >= 1) {
         // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
@@ -1958,22 +2010,38 @@ static bool conv_fwd_tma(ddg_predictor* P, const LoadCat& ld, int B, int H, int 
     const Layer& Ly = P->layers[li];
     const int Ci = ci_pad > 0 ? ci_pad : Ly.ci, Co = Ly.co;
     if (Ci < Ly.ci) return false;
-    const size_t smem = tmc::smem_bytes(Ci, Co);
-    if ((P->tensor_cores & 5) != 5 || ld.up1 || ld.c2 != 0 || !ld.x1 || ld.c1 != Ci || Ci % 16 != 0 ||
-        Co % 16 != 0 || Co > 256 || H % tmc::TH != 0 || W % tmc::TW != 0 ||
-        (reinterpret_cast<uintptr_t>(ld.x1) & 15) != 0 || smem > 227 * 1024)
+    // the decoder's input: nearest-upsampled x1 (half resolution) then x2
+    const bool up = ld.up1 && ld.c2 > 0;
+    const int c1 = up ? ld.c1 : 0;
+    const size_t smem = tmc::smem_bytes(Ci, Co, c1);
+    const bool shapes = up ? (ci_pad == 0 && ld.c1 + ld.c2 == Ci && ld.c1 % 8 == 0 && ld.c2 % 8 == 0 && ld.x2 &&
+                              ld.h1 * 2 == H && ld.w1 * 2 == W && (reinterpret_cast<uintptr_t>(ld.x2) & 15) == 0)
+                           : (!ld.up1 && ld.c2 == 0 && ld.c1 == Ci);
+    if ((P->tensor_cores & 5) != 5 || !shapes || !ld.x1 || Ci % 16 != 0 || Co % 16 != 0 || Co > 256 ||
+        H % tmc::TH != 0 || W % tmc::TW != 0 || (reinterpret_cast<uintptr_t>(ld.x1) & 15) != 0 ||
+        smem > 227 * 1024)
         return false;
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
-    CUtensorMap map;
-    const cuuint64_t dims[4] = {(cuuint64_t)Ci, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
-    const cuuint64_t strides[3] = {(cuuint64_t)Ci * 2, (cuuint64_t)W * Ci * 2, (cuuint64_t)H * W * Ci * 2};
-    const cuuint32_t box[4] = {8, (cuuint32_t)tmc::HWD, (cuuint32_t)tmc::HH, 1};
-    const cuuint32_t es[4] = {1, 1, 1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(ld.x1), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return false;
+    // 4D maps over (C, W, H, B) of an NHWC BF16 tensor, boxes of 8 channels
+    auto make_map = [&](CUtensorMap* m, const bf16* base, int C, int Wd, int Hd, int bw, int bh) {
+        const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)Wd, (cuuint64_t)Hd, (cuuint64_t)B};
+        const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)Wd * C * 2, (cuuint64_t)Hd * Wd * C * 2};
+        const cuuint32_t box[4] = {8, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    CUtensorMap map, mapu;
+    if (up) {
+        if (!make_map(&map, ld.x2, ld.c2, W, H, tmc::HWD, tmc::HH) ||
+            !make_map(&mapu, ld.x1, ld.c1, W / 2, H / 2, tmc::CW, tmc::CH))
+            return false;
+    } else {
+        if (!make_map(&map, ld.x1, Ci, W, H, tmc::HWD, tmc::HH)) return false;
+        mapu = map;   // unused
+    }
     *status = DDG_OK;
     auto fail = [&](cudaError_t e, const char* what) {
         *status = cuda_status(e, what);
@@ -1992,7 +2060,8 @@ static bool conv_fwd_tma(ddg_predictor* P, const LoadCat& ld, int B, int H, int 
     const unsigned grid = (unsigned)std::min<long long>(ntiles, (long long)P->sm_count * nb);
     P->launches += 2;
     k_w_tma<<<nblk((long long)Co * Ci * 9), 256, 0, st>>>(wbf(P, li), Co, Ly.ci, Ci, P->wk);
-    k_conv3_tma<<<grid, tmc::kThreads, smem, st>>>(map, B, H, W, Ci, Co, P->wk, bias32(P, li), 1, out, P->d_err);
+    k_conv3_tma<<<grid, up ? tmc::kThreadsUp : tmc::kThreads, smem, st>>>(map, mapu, c1, B, H, W, Ci, Co, P->wk,
+                                                                         bias32(P, li), 1, out, P->d_err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(e, "k_conv3_tma");
     return true;
