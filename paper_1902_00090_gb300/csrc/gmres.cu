@@ -223,6 +223,27 @@ template <typename V> __device__ __forceinline__ V reduce8(const V (&x)[8], int 
     return y1;
 }
 
+// reduce8 for values a lane already holds in its butterfly order: the lane
+// whose partner at level 16 / 8 / 4 keeps a given half holds that half in the
+// other position, so every level keeps x[0 .. h) and sends x[h .. 2h) with no
+// per-lane selects (5 of the 9 exchanges' instructions were selects).  The
+// caller arranges the order: with lane bits b16, b8, b4 a lane must hold in
+// x[w] (w < 4) the value that reduce8 expects at index
+// (w ^ (2 b8 + b4)) + 4 b16, and in x[w + 4] the one at (w ^ (2 b8 + b4)) + 4 (1 - b16).
+// On return lane L holds the same total as reduce8's.
+template <typename V> __device__ __forceinline__ V reduce8_ordered(const V (&x)[8]) {
+    V y4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) y4[i] = cadd(x[i], shfl_xor(x[i + 4], 16));
+    V y2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) y2[i] = cadd(y4[i], shfl_xor(y4[i + 2], 8));
+    V y1 = cadd(y2[0], shfl_xor(y2[1], 4));
+    y1 = cadd(y1, shfl_xor(y1, 2));
+    y1 = cadd(y1, shfl_xor(y1, 1));
+    return y1;
+}
+
 #define SOLVE_PROLOGUE()                                  \
     const int s = a.blk_solve[blockIdx.x];                \
     SolveScal* S = a.S + s;                               \
@@ -1036,6 +1057,15 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
         for (int q = 0; q < VEC; ++q) z[q] = mk((T)0, (T)0);
     }
     __shared__ T smt[kWarps];
+    // this thread's terms of alpha = u^H u and gamma = u^H z, formed now so that
+    // u and z need not stay live through the stage loop
+    T al_p = (T)0;
+    V gg_p = mk((T)0, (T)0);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+        al_p += u[q].x * u[q].x + u[q].y * u[q].y;
+        cfmac(gg_p, u[q], z[q]);
+    }
     // partial sums stay in the Krylov precision until the last CTA
     V* part = reinterpret_cast<V*>(P.part) + (long long)chunk * a.KP;
     bool ok = true;
@@ -1129,7 +1159,18 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
             (void)nv;
         }
     } else {
-    const DotPairs<T> dp(z, u);
+    // The lanes hold their partials in reduce8_ordered's order: a lane with bit
+    // 16 set forms [s | t] (z and u swapped), and lanes with bits 8 / 4 set read
+    // the stage's four columns in the order w ^ 2 / w ^ 1.
+    const bool b16 = lane & 16;
+    const int cperm = ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    V zz[VEC], uu[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+        zz[q] = b16 ? u[q] : z[q];
+        uu[q] = b16 ? z[q] : u[q];
+    }
+    const DotPairs<T> dp(zz, uu);
     const int vidx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     __shared__ V red_t[kWarps][32];
     __shared__ V red_s[kWarps][32];
@@ -1151,8 +1192,12 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
         if (!mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u, a.wait_ns)) ok = false;
         const BP* stg = reinterpret_cast<const BP*>(smraw2 + (b % kRing) * (kRingCols * kColBytes));
         BP m[kRingCols];
+        static_assert(kRingCols == 4, "one butterfly group per stage");
 #pragma unroll
-        for (int w = 0; w < kRingCols; ++w) m[w] = (w < nv) ? stg[w * kBlock + threadIdx.x] : BP{};
+        for (int w = 0; w < kRingCols; ++w) {
+            const int c = w ^ cperm;   // this lane's column for butterfly position w
+            m[w] = (c < nv) ? stg[c * kBlock + threadIdx.x] : BP{};
+        }
 #pragma unroll
         for (int g = 0; g < kRingCols / 4; ++g) {
             V acc[8];
@@ -1162,7 +1207,7 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
                 BS::load(m[4 * g + w], mv);
                 dp.dots(mv, acc[w], acc[w + 4]);
             }
-            const V r = reduce8(acc, lane);
+            const V r = reduce8_ordered(acc);
             if ((lane & 3) == 0 && 4 * g + (vidx & 3) < nv) {
                 if (vidx < 4) red_t[wid][kk + 4 * g + vidx] = r;
                 else red_s[wid][kk + 4 * g + vidx - 4] = r;
@@ -1198,16 +1243,9 @@ __global__ void __launch_bounds__(kBlock, HB ? 3 : 4) k_dots2(BatchArgs a, int i
         for (int b = max(0, issued - kRing); b < issued; ++b) mbar_wait(&full[b % kRing], (unsigned)(b / kRing) & 1u);
     }
     {
-        T al = (T)0;
-        V gg = mk((T)0, (T)0);
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) {
-            al += u[q].x * u[q].x + u[q].y * u[q].y;
-            cfmac(gg, u[q], z[q]);
-        }
-        al = block_sum_all(al, smt);
-        const T gr = block_sum_all(gg.x, smt);
-        const T gi = block_sum_all(gg.y, smt);
+        const T al = block_sum_all(al_p, smt);
+        const T gr = block_sum_all(gg_p.x, smt);
+        const T gi = block_sum_all(gg_p.y, smt);
         if (threadIdx.x == 0) {
             part[N + 2 * i] = mk(al, (T)0);
             part[N + 2 * i + 1] = mk(gr, gi);
