@@ -58,6 +58,12 @@ METRIC = "FDFD solves/s to rel-residual 1e-6 on 1 GB300: CNN-augmented vs plain 
 WAVELENGTHS = (1300e-9, 1550e-9)
 N_TRAIN_TRAJ, N_TEST_TRAJ, TRAJ_STEPS = 256, 16, 16
 N_VAL_TRAJ = 2          # the last training trajectories, kept apart for choosing restart policies
+# held-out trajectories per timed step: 2 x 16 permittivities x 2 wavelengths =
+# 64 solves in one lock-step batch (a step of 32 leaves more of its time to
+# the last few solves of its tail: 4.8 % fewer solves/s measured); 8 steps
+# are one pass over the 512 held-out solves
+TRAJ_PER_STEP = 2
+N_STEPS_PASS = N_TEST_TRAJ // TRAJ_PER_STEP
 POLICY_MARGIN = 0.03    # step saving a policy that keeps more columns must show to be chosen
 SEED_CONFIG = 3          # trajectory t of this workload: PCG64(1000 * 3 + t)
 
@@ -323,6 +329,11 @@ def splitter_grids():
     return [inputs.grid_for(256, 256, wavelength=lam) for lam in WAVELENGTHS]
 
 
+def step_traj(st: int):
+    """Held-out trajectories (offsets from the first held-out one) of timed step st."""
+    return [TRAJ_PER_STEP * st + j for j in range(TRAJ_PER_STEP)]
+
+
 def trajectory(t: int):
     """Permittivities of design trajectory t (16, 256, 256); the grid's
     wavelength does not enter the permittivity."""
@@ -391,24 +402,26 @@ def run_ours(args, rank, world):
                 train_ops[g.wavelength].append(ddg.fdfd_operator(g, ed))
     test_eps = [trajectory(N_TRAIN_TRAJ + t) for t in range(N_TEST_TRAJ)]
     test_ops, test_b, test_wl = [], [], []
-    for t in range(N_TEST_TRAJ):      # step t: trajectory t at both wavelengths (32 solves)
-        ops_t = [ddg.fdfd_operator(g, torch.as_tensor(e, device=dev)) for g in grids for e in test_eps[t]]
+    for st in range(N_STEPS_PASS):    # step st: trajectories step_traj(st) at both wavelengths (64 solves)
+        ops_t = [ddg.fdfd_operator(g, torch.as_tensor(e, device=dev))
+                 for g in grids for t in step_traj(st) for e in test_eps[t]]
         test_ops.append(ops_t)
         test_b.append([ddg.fdfd_source(op, *src) for op in ops_t])
-        test_wl.append([int(round(g.wavelength * 1e9)) for g in grids for _ in test_eps[t]])
+        test_wl.append([int(round(g.wavelength * 1e9)) for g in grids for t in step_traj(st) for _ in test_eps[t]])
     b_of = {lam: ddg.fdfd_source(train_ops[lam][0], *src) for lam in WAVELENGTHS}
     setup_s = time.time() - t0
 
     # the last N_VAL_TRAJ training trajectories are kept apart for choosing
     # the restart policies (neither the PCA fit nor the CNN's training sees
-    # them); validation step v = trajectory v at both wavelengths, in the
-    # order of a timed step
+    # them); a validation step holds TRAJ_PER_STEP of them at both
+    # wavelengths, in the order of a timed step
     n_val = N_VAL_TRAJ * TRAJ_STEPS
     val_steps = []
-    for v in range(N_VAL_TRAJ):
-        lo = len(train_ops[WAVELENGTHS[0]]) - n_val + v * TRAJ_STEPS
-        ops_v = [op for lam in WAVELENGTHS for op in train_ops[lam][lo:lo + TRAJ_STEPS]]
-        val_steps.append((ops_v, [b_of[lam] for lam in WAVELENGTHS for _ in range(TRAJ_STEPS)]))
+    for v0 in range(0, N_VAL_TRAJ, TRAJ_PER_STEP):
+        lo = len(train_ops[WAVELENGTHS[0]]) - n_val + v0 * TRAJ_STEPS
+        n_v = TRAJ_PER_STEP * TRAJ_STEPS
+        ops_v = [op for lam in WAVELENGTHS for op in train_ops[lam][lo:lo + n_v]]
+        val_steps.append((ops_v, [b_of[lam] for lam in WAVELENGTHS for _ in range(n_v)]))
     for lam in WAVELENGTHS:
         del train_ops[lam][-n_val:]
 
@@ -530,9 +543,10 @@ def run_ours(args, rank, world):
         return solve_plain(test_ops[t], test_b[t])
 
     def timed(step, K, W, start=0, profile=False, clocks=False):
-        """W untimed then K timed steps on held-out trajectories start, start+1, ...
-        (mod 16); CUDA events around the whole region and around each step."""
-        seq = [(start + q) % N_TEST_TRAJ for q in range(W + K)]
+        """W untimed then K timed steps start, start+1, ... (mod N_STEPS_PASS, each
+        TRAJ_PER_STEP held-out trajectories); CUDA events around the whole
+        region and around each step."""
+        seq = [(start + q) % N_STEPS_PASS for q in range(W + K)]
         for q in range(W):
             step(seq[q])
         if world > 1:
@@ -567,11 +581,12 @@ def run_ours(args, rank, world):
                     clocks=clk)
 
     def pass_of(r):
-        """The first 16 timed steps of r (every held-out trajectory once: the 512
-        solves): converged solves per second and the statistics per wavelength."""
-        steps = r["infos"][:N_TEST_TRAJ]
-        assert sorted(t for t, _ in steps) == list(range(N_TEST_TRAJ))
-        ms = float(sum(r["per_step"][:N_TEST_TRAJ]))
+        """The first N_STEPS_PASS timed steps of r (every held-out trajectory
+        once: the 512 solves): converged solves per second and the statistics
+        per wavelength."""
+        steps = r["infos"][:N_STEPS_PASS]
+        assert sorted(t for t, _ in steps) == list(range(N_STEPS_PASS))
+        ms = float(sum(r["per_step"][:N_STEPS_PASS]))
         flat = [i for _, inf in steps for i in inf]
         wl = [w for t, _ in steps for w in test_wl[t]]
         solved = int(sum(i["converged"] for i in flat))
@@ -579,7 +594,7 @@ def run_ours(args, rank, world):
                 **summarize(flat, wl)}
 
     def one_pass(step):
-        r = timed(step, N_TEST_TRAJ, 1)
+        r = timed(step, N_STEPS_PASS, 1)
         return pass_of(r), r
 
     K, W = args.steps, args.warmup
@@ -598,9 +613,10 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     predict_ms = e0.elapsed_time(e1)
 
-    # the CNN's pass over the 512 held-out solves: the first 16 timed steps
-    # when there are that many (they start at trajectory W mod 16 and go round)
-    cnn_pass = pass_of(head) if K >= N_TEST_TRAJ else one_pass(step_cnn)[0]
+    # the CNN's pass over the 512 held-out solves: the first N_STEPS_PASS
+    # timed steps when there are that many (they start at step W mod
+    # N_STEPS_PASS and go round)
+    cnn_pass = pass_of(head) if K >= N_STEPS_PASS else one_pass(step_cnn)[0]
     pca_pass = None
     if not args.no_pca:
         set_policy(pol_pca)
@@ -615,7 +631,8 @@ def run_ours(args, rank, world):
             x.zero_()
         _, inf_u, _ = ddg.gmres_solve_batched(ctx, test_ops[0], test_b[0], x=xs, tol=1e-6, restart=args.restart,
                                               maxit=20000, precision=args.precision)
-        plain_sample = {"trajectory": N_TRAIN_TRAJ, "maxit": 20000, **summarize(inf_u, test_wl[0])}
+        plain_sample = {"trajectories": [N_TRAIN_TRAJ + t for t in step_traj(0)], "maxit": 20000,
+                        **summarize(inf_u, test_wl[0])}
 
     levers = None
     if args.levers:
@@ -677,8 +694,8 @@ def run_ours(args, rank, world):
 
     set_policy(pol_cnn)
 
-    def step_e2e(t):
-        ep = [eps_host[t][j] for _ in grids for j in range(n_step // len(grids))]
+    def step_e2e(st):
+        ep = [eps_host[t][j] for _ in grids for t in step_traj(st) for j in range(TRAJ_STEPS)]
         inf, st_ = ddg.fdfd_solve_host(ctx, e2e_grids, ep, src, x_host, P=P, U_fixed=U_pca_step, **kw)
         return None, inf, st_
 
@@ -704,8 +721,9 @@ def run_ours(args, rank, world):
                                "wavelengths) to rel. residual 1e-6, cap 5000; plain and PCA-20 GMRES alongside",
                    "grid": "256x256", "dx_nm": 40, "wavelengths_nm": [1300, 1550], "npml": 10,
                    "restart": args.restart, "tol": 1e-6, "maxit": args.maxit, "solves_per_step": n_step,
-                   "step": "one held-out trajectory (16 permittivities) at both wavelengths; steps go round "
-                           "the 16 held-out trajectories",
+                   "step": f"{TRAJ_PER_STEP} held-out trajectories ({TRAJ_PER_STEP * TRAJ_STEPS} permittivities) "
+                           f"at both wavelengths, one batched solve; steps go round the {N_TEST_TRAJ} held-out "
+                           f"trajectories ({N_STEPS_PASS} steps per pass)",
                    "predictor": f"cnn k={args.cnn_k} (6 levels, 32-128 channels, bf16 weights and activations, "
                                 "FP32 accumulation; inputs eps, wavelength, PML mask, source; output offset = "
                                 "the k leading PCs of the solved training fields of each wavelength; output "
@@ -720,7 +738,8 @@ def run_ours(args, rank, world):
                                             "f16": "IEEE half (arithmetic FP32, true residual FP64)"}[args.basis],
                    "training_problems": 2 * (N_TRAIN_TRAJ - N_VAL_TRAJ) * TRAJ_STEPS,
                    "validation_problems": 2 * N_VAL_TRAJ * TRAJ_STEPS,
-                   "l2": "no flush: the per-step working set (32 Krylov bases of 105 MB) exceeds the 129 MB L2",
+                   "l2": f"no flush: the per-step working set ({n_step} Krylov bases of 105 MB) exceeds the "
+                         "129 MB L2",
                    "parallelism": f"replicas x{world}",
                    "solve_loop": ("one CUDA graph launch per batched solve (restart cycles and Arnoldi steps "
                                   "under device-side WHILE/IF nodes)") if args.graphs == "on" else "host-launched"},
@@ -1060,8 +1079,9 @@ def oracle_sample_spec(P, U_base, test_eps, grids, flat, wl, step_infos, U_pca=N
     1550 nm, and the GPU's restart cycles for the sampled problem (the first
     held-out permittivity at 1550 nm) to scale the sample."""
     lam = WAVELENGTHS[1]
-    t0, inf0 = step_infos[0]
-    j = len(test_eps[0])          # first 1550 nm solve of the step (the 1300 nm ones come first)
+    st0, inf0 = step_infos[0]
+    t0 = step_traj(st0)[0]
+    j = TRAJ_PER_STEP * len(test_eps[0])   # first 1550 nm solve of the step (the 1300 nm ones come first)
     spec = {"theta": P.get_params(), "channels": P.channels, "k": P.k,
             "base": U_base[lam][: P.k].cpu().numpy(), "eps": test_eps[t0][0], "grid": grids[1],
             "gpu_cycles": int(inf0[j]["cycles"]), "gpu_iters": int(inf0[j]["iters"])}
