@@ -1073,71 +1073,112 @@ def run_batched(args, rank, world):
 
 
 # ------------------------------------------------------------------ oracle (CPU)
-def oracle_sample_spec(P, U_base, test_eps, grids, flat, wl, step_infos, U_pca=None, policy=None):
+def oracle_sample_spec(P, U_base, test_eps, grids, flat, wl, step_infos, U_pca=None, policy=None, per_wl=8):
     """What the CPU baseline needs from the GPU run: the trained weights, the
-    output offset of 1550 nm, the headline's PCA rows and restart policy at
-    1550 nm, and the GPU's restart cycles for the sampled problem (the first
-    held-out permittivity at 1550 nm) to scale the sample."""
-    lam = WAVELENGTHS[1]
+    output offset, PCA rows and restart policy of each wavelength, and the
+    sampled problems (the first `per_wl` permittivities of the first timed
+    step at each wavelength) with the restart cycles and steps their GPU
+    solves needed, to scale the sample."""
     st0, inf0 = step_infos[0]
     t0 = step_traj(st0)[0]
-    j = TRAJ_PER_STEP * len(test_eps[0])   # first 1550 nm solve of the step (the 1300 nm ones come first)
+    n_wl = TRAJ_PER_STEP * len(test_eps[0])      # solves of one wavelength in a step (1300 nm first)
     spec = {"theta": P.get_params(), "channels": P.channels, "k": P.k,
-            "base": U_base[lam][: P.k].cpu().numpy(), "eps": test_eps[t0][0], "grid": grids[1],
-            "gpu_cycles": int(inf0[j]["cycles"]), "gpu_iters": int(inf0[j]["iters"])}
+            "base": {g.wavelength: U_base[g.wavelength][: P.k].cpu().numpy() for g in grids},
+            "problems": [{"eps": test_eps[t0][j], "grid": g, "gpu_cycles": int(inf0[w * n_wl + j]["cycles"]),
+                          "gpu_iters": int(inf0[w * n_wl + j]["iters"])}
+                         for w, g in enumerate(grids) for j in range(per_wl)]}
     if U_pca is not None:
-        spec["pca"] = U_pca[lam].cpu().numpy()             # (k_pca, D)
+        spec["pca"] = {g.wavelength: U_pca[g.wavelength].cpu().numpy() for g in grids}   # (k_pca, D) each
     if policy is not None:
-        spec["policy"] = tuple(int(v) for v in policy[lam])
+        spec["policy"] = {g.wavelength: tuple(int(v) for v in policy[g.wavelength]) for g in grids}
     return spec
 
 
-def oracle_cnn_subspace(spec):
-    """The headline variant's subspace for the sampled problem, computed by the
-    oracle: [PCA-20 rows | its fp64 forward pass of the trained weights plus
-    the offset] (the CNN part alone without PCA rows in the spec)."""
+def oracle_cnn_subspace(spec, prob):
+    """The headline variant's subspace for one sampled problem, computed by the
+    oracle: [PCA rows of its wavelength | its fp64 forward pass of the trained
+    weights plus the offset] (the CNN part alone without PCA rows in the spec)."""
     from oracle import cnn as ocnn
-    g = spec["grid"]
+    g = prob["grid"]
     cfg = ocnn.CNNConfig(cin=4, channels=tuple(spec["channels"]), k=spec["k"])
-    x = ocnn.input_channels(spec["eps"], g.wavelength, g.npml, g.i_src, g.sigma_src, g.j_src)[None]
+    x = ocnn.input_channels(prob["eps"], g.wavelength, g.npml, g.i_src, g.sigma_src, g.j_src)[None]
     y = ocnn.forward(cfg, spec["theta"].astype(np.float64), x)
     V = ocnn.to_complex_fields(y)[0]                       # (D, k)
-    V = V + np.sqrt(g.D) * spec["base"].T
+    V = V + np.sqrt(g.D) * spec["base"][g.wavelength].T
     if "pca" in spec:
-        V = np.concatenate([spec["pca"].T, V], axis=1)
+        V = np.concatenate([spec["pca"][g.wavelength].T, V], axis=1)
     return V
 
 
-def cpu_baseline(args, spec, cycles=2):
-    """The oracle (numpy/scipy complex128, every host core) on a bounded sample:
-    the first `cycles` restart cycles of one held-out solve of the headline
-    variant (1550 nm: the subspace [PCA-20 | CNN-8] from the oracle's own CNN
-    forward pass of the trained weights, the headline's restart policy at that
-    wavelength), scaled to a whole solve by the restart cycles the GPU needed
-    for that problem."""
+def _oracle_job(job):
+    """One sampled problem in a worker process: the oracle's subspace and
+    `cycles` restart cycles of its augmented GMRES; (prediction s, solve s,
+    cycles run, first-step residual)."""
     from oracle import fdfd, gmres
-    g = spec["grid"]
-    A = fdfd.operator_for(g, spec["eps"])
+    spec, prob, restart, cycles = job
+    g = prob["grid"]
+    A = fdfd.operator_for(g, prob["eps"])
     b = fdfd.source_for(g)
     t0 = time.time()
-    V = oracle_cnn_subspace(spec)
+    V = oracle_cnn_subspace(spec, prob)
     t_pred = time.time() - t0
-    cyc, keep = spec.get("policy", (10**6, V.shape[1]))
+    cyc, keep = spec.get("policy", {}).get(g.wavelength, (10**6, V.shape[1]))
     t0 = time.time()
-    x, info = gmres.augmented_gmres(A, b, V, tol=1e-6, restart=args.restart, maxit=cycles * args.restart,
+    _, info = gmres.augmented_gmres(A, b, V, tol=1e-6, restart=restart, maxit=cycles * restart,
                                     aug_cycles=cyc, aug_keep=keep)
-    t_solve = time.time() - t0
-    per_cycle = t_solve / max(1, info.cycles)
-    sec_per_solve = t_pred + per_cycle * spec["gpu_cycles"]
-    sub = f"[PCA-{spec['pca'].shape[0]} | CNN-{spec['k']}]" if "pca" in spec else f"CNN-{spec['k']}"
-    return {"value": round(1.0 / sec_per_solve, 6), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"1 held-out 256x256 solve at 1550 nm, augmented GMRES({args.restart}) with the headline's "
-                      f"subspace {sub} (the trained network's fp64 forward pass, {t_pred:.1f} s) and restart "
-                      f"policy (all columns for {cyc} cycle(s), then {keep} kept), {info.cycles} restart cycles "
-                      f"({info.iters} Arnoldi steps, {t_solve:.1f} s, complex128 numpy/scipy), scaled to the "
-                      f"{spec['gpu_cycles']} cycles ({spec['gpu_iters']} steps) the GPU solve needed; BLAS threads "
-                      f"= os.cpu_count() = {os.cpu_count()}",
-            "oracle_first_step_rel_residual": float(info.first_step_rel_residual)}
+    return t_pred, time.time() - t0, int(info.cycles), float(info.first_step_rel_residual)
+
+
+def cpu_baseline(args, spec, cycles=1, procs=None):
+    """The oracle (numpy/scipy complex128) on every host core, on a bounded
+    sample: the sampled held-out problems of the headline variant (the
+    subspace [PCA rows | CNN-k] from the oracle's own fp64 forward pass of the
+    trained weights, the restart policy of each problem's wavelength), each in
+    a process of its own with one BLAS thread, all at once; each runs its
+    first `cycles` restart cycles, scaled to a whole solve by the restart
+    cycles its GPU solve needed.  Solves/s = processes / mean seconds per
+    solve (each core working through solves one after another).  The pool is
+    started with spawn (this process has a CUDA context)."""
+    import multiprocessing as mp
+    probs = spec["problems"]
+    nproc = max(1, min(len(probs), procs or os.cpu_count() or 1))
+    shared = {k: v for k, v in spec.items() if k != "problems"}
+    jobs = [({**shared, "base": {p["grid"].wavelength: shared["base"][p["grid"].wavelength]},
+              **({"pca": {p["grid"].wavelength: shared["pca"][p["grid"].wavelength]}} if "pca" in shared else {})},
+             p, args.restart, cycles) for p in probs]
+    saved = {v: os.environ.get(v) for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for v in saved:
+        os.environ[v] = "1"      # inherited by the spawned workers before they load numpy
+    try:
+        t0 = time.time()
+        with mp.get_context("spawn").Pool(nproc) as pool:
+            res = pool.map(_oracle_job, jobs, chunksize=1)
+        wall = time.time() - t0
+    finally:
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+    sec = [tp + ts / max(1, c) * p["gpu_cycles"] for (tp, ts, c, _), p in zip(res, probs)]
+    mean_sec = float(np.mean(sec))
+    per_cycle = float(np.mean([ts / max(1, c) for _, ts, c, _ in res]))
+    n_wl = len({p["grid"].wavelength for p in probs})
+    sub = (f"[PCA-{next(iter(spec['pca'].values())).shape[0]} | CNN-{spec['k']}]" if "pca" in spec
+           else f"CNN-{spec['k']}")
+    pol = "; ".join(f"{int(round(l * 1e9))} nm: all columns for {c} cycle(s), then {k} kept"
+                    for l, (c, k) in sorted(spec.get("policy", {}).items()))
+    return {"value": round(nproc / mean_sec, 6), "unit": "solves/s", "cores": nproc, "kind": "oracle",
+            "sample": f"{len(probs)} held-out {probs[0]['grid'].nx}x{probs[0]['grid'].ny} solves "
+                      f"({len(probs) // n_wl} per wavelength, the first permittivities of the first timed step), "
+                      f"augmented GMRES({args.restart}) with the headline's subspace {sub} (the trained network's "
+                      f"fp64 forward pass) and restart policy ({pol}), {cycles} restart cycle(s) each "
+                      f"({per_cycle:.1f} s per cycle on average, complex128 numpy/scipy), scaled to the "
+                      f"{np.mean([p['gpu_cycles'] for p in probs]):.1f} cycles "
+                      f"({np.mean([p['gpu_iters'] for p in probs]):.0f} steps) their GPU solves needed on "
+                      f"average; {nproc} spawned processes with one BLAS thread each, all at once "
+                      f"({wall:.1f} s wall); solves/s = processes / mean seconds per solve",
+            "oracle_first_step_rel_residual": round(float(np.mean([r[3] for r in res])), 5)}
 
 
 def run_reference(args, rank, world):

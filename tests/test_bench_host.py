@@ -67,22 +67,30 @@ def test_policy_choice_needs_a_margin_to_keep_more_columns():
 
 def test_cpu_baseline_runs_the_headline_subspace_and_policy():
     # The CPU baseline's oracle sample uses the headline variant's subspace
-    # [PCA rows | CNN-k] and its restart policy (a tiny network on a 32x32 grid).
+    # [PCA rows | CNN-k] and the restart policy of each problem's wavelength
+    # (a tiny network on a 32x32 grid), one spawned single-thread process per
+    # sampled problem.
     import numpy as np
     from types import SimpleNamespace
     from oracle import cnn as ocnn
     from paper_1902_00090_gb300 import inputs
-    g = inputs.Grid(nx=32, ny=32, npml=4, i_src=6, sigma_src=3.0, slab_cells=2, wavelength=1550e-9)
+    grids = [inputs.Grid(nx=32, ny=32, npml=4, i_src=6, sigma_src=3.0, slab_cells=2, wavelength=lam)
+             for lam in (1300e-9, 1550e-9)]
     channels, k = (4, 4, 4, 4, 4, 4), 2
     cfg = ocnn.CNNConfig(cin=4, channels=channels, k=k)
     n = ocnn.num_params(cfg)
     rng = np.random.default_rng(0)
-    pca = np.linalg.qr(rng.standard_normal((g.D, 3)) + 1j * rng.standard_normal((g.D, 3)))[0].T
+    D = grids[0].D
+    pca = {g.wavelength: np.linalg.qr(rng.standard_normal((D, 3)) + 1j * rng.standard_normal((D, 3)))[0].T
+           for g in grids}
     spec = {"theta": 0.1 * rng.standard_normal(n).astype(np.float32), "channels": channels, "k": k,
-            "base": np.zeros((k, g.D), dtype=np.complex128), "eps": inputs.bernoulli_eps(g, 0), "grid": g,
-            "gpu_cycles": 3, "gpu_iters": 90, "pca": pca, "policy": (1, 0)}
-    V = bench.oracle_cnn_subspace(spec)
-    assert V.shape == (g.D, 3 + k) and np.array_equal(V[:, :3], pca.T)
-    r = bench.cpu_baseline(SimpleNamespace(restart=30), spec, cycles=2)
-    assert r["kind"] == "oracle" and r["value"] > 0
-    assert "[PCA-3 | CNN-2]" in r["sample"] and "all columns for 1 cycle(s), then 0 kept" in r["sample"]
+            "base": {g.wavelength: np.zeros((k, D), dtype=np.complex128) for g in grids},
+            "pca": pca, "policy": {1300e-9: (10**6, 3), 1550e-9: (1, 0)},
+            "problems": [{"eps": inputs.bernoulli_eps(g, j), "grid": g, "gpu_cycles": 3, "gpu_iters": 90}
+                         for g in grids for j in range(2)]}
+    V = bench.oracle_cnn_subspace(spec, spec["problems"][2])
+    assert V.shape == (D, 3 + k) and np.array_equal(V[:, :3], pca[1550e-9].T)
+    r = bench.cpu_baseline(SimpleNamespace(restart=30), spec, cycles=2, procs=2)
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] == 2
+    assert "[PCA-3 | CNN-2]" in r["sample"] and "1550 nm: all columns for 1 cycle(s), then 0 kept" in r["sample"]
+    assert "4 held-out 32x32 solves (2 per wavelength" in r["sample"]
