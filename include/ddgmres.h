@@ -216,7 +216,7 @@ ddg_status ddg_context_set_inner_tol(ddg_context* ctx, double eta);
  * i.e. Eq. 1 times h^2, with stretch s(p) = 1 - i smax (d(p)/L)^m at integer
  * nodes (sxb) and half nodes p = i + 1/2 (sxf), d(p) the depth into the PML in
  * cells, smax = -(m+1) ln(R) / (2 k0 h L).
- *   g    (host)  grid description; nx, ny >= 3; 0 <= npml <= n/2; R in (0,1).
+ *   g    (host)  grid description; nx, ny >= 3; nx*ny < 2^31; 0 <= npml <= n/2; R in (0,1).
  *   eps  device, ny*nx doubles, row-major; every value finite and > 0, else DDG_EINVAL.
  *   A    (host)  receives the new handle; the operator keeps its own copy of eps.
  * Synchronises `stream` (the eps check reads back one flag).

@@ -77,11 +77,14 @@ __device__ __forceinline__ bool arrive_last(unsigned* ticket, int n) {
 }
 
 // 5-point stencil of A at cell e; ld(idx) returns the input vector at idx.
+// The cell's row and column come from 32-bit division: fdfd_operator accepts
+// no grid of 2^31 cells or more.
 template <typename V, typename S, typename LD>
 __device__ __forceinline__ V stencil(long long e, int nx, int ny, const V* __restrict__ coef, S kh2eps,
                                      const LD& ld) {
-    const int j = (int)(e / nx);
-    const int i = (int)(e - (long long)j * nx);
+    const unsigned eu = (unsigned)e;
+    const int j = (int)(eu / (unsigned)nx);
+    const int i = (int)(eu - (unsigned)j * (unsigned)nx);
     const V axp = coef[i], axm = coef[nx + i];
     const V ayp = coef[2 * nx + j], aym = coef[2 * nx + ny + j];
     const long long ip = (i == nx - 1) ? e - (nx - 1) : e + 1;
@@ -775,17 +778,19 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 }
 template <typename T> struct DotPairs;
 template <> struct DotPairs<float> {
-    float2 zx, zy, nzx, ux, uy, nux;
+    // each element m = (mr, mi) is used as it is stored, an aligned register
+    // pair: (mr, mi) * (zr, zi) gives the terms of Re(conj(m) z) and
+    // (mr, mi) * (zi, -zr) those of Im(conj(m) z)
+    float2 z0, z1, zs0, zs1, u0, u1, us0, us1;
     __device__ __forceinline__ DotPairs(const float2 (&z)[2], const float2 (&u)[2])
-        : zx(make_float2(z[0].x, z[1].x)), zy(make_float2(z[0].y, z[1].y)), nzx(make_float2(-z[0].x, -z[1].x)),
-          ux(make_float2(u[0].x, u[1].x)), uy(make_float2(u[0].y, u[1].y)), nux(make_float2(-u[0].x, -u[1].x)) {}
+        : z0(z[0]), z1(z[1]), zs0(make_float2(z[0].y, -z[0].x)), zs1(make_float2(z[1].y, -z[1].x)),
+          u0(u[0]), u1(u[1]), us0(make_float2(u[0].y, -u[0].x)), us1(make_float2(u[1].y, -u[1].x)) {}
     __device__ __forceinline__ void dots(const float2 (&m)[2], float2& t, float2& s) const {
-        const float2 mx = make_float2(m[0].x, m[1].x), my = make_float2(m[0].y, m[1].y);
         const float2 zero = make_float2(0.f, 0.f);
-        const float2 tr = fma2(my, zy, fma2(mx, zx, zero));    // sum of Re(conj(m) z) terms
-        const float2 ti = fma2(my, nzx, fma2(mx, zy, zero));   // sum of Im(conj(m) z) terms
-        const float2 sr = fma2(my, uy, fma2(mx, ux, zero));
-        const float2 si = fma2(my, nux, fma2(mx, uy, zero));
+        const float2 tr = fma2(m[1], z1, fma2(m[0], z0, zero));     // terms of Re(conj(m) z)
+        const float2 ti = fma2(m[1], zs1, fma2(m[0], zs0, zero));   // terms of Im(conj(m) z)
+        const float2 sr = fma2(m[1], u1, fma2(m[0], u0, zero));
+        const float2 si = fma2(m[1], us1, fma2(m[0], us0, zero));
         t = make_float2(tr.x + tr.y, ti.x + ti.y);
         s = make_float2(sr.x + sr.y, si.x + si.y);
     }

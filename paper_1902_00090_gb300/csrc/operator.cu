@@ -238,6 +238,10 @@ extern "C" ddg_status fdfd_operator(const ddg_grid* g, const double* eps, ddg_op
                   g->ny, g->npml_x, g->npml_y, g->dx, g->wavelength, g->pml_order, g->pml_R);
         return DDG_EINVAL;
     }
+    if ((long long)g->nx * g->ny >= (1ll << 31)) {   // the kernels index cells with 32-bit division
+        set_error("fdfd_operator: nx*ny = %lld cells, at most 2^31 - 1", (long long)g->nx * g->ny);
+        return DDG_EINVAL;
+    }
     cudaStream_t s = as_stream(stream);
     ddg_op* A = new (std::nothrow) ddg_op();
     if (!A) return DDG_ENOMEM;

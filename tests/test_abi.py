@@ -59,6 +59,11 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     g = binding.ddg_grid(2, 2, 1e-8, 1.55e-6, 0, 0, 3.0, 1e-8)
     h = ctypes.c_void_p()
     assert L.fdfd_operator(ctypes.byref(g), ctypes.c_void_p(16), ctypes.byref(h), None) == 1
+    # grids of 2^31 cells or more are refused before any allocation (the
+    # kernels find a cell's row and column by 32-bit division)
+    g = binding.ddg_grid(65536, 32768, 1e-8, 1.55e-6, 0, 0, 3.0, 1e-8)
+    assert L.fdfd_operator(ctypes.byref(g), ctypes.c_void_p(16), ctypes.byref(h), None) == 1
+    assert b"2^31" in L.ddg_last_error()
 
 
 def test_context_setters_reject_null_and_bad_kinds(lib):
