@@ -1589,30 +1589,49 @@ __global__ void __launch_bounds__(kBlock) k_aug_av(BatchArgs a) {
 // solve as rank deficient: it then runs as plain GMRES (N = 0, fallback = 1).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_aug_gram(BatchArgs a, int pass) {
-    constexpr int VEC = vec_of<T>();
     SOLVE_PROLOGUE();
     const int N = S->N;
     if (N == 0) return;
     const long long ld = P.ld;
-    const long long e0 = (long long)chunk * chunk_rows<T>() + (long long)threadIdx.x * VEC;
-    __shared__ double2 red[kWarps];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double2* part = P.part + (long long)chunk * a.KP;
-    for (int p = 0; p < N; ++p)
-        for (int q = p; q < N; ++q) {
-            double2 acc = make_double2(0.0, 0.0);
+    // The chunk's rows of W pass through shared memory in tiles of kTR rows;
+    // each thread owns up to kSlots pairs (p <= q) of the Gram matrix and
+    // accumulates them over the whole chunk (the FP64 products are the cost:
+    // N(N+1)/2 complex MACs per row, with no block barrier per pair).
+    constexpr int kTR = 32;
+    constexpr int kSlots = (kMaxAug * (kMaxAug + 1) / 2 + kBlock - 1) / kBlock;
+    __shared__ double2 tile[kTR][kMaxAug + 1];
+    const int npairs = N * (N + 1) / 2;
+    int pp[kSlots], qq[kSlots];
+    double2 acc[kSlots];
 #pragma unroll
-            for (int t = 0; t < VEC; ++t) cfmac(acc, P.W[(long long)p * ld + e0 + t], P.W[(long long)q * ld + e0 + t]);
-            acc = warp_sum(acc);
-            __syncthreads();
-            if (lane == 0) red[wid] = acc;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double2 t = make_double2(0.0, 0.0);
-                for (int w = 0; w < kWarps; ++w) t = cadd(t, red[w]);
-                part[p * N + q] = t;
-            }
+    for (int k = 0; k < kSlots; ++k) {
+        acc[k] = make_double2(0.0, 0.0);
+        int idx = threadIdx.x + k * kBlock, p = 0;
+        if (idx < npairs)
+            while (idx >= N - p) idx -= N - p++;   // pairs in row-major order of the upper triangle
+        pp[k] = p;
+        qq[k] = p + idx;                          // meaningful only when the pair exists
+    }
+    const long long r0 = (long long)chunk * chunk_rows<T>();
+    for (int rt = 0; rt < (int)chunk_rows<T>(); rt += kTR) {
+        for (int idx = threadIdx.x; idx < kTR * N; idx += kBlock) {
+            const int n = idx / kTR, r = idx - n * kTR;   // consecutive threads: consecutive rows of a column
+            tile[r][n] = P.W[(long long)n * ld + r0 + rt + r];
         }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k)
+            if (threadIdx.x + k * kBlock < npairs) {
+                const int p = pp[k], q = qq[k];
+#pragma unroll 8
+                for (int r = 0; r < kTR; ++r) cfmac(acc[k], tile[r][p], tile[r][q]);
+            }
+        __syncthreads();
+    }
+    double2* part = P.part + (long long)chunk * a.KP;
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k)
+        if (threadIdx.x + k * kBlock < npairs) part[pp[k] * N + qq[k]] = acc[k];
     if (!arrive_last(P.ticket, P.nchunks)) return;
     double2* G = P.hp;  // N x N, column-major, upper triangle used
     for (int idx = threadIdx.x; idx < N * N; idx += kBlock) {
