@@ -377,6 +377,39 @@ def summarize(infos, wl_of=None):
     return out
 
 
+def headline_config(args, world):
+    """The `config` object of the headline workload (both arms print it)."""
+    n_step = len(WAVELENGTHS) * TRAJ_PER_STEP * TRAJ_STEPS
+    return {
+        "workload": "splitter256: CNN-augmented GMRES(200) (subspace [PCA-20 | CNN-8], one network for both "
+                    "wavelengths, residual-loss training on 8128 problems), 256x256 Yee grid at 40 nm, 1300 and "
+                    "1550 nm, 512 held-out solves (16 trajectories x 16 steps x 2 wavelengths) to rel. residual "
+                    "1e-6, cap 5000; plain and PCA-20 GMRES alongside",
+        "grid": "256x256", "dx_nm": 40, "wavelengths_nm": [1300, 1550], "npml": 10,
+        "restart": args.restart, "tol": 1e-6, "maxit": args.maxit, "solves_per_step": n_step,
+        "step": f"{TRAJ_PER_STEP} held-out trajectories ({TRAJ_PER_STEP * TRAJ_STEPS} permittivities) at both "
+                f"wavelengths, one batched solve; steps go round the {N_TEST_TRAJ} held-out trajectories "
+                f"({N_STEPS_PASS} steps per pass)",
+        "predictor": f"cnn k={args.cnn_k} (6 levels, 32-128 channels, bf16 weights and activations, FP32 "
+                     "accumulation; inputs eps, wavelength, PML mask, source; output offset = the k leading PCs "
+                     "of the solved training fields of each wavelength; output orthonormalised on the device)",
+        "restart_policy": "per wavelength, chosen on two validation trajectories (fewest steps; a policy keeping "
+                          "more columns must save 3 %) among: all 28 vectors in the first cycle then plain GMRES "
+                          "/ then the PCA-20 columns kept / all kept (cnn.policy); V-only residual > 0.5 -> its "
+                          "step, then plain",
+        "precision": "complex64 Arnoldi and matvecs, FP64 true residual, Givens, least squares and x (refinement "
+                     "every restart)" if args.precision == "c64" else "complex128",
+        "krylov_basis_storage": {"f32": "FP32 (complex64)",
+                                 "f16": "IEEE half (arithmetic FP32, true residual FP64)"}[args.basis],
+        "training_problems": 2 * (N_TRAIN_TRAJ - N_VAL_TRAJ) * TRAJ_STEPS,
+        "validation_problems": 2 * N_VAL_TRAJ * TRAJ_STEPS,
+        "l2": f"no flush: the per-step working set ({n_step} Krylov bases of 105 MB) exceeds the 129 MB L2",
+        "parallelism": f"replicas x{world}",
+        "solve_loop": ("one CUDA graph launch per batched solve (restart cycles and Arnoldi steps under "
+                       "device-side WHILE/IF nodes)") if args.graphs == "on" else "host-launched",
+    }
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_1902_00090_gb300 as ddg
@@ -714,35 +747,7 @@ def run_ours(args, rank, world):
         "warmup": W, "ms_per_step": round(head["ms"] / K, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64+f64" if args.precision == "c64" else "c128",
         "data": "synthetic",
-        "config": {"workload": "splitter256: CNN-augmented GMRES(200) (subspace [PCA-20 | CNN-8], one network "
-                               "for both wavelengths, residual-loss training on 8128 problems), 256x256 Yee grid "
-                               "at 40 nm, "
-                               "1300 and 1550 nm, 512 held-out solves (16 trajectories x 16 steps x 2 "
-                               "wavelengths) to rel. residual 1e-6, cap 5000; plain and PCA-20 GMRES alongside",
-                   "grid": "256x256", "dx_nm": 40, "wavelengths_nm": [1300, 1550], "npml": 10,
-                   "restart": args.restart, "tol": 1e-6, "maxit": args.maxit, "solves_per_step": n_step,
-                   "step": f"{TRAJ_PER_STEP} held-out trajectories ({TRAJ_PER_STEP * TRAJ_STEPS} permittivities) "
-                           f"at both wavelengths, one batched solve; steps go round the {N_TEST_TRAJ} held-out "
-                           f"trajectories ({N_STEPS_PASS} steps per pass)",
-                   "predictor": f"cnn k={args.cnn_k} (6 levels, 32-128 channels, bf16 weights and activations, "
-                                "FP32 accumulation; inputs eps, wavelength, PML mask, source; output offset = "
-                                "the k leading PCs of the solved training fields of each wavelength; output "
-                                "orthonormalised on the device)",
-                   "restart_policy": "per wavelength, chosen on two validation trajectories (fewest steps; a policy "
-                                     "keeping more columns must save 3 %) among: all 28 vectors in "
-                                     "the first cycle then plain GMRES / then the PCA-20 columns kept / all kept "
-                                     "(cnn.policy); V-only residual > 0.5 -> its step, then plain",
-                   "precision": "complex64 Arnoldi and matvecs, FP64 true residual, Givens, least squares and x "
-                                "(refinement every restart)" if args.precision == "c64" else "complex128",
-                   "krylov_basis_storage": {"f32": "FP32 (complex64)",
-                                            "f16": "IEEE half (arithmetic FP32, true residual FP64)"}[args.basis],
-                   "training_problems": 2 * (N_TRAIN_TRAJ - N_VAL_TRAJ) * TRAJ_STEPS,
-                   "validation_problems": 2 * N_VAL_TRAJ * TRAJ_STEPS,
-                   "l2": f"no flush: the per-step working set ({n_step} Krylov bases of 105 MB) exceeds the "
-                         "129 MB L2",
-                   "parallelism": f"replicas x{world}",
-                   "solve_loop": ("one CUDA graph launch per batched solve (restart cycles and Arnoldi steps "
-                                  "under device-side WHILE/IF nodes)") if args.graphs == "on" else "host-launched"},
+        "config": headline_config(args, world),
         "cnn": {**summarize(flat, wl), "subspace": f"[PCA-{args.k} of the wavelength | CNN-{args.cnn_k}]",
                 "policy": rep_cnn, "pass": cnn_pass, "predict_ms_per_step": round(predict_ms, 2),
                 "train_s": round(cnn_s, 1), "loss": "Eq. 6 (residual)", "train_steps": args.cnn_steps,
@@ -1223,15 +1228,14 @@ def run_reference(args, rank, world):
     v = 1.0 / (per_cycle * need)
     cb = {"value": round(v, 6), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
           "sample": f"each step: one GMRES({args.restart}) restart cycle of a held-out 256x256 1550 nm solve "
-                    f"augmented by k={args.k} PCs of 8 oracle-solved training fields (complex128 numpy/scipy, "
+                    f"augmented by k={args.k} PCs of 8 oracle-solved training fields (the workload's PCA variant: "
+                    f"the trained CNN exists only in the GPU arm's run; complex128 numpy/scipy, "
                     f"{per_cycle:.2f} s per cycle), scaled by {need} cycles per solve ({how}); BLAS threads = "
                     f"os.cpu_count() = {os.cpu_count()}"}
     return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_cycle * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": "splitter256 (oracle sample, PCA variant)",
-                                              "grid": "256x256", "wavelengths_nm": [1300, 1550],
-                                              "restart": args.restart, "tol": 1e-6, "maxit": args.maxit},
+            "data": "synthetic", "config": headline_config(args, world),
             "cpu_baseline": cb,
             "e2e": {"value": round(v, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
