@@ -94,3 +94,58 @@ def test_cpu_baseline_runs_the_headline_subspace_and_policy():
     assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] == 2
     assert "[PCA-3 | CNN-2]" in r["sample"] and "1550 nm: all columns for 1 cycle(s), then 0 kept" in r["sample"]
     assert "4 held-out 32x32 solves (2 per wavelength" in r["sample"]
+
+
+def test_timed_steps_cover_the_held_out_set_once_per_pass():
+    # one pass of timed steps holds every held-out trajectory exactly once
+    trajs = [t for st in range(bench.N_STEPS_PASS) for t in bench.step_traj(st)]
+    assert sorted(trajs) == list(range(bench.N_TEST_TRAJ))
+    assert len(bench.step_traj(0)) == bench.TRAJ_PER_STEP
+
+
+def test_headline_config_names_the_step_it_times():
+    import sys
+    argv = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        args = bench.parse()
+    finally:
+        sys.argv = argv
+    cfg = bench.headline_config(args, 1)
+    n = len(bench.WAVELENGTHS) * bench.TRAJ_PER_STEP * bench.TRAJ_STEPS
+    assert cfg["solves_per_step"] == n and f"{n} Krylov bases" in cfg["l2"]
+    assert cfg["restart"] == 200 and cfg["tol"] == 1e-6 and cfg["maxit"] == 5000
+    assert cfg["krylov_basis_storage"] == "FP32 (complex64)"
+    assert bench.headline_config(args, 2)["parallelism"] == "replicas x2"
+
+
+def test_oracle_sample_takes_the_first_problems_of_each_wavelength():
+    # The CPU baseline samples the first permittivities of the first timed
+    # step at each wavelength (1300 nm solves come first in a step) and keeps
+    # the GPU's restart cycles of exactly those solves.
+    import numpy as np
+    import torch
+    from types import SimpleNamespace
+    from paper_1902_00090_gb300 import inputs
+    grids = [inputs.Grid(nx=8, ny=8, npml=2, i_src=2, sigma_src=1.0, slab_cells=2, wavelength=lam)
+             for lam in bench.WAVELENGTHS]
+    test_eps = [np.full((bench.TRAJ_STEPS, 8, 8), float(t)) + np.arange(bench.TRAJ_STEPS)[:, None, None] / 100
+                for t in range(bench.N_TEST_TRAJ)]
+    n_step = len(grids) * bench.TRAJ_PER_STEP * bench.TRAJ_STEPS
+    infos = [{"cycles": i, "iters": 10 * i} for i in range(n_step)]
+    P = SimpleNamespace(get_params=lambda: np.zeros(3, np.float32), channels=(4,) * 6, k=2)
+    U = {g.wavelength: torch.zeros((5, 64), dtype=torch.complex128) for g in grids}
+    st0 = 3
+    spec = bench.oracle_sample_spec(P, U, test_eps, grids, None, None, [(st0, infos)], U_pca=U,
+                                    policy={g.wavelength: (1, 0) for g in grids}, per_wl=4)
+    probs = spec["problems"]
+    assert len(probs) == 8
+    t0 = bench.step_traj(st0)[0]
+    n_wl = bench.TRAJ_PER_STEP * bench.TRAJ_STEPS
+    for w, g in enumerate(grids):
+        for j in range(4):
+            p = probs[w * 4 + j]
+            assert p["grid"].wavelength == g.wavelength
+            assert p["gpu_cycles"] == w * n_wl + j and p["gpu_iters"] == 10 * (w * n_wl + j)
+            assert np.array_equal(p["eps"], test_eps[t0][j])
+    assert spec["base"][grids[0].wavelength].shape == (2, 64) and spec["pca"][grids[1].wavelength].shape == (5, 64)
