@@ -262,7 +262,7 @@ ddg_status gmres_solve(ddg_context* ctx, const ddg_op* A, const double* b, doubl
  * f = V R^-1 x_V + Q y.  Restarts solve the residual equation with the same V.
  *   U     device, D x k complex128, column-major (column n at U + 2*D*n), the
  *         predicted vectors v_1..v_k; need not be orthonormal.
- *   k     1 <= k <= 64.  If A U is numerically rank deficient the solve runs as
+ *   k     1 <= k <= 32.  If A U is numerically rank deficient the solve runs as
  *         plain GMRES and info.fallback_used = 1 (status DDG_OK).
  * Other arguments as gmres_solve.
  */
