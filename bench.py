@@ -85,6 +85,8 @@ def parse():
     p.add_argument("--cnn-lr", type=float, default=3e-4)
     p.add_argument("--n-pca", type=int, default=64, help="training problems solved per wavelength for the PCA bases")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--log-jsonl", default=None,
+                   help="write one JSON line per solve of the headline workload's passes to this file")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-pca", action="store_true", help="skip the PCA variant's pass (profiling runs)")
     p.add_argument("--levers", action="store_true",
@@ -410,6 +412,31 @@ def headline_config(args, world):
     }
 
 
+def solve_records(variant, step_infos, per_step_ms, grids):
+    """One dict per solve of the timed steps `step_infos` ([(step, infos)],
+    infos in the step's order: wavelength, then trajectory, then permittivity)
+    of the two-wavelength workload: which problem it was (held-out trajectory,
+    permittivity, wavelength, the trajectory's seed), what the solve reported,
+    and its step's wall time (the solves of a step share every launch)."""
+    n_traj = TRAJ_PER_STEP * TRAJ_STEPS
+    out = []
+    for q, (st, infos) in enumerate(step_infos):
+        for i, inf in enumerate(infos):
+            w, rem = divmod(i, n_traj)
+            t = N_TRAIN_TRAJ + step_traj(st)[rem // TRAJ_STEPS]
+            g = grids[w]
+            out.append({"workload": "splitter256", "variant": variant, "timed_step": q, "step": st,
+                        "trajectory": t, "seed": f"PCG64({1000 * SEED_CONFIG + t})",
+                        "permittivity": rem % TRAJ_STEPS, "wavelength_nm": int(round(g.wavelength * 1e9)),
+                        "grid": f"{g.nx}x{g.ny}", "iterations": int(inf["iters"]),
+                        "restart_cycles": int(inf["cycles"]), "converged": bool(inf["converged"]),
+                        "true_rel_residual": float(inf["true_rel_residual"]),
+                        "first_step_rel_residual": float(inf["first_step_rel_residual"]),
+                        "fallback_used": bool(inf["fallback_used"]), "breakdown": bool(inf["breakdown"]),
+                        "step_ms": round(float(per_step_ms[q]), 3), "solves_in_step": len(infos)})
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_1902_00090_gb300 as ddg
@@ -650,14 +677,14 @@ def run_ours(args, rank, world):
     # timed steps when there are that many (they start at step W mod
     # N_STEPS_PASS and go round)
     cnn_pass = pass_of(head) if K >= N_STEPS_PASS else one_pass(step_cnn)[0]
-    pca_pass = None
+    pca_pass = pca_run = None
     if not args.no_pca:
         set_policy(pol_pca)
-        pca_pass, _ = one_pass(step_pca)
-    plain_pass = None
+        pca_pass, pca_run = one_pass(step_pca)
+    plain_pass = plain_run = None
     plain_sample = None
     if not args.no_plain:
-        plain_pass, _ = one_pass(step_plain)
+        plain_pass, plain_run = one_pass(step_plain)
         # plain GMRES(200) without the cap on one held-out trajectory (context:
         # how far past the cap the 1300 nm solves go)
         for x in xs:
@@ -770,6 +797,14 @@ def run_ours(args, rank, world):
     }
     line["_oracle_sample"] = oracle_sample_spec(P, U_base, test_eps, grids, flat, wl, head["infos"],
                                                 U_pca=U_pca, policy=pol_cnn)
+    if args.log_jsonl and rank == 0:
+        recs = solve_records("cnn", head["infos"], head["per_step"], grids)
+        for name, run in (("pca", pca_run), ("plain", plain_run)):
+            if run is not None:
+                recs += solve_records(name, run["infos"], run["per_step"], grids)
+        with open(args.log_jsonl, "w") as f:
+            for r in recs:
+                f.write(json.dumps(r) + "\n")
     return line
 
 

@@ -149,3 +149,26 @@ def test_oracle_sample_takes_the_first_problems_of_each_wavelength():
             assert p["gpu_cycles"] == w * n_wl + j and p["gpu_iters"] == 10 * (w * n_wl + j)
             assert np.array_equal(p["eps"], test_eps[t0][j])
     assert spec["base"][grids[0].wavelength].shape == (2, 64) and spec["pca"][grids[1].wavelength].shape == (5, 64)
+
+
+def test_solve_records_name_each_problem():
+    # The per-solve log (--log-jsonl): solve i of a timed step is wavelength
+    # i // (TRAJ_PER_STEP * TRAJ_STEPS), then trajectory, then permittivity.
+    import json
+    from paper_1902_00090_gb300 import inputs
+    grids = [inputs.Grid(nx=8, ny=8, npml=2, i_src=2, sigma_src=1.0, slab_cells=2, wavelength=lam)
+             for lam in bench.WAVELENGTHS]
+    n_step = len(grids) * bench.TRAJ_PER_STEP * bench.TRAJ_STEPS
+    infos = [{"iters": i, "cycles": 1, "converged": 1, "true_rel_residual": 1e-7,
+              "first_step_rel_residual": 0.05, "fallback_used": 0, "breakdown": 0} for i in range(n_step)]
+    recs = bench.solve_records("cnn", [(5, infos), (6, infos)], [100.0, 200.0], grids)
+    assert len(recs) == 2 * n_step
+    r = recs[bench.TRAJ_STEPS + 3]       # first wavelength, the step's second trajectory, permittivity 3
+    t = bench.N_TRAIN_TRAJ + bench.step_traj(5)[1]
+    assert (r["trajectory"], r["permittivity"], r["wavelength_nm"], r["iterations"]) == (t, 3, 1300,
+                                                                                         bench.TRAJ_STEPS + 3)
+    assert r["seed"] == f"PCG64({1000 * bench.SEED_CONFIG + t})" and r["step_ms"] == 100.0
+    last = recs[-1]
+    assert last["wavelength_nm"] == 1550 and last["timed_step"] == 1 and last["step"] == 6
+    assert last["permittivity"] == bench.TRAJ_STEPS - 1 and last["solves_in_step"] == n_step
+    json.dumps(recs)                      # every field serialises
